@@ -1,0 +1,533 @@
+#!/usr/bin/env python
+"""Benchmark: streaming SINNAMON on the text-like workload (one JSON line).
+
+One step = one pass of the whole path over one batch of synthetic input:
+delete D live vectors (Sec. 4.3), insert D new ones (Alg. 5; they reuse the
+freed ids), then search a batch of Q queries (Alg. 6 + Alg. 7).  The metric is
+queries/s (Q per step); recall@10 against the FP64 exact top-10 is measured on
+the same index and reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank holds its own replica of the index and searches its
+own query batch (replicas only: the method's path does not shard), so value =
+all ranks' queries / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at recall@10>=0.9 (batched search, fixed k'=1000 fallback)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- inputs
+
+def cached(name, fn):
+    """Generated inputs are cached in /tmp (regenerated when absent)."""
+    path = f"/tmp/sinn_bench_{name}.npz"
+    if os.path.exists(path):
+        z = np.load(path)
+        from paper_2301_10622_gb300.synth import CSR
+        return CSR(z["indptr"], z["indices"], z["values"])
+    c = fn()
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, indptr=c.indptr, indices=c.indices, values=c.values)
+    os.replace(tmp, path)
+    return c
+
+
+def make_inputs(args, rank):
+    from paper_2301_10622_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    nd = args.docs or w.n_docs
+    t0 = time.time()
+    docs = cached(f"{w.name}_docs_{nd}", lambda: synth.make_docs(w, n_docs=nd))
+    pool_n = args.churn * (args.steps + args.warmup + 1)
+    pool = cached(f"{w.name}_pool_{pool_n}", lambda: synth.make_docs(w, n_docs=pool_n, seed=5000))
+    nq = args.queries or w.n_queries
+    qs = cached(f"{w.name}_q_{nq}_{rank}", lambda: synth.make_queries(
+        w, n_q=nq, seed=2000 + 2 + 100 * rank))
+    log(f"inputs ready in {time.time() - t0:.1f}s: docs={docs.rows} nnz={docs.nnz} "
+        f"queries={qs.rows} pool={pool.rows}")
+    return w, docs, pool, qs
+
+
+def algorithmic_bytes(w, docs, qs, cap, tiles):
+    """Bytes the scoring kernel must move per query: each
+    posting of the query's lists (2-byte id + h 4-byte sketch reads), one 4-byte
+    score key per id slot written, the tile offsets read and the live bitmap."""
+    nz = docs.values != 0
+    lens = np.bincount(docs.indices[nz], minlength=w.n).astype(np.int64)
+    rows = np.repeat(np.arange(qs.rows), np.diff(qs.indptr.astype(np.int64)))
+    qnz = qs.values != 0
+    P = np.bincount(rows[qnz], weights=lens[qs.indices[qnz]], minlength=qs.rows)
+    psi = np.bincount(rows[qnz], minlength=qs.rows)
+    per_q = P * (2 + 4 * w.h) + 4 * cap + 8 * tiles * psi + cap / 8
+    return per_q, P
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle side
+
+def oracle_index(w, docs):
+    import oracle
+    ora = oracle.OracleIndex(w.n, w.m, w.h)
+    t0 = time.time()
+    ora.insert(docs.indptr, docs.indices, docs.values)
+    log(f"oracle index built in {time.time() - t0:.1f}s")
+    return ora
+
+
+def cpu_baseline(ora, w, qs, target_s, k, kp):
+    """The oracle (Alg. 6 + Alg. 7, FP64) on a bounded sample of the queries,
+    all host cores."""
+    cores = os.cpu_count() or 1
+    one = qs.slice(0, 1)
+    t0 = time.time()
+    ora.search(one.indptr, one.indices, one.values, k=k, k_prime=kp, threads=1)
+    t1 = max(time.time() - t0, 1e-4)
+    s = int(min(qs.rows, max(cores, target_s * cores / t1 * 0.8)))
+    sample = qs.slice(0, s)
+    t0 = time.time()
+    ora.search(sample.indptr, sample.indices, sample.values, k=k, k_prime=kp, threads=cores)
+    dt = time.time() - t0
+    return {"value": s / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {s} of {qs.rows} queries over the full index "
+                      f"(k={k}, k'={kp}), FP64 Alg. 6+7, {dt:.1f}s"}
+
+
+def recall_at_10(ora, qs_sample, gpu_ids, threads):
+    """recall@10 of the GPU's top-10 against the FP64 exact top-10 (LinScan);
+    a returned id whose exact score ties the exact 10th score counts as a hit."""
+    ex = ora.linscan_topk(qs_sample.indptr, qs_sample.indices, qs_sample.values, k=10,
+                          threads=threads)
+    hits = 0
+    for r in range(qs_sample.rows):
+        truth = set(int(x) for x in ex["ids"][r])
+        qi, qv = qs_sample.row(r)
+        tenth = ex["scores"][r][9]
+        got = [int(x) & 0xFFFFFFFF for x in gpu_ids[r][:10]]
+        exact = None
+        for g in got:
+            if g in truth:
+                hits += 1
+            else:
+                if exact is None:
+                    exact = ora.exact_scores(qi, qv)
+                if g < exact.size and exact[g] >= tenth - 1e-9 * max(1.0, abs(tenth)):
+                    hits += 1
+    return hits / (10 * qs_sample.rows)
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2301_10622_gb300 import synth  # noqa: F401
+    import oracle
+    oracle.build()
+    w, docs, pool, qs = make_inputs(args, 0)
+    ora = oracle_index(w, docs)
+    cores = os.cpu_count() or 1
+    one = qs.slice(0, 1)
+    t0 = time.time()
+    ora.search(one.indptr, one.indices, one.values, k=w.k, k_prime=w.k_prime, threads=1)
+    t1 = max(time.time() - t0, 1e-4)
+    per_step_s = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    s = int(min(qs.rows, max(cores, per_step_s * cores / t1 * 0.8)))
+    churn = max(1, min(args.churn, 20))
+    rng = np.random.default_rng(11)
+    times = []
+    pos = 0
+    n_live = docs.rows
+    for step in range(args.warmup + args.steps):
+        t0 = time.time()
+        dele = rng.choice(n_live, size=churn, replace=False).astype(np.uint32)
+        ora.delete(dele)
+        part = pool.slice(pos, pos + churn)
+        pos += churn
+        ora.insert(part.indptr, part.indices, part.values)
+        sample = qs.slice((step * s) % max(1, qs.rows - s), (step * s) % max(1, qs.rows - s) + s)
+        ora.search(sample.indptr, sample.indices, sample.values, k=w.k, k_prime=w.k_prime,
+                   threads=cores)
+        dt = time.time() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1000 * float(np.mean(times))
+    value = s / (ms / 1000)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": config_dict(args, w, docs, qs, None),
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step: delete {churn} + insert {churn} vectors, then "
+                                   f"{s} of {qs.rows} queries (k={w.k}, k'={w.k_prime}), FP64"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(args, w, docs, qs, tile_docs):
+    return {"workload": (f"text-like streaming: n={w.n}, {docs.rows} docs with Zipf(1) "
+                         f"coordinates, nnz/doc lognormal(mean 120, sigma 0.5), values "
+                         f"lognormal(0,0.7); {qs.rows} queries/step nnz lognormal(mean 45); "
+                         f"m={w.m}, h={w.h}, k={w.k}, k'={w.k_prime}; churn "
+                         f"{args.churn} deletes + {args.churn} inserts per step"),
+            "docs": docs.rows, "queries_per_step": qs.rows, "churn_per_step": args.churn,
+            "n": w.n, "m": w.m, "h": w.h, "k": w.k, "k_prime": w.k_prime,
+            "tile_docs": tile_docs,
+            "l2": "inputs larger than L2: the index (~0.8 GB) and per-query score keys "
+                  "(4 MB each) are streamed every step"}
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2301_10622_gb300 import sinnamon
+
+    w, docs, pool, qs = make_inputs(args, rank)
+    k, kp = w.k, w.k_prime
+    T = args.tile_docs
+    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
+                        scratch_bytes=args.scratch_gb << 30)
+    t0 = time.time()
+    step_docs = 200_000
+    for a in range(0, docs.rows, step_docs):
+        part = docs.slice(a, min(docs.rows, a + step_docs))
+        ix.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+    torch.cuda.synchronize()
+    st = ix.stats()
+    log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
+    cap, tiles = st["capacity"], st["capacity"] // st["tile_docs"]
+
+    # device-resident step inputs
+    g_qip = torch.from_numpy(qs.indptr.astype(np.int64)).to(dev)
+    g_qix = torch.from_numpy(qs.indices.astype(np.int32)).to(dev)
+    g_qv = torch.from_numpy(qs.values).to(dev)
+    out_ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
+    out_sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
+    nsteps = args.warmup + args.steps
+    rng = np.random.default_rng(7 + rank)
+    dels = [torch.from_numpy(rng.choice(docs.rows, size=args.churn, replace=False)
+                             .astype(np.int32)).to(dev) for _ in range(2 * nsteps + 2)]
+    parts = []
+    for s_ in range(2 * nsteps + 2):
+        p = pool.slice((s_ * args.churn) % max(1, pool.rows - args.churn),
+                       (s_ * args.churn) % max(1, pool.rows - args.churn) + args.churn)
+        parts.append((torch.from_numpy(p.indptr.astype(np.int64)).to(dev),
+                      torch.from_numpy(p.indices.astype(np.int32)).to(dev),
+                      torch.from_numpy(p.values).to(dev), p))
+    new_ids = torch.empty(args.churn, dtype=torch.int32, device=dev)
+    h = ix.handle
+    executed = []
+
+    def step(si):
+        executed.append(si)
+        sinnamon.sinn_delete(h, dels[si])
+        ip, ii, vv, _ = parts[si]
+        sinnamon.sinn_insert(h, ip, ii, vv, new_ids)
+        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, out_ids, out_sc)
+
+    for si in range(args.warmup):
+        step(si)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    with clocks:
+        sinnamon.sinn_timing_start(h)
+        ev0.record()
+        for si in range(args.warmup, nsteps):
+            step(si)
+        ev1.record()
+        torch.cuda.synchronize()
+        tm = sinnamon.sinn_timing_stop(h)
+    ix.sync()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    value = world * qs.rows * args.steps / elapsed
+    ms_step = 1000 * elapsed / args.steps
+
+    # roofline of the scoring kernel (live CUDA-event durations from the library)
+    per_q, P = algorithmic_bytes(w, docs, qs, cap, tiles)
+    score_ms = tm["ms"]["score"]
+    alg_bytes = float(per_q.sum()) * args.steps
+    achieved = alg_bytes / (score_ms / 1000.0) / 1e9 if score_ms > 0 else None
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "k_score", "launches": tm["spans"]["score"],
+            "avg_launch_ms": score_ms / max(1, tm["spans"]["score"]),
+            "peak_source": "measured" if peaks else "fallback",
+            "alg_bytes_per_query": float(per_q.mean()), "postings_per_query": float(P.mean())}
+
+    # ---- untimed extras on rank 0: e2e, plain per-query, recall, CPU baseline
+    extras = {}
+    if rank == 0:
+        # e2e through the host-buffer C ABI call (copies inside the timed region)
+        h_qip = qs.indptr.astype(np.uint64)
+        h_ids = np.zeros((qs.rows, k), np.uint32)
+        h_sc = np.zeros((qs.rows, k), np.float32)
+        pin = {}
+        for si in range(2):
+            ip, ii, vv, p = parts[si + nsteps]
+            pin[si] = (torch.from_numpy(p.indptr.astype(np.int64)).pin_memory(),
+                       torch.from_numpy(p.indices.astype(np.int32)).pin_memory(),
+                       torch.from_numpy(p.values).pin_memory(),
+                       torch.from_numpy(dels[si + nsteps].cpu().numpy()).pin_memory())
+        qidx_pin = torch.from_numpy(qs.indices).pin_memory()
+        qval_pin = torch.from_numpy(qs.values).pin_memory()
+        hid_pin = torch.empty(args.churn, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        e_times = []
+        for si in range(2):
+            t0 = time.perf_counter()
+            pip, pii, pvv, pdl = pin[si]
+            executed.append(si + nsteps)
+            d_dl = pdl.to(dev, non_blocking=True)
+            sinnamon.sinn_delete(h, d_dl)
+            d_ip, d_ii, d_vv = (pip.to(dev, non_blocking=True), pii.to(dev, non_blocking=True),
+                                pvv.to(dev, non_blocking=True))
+            sinnamon.sinn_insert(h, d_ip, d_ii, d_vv, new_ids)
+            hid_pin.copy_(new_ids, non_blocking=True)
+            sinnamon.sinn_search_host(h, h_qip, qidx_pin.numpy(), qval_pin.numpy(), k, kp,
+                                      h_ids, h_sc)
+            torch.cuda.synchronize()
+            e_times.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(e_times))
+        h2d = int(qs.indptr.nbytes + qs.indices.nbytes + qs.values.nbytes
+                  + parts[0][3].indptr.nbytes + parts[0][3].indices.nbytes
+                  + parts[0][3].values.nbytes + args.churn * 4)
+        d2h = int(qs.rows * k * 8 + args.churn * 4)
+        extras["e2e"] = {"value": qs.rows / e2e_s, "unit": "queries/s",
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+        # plain per-query search: one query per call
+        npl = min(args.plain_queries, qs.rows)
+        lat = []
+        one_ids = torch.empty((1, k), dtype=torch.int32, device=dev)
+        one_sc = torch.empty((1, k), dtype=torch.float32, device=dev)
+        offs = qs.indptr.astype(np.int64)
+        qip1 = [torch.tensor([0, offs[r + 1] - offs[r]], dtype=torch.int64, device=dev)
+                for r in range(npl)]
+        for r in range(min(3, npl)):
+            a = int(offs[r])
+            sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(npl)]
+        t0 = time.perf_counter()
+        for r in range(npl):
+            a = int(offs[r])
+            evs[r][0].record()
+            sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
+            evs[r][1].record()
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+        extras["plain"] = {"qps": npl / plain_s, "p50_ms": float(np.percentile(lat, 50)),
+                           "p99_ms": float(np.percentile(lat, 99)), "queries": npl}
+
+        # batched latency and recall on the (post-churn) index vs a fresh oracle
+        ev0.record()
+        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, out_ids, out_sc)
+        ev1.record()
+        torch.cuda.synchronize()
+        extras["batched"] = {"qps": value / world, "batch_ms": ev0.elapsed_time(ev1),
+                             "p50_ms": ev0.elapsed_time(ev1), "p99_ms": ev0.elapsed_time(ev1)}
+        if not args.skip_oracle:
+            import oracle
+            oracle.build()
+            # the GPU index after churn: rebuild the same collection on the oracle
+            live_docs = reconstruct(docs, parts, dels, executed)
+            ora = oracle_index(w, live_docs)
+            nr = min(args.recall_queries, qs.rows)
+            samp = qs.slice(0, nr)
+            gids = out_ids.cpu().numpy()[:nr]
+            extras["recall_at_10"] = recall_at_10(ora, samp, gids, os.cpu_count() or 1)
+            extras["recall_queries"] = nr
+            extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": config_dict(args, w, docs, qs, T),
+        "roofline": roof,
+        "cpu_baseline": extras.get("cpu_baseline"),
+        "e2e": extras.get("e2e"),
+        "gpu_launches": tm["launches"],
+        "clocks": clocks.summary(),
+        "recall_at_10": extras.get("recall_at_10"),
+        "recall_queries": extras.get("recall_queries"),
+        "plain": extras.get("plain"),
+        "batched": extras.get("batched"),
+        "phases_ms_per_step": {p: v / args.steps for p, v in tm["ms"].items()},
+        "index": st,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def reconstruct(docs, parts, dels, executed):
+    """The collection after the executed steps, in id order.  Every step deleted
+    a set of ids and re-inserted as many vectors, which took exactly the freed
+    ids in ascending order (smallest free id first)."""
+    from paper_2301_10622_gb300.synth import CSR
+    src = np.full(docs.rows, -1, np.int64)   # -1: original collection
+    srow = np.arange(docs.rows, dtype=np.int64)
+    for si in executed:
+        d = np.sort(dels[si].cpu().numpy().astype(np.int64))
+        src[d] = si
+        srow[d] = np.arange(d.size)
+    lens = np.diff(docs.indptr.astype(np.int64))[srow] * (src < 0)
+    for si in np.unique(src[src >= 0]):
+        sel = src == si
+        lens[sel] = np.diff(parts[si][3].indptr.astype(np.int64))[srow[sel]]
+    ip = np.zeros(docs.rows + 1, np.uint64)
+    ip[1:] = np.cumsum(lens)
+    idx = np.zeros(int(ip[-1]), np.uint32)
+    val = np.zeros(int(ip[-1]), np.float32)
+    orig = np.nonzero(src < 0)[0]
+    # original rows: vectorised gather
+    o_ip = docs.indptr.astype(np.int64)
+    starts, cnt = o_ip[srow[orig]], lens[orig]
+    gather = np.repeat(starts - np.cumsum(np.concatenate(([0], cnt[:-1]))), cnt) + np.arange(cnt.sum())
+    dst = np.repeat(ip[orig].astype(np.int64) - np.cumsum(np.concatenate(([0], cnt[:-1]))), cnt) + np.arange(cnt.sum())
+    idx[dst] = docs.indices[gather]
+    val[dst] = docs.values[gather]
+    for i in np.nonzero(src >= 0)[0]:
+        s_ = parts[src[i]][3]
+        a_, b_ = int(s_.indptr[srow[i]]), int(s_.indptr[srow[i] + 1])
+        idx[int(ip[i]):int(ip[i + 1])] = s_.indices[a_:b_]
+        val[int(ip[i]):int(ip[i + 1])] = s_.values[a_:b_]
+    return CSR(ip, idx, val)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="text")
+    ap.add_argument("--docs", type=int, default=0)
+    ap.add_argument("--queries", type=int, default=0)
+    ap.add_argument("--churn", type=int, default=1000)
+    ap.add_argument("--tile-docs", type=int, default=4096)
+    ap.add_argument("--scratch-gb", type=int, default=8)
+    ap.add_argument("--plain-queries", type=int, default=300)
+    ap.add_argument("--recall-queries", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-oracle", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * sinnamon.h -- C ABI of the GB300 (sm_103a) SINNAMON library.
+ *
+ * SINNAMON (Bruch, Nardini, Ingber, Liberty, "An Approximate Algorithm for
+ * Maximum Inner Product Search over Streaming Sparse Vectors") answers Eq. 2,
+ * argmax^(k)_{x in X} <q, x>, approximately over a collection X of sparse
+ * real vectors that changes online (Sec. 1: insertions and deletions arrive
+ * while queries run).  The index keeps, on one GPU:
+ *   - an inverted index I: coordinate -> ids of the vectors non-zero there
+ *     (Alg. 5 line 2), stored per tile of T consecutive ids as sorted 16-bit
+ *     local ids; a deleted posting is tombstoned in place (Sec. 4.3);
+ *   - the sketch matrix [U; L] (Alg. 5): 2m rows of fp32 over all id slots,
+ *     row-major, so one query coordinate reads a fixed set of h rows;
+ *   - the vector store S that Alg. 7 re-ranks from (Fig. 1): each vector's
+ *     (coordinate, value) pairs.
+ *
+ * Conventions for every call:
+ *   - Return value: SINN_OK (0) or one of the SINN_E* codes below.
+ *     sinn_strerror() names a code.
+ *   - "device" pointers are CUDA device memory of the device the index was
+ *     created on (for example PyTorch CUDA tensors); "host" pointers are CPU
+ *     memory.  The caller owns every buffer it passes; the library owns the
+ *     index and its scratch, and never frees a caller's buffer.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; sinn_insert and sinn_delete also wait for it,
+ *     because they update host-side bookkeeping (ids, sizes).
+ *   - A handle is not thread-safe: calls on one handle must be serialised.
+ *   - Sparse inputs are CSR: indptr[rows+1] (uint64), indices (uint32, each
+ *     < n, strictly increasing within a row), values (float32, finite).
+ *     Entries equal to zero are not non-zeros (Alg. 5 line 1, Alg. 6 line 1):
+ *     they are neither indexed nor sketched nor scored.
+ *   - Ties: every ranking puts the larger score first and, among equal
+ *     scores, the smaller id first.
+ */
+#ifndef SINNAMON_H
+#define SINNAMON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SINN_OK 0
+#define SINN_EINVAL 1    /* bad argument or malformed input; nothing changed */
+#define SINN_ENOTFOUND 2 /* delete of an id that is not live; nothing changed */
+#define SINN_ENOMEM 3    /* device or host allocation failed */
+#define SINN_ECUDA 4     /* a CUDA runtime call failed */
+#define SINN_EDEVICE 5   /* a kernel reported an error (see sinn_sync) */
+
+typedef struct sinn_index sinn_index; /* opaque; owned by the library */
+
+/* Index parameters.  Zero fields take the defaults noted. */
+typedef struct sinn_config {
+  uint32_t n;              /* dimensionality; coordinates are [0, n) */
+  uint32_t m;              /* sketch bins per side (U and L have m rows each), m <= 4096 */
+  uint32_t h;              /* number of random mappings pi_o: [n] -> [m], 1 <= h <= min(m, 8) */
+  uint32_t tile_docs;      /* ids per tile T: power of two in [1024, 32768]; 0 -> 4096 */
+  uint64_t seed;           /* seed of the mappings; 0 -> 0x5151 */
+  uint64_t capacity_hint;  /* id slots to reserve up front; 0 -> one tile */
+  const uint32_t *table;   /* optional host table[n*h] with table[j*h+o] = pi_o(j) < m;
+                              NULL -> pi_o(j) = mix64(seed ^ (o+1)*0x9E3779B97F4A7C15 ^ j) mod m,
+                              mix64 being SplitMix64's output function */
+  uint32_t max_query_nnz;  /* largest query non-zero count sinn_search accepts; 0 -> 1024 */
+  uint32_t reserved;
+  uint64_t scratch_bytes;  /* device scratch budget of one search launch; 0 -> 4 GiB */
+} sinn_config;
+
+/* Counters reported by sinn_stats. */
+typedef struct sinn_stats {
+  uint64_t live;           /* live vectors |X| */
+  uint64_t capacity;       /* id slots with storage (a multiple of tile_docs) */
+  uint64_t next_id;        /* ids ever handed out: live + free */
+  uint64_t postings;       /* postings held in the inverted index, tombstones included */
+  uint64_t tombstones;     /* deleted postings not yet compacted away */
+  uint64_t bytes_lists;    /* device bytes of the inverted index (postings + tile offsets) */
+  uint64_t bytes_sketch;   /* device bytes of U and L */
+  uint64_t bytes_store;    /* device bytes of the vector store */
+  uint64_t bytes_scratch;  /* device bytes of search scratch currently held */
+  uint32_t n, m, h, tile_docs;
+} sinn_stats_t;
+
+/* Create an empty index on the current CUDA device with default settings.
+ * n, m, h as in Alg. 5 (Sec. 4.1).  EINVAL if n = 0, m = 0, h = 0, h > m or
+ * h > 8.  *out receives the handle. */
+int sinn_create(uint32_t n, uint32_t m, uint32_t h, sinn_index **out);
+
+/* Create with explicit parameters (see sinn_config). */
+int sinn_create_ex(const sinn_config *cfg, sinn_index **out);
+
+/* Release the index and all device memory it owns.  NULL is accepted. */
+int sinn_destroy(sinn_index *ix);
+
+/* Insert n_docs vectors (Alg. 5: inverted-list append and sketch columns; the
+ * vectors also enter the store S).  indptr/indices/values: device CSR.
+ * out_ids: device uint32[n_docs] receiving each vector's id: free ids in
+ * ascending order first (Sec. 4.3 reuse), then fresh ids, in row order.
+ * The whole batch is validated before anything changes (EINVAL).  Waits for
+ * the stream before returning. */
+int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                const float *values, uint32_t n_docs, uint32_t *out_ids, void *stream);
+
+/* Delete n_ids vectors by id (Sec. 4.3): each id is removed from every
+ * inverted list it is in (tombstoned in place), its sketch column is left as
+ * it is, and the id becomes free for reuse.  ids: device uint32[n_ids].
+ * ENOTFOUND if an id is not live, EINVAL if an id repeats; then nothing
+ * changes.  Waits for the stream before returning. */
+int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, void *stream);
+
+/* Approximate top-k search for n_q queries: Alg. 6 scoring (T = infinity),
+ * then Alg. 7: the k' best approximate scores among live ids, re-ranked by
+ * exact inner product <q, S.Fetch(v)>, best k returned.
+ * q_indptr/q_indices/q_values: device CSR (each row <= max_query_nnz
+ * non-zeros).  out_ids: device uint32[n_q*k], out_scores: device
+ * float[n_q*k], row-major, best first; rows with fewer than k live vectors
+ * are padded with id 0xFFFFFFFF and score -inf.  1 <= k <= 1024, k <= k'.
+ * Asynchronous: a malformed query sets the device error that sinn_sync
+ * returns, and that query's row is padded. */
+int sinn_search(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                uint32_t *out_ids, float *out_scores, void *stream);
+
+/* As sinn_search with a per-query k': k_prime[q] (device uint32[n_q]) is
+ * clamped to [k, k_prime_max]. */
+int sinn_search_kp(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                   const float *q_values, uint32_t n_q, uint32_t k, const uint32_t *k_prime,
+                   uint32_t k_prime_max, uint32_t *out_ids, float *out_scores, void *stream);
+
+/* As sinn_search with every buffer in host memory: the call copies the
+ * queries to the device, searches, copies the results back and waits.
+ * Device errors are returned directly. */
+int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                     const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                     uint32_t *out_ids, float *out_scores, void *stream);
+
+/* Wait for the stream, then return and clear the sticky device error
+ * (SINN_OK if none; SINN_EINVAL for a malformed query; SINN_EDEVICE for an
+ * internal kernel error). */
+int sinn_sync(sinn_index *ix, void *stream);
+
+/* Fill *out with the counters above (host). */
+int sinn_stats(sinn_index *ix, sinn_stats_t *out);
+
+/* Per-phase device timing, for benchmarks.  Phases: 0 query preparation,
+ * 1 scoring (Alg. 6), 2 top-k' selection (Alg. 7 line 1), 3 re-rank and
+ * top-k (Alg. 7 lines 2-4), 4 insert (Alg. 5), 5 delete (Sec. 4.3). */
+#define SINN_PHASES 6
+typedef struct sinn_timing {
+  double ms[SINN_PHASES];        /* summed CUDA-event durations per phase */
+  uint64_t spans[SINN_PHASES];   /* timed spans per phase */
+  uint64_t launches;             /* kernels the library launched meanwhile */
+} sinn_timing_t;
+
+/* Start recording: every later phase is bracketed by CUDA events on the
+ * stream it runs on.  Resets the counters. */
+int sinn_timing_start(sinn_index *ix);
+
+/* Stop recording, wait for the recorded events and fill *out (host). */
+int sinn_timing_stop(sinn_index *ix, sinn_timing_t *out);
+
+/* Name of a status code (static string). */
+const char *sinn_strerror(int code);
+
+/* ---- Inspection (used by tests; not on the hot path) ------------------- */
+
+/* Copy the mappings to host table[n*h]: table[j*h+o] = pi_o(j). */
+int sinn_hash_table(sinn_index *ix, uint32_t *table);
+
+/* Sketch columns of the given ids (Alg. 5's u and l): ids device
+ * uint32[n_ids]; u_out, l_out device float[n_ids*m], row r = column ids[r].
+ * A deleted id yields its stale column (Sec. 4.3 leaves it in place). */
+int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, float *u_out,
+                        float *l_out, void *stream);
+
+/* Live ids of inverted list I[coord] in ascending order, into host
+ * out[cap]; *len receives the list length (copy truncated at cap). */
+int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out, uint64_t cap,
+                       uint64_t *len);
+
+/* Alg. 6 scores of n_q queries over every id slot: device out[n_q*capacity]
+ * (capacity from sinn_stats), -inf for slots that are not live. */
+int sinn_scores(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                const float *q_values, uint32_t n_q, float *out, void *stream);
+
+/* Alg. 7 line 1 only: the min(k', live) candidates of each query with their
+ * approximate scores, in no particular order.  out_ids device uint32[n_q*k'],
+ * out_scores device float[n_q*k'], out_count device uint32[n_q]. */
+int sinn_candidates(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                    const float *q_values, uint32_t n_q, uint32_t k_prime, uint32_t *out_ids,
+                    float *out_scores, uint32_t *out_count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SINNAMON_H */

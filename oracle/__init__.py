@@ -71,6 +71,7 @@ def _load():
         lib.orc_live_count.argtypes = [vp]
         lib.orc_is_live.restype = C.c_int
         lib.orc_is_live.argtypes = [vp, C.c_uint32]
+        lib.orc_live_mask.argtypes = [vp, vp]
         lib.orc_insert.restype = C.c_int
         lib.orc_insert.argtypes = [vp, u64p, u32p, f32p, C.c_uint32, u32p]
         lib.orc_delete.restype = C.c_int
@@ -85,7 +86,7 @@ def _load():
         lib.orc_scores.restype = C.c_int
         lib.orc_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p, vp]
         lib.orc_exact_scores.restype = C.c_int
-        lib.orc_exact_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p]
+        lib.orc_exact_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p, vp]
         lib.orc_search.restype = C.c_int
         lib.orc_search.argtypes = [vp, u64p, u32p, f32p, C.c_uint32, C.c_uint32, C.c_uint32,
                                    u32p, f64p, vp, vp, vp, u32p, C.c_uint32]
@@ -176,8 +177,13 @@ class OracleIndex:
     def is_live(self, i: int) -> bool:
         return bool(self._lib.orc_is_live(self._p, i))
 
+    def live_mask(self) -> np.ndarray:
+        out = np.zeros(max(self.n_slots, 1), np.uint8)
+        self._lib.orc_live_mask(self._p, _ptr(out))
+        return out[: self.n_slots].astype(bool)
+
     def live_ids(self) -> np.ndarray:
-        return np.array([i for i in range(self.n_slots) if self.is_live(i)], np.uint32)
+        return np.nonzero(self.live_mask())[0].astype(np.uint32)
 
     def hash_table(self) -> np.ndarray:
         out = np.zeros(self.n * self.h, np.uint32)
@@ -233,14 +239,16 @@ class OracleIndex:
         out = out[: self.n_slots]
         return (out, mag[: self.n_slots]) if with_magnitude else out
 
-    def exact_scores(self, qi, qv):
+    def exact_scores(self, qi, qv, with_magnitude: bool = False):
         qi = np.ascontiguousarray(qi, dtype=np.uint32)
         qv = np.ascontiguousarray(qv, dtype=np.float32)
         out = np.zeros(max(self.n_slots, 1), np.float64)
-        st = self._lib.orc_exact_scores(self._p, qi, qv, qi.size, out)
+        mag = np.zeros(max(self.n_slots, 1), np.float64) if with_magnitude else None
+        st = self._lib.orc_exact_scores(self._p, qi, qv, qi.size, out, _ptr(mag))
         if st:
             raise OracleError(st)
-        return out[: self.n_slots]
+        out = out[: self.n_slots]
+        return (out, mag[: self.n_slots]) if with_magnitude else out
 
     def search(self, indptr, indices, values, k: int, k_prime: int, threads: int = 1,
                candidates: bool = False):

@@ -163,6 +163,7 @@ void orc_hash_table(const orc_index *ix, uint32_t *out) {
 uint32_t orc_n_slots(const orc_index *ix) { return ix->n_slots; }
 uint32_t orc_live_count(const orc_index *ix) { return ix->live_count; }
 int orc_is_live(const orc_index *ix, uint32_t id) { return id < ix->n_slots && ix->live[id]; }
+void orc_live_mask(const orc_index *ix, uint8_t *out) { memcpy(out, ix->live, ix->n_slots); }
 
 /* free-id min-heap */
 static void heap_push_u32(orc_index *ix, uint32_t v) {
@@ -768,13 +769,18 @@ int orc_exact_topk(const orc_index *ix, const uint64_t *indptr, const uint32_t *
   return run_batch(jb, n_q, n_threads);
 }
 
-/* Dense exact scores <q, x_i> for every slot (0 for vacant slots). */
+/* Dense exact scores <q, x_i> for every slot (0 for vacant slots); if mag is
+ * given it receives sum_j |q_j * x_i[j]| per slot. */
 int orc_exact_scores(const orc_index *ix, const uint32_t *qi, const float *qv, uint32_t qnnz,
-                     double *scores) {
+                     double *scores, double *mag) {
   if (validate_query(ix, qi, qv, qnnz)) return ORC_EINVAL;
   double *qd = (double *)calloc(ix->n, sizeof(double));
   for (uint32_t t = 0; t < qnnz; ++t) qd[qi[t]] = (double)qv[t];
-  for (uint32_t i = 0; i < ix->n_slots; ++i) scores[i] = ix->live[i] ? exact_dot(ix, qd, i, NULL) : 0.0;
+  for (uint32_t i = 0; i < ix->n_slots; ++i) {
+    double a = 0.0;
+    scores[i] = ix->live[i] ? exact_dot(ix, qd, i, &a) : 0.0;
+    if (mag) mag[i] = a;
+  }
   free(qd);
   return ORC_OK;
 }

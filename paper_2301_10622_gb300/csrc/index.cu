@@ -1,0 +1,912 @@
+// Index construction and maintenance on the GPU: Alg. 5 (indexing) and
+// Sec. 4.3 (deletion) of SINNAMON, plus the C ABI calls that own the index.
+//
+// Layout (device):
+//   d_pi        n*h uint32      pi_o(j) at [j*h + o]
+//   d_U, d_L    m x cap fp32    row k holds bin k of every id slot (row-major,
+//                               as the paper stores the sketch matrix)
+//   d_live      cap bits        live ids
+//   d_fwd*      vector store    (coordinate, value) pairs per id
+//   d_tile_off  tiles x (n+1)   per tile t and coordinate j, the postings of
+//                               I[j] with ids in [t*T, (t+1)*T) are
+//                               post_t[off[t][j] .. off[t][j+1]), as 16-bit
+//                               local ids sorted ascending; bit 15 marks a
+//                               deleted (tombstoned) posting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "sinn_internal.cuh"
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return sinn_check_cuda(e_); \
+  } while (0)
+
+int sinn_check_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return SINN_OK;
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? SINN_ENOMEM : SINN_ECUDA;
+}
+
+// SplitMix64's output function (Steele, Lea, Flood, OOPSLA 2014).
+static uint64_t lib_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// -------------------------------------------------------------- kernels
+
+// Insert-batch validation: coordinates < n and strictly increasing per row,
+// values finite.  One warp per row.
+__global__ void k_validate_csr(const uint64_t *__restrict__ indptr,
+                               const uint32_t *__restrict__ indices,
+                               const float *__restrict__ values, uint32_t rows, uint32_t n,
+                               uint32_t *err, uint32_t bit) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= rows) return;
+  const uint64_t s = indptr[w], e = indptr[w + 1];
+  bool bad = false;
+  for (uint64_t p = s + lane; p < e; p += 32) {
+    uint32_t c = indices[p];
+    float v = values[p];
+    if (c >= n || !isfinite(v)) bad = true;
+    if (p > s && indices[p - 1] >= c) bad = true;
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, bit);
+}
+
+// Copy each row into the vector store at its assigned offset.  One warp per row.
+__global__ void k_fwd_write(const uint64_t *__restrict__ indptr,
+                            const uint32_t *__restrict__ indices,
+                            const float *__restrict__ values, uint32_t rows,
+                            const uint32_t *__restrict__ ids, const uint64_t *__restrict__ offs,
+                            uint2 *__restrict__ fwd, uint64_t *__restrict__ fwd_off,
+                            uint32_t *__restrict__ fwd_nnz) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= rows) return;
+  const uint64_t s = indptr[w], e = indptr[w + 1], o = offs[w];
+  for (uint64_t p = s + lane; p < e; p += 32)
+    fwd[o + (p - s)] = make_uint2(indices[p], __float_as_uint(values[p]));
+  if (lane == 0) {
+    fwd_off[ids[w]] = o;
+    fwd_nnz[ids[w]] = (uint32_t)(e - s);
+  }
+}
+
+// Alg. 5 lines 3-9: u[k] = max and l[k] = min of x_i[j] over the non-zeros j
+// with pi_o(j) = k for some o; empty bins -inf / +inf.  Max and min are taken
+// on order-preserving integer keys, so the stored bins are the input floats
+// bit for bit.  A block sketches G rows in shared memory, then writes the
+// columns out row by row of the sketch (consecutive ids -> coalesced stores).
+__global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__restrict__ indices,
+                         const float *__restrict__ values, uint32_t rows,
+                         const uint32_t *__restrict__ ids, const uint32_t *__restrict__ pi,
+                         uint32_t m, uint32_t h, uint64_t cap, uint32_t G, float *__restrict__ U,
+                         float *__restrict__ L) {
+  extern __shared__ uint32_t sk[];
+  uint32_t *uk = sk;          // G*m
+  uint32_t *lk = sk + G * m;  // G*m
+  const uint32_t r0 = blockIdx.x * G;
+  const uint32_t g_cnt = min(G, rows - r0);
+  const uint32_t NEG_INF_KEY = 0x007FFFFFu;  // key of -inf
+  const uint32_t POS_INF_KEY = 0xFF800000u;  // key of +inf
+  for (uint32_t t = threadIdx.x; t < g_cnt * m; t += blockDim.x) {
+    uk[t] = NEG_INF_KEY;
+    lk[t] = POS_INF_KEY;
+  }
+  __syncthreads();
+  for (uint32_t g = 0; g < g_cnt; ++g) {
+    const uint64_t s = indptr[r0 + g], e = indptr[r0 + g + 1];
+    for (uint64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+      float v = values[p];
+      if (v == 0.0f) continue;  // not a non-zero
+      uint32_t key = sinn_f2key(v);
+      uint32_t c = indices[p];
+      for (uint32_t o = 0; o < h; ++o) {
+        uint32_t k = pi[(uint64_t)c * h + o];
+        atomicMax(&uk[g * m + k], key);
+        atomicMin(&lk[g * m + k], key);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < g_cnt * m; t += blockDim.x) {
+    uint32_t k = t / g_cnt, g = t % g_cnt;
+    uint64_t id = ids[r0 + g];
+    U[(uint64_t)k * cap + id] = sinn_key2f(uk[g * m + k]);
+    L[(uint64_t)k * cap + id] = sinn_key2f(lk[g * m + k]);
+  }
+}
+
+__global__ void k_set_live(const uint32_t *__restrict__ ids, uint32_t cnt, uint32_t *live,
+                           int set) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  uint32_t id = ids[i];
+  if (set) atomicOr(&live[id >> 5], 1u << (id & 31));
+  else atomicAnd(&live[id >> 5], ~(1u << (id & 31)));
+}
+
+// Block-wide exclusive scan of a[0..cnt) in place (any memory space), returning
+// the total.  Every thread of the block must call it.  Uses smem_part
+// (blockDim.x/32 + 1 words).
+__device__ uint32_t block_excl_scan(uint32_t *a, uint32_t cnt, uint32_t *smem_part) {
+  const uint32_t nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t per = (cnt + nt - 1) / nt;
+  const uint32_t b = min(cnt, tid * per), e = min(cnt, b + per);
+  uint32_t s = 0;
+  for (uint32_t i = b; i < e; ++i) s += a[i];
+  uint32_t x = s;
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) smem_part[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t nw = nt >> 5;
+    uint32_t v = lane < nw ? smem_part[lane] : 0, z = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, d);
+      if (lane >= (uint32_t)d) z += y;
+    }
+    if (lane < nw) smem_part[lane] = z - v;  // exclusive warp offsets
+    if (lane == nw - 1) smem_part[32] = z;   // total
+  }
+  __syncthreads();
+  uint32_t run = smem_part[wid] + x - s;
+  for (uint32_t i = b; i < e; ++i) {
+    uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  uint32_t total = smem_part[32];
+  __syncthreads();
+  return total;
+}
+
+// Rebuild the postings of one tile per block from the vector store: for every
+// live id of the tile and each of its non-zero coordinates j, the local id is
+// placed in list (tile, j); lists come out sorted by local id because entries
+// are placed in id order (a stable counting sort by coordinate).  Tombstones
+// disappear: only live vectors contribute.
+//   E     scratch of the block: one (coordinate<<16 | local id) entry per stored
+//         entry of the tile's live vectors, in id order (skipped entries are
+//         all-ones)
+//   dpref scratch: T+1 per-id entry offsets into E
+struct RebuildArgs {
+  const uint32_t *tiles;      // tile index per block
+  uint16_t *const *new_post;  // posting array per block
+  const uint64_t *e_off;      // offset of each block's E region
+  uint64_t *E;
+  uint32_t *dpref;            // (T+1) per block
+  uint32_t *out_len;          // postings written per block
+};
+
+__global__ void __launch_bounds__(512)
+    k_tile_rebuild(RebuildArgs a, const uint32_t *__restrict__ live,
+                   const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
+                   const uint2 *__restrict__ fwd, uint32_t *__restrict__ tile_off,
+                   uint16_t **tile_post, uint32_t n, uint32_t T, uint32_t log2T, uint32_t W) {
+  extern __shared__ uint32_t cursor[];  // W coordinate cursors
+  __shared__ uint32_t part[33];
+  const uint32_t t = a.tiles[blockIdx.x];
+  uint16_t *post = a.new_post[blockIdx.x];
+  uint64_t *E = a.E + a.e_off[blockIdx.x];
+  uint32_t *dpref = a.dpref + (uint64_t)blockIdx.x * (T + 1);
+  uint32_t *off = tile_off + (uint64_t)t * (n + 1);
+  const uint64_t id0 = (uint64_t)t << log2T;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+
+  // phase 1: entries per id, then offsets into E
+  for (uint32_t d = tid; d < T; d += blockDim.x)
+    dpref[d] = sinn_is_live(live, id0 + d) ? fwd_nnz[id0 + d] : 0u;
+  __syncthreads();
+  const uint32_t total = block_excl_scan(dpref, T, part);
+  if (tid == 0) dpref[T] = total;
+  __syncthreads();
+
+  // phase 2: fill E in id order (one warp per id)
+  for (uint32_t d = wid; d < T; d += nw) {
+    const uint32_t c0 = dpref[d], c1 = dpref[d + 1];
+    if (c1 == c0) continue;
+    const uint64_t fo = fwd_off[id0 + d];
+    for (uint32_t e = lane; e < c1 - c0; e += 32) {
+      uint2 pr = fwd[fo + e];
+      bool nz = (pr.y & 0x7FFFFFFFu) != 0u;
+      E[c0 + e] = nz ? (((uint64_t)pr.x << 16) | d) : ~0ull;
+    }
+  }
+  __syncthreads();
+
+  // phases 3-5 per window of W coordinates
+  uint32_t base = 0;
+  for (uint32_t w0 = 0; w0 < n; w0 += W) {
+    const uint32_t wn = min(W, n - w0);
+    for (uint32_t i = tid; i < wn; i += blockDim.x) cursor[i] = 0;
+    __syncthreads();
+    for (uint32_t e = tid; e < total; e += blockDim.x) {
+      uint64_t key = E[e];
+      uint32_t c = (uint32_t)(key >> 16);
+      if (key != ~0ull && c >= w0 && c < w0 + wn) atomicAdd(&cursor[c - w0], 1u);
+    }
+    __syncthreads();
+    const uint32_t wtot = block_excl_scan(cursor, wn, part);
+    for (uint32_t i = tid; i < wn; i += blockDim.x) {
+      cursor[i] += base;
+      off[w0 + i] = cursor[i];
+    }
+    __syncthreads();
+    if (wid == 0) {  // stable scatter: entries in id order, lanes in order
+      const uint32_t lt = (1u << lane) - 1u;
+      for (uint32_t e0 = 0; e0 < total; e0 += 128) {
+        uint64_t kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t e = e0 + u * 32 + lane;
+          kk[u] = e < total ? E[e] : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t c = (uint32_t)(kk[u] >> 16);
+          bool ok = kk[u] != ~0ull && c >= w0 && c < w0 + wn;
+          uint32_t okm = __ballot_sync(0xFFFFFFFFu, ok);
+          if (ok) {
+            uint32_t grp = __match_any_sync(okm, c);
+            uint32_t rank = __popc(grp & lt);
+            uint32_t pos = cursor[c - w0];
+            post[pos + rank] = (uint16_t)(kk[u] & 0xFFFFu);
+            if ((grp >> lane) == 1u) cursor[c - w0] = pos + __popc(grp);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    base += wtot;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    off[n] = base;
+    tile_post[t] = post;
+    a.out_len[blockIdx.x] = base;
+  }
+}
+
+// Sec. 4.3 deletion: for each deleted id, remove it from every list it is in
+// by setting the tombstone bit of its posting (binary search within the
+// sorted tile list), then clear its live bit.  One warp per id.
+__global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
+                            const uint64_t *__restrict__ fwd_off,
+                            const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd,
+                            const uint32_t *__restrict__ tile_off, uint16_t *const *tile_post,
+                            uint32_t *live, uint32_t n, uint32_t log2T, uint32_t *tomb_count,
+                            uint32_t *err) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= cnt) return;
+  const uint32_t id = ids[w];
+  const uint32_t t = id >> log2T;
+  const uint16_t d = (uint16_t)(id & ((1u << log2T) - 1u));
+  const uint32_t *off = tile_off + (uint64_t)t * (n + 1);
+  uint16_t *post = tile_post[t];
+  const uint64_t fo = fwd_off[id];
+  const uint32_t nz = fwd_nnz[id];
+  uint32_t marked = 0;
+  for (uint32_t e = lane; e < nz; e += 32) {
+    uint2 pr = fwd[fo + e];
+    if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
+    uint32_t lo = off[pr.x], hi = off[pr.x + 1];
+    while (lo < hi) {  // first position with local id >= d
+      uint32_t mid = (lo + hi) >> 1;
+      if ((post[mid] & 0x7FFFu) < d) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < off[pr.x + 1] && (post[lo] & 0x7FFFu) == d && !(post[lo] & SINN_TOMB)) {
+      post[lo] = (uint16_t)(post[lo] | SINN_TOMB);
+      marked++;
+    } else {
+      atomicOr(err, SINN_DERR_INTERNAL);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) marked += __shfl_xor_sync(0xFFFFFFFFu, marked, s);
+  if (lane == 0) {
+    atomicAnd(&live[id >> 5], ~(1u << (id & 31)));
+    tomb_count[w] = marked;
+  }
+}
+
+__global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
+                                 const float *__restrict__ U, const float *__restrict__ L,
+                                 uint32_t m, uint64_t cap, float *u_out, float *l_out) {
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)cnt * m) return;
+  uint32_t r = (uint32_t)(i / m), k = (uint32_t)(i % m);
+  uint64_t id = ids[r];
+  if (id >= cap) {  // no storage for this id: report NaN
+    u_out[i] = __int_as_float(0x7FC00000);
+    l_out[i] = __int_as_float(0x7FC00000);
+    return;
+  }
+  u_out[i] = U[(uint64_t)k * cap + id];
+  l_out[i] = L[(uint64_t)k * cap + id];
+}
+
+// ------------------------------------------------------------- host side
+
+static cudaEvent_t tm_event(sinn_index *ix) {
+  if (!ix->tm_pool.empty()) {
+    cudaEvent_t e = ix->tm_pool.back();
+    ix->tm_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+SinnPhase::SinnPhase(sinn_index *ix_, cudaStream_t s_, int ph) : ix(ix_), s(s_), phase(ph) {
+  if (ix->tm_on) {
+    a = tm_event(ix);
+    cudaEventRecord(a, s);
+  }
+}
+
+SinnPhase::~SinnPhase() {
+  if (a) {
+    cudaEvent_t b = tm_event(ix);
+    cudaEventRecord(b, s);
+    ix->tm_spans.push_back({phase, a, b});
+  }
+}
+
+extern "C" int sinn_timing_start(sinn_index *ix) {
+  if (!ix) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  for (auto &sp : ix->tm_spans) {
+    ix->tm_pool.push_back(sp.a);
+    ix->tm_pool.push_back(sp.b);
+  }
+  ix->tm_spans.clear();
+  ix->launches = 0;
+  ix->tm_on = true;
+  return SINN_OK;
+}
+
+extern "C" int sinn_timing_stop(sinn_index *ix, sinn_timing_t *out) {
+  if (!ix || !out) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  memset(out, 0, sizeof(*out));
+  ix->tm_on = false;
+  for (auto &sp : ix->tm_spans) {
+    CK(cudaEventSynchronize(sp.b));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, sp.a, sp.b));
+    if (sp.phase >= 0 && sp.phase < SINN_PHASES) {
+      out->ms[sp.phase] += ms;
+      out->spans[sp.phase] += 1;
+    }
+    ix->tm_pool.push_back(sp.a);
+    ix->tm_pool.push_back(sp.b);
+  }
+  ix->tm_spans.clear();
+  out->launches = ix->launches;
+  return SINN_OK;
+}
+
+static void release(sinn_index *ix) {
+  if (!ix) return;
+  cudaSetDevice(ix->device);
+  cudaDeviceSynchronize();
+  for (uint16_t *p : ix->tile_post)
+    if (p) cudaFree(p);
+  for (auto &sp : ix->tm_spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  for (cudaEvent_t e : ix->tm_pool) cudaEventDestroy(e);
+  cudaFree(ix->d_pi);
+  cudaFree(ix->d_U);
+  cudaFree(ix->d_L);
+  cudaFree(ix->d_live);
+  cudaFree(ix->d_fwd_off);
+  cudaFree(ix->d_fwd_nnz);
+  cudaFree(ix->d_fwd);
+  cudaFree(ix->d_tile_off);
+  cudaFree(ix->d_tile_post);
+  cudaFree(ix->d_err);
+  cudaFree(ix->scratch);
+  cudaFree(ix->iscratch);
+  cudaFree(ix->hstage);
+  if (ix->pinned) cudaFreeHost(ix->pinned);
+  delete ix;
+}
+
+int sinn_ensure_scratch(sinn_index *ix, size_t bytes) {
+  if (bytes <= ix->scratch_size) return SINN_OK;
+  if (ix->scratch) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(ix->scratch));
+    ix->scratch = nullptr;
+    ix->scratch_size = 0;
+  }
+  CK(cudaMalloc(&ix->scratch, bytes));
+  ix->scratch_size = bytes;
+  return SINN_OK;
+}
+
+static int ensure_iscratch(sinn_index *ix, size_t bytes) {
+  if (bytes <= ix->iscratch_size) return SINN_OK;
+  if (ix->iscratch) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(ix->iscratch));
+    ix->iscratch = nullptr;
+    ix->iscratch_size = 0;
+  }
+  size_t b = std::max(bytes, ix->iscratch_size * 3 / 2);
+  CK(cudaMalloc(&ix->iscratch, b));
+  ix->iscratch_size = b;
+  return SINN_OK;
+}
+
+int sinn_ensure_pinned(sinn_index *ix, size_t bytes) {
+  if (bytes <= ix->pinned_size) return SINN_OK;
+  if (ix->pinned) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFreeHost(ix->pinned));
+    ix->pinned = nullptr;
+    ix->pinned_size = 0;
+  }
+  size_t b = std::max(bytes, ix->pinned_size * 3 / 2);
+  CK(cudaMallocHost(&ix->pinned, b));
+  ix->pinned_size = b;
+  return SINN_OK;
+}
+
+template <typename T>
+static int realloc_copy(T **p, uint64_t old_elems, uint64_t new_elems, bool zero_rest) {
+  T *q = nullptr;
+  CK(cudaMalloc(&q, new_elems * sizeof(T)));
+  if (zero_rest) CK(cudaMemset(q, 0, new_elems * sizeof(T)));
+  if (*p && old_elems) CK(cudaMemcpy(q, *p, old_elems * sizeof(T), cudaMemcpyDeviceToDevice));
+  if (*p) CK(cudaFree(*p));
+  *p = q;
+  return SINN_OK;
+}
+
+// Grow id capacity to hold ids < need (rounded up to whole tiles).
+static int grow_capacity(sinn_index *ix, uint64_t need) {
+  if (need <= ix->cap) return SINN_OK;
+  uint64_t nc = std::max<uint64_t>(ix->cap * 2, need);
+  nc = (nc + ix->T - 1) / ix->T * ix->T;
+  const uint64_t ot = ix->cap / ix->T, nt = nc / ix->T;
+  CK(cudaDeviceSynchronize());
+  // sketch planes: copy the m rows into the wider layout
+  for (int plane = 0; plane < 2; ++plane) {
+    float **pp = plane ? &ix->d_L : &ix->d_U;
+    float *q = nullptr;
+    CK(cudaMalloc(&q, (uint64_t)ix->m * nc * sizeof(float)));
+    if (*pp && ix->cap)
+      CK(cudaMemcpy2D(q, nc * sizeof(float), *pp, ix->cap * sizeof(float), ix->cap * sizeof(float),
+                      ix->m, cudaMemcpyDeviceToDevice));
+    if (*pp) CK(cudaFree(*pp));
+    *pp = q;
+  }
+  int st;
+  if ((st = realloc_copy(&ix->d_live, ix->cap / 32, nc / 32, true))) return st;
+  if ((st = realloc_copy(&ix->d_fwd_off, ix->cap, nc, true))) return st;
+  if ((st = realloc_copy(&ix->d_fwd_nnz, ix->cap, nc, true))) return st;
+  if ((st = realloc_copy(&ix->d_tile_off, ot * (ix->n + 1), nt * (ix->n + 1), true))) return st;
+  if ((st = realloc_copy(&ix->d_tile_post, ot, nt, true))) return st;
+  ix->cap = nc;
+  ix->live.resize(nc, 0);
+  ix->nnz.resize(nc, 0);
+  ix->tile_post.resize(nt, nullptr);
+  ix->tile_post_len.resize(nt, 0);
+  ix->tile_nnz.resize(nt, 0);
+  ix->tile_tombs.resize(nt, 0);
+  return SINN_OK;
+}
+
+static int grow_store(sinn_index *ix, uint64_t need) {
+  if (need <= ix->fwd_cap) return SINN_OK;
+  uint64_t nc = std::max<uint64_t>(need, ix->fwd_cap * 2);
+  nc = std::max<uint64_t>(nc, 1 << 16);
+  CK(cudaDeviceSynchronize());
+  int st = realloc_copy(&ix->d_fwd, ix->fwd_used, nc, false);
+  if (st) return st;
+  ix->fwd_cap = nc;
+  return SINN_OK;
+}
+
+extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
+  if (!cfg || !out) return SINN_EINVAL;
+  *out = nullptr;
+  const uint32_t n = cfg->n, m = cfg->m, h = cfg->h;
+  if (n == 0 || m == 0 || h == 0 || h > m || h > SINN_MAX_H || m > 4096) return SINN_EINVAL;
+  uint32_t T = cfg->tile_docs ? cfg->tile_docs : 4096;
+  if (T < 1024 || T > 32768 || (T & (T - 1))) return SINN_EINVAL;
+  if (cfg->table)
+    for (uint64_t t = 0; t < (uint64_t)n * h; ++t)
+      if (cfg->table[t] >= m) return SINN_EINVAL;
+  sinn_index *ix = new (std::nothrow) sinn_index();
+  if (!ix) return SINN_ENOMEM;
+  cudaGetDevice(&ix->device);
+  ix->n = n;
+  ix->m = m;
+  ix->h = h;
+  ix->T = T;
+  ix->log2T = 0;
+  while ((1u << ix->log2T) < T) ix->log2T++;
+  ix->seed = cfg->seed ? cfg->seed : 0x5151ULL;
+  ix->max_qnnz = cfg->max_query_nnz ? cfg->max_query_nnz : 1024;
+  ix->scratch_budget = cfg->scratch_bytes ? cfg->scratch_bytes : (4ULL << 30);
+  std::vector<uint32_t> tab((uint64_t)n * h);
+  for (uint32_t j = 0; j < n; ++j)
+    for (uint32_t o = 0; o < h; ++o) {
+      uint64_t t = (uint64_t)j * h + o;
+      if (cfg->table) {
+        tab[t] = cfg->table[t];
+      } else {
+        uint64_t x = ix->seed ^ ((uint64_t)(o + 1) * 0x9E3779B97F4A7C15ULL) ^ (uint64_t)j;
+        tab[t] = (uint32_t)(lib_mix64(x) % m);
+      }
+    }
+  int st = SINN_OK;
+  auto fail = [&](int s) {
+    release(ix);
+    return s;
+  };
+  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_pi, tab.size() * sizeof(uint32_t))))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemcpy(ix->d_pi, tab.data(), tab.size() * sizeof(uint32_t),
+                                       cudaMemcpyHostToDevice))))
+    return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_err, sizeof(uint32_t) * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(ix->d_err, 0, sizeof(uint32_t) * 4)))) return fail(st);
+  uint64_t hint = std::max<uint64_t>(cfg->capacity_hint, T);
+  if ((st = grow_capacity(ix, hint))) return fail(st);
+  *out = ix;
+  return SINN_OK;
+}
+
+extern "C" int sinn_create(uint32_t n, uint32_t m, uint32_t h, sinn_index **out) {
+  sinn_config c;
+  memset(&c, 0, sizeof(c));
+  c.n = n;
+  c.m = m;
+  c.h = h;
+  return sinn_create_ex(&c, out);
+}
+
+extern "C" int sinn_destroy(sinn_index *ix) {
+  release(ix);
+  return SINN_OK;
+}
+
+extern "C" const char *sinn_strerror(int code) {
+  switch (code) {
+    case SINN_OK: return "ok";
+    case SINN_EINVAL: return "invalid argument";
+    case SINN_ENOTFOUND: return "id not live";
+    case SINN_ENOMEM: return "out of memory";
+    case SINN_ECUDA: return "CUDA runtime error";
+    case SINN_EDEVICE: return "device-side error";
+    default: return "unknown error";
+  }
+}
+
+static int read_and_clear_err(sinn_index *ix, cudaStream_t s, uint32_t *bits) {
+  CK(cudaMemcpyAsync(bits, ix->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*bits) CK(cudaMemsetAsync(ix->d_err, 0, sizeof(uint32_t), s));
+  return SINN_OK;
+}
+
+extern "C" int sinn_sync(sinn_index *ix, void *stream) {
+  if (!ix) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t bits = 0;
+  int st = read_and_clear_err(ix, s, &bits);
+  if (st) return st;
+  CK(cudaStreamSynchronize(s));
+  if (bits & SINN_DERR_INTERNAL) return SINN_EDEVICE;
+  if (bits) return SINN_EINVAL;
+  return SINN_OK;
+}
+
+// Rebuild the postings of the given tiles (sorted, unique) from the store.
+static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s) {
+  if (tiles.empty()) return SINN_OK;
+  const uint32_t nb = (uint32_t)tiles.size();
+  std::vector<uint64_t> eoff(nb);
+  uint64_t etot = 0;
+  for (uint32_t i = 0; i < nb; ++i) {
+    eoff[i] = etot;
+    etot += ix->tile_nnz[tiles[i]];
+  }
+  // scratch: E, dpref, tiles, ptrs, eoff, out_len
+  size_t o_E = 0;
+  size_t o_dp = o_E + etot * 8;
+  size_t o_tl = (o_dp + (uint64_t)nb * (ix->T + 1) * 4 + 15) / 16 * 16;
+  size_t o_pt = (o_tl + nb * 4 + 15) / 16 * 16;
+  size_t o_eo = o_pt + nb * 8;
+  size_t o_ln = o_eo + nb * 8;
+  size_t bytes = o_ln + nb * 4;
+  int st = ensure_iscratch(ix, bytes);
+  if (st) return st;
+  std::vector<uint16_t *> newp(nb);
+  for (uint32_t i = 0; i < nb; ++i) {
+    uint32_t t = tiles[i];
+    uint64_t need = std::max<uint64_t>(ix->tile_nnz[t], 1);
+    CK(cudaMallocAsync((void **)&newp[i], need * sizeof(uint16_t), s));
+  }
+  size_t hb = nb * 4 + nb * 8 + nb * 8 + nb * 4;
+  CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
+  if ((st = sinn_ensure_pinned(ix, hb))) return st;
+  char *hp = (char *)ix->pinned;
+  memcpy(hp, tiles.data(), nb * 4);
+  memcpy(hp + nb * 4, newp.data(), nb * 8);
+  memcpy(hp + nb * 12, eoff.data(), nb * 8);
+  char *sp = (char *)ix->iscratch;
+  CK(cudaMemcpyAsync(sp + o_tl, hp, nb * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_pt, hp + nb * 4, nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_eo, hp + nb * 12, nb * 8, cudaMemcpyHostToDevice, s));
+  RebuildArgs a;
+  a.tiles = (const uint32_t *)(sp + o_tl);
+  a.new_post = (uint16_t *const *)(sp + o_pt);
+  a.e_off = (const uint64_t *)(sp + o_eo);
+  a.E = (uint64_t *)(sp + o_E);
+  a.dpref = (uint32_t *)(sp + o_dp);
+  a.out_len = (uint32_t *)(sp + o_ln);
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device);
+  uint32_t W = std::min<uint32_t>(ix->n, (uint32_t)((dev_smem - 4096) / 4));
+  size_t smem = (size_t)W * 4;
+  CK(cudaFuncSetAttribute(k_tile_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_tile_rebuild<<<nb, 512, smem, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz, ix->d_fwd,
+                                       ix->d_tile_off, ix->d_tile_post, ix->n, ix->T, ix->log2T,
+                                       W);
+  CK(cudaGetLastError());
+  for (uint32_t i = 0; i < nb; ++i) {
+    uint32_t t = tiles[i];
+    if (ix->tile_post[t]) CK(cudaFreeAsync(ix->tile_post[t], s));
+    ix->tile_post[t] = newp[i];
+  }
+  std::vector<uint32_t> lens(nb);
+  CK(cudaMemcpyAsync(hp, sp + o_ln, nb * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(lens.data(), hp, nb * 4);
+  for (uint32_t i = 0; i < nb; ++i) {
+    uint32_t t = tiles[i];
+    ix->tile_post_len[t] = lens[i];
+    ix->tombstones -= ix->tile_tombs[t];  // a rebuild compacts tombstones away
+    ix->tile_tombs[t] = 0;
+  }
+  return SINN_OK;
+}
+
+extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                           const float *values, uint32_t n_docs, uint32_t *out_ids,
+                           void *stream) {
+  if (!ix) return SINN_EINVAL;
+  if (n_docs == 0) return SINN_OK;
+  if (!indptr || !out_ids) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  // host copy of the row pointers (sizes drive allocation)
+  const size_t ipb = ((size_t)n_docs + 1) * 8;
+  if ((st = sinn_ensure_pinned(ix, ipb + (size_t)n_docs * 12 + 64))) return st;
+  uint64_t *hip = (uint64_t *)ix->pinned;
+  CK(cudaMemcpyAsync(hip, indptr, ipb, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<uint64_t> ip(hip, hip + n_docs + 1);
+  for (uint32_t r = 0; r < n_docs; ++r)
+    if (ip[r + 1] < ip[r]) return SINN_EINVAL;
+  const uint64_t total = ip[n_docs] - ip[0];
+  if (total && (!indices || !values)) return SINN_EINVAL;
+  for (uint32_t r = 0; r < n_docs; ++r)
+    if (ip[r + 1] - ip[r] > 0xFFFFFFFFull) return SINN_EINVAL;
+  SinnPhase phase(ix, s, 4);
+  // validation before any change
+  if (total) {
+    ix->launches++;
+    uint32_t bits = 0;
+    k_validate_csr<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, ix->n,
+                                                    ix->d_err, SINN_DERR_INSERT);
+    CK(cudaGetLastError());
+    if ((st = read_and_clear_err(ix, s, &bits))) return st;
+    if (bits & SINN_DERR_INSERT) return SINN_EINVAL;
+  }
+  // ids: smallest free first, then fresh
+  std::vector<uint32_t> ids(n_docs);
+  const uint64_t n_free = ix->free_ids.size();
+  if (ix->next_id + (n_docs > n_free ? n_docs - n_free : 0) > 0xFFFFFFFEull) return SINN_ENOMEM;
+  uint64_t max_id = 0;
+  {
+    auto fq = ix->free_ids;  // commit only after allocations succeed
+    uint64_t nid = ix->next_id;
+    for (uint32_t r = 0; r < n_docs; ++r) {
+      if (!fq.empty()) {
+        ids[r] = fq.top();
+        fq.pop();
+      } else {
+        ids[r] = (uint32_t)nid++;
+      }
+      max_id = std::max<uint64_t>(max_id, ids[r]);
+    }
+    if ((st = grow_capacity(ix, max_id + 1))) return st;
+    if ((st = grow_store(ix, ix->fwd_used + total))) return st;
+    ix->free_ids = fq;
+    ix->next_id = nid;
+  }
+  // offsets in the store, staged with the ids
+  uint32_t *hids = (uint32_t *)((char *)ix->pinned + ipb);
+  uint64_t *hoff = (uint64_t *)((char *)ix->pinned + ipb + (((size_t)n_docs * 4 + 7) / 8 * 8));
+  for (uint32_t r = 0; r < n_docs; ++r) {
+    hids[r] = ids[r];
+    hoff[r] = ix->fwd_used + (ip[r] - ip[0]);
+  }
+  ix->fwd_used += total;
+  const size_t o_off = ((size_t)n_docs * 4 + 15) / 16 * 16;
+  if ((st = ensure_iscratch(ix, o_off + (size_t)n_docs * 8))) return st;
+  uint32_t *d_ids = (uint32_t *)ix->iscratch;
+  uint64_t *d_off = (uint64_t *)((char *)ix->iscratch + o_off);
+  CK(cudaMemcpyAsync(d_ids, hids, (size_t)n_docs * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_off, hoff, (size_t)n_docs * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(out_ids, d_ids, (size_t)n_docs * 4, cudaMemcpyDeviceToDevice, s));
+  ix->launches += 4;  // store, sketch, live bits, tile rebuild
+  k_fwd_write<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, d_ids, d_off,
+                                              ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz);
+  CK(cudaGetLastError());
+  uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(32, 6144 / ix->m));
+  k_sketch<<<(n_docs + G - 1) / G, 256, (size_t)2 * G * ix->m * 4, s>>>(
+      indptr, indices, values, n_docs, d_ids, ix->d_pi, ix->m, ix->h, ix->cap, G, ix->d_U,
+      ix->d_L);
+  CK(cudaGetLastError());
+  k_set_live<<<(n_docs + 255) / 256, 256, 0, s>>>(d_ids, n_docs, ix->d_live, 1);
+  CK(cudaGetLastError());
+  std::vector<uint32_t> tiles;
+  tiles.reserve(n_docs);
+  for (uint32_t r = 0; r < n_docs; ++r) {
+    uint32_t id = ids[r];
+    ix->live[id] = 1;
+    ix->nnz[id] = (uint32_t)(ip[r + 1] - ip[r]);
+    ix->tile_nnz[id >> ix->log2T] += ix->nnz[id];
+    ix->live_count++;
+    tiles.push_back(id >> ix->log2T);
+  }
+  std::sort(tiles.begin(), tiles.end());
+  tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
+  if ((st = rebuild_tiles(ix, tiles, s))) return st;
+  uint32_t bits = 0;
+  if ((st = read_and_clear_err(ix, s, &bits))) return st;
+  return bits ? SINN_EDEVICE : SINN_OK;
+}
+
+extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, void *stream) {
+  if (!ix) return SINN_EINVAL;
+  if (n_ids == 0) return SINN_OK;
+  if (!ids) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
+  uint32_t *h = (uint32_t *)ix->pinned;
+  CK(cudaMemcpyAsync(h, ids, (size_t)n_ids * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<uint32_t> v(h, h + n_ids);
+  for (uint32_t id : v)
+    if (id >= ix->next_id || !ix->live[id]) return SINN_ENOTFOUND;
+  {
+    std::vector<uint32_t> srt(v);
+    std::sort(srt.begin(), srt.end());
+    if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SINN_EINVAL;
+  }
+  const size_t o_cnt = ((size_t)n_ids * 4 + 15) / 16 * 16;
+  if ((st = ensure_iscratch(ix, o_cnt + (size_t)n_ids * 4))) return st;
+  if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
+  uint32_t *d_ids = (uint32_t *)ix->iscratch;
+  uint32_t *d_cnt = (uint32_t *)((char *)ix->iscratch + o_cnt);
+  CK(cudaMemcpyAsync(d_ids, ids, (size_t)n_ids * 4, cudaMemcpyDeviceToDevice, s));
+  SinnPhase phase(ix, s, 5);
+  ix->launches++;
+  k_tombstone<<<(n_ids + 7) / 8, 256, 0, s>>>(d_ids, n_ids, ix->d_fwd_off, ix->d_fwd_nnz,
+                                              ix->d_fwd, ix->d_tile_off, ix->d_tile_post,
+                                              ix->d_live, ix->n, ix->log2T, d_cnt, ix->d_err);
+  CK(cudaGetLastError());
+  uint32_t *hc = (uint32_t *)ix->pinned;
+  CK(cudaMemcpyAsync(hc, d_cnt, (size_t)n_ids * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (uint32_t i = 0; i < n_ids; ++i) {
+    ix->tile_tombs[v[i] >> ix->log2T] += hc[i];
+    ix->tombstones += hc[i];
+  }
+  for (uint32_t id : v) {
+    ix->live[id] = 0;
+    ix->tile_nnz[id >> ix->log2T] -= ix->nnz[id];
+    ix->nnz[id] = 0;
+    ix->live_count--;
+    ix->free_ids.push(id);
+  }
+  uint32_t bits = 0;
+  if ((st = read_and_clear_err(ix, s, &bits))) return st;
+  return bits ? SINN_EDEVICE : SINN_OK;
+}
+
+extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
+  if (!ix || !out) return SINN_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->live = ix->live_count;
+  out->capacity = ix->cap;
+  out->next_id = ix->next_id;
+  uint64_t post = 0, pbytes = 0;
+  for (size_t t = 0; t < ix->tile_post.size(); ++t) {
+    post += ix->tile_post_len[t];
+    pbytes += ix->tile_post[t] ? std::max<uint64_t>(ix->tile_nnz[t], 1) * 2 : 0;
+  }
+  out->postings = post;
+  out->tombstones = ix->tombstones;
+  out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)(ix->n + 1) * 4;
+  out->bytes_sketch = 2ull * ix->m * ix->cap * 4;
+  out->bytes_store = ix->fwd_cap * 8 + ix->cap * 12;
+  out->bytes_scratch = ix->scratch_size + ix->iscratch_size;
+  out->n = ix->n;
+  out->m = ix->m;
+  out->h = ix->h;
+  out->tile_docs = ix->T;
+  return SINN_OK;
+}
+
+extern "C" int sinn_hash_table(sinn_index *ix, uint32_t *table) {
+  if (!ix || !table) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  CK(cudaMemcpy(table, ix->d_pi, (size_t)ix->n * ix->h * 4, cudaMemcpyDeviceToHost));
+  return SINN_OK;
+}
+
+extern "C" int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t n_ids,
+                                   float *u_out, float *l_out, void *stream) {
+  if (!ix || (n_ids && (!ids || !u_out || !l_out))) return SINN_EINVAL;
+  if (n_ids == 0) return SINN_OK;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t tot = (uint64_t)n_ids * ix->m;
+  k_gather_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ids, n_ids, ix->d_U, ix->d_L,
+                                                                  ix->m, ix->cap, u_out, l_out);
+  CK(cudaGetLastError());
+  return SINN_OK;
+}
+
+extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out, uint64_t cap,
+                                  uint64_t *len) {
+  if (!ix || coord >= ix->n || !len || (cap && !out)) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  CK(cudaDeviceSynchronize());
+  const uint64_t nt = ix->cap / ix->T;
+  std::vector<uint32_t> lo(nt), hi(nt);
+  CK(cudaMemcpy2D(lo.data(), 4, ix->d_tile_off + coord, (size_t)(ix->n + 1) * 4, 4, nt,
+                  cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy2D(hi.data(), 4, ix->d_tile_off + coord + 1, (size_t)(ix->n + 1) * 4, 4, nt,
+                  cudaMemcpyDeviceToHost));
+  uint64_t cnt = 0;
+  std::vector<uint16_t> buf;
+  for (uint64_t t = 0; t < nt; ++t) {
+    if (hi[t] <= lo[t] || !ix->tile_post[t]) continue;
+    buf.resize(hi[t] - lo[t]);
+    CK(cudaMemcpy(buf.data(), ix->tile_post[t] + lo[t], buf.size() * 2, cudaMemcpyDeviceToHost));
+    for (uint16_t d : buf) {
+      if (d & SINN_TOMB) continue;
+      if (cnt < cap) out[cnt] = (uint32_t)((t << ix->log2T) + d);
+      cnt++;
+    }
+  }
+  *len = cnt;
+  return SINN_OK;
+}

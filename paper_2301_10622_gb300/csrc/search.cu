@@ -1,0 +1,932 @@
+// Retrieval on the GPU: Alg. 6 (scoring) and Alg. 7 (ranking) of SINNAMON.
+//
+// One search launch handles a batch of B queries:
+//   k_qprep      nz(q), sorted by |q_j| descending, ties by j (Alg. 6 lines 1-2)
+//   k_score      grid (tile, query): walks the query's lists inside one tile of
+//                T ids, decodes each posting from the sketch (least upper bound
+//                from U for q_j > 0, greatest lower bound from L for q_j < 0,
+//                Alg. 6 lines 5-12) and accumulates q_j * x~ in shared memory;
+//                writes one order-preserving 32-bit score key per id and a
+//                4096-bin histogram of the keys' top 12 bits
+//   k_pick/k_hist_level/k_compact/k_refine
+//                FindLargest(scores, k') of Alg. 7 line 1 as a radix select
+//                over the keys: find the bin holding the k'-th largest, narrow
+//                it with finer histograms while it is large, collect the keys
+//                above it, then pick the rest of the bin by (score, -id)
+//   k_rerank     s_v = <q, S.Fetch(v)> for every candidate (Alg. 7 lines 2-3)
+//   k_final      FindLargest({s_v}, k) (Alg. 7 line 4), sorted best first
+// Ties rank the smaller id first: keys carry ~id in their low 32 bits.
+#include <algorithm>
+#include <cstring>
+
+#include "sinn_internal.cuh"
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) return sinn_check_cuda(e_); \
+  } while (0)
+
+namespace {
+
+constexpr uint32_t kBoundCap = 65536;  // boundary-bin entries kept per query
+constexpr uint32_t kScoreThreads = 256;
+constexpr uint32_t kChunk = 8192;      // keys per block in the dense select passes
+
+enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
+
+struct SelState {
+  uint32_t mode;    // SelMode
+  uint32_t prefix;  // top pbits of the boundary key
+  uint32_t pbits;
+  uint32_t rem;     // keys still to take from the boundary bin
+  uint32_t cnt;     // keys in the boundary bin
+  uint32_t kq;      // candidates wanted: min(k', live)
+  uint32_t ncand;   // candidates collected so far
+  uint32_t nbnd;    // boundary keys collected
+};
+
+struct QTerm {
+  uint32_t j;
+  float v;
+};
+
+struct Batch {  // device scratch views of one launch
+  QTerm *terms;     // B x qmax
+  uint32_t *nt;     // B
+  uint32_t *keys;   // B x cap
+  uint32_t *hist0;  // B x 4096
+  uint32_t *hist1;  // B x 4096
+  uint32_t *hist2;  // B x 256
+  SelState *sel;    // B
+  uint64_t *cand;   // B x kpmax
+  uint64_t *bnd;    // B x kBoundCap
+  uint64_t *ekeys;  // B x kpmax
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+// Warp-aggregated append: returns the slot for lanes with pred set.
+__device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t *counter) {
+  const uint32_t m = __ballot_sync(0xFFFFFFFFu, pred);
+  if (!m) return 0;
+  const uint32_t leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if ((threadIdx.x & 31) == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  return base + __popc(m & lanemask_lt());
+}
+
+// --------------------------------------------------------------- query prep
+__global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *__restrict__ q_idx,
+                        const float *__restrict__ q_val, uint32_t q0, uint32_t n, uint32_t qmax,
+                        uint32_t kp_scalar, const uint32_t *__restrict__ kp_arr, uint32_t kp_min,
+                        uint32_t kp_max, uint64_t live_count, Batch bt, uint32_t *err) {
+  extern __shared__ uint32_t sq[];
+  uint32_t *sj = sq;                  // qmax
+  float *sv = (float *)(sq + qmax);   // qmax
+  __shared__ uint32_t s_cnt, s_bad;
+  const uint32_t b = blockIdx.x, q = q0 + b;
+  const uint64_t s = q_indptr[q], e = q_indptr[q + 1];
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    s_bad = (e < s || e - s > qmax) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_bad) {
+    for (uint64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+      uint32_t c = q_idx[p];
+      float v = q_val[p];
+      bool bad = c >= n || !isfinite(v) || (p > s && q_idx[p - 1] >= c);
+      if (bad) atomicOr(&s_bad, 1u);
+      if (v != 0.0f && !bad) {
+        uint32_t slot = atomicAdd(&s_cnt, 1u);
+        sj[slot] = c;
+        sv[slot] = v;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t cnt = s_bad ? 0u : s_cnt;
+  QTerm *out = bt.terms + (uint64_t)b * qmax;
+  // Alg. 6 line 2: rank by |q_j| descending, ties by j ascending
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const float ai = fabsf(sv[i]);
+    const uint32_t ji = sj[i];
+    uint32_t r = 0;
+    for (uint32_t t = 0; t < cnt; ++t) {
+      float at = fabsf(sv[t]);
+      r += (at > ai) || (at == ai && sj[t] < ji);
+    }
+    out[r].j = ji;
+    out[r].v = sv[i];
+  }
+  if (threadIdx.x == 0) {
+    if (s_bad) atomicOr(err, SINN_DERR_QUERY);
+    bt.nt[b] = cnt;
+    uint32_t kp = kp_arr ? min(max(kp_arr[q], kp_min), kp_max) : kp_scalar;
+    SelState st;
+    st.mode = SEL_DONE;
+    st.prefix = 0;
+    st.pbits = 0;
+    st.rem = 0;
+    st.cnt = 0;
+    st.kq = s_bad ? 0u : (uint32_t)(live_count < kp ? live_count : (uint64_t)kp);
+    st.ncand = 0;
+    st.nbnd = 0;
+    bt.sel[b] = st;
+  }
+}
+
+// ------------------------------------------------------------------ scoring
+// Alg. 6 for one (tile, query) pair.  The block first stages the query terms
+// that have postings in this tile, then walks the flattened (term, posting)
+// space so every thread stays busy whatever the list lengths.
+struct ScoreArgs {
+  const uint32_t *tile_off;
+  uint16_t *const *tile_post;
+  const float *U;
+  const float *L;
+  const uint32_t *pi;
+  const uint32_t *live;
+  uint64_t cap;
+  uint32_t n, h, T, log2T, qmax;
+};
+
+__global__ void __launch_bounds__(kScoreThreads)
+    k_score(ScoreArgs a, Batch bt) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t T = a.T;
+  float *acc = (float *)sm;                      // T
+  uint32_t *hist = sm + T;                       // 4096
+  uint32_t *t_lo = hist + 4096;                  // qmax
+  uint32_t *t_pref = t_lo + a.qmax;              // qmax+1
+  float *t_v = (float *)(t_pref + a.qmax + 1);   // qmax
+  uint32_t *t_bin = (uint32_t *)(t_v + a.qmax);  // qmax*h
+  __shared__ uint32_t part[kScoreThreads / 32 + 1];
+
+  const uint32_t t = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const uint32_t nt = bt.nt[b];
+  const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
+  const uint32_t *off = a.tile_off + (uint64_t)t * (a.n + 1);
+  const uint16_t *post = a.tile_post[t];
+
+  for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
+  for (uint32_t i = tid; i < 4096; i += kScoreThreads) hist[i] = 0;
+  for (uint32_t i = tid; i < nt; i += kScoreThreads) {
+    const uint32_t j = terms[i].j;
+    const uint32_t lo = off[j], hi = off[j + 1];
+    t_lo[i] = lo;
+    t_pref[i] = hi - lo;
+    t_v[i] = terms[i].v;
+    for (uint32_t o = 0; o < a.h; ++o) t_bin[i * a.h + o] = a.pi[(uint64_t)j * a.h + o];
+  }
+  __syncthreads();
+  // exclusive prefix of the per-term posting counts (one warp: nt is small)
+  if (tid < 32) {
+    uint32_t run = 0;
+    for (uint32_t base = 0; base < nt; base += 32) {
+      uint32_t i = base + tid;
+      uint32_t v = i < nt ? t_pref[i] : 0, x = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (tid >= (uint32_t)d) x += y;
+      }
+      if (i < nt) t_pref[i] = run + x - v;
+      run += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+    if (tid == 0) {
+      t_pref[nt] = run;
+      part[0] = run;
+    }
+  }
+  __syncthreads();
+  const uint32_t P = part[0];
+  const uint64_t id0 = (uint64_t)t << a.log2T;
+
+  // flattened walk: element f belongs to the term i with t_pref[i] <= f < t_pref[i+1]
+  for (uint32_t f0 = tid; f0 < P; f0 += 4 * kScoreThreads) {
+    uint32_t ti[4], d16[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t f = f0 + u * kScoreThreads;
+      ti[u] = 0xFFFFFFFFu;
+      d16[u] = SINN_TOMB;
+      if (f < P) {
+        uint32_t lo = 0, hi = nt;  // last i with t_pref[i] <= f
+        while (hi - lo > 1) {
+          uint32_t mid = (lo + hi) >> 1;
+          if (t_pref[mid] <= f) lo = mid;
+          else hi = mid;
+        }
+        ti[u] = lo;
+        d16[u] = __ldg(post + t_lo[lo] + (f - t_pref[lo]));
+      }
+    }
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = 0.0f;
+      if (!(d16[u] & SINN_TOMB)) {
+        const uint32_t i = ti[u];
+        const float v = t_v[i];
+        const float *plane = v > 0.0f ? a.U : a.L;
+        const uint64_t gid = id0 + d16[u];
+        float y = __ldg(plane + (uint64_t)t_bin[i * a.h] * a.cap + gid);
+        for (uint32_t o = 1; o < a.h; ++o) {
+          float z = __ldg(plane + (uint64_t)t_bin[i * a.h + o] * a.cap + gid);
+          y = v > 0.0f ? fminf(y, z) : fmaxf(y, z);
+        }
+        x[u] = y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (!(d16[u] & SINN_TOMB)) atomicAdd(&acc[d16[u]], t_v[ti[u]] * x[u]);
+  }
+  __syncthreads();
+
+  // epilogue: one key per id slot of the tile (0 = not live), histogram
+  uint32_t *keys = bt.keys + (uint64_t)b * a.cap + id0;
+  for (uint32_t d = tid; d < T; d += kScoreThreads) {
+    const bool lv = sinn_is_live(a.live, id0 + d);
+    const uint32_t key = lv ? sinn_f2key(acc[d] + 0.0f) : 0u;
+    keys[d] = key;
+    if (lv) atomicAdd(&hist[key >> 20], 1u);
+  }
+  __syncthreads();
+  uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
+  for (uint32_t i = tid; i < 4096; i += kScoreThreads)
+    if (hist[i]) atomicAdd(&gh[i], hist[i]);
+}
+
+// ------------------------------------------------------------------ select
+// Find, scanning bins from the top, the bin where the running count reaches
+// rem.  Returns (bin, count above the bin).  Block of 128 threads.
+__device__ void find_bin(const uint32_t *hist, uint32_t nb, uint32_t rem, uint32_t *out_bin,
+                         uint32_t *out_above) {
+  __shared__ uint32_t sums[128];
+  __shared__ uint32_t res[2];
+  const uint32_t tid = threadIdx.x, per = nb / 128;
+  // thread tid owns bins [nb - (tid+1)*per, nb - tid*per), highest first
+  const uint32_t hi = nb - tid * per;
+  uint32_t s = 0;
+  for (uint32_t i = 0; i < per; ++i) s += hist[hi - 1 - i];
+  sums[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0, found = 0;
+    for (uint32_t w = 0; w < 128 && !found; ++w) {
+      if (run + sums[w] >= rem) {
+        uint32_t top = nb - w * per;
+        for (uint32_t i = 0; i < per; ++i) {
+          uint32_t c = hist[top - 1 - i];
+          if (run + c >= rem) {
+            res[0] = top - 1 - i;
+            res[1] = run;
+            found = 1;
+            break;
+          }
+          run += c;
+        }
+      } else {
+        run += sums[w];
+      }
+    }
+    if (!found) {  // cannot happen when rem <= sum(hist)
+      res[0] = 0;
+      res[1] = run;
+    }
+  }
+  __syncthreads();
+  *out_bin = res[0];
+  *out_above = res[1];
+}
+
+__global__ void k_pick(Batch bt, uint32_t level) {
+  const uint32_t b = blockIdx.x;
+  SelState st = bt.sel[b];
+  if (level == 0) {
+    if (st.kq == 0) return;  // SEL_DONE already
+    st.rem = st.kq;
+  } else if ((level == 1 && st.mode != SEL_L1) || (level == 2 && st.mode != SEL_L2)) {
+    return;
+  }
+  const uint32_t nb = level == 2 ? 256u : 4096u;
+  const uint32_t *h = level == 0 ? bt.hist0 + (uint64_t)b * 4096
+                                 : level == 1 ? bt.hist1 + (uint64_t)b * 4096
+                                              : bt.hist2 + (uint64_t)b * 256;
+  uint32_t bin, above;
+  find_bin(h, nb, st.rem, &bin, &above);
+  if (threadIdx.x == 0) {
+    const uint32_t digits = level == 2 ? 8u : 12u;
+    st.prefix = (st.prefix << digits) | bin;
+    st.pbits += digits;
+    st.rem -= above;
+    st.cnt = h[bin];
+    if (st.cnt <= kBoundCap) st.mode = SEL_COMPACT;
+    else st.mode = level == 0 ? SEL_L1 : level == 1 ? SEL_L2 : SEL_TIES;
+    bt.sel[b] = st;
+  }
+}
+
+// Histogram of the next digit over keys matching the current prefix.
+__global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
+  __shared__ uint32_t hist[4096];
+  const uint32_t b = blockIdx.y;
+  const SelState st = bt.sel[b];
+  if (st.mode != (level == 1 ? SEL_L1 : SEL_L2)) return;
+  const uint32_t nb = level == 1 ? 4096u : 256u;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const uint32_t shift_p = 32 - st.pbits;       // 20 or 8
+  const uint32_t shift_d = level == 1 ? 8u : 0u;
+  const uint32_t dmask = nb - 1;
+  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+  const uint64_t beg = (uint64_t)blockIdx.x * kChunk;
+  const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+  for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const uint32_t key = keys[i];
+    if (key != 0u && (key >> shift_p) == st.prefix) atomicAdd(&hist[(key >> shift_d) & dmask], 1u);
+  }
+  __syncthreads();
+  uint32_t *gh = level == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+    if (hist[i]) atomicAdd(&gh[i], hist[i]);
+}
+
+// Collect keys above the boundary bin (certain candidates) and, in COMPACT
+// mode, the keys of the boundary bin itself.
+__global__ void k_compact(Batch bt, uint64_t cap, uint32_t kpmax) {
+  const uint32_t b = blockIdx.y;
+  const SelState st = bt.sel[b];
+  if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) return;
+  const uint32_t shift = 32 - st.pbits;
+  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+  uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
+  uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
+  uint32_t *ncand = &bt.sel[b].ncand, *nbnd = &bt.sel[b].nbnd;
+  const uint64_t beg = (uint64_t)blockIdx.x * kChunk;
+  const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+  for (uint64_t i0 = beg; i0 < end; i0 += blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    const uint32_t key = i < end ? keys[i] : 0u;
+    const uint32_t top = shift == 32 ? 0u : (key >> shift);
+    const bool up = key != 0u && top > st.prefix;
+    const bool eq = key != 0u && top == st.prefix && st.mode == SEL_COMPACT;
+    const uint64_t k64 = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)i;
+    uint32_t p = warp_append(up, ncand);
+    if (up) cand[p] = k64;
+    p = warp_append(eq, nbnd);
+    if (eq) bnd[p] = k64;
+  }
+}
+
+// Block-level selection of the r largest of n distinct 64-bit keys held in
+// global memory: one 8-bit digit per pass from the top, stopping early once
+// the prefix pins down exactly r keys.  Returns (prefix, mask): the selected
+// keys are those with (key & mask) >= prefix.
+__device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
+                                 uint64_t *out_prefix, uint64_t *out_mask) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_rem, s_stop;
+  __shared__ uint64_t s_prefix, s_mask;
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_mask = 0;
+    s_rem = r;
+    s_stop = (r >= n) ? 1u : 0u;
+  }
+  __syncthreads();
+  for (int shift = 56; shift >= 0 && !s_stop; shift -= 8) {
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint64_t pre = s_prefix, msk = s_mask;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t k = keys[i];
+      if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0, rem = s_rem, dsel = 0;
+      for (int d = 255; d >= 0; --d) {
+        if (run + hist[d] >= rem) {
+          dsel = (uint32_t)d;
+          break;
+        }
+        run += hist[d];
+      }
+      s_rem = rem - run;
+      s_prefix = pre | ((uint64_t)dsel << shift);
+      s_mask = msk | (0xFFull << shift);
+      if (hist[dsel] == s_rem) s_stop = 1u;  // the whole digit bucket is in
+    }
+    __syncthreads();
+  }
+  *out_prefix = s_prefix;
+  *out_mask = s_mask;
+  __syncthreads();
+}
+
+// Rest of the boundary bin: the rem best of its keys (COMPACT), or in TIES
+// mode the rem smallest ids whose key equals the boundary value exactly.
+__global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint32_t kpmax) {
+  const uint32_t b = blockIdx.x;
+  __shared__ SelState st;
+  __shared__ uint32_t s_base, wsum[16];
+  if (threadIdx.x == 0) st = bt.sel[b];
+  __syncthreads();
+  if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) return;
+  uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
+  uint32_t *ncand = &bt.sel[b].ncand;
+  if (st.mode == SEL_COMPACT) {
+    const uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
+    const uint32_t nb = min(st.nbnd, kBoundCap);
+    uint64_t pre, msk;
+    block_select_u64(bnd, nb, st.rem, &pre, &msk);
+    for (uint32_t i0 = 0; i0 < nb; i0 += blockDim.x) {
+      const uint32_t i = i0 + threadIdx.x;
+      const uint64_t k = i < nb ? bnd[i] : 0ull;
+      const bool take = i < nb && (k & msk) >= pre;
+      const uint32_t p = warp_append(take, ncand);
+      if (take) cand[p] = k;
+    }
+    return;
+  }
+  // SEL_TIES: ordered scan in id order
+  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+  const uint32_t tau = st.prefix;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t i0 = 0; i0 < cap && s_base < st.rem; i0 += blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    const bool m = i < cap && keys[i] == tau;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    uint32_t before = s_base;
+    for (uint32_t w = 0; w < wid; ++w) before += wsum[w];
+    before += __popc(bal & lanemask_lt());
+    if (m && before < st.rem) {
+      const uint32_t p = atomicAdd(ncand, 1u);
+      cand[p] = ((uint64_t)tau << 32) | (uint32_t)~(uint32_t)i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (uint32_t w = 0; w < blockDim.x / 32; ++w) tot += wsum[w];
+      s_base += tot;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ re-rank
+struct RerankArgs {
+  const uint64_t *fwd_off;
+  const uint32_t *fwd_nnz;
+  const uint2 *fwd;
+  uint32_t qmax, kpmax, per_block;
+};
+
+__device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
+  return (c * 0x9E3779B1u) >> 7 & mask;
+}
+
+// Alg. 7 lines 2-3: exact <q, x_v> from the vector store for each candidate v.
+// The query lives in a shared-memory hash table; one warp per candidate, lanes
+// over the vector's entries, fixed-order reduction.
+__global__ void k_rerank(RerankArgs a, Batch bt) {
+  extern __shared__ uint32_t hs[];
+  const uint32_t b = blockIdx.y;
+  const uint32_t kq = bt.sel[b].kq;
+  const uint32_t c0 = blockIdx.x * a.per_block;
+  if (c0 >= kq) return;
+  const uint32_t nt = bt.nt[b];
+  uint32_t tsz = 64;
+  while (tsz < 2 * nt) tsz <<= 1;
+  const uint32_t mask = tsz - 1;
+  uint32_t *hk = hs;
+  float *hv = (float *)(hs + tsz);
+  for (uint32_t i = threadIdx.x; i < tsz; i += blockDim.x) hk[i] = 0xFFFFFFFFu;
+  __syncthreads();
+  const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
+  for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) {
+    uint32_t c = terms[i].j, s = hslot(c, mask);
+    while (atomicCAS(&hk[s], 0xFFFFFFFFu, c) != 0xFFFFFFFFu) s = (s + 1) & mask;
+    hv[s] = terms[i].v;
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t *cand = bt.cand + (uint64_t)b * a.kpmax;
+  uint64_t *ek = bt.ekeys + (uint64_t)b * a.kpmax;
+  const uint32_t c1 = min(kq, c0 + a.per_block);
+  for (uint32_t c = c0 + wid; c < c1; c += nw) {
+    const uint32_t id = ~(uint32_t)cand[c];
+    const uint64_t fo = a.fwd_off[id];
+    const uint32_t nz = a.fwd_nnz[id];
+    float s = 0.0f;
+    for (uint32_t e = lane; e < nz; e += 32) {
+      const uint2 pr = __ldg(a.fwd + fo + e);
+      uint32_t h = hslot(pr.x, mask);
+      float qv = 0.0f;
+      while (true) {
+        uint32_t kk = hk[h];
+        if (kk == pr.x) {
+          qv = hv[h];
+          break;
+        }
+        if (kk == 0xFFFFFFFFu) break;
+        h = (h + 1) & mask;
+      }
+      s = fmaf(qv, __uint_as_float(pr.y), s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) ek[c] = ((uint64_t)sinn_f2key(s + 0.0f) << 32) | (uint32_t)~id;
+  }
+}
+
+// Alg. 7 line 4: best k of the re-ranked candidates, sorted best first.
+__global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32_t k, uint32_t q0,
+                                                uint32_t *out_ids, float *out_scores) {
+  __shared__ uint64_t sk[SINN_MAX_K];
+  __shared__ uint32_t s_cnt;
+  const uint32_t b = blockIdx.x;
+  const uint32_t kq = bt.sel[b].kq;
+  const uint32_t r = min(k, kq);
+  const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
+  uint64_t pre = 0, msk = 0;
+  if (kq > 0) block_select_u64(ek, kq, r, &pre, &msk);
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kq; i += blockDim.x) {
+    const uint64_t key = ek[i];
+    if ((key & msk) >= pre) sk[atomicAdd(&s_cnt, 1u)] = key;
+  }
+  for (uint32_t i = r + threadIdx.x; i < SINN_MAX_K; i += blockDim.x) sk[i] = 0ull;
+  __syncthreads();
+  // bitonic sort, descending
+  for (uint32_t size = 2; size <= SINN_MAX_K; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < SINN_MAX_K; i += blockDim.x) {
+        const uint32_t j = i ^ stride;
+        if (j > i) {
+          const bool desc = (i & size) == 0;
+          const uint64_t x = sk[i], y = sk[j];
+          if (desc ? (x < y) : (x > y)) {
+            sk[i] = y;
+            sk[j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const uint64_t ob = (uint64_t)(q0 + b) * k;
+  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+    if (i < r) {
+      out_ids[ob + i] = ~(uint32_t)sk[i];
+      out_scores[ob + i] = sinn_key2f((uint32_t)(sk[i] >> 32));
+    } else {
+      out_ids[ob + i] = 0xFFFFFFFFu;
+      out_scores[ob + i] = -INFINITY;
+    }
+  }
+}
+
+__global__ void k_keys_to_scores(const uint32_t *__restrict__ keys, uint64_t cnt, float *out) {
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  uint32_t k = keys[i];
+  out[i] = k ? sinn_key2f(k) : -INFINITY;
+}
+
+__global__ void k_cand_out(Batch bt, uint32_t kpmax, uint32_t q0, uint32_t *out_ids,
+                           float *out_scores, uint32_t *out_count) {
+  const uint32_t b = blockIdx.x;
+  const uint32_t kq = bt.sel[b].kq;
+  const uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
+  const uint64_t ob = (uint64_t)(q0 + b) * kpmax;
+  for (uint32_t i = threadIdx.x; i < kpmax; i += blockDim.x) {
+    if (i < kq) {
+      out_ids[ob + i] = ~(uint32_t)cand[i];
+      out_scores[ob + i] = sinn_key2f((uint32_t)(cand[i] >> 32));
+    } else {
+      out_ids[ob + i] = 0xFFFFFFFFu;
+      out_scores[ob + i] = -INFINITY;
+    }
+  }
+  if (threadIdx.x == 0) out_count[q0 + b] = kq;
+}
+
+// ------------------------------------------------------------- host driver
+struct Layout {
+  size_t terms, nt, keys, hist0, hist1, hist2, sel, cand, bnd, ekeys, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+Layout layout_for(const sinn_index *ix, uint32_t B, uint32_t kpmax) {
+  Layout L;
+  size_t o = 0;
+  L.terms = o; o = align256(o + (size_t)B * ix->max_qnnz * sizeof(QTerm));
+  L.nt = o;    o = align256(o + (size_t)B * 4);
+  L.keys = o;  o = align256(o + (size_t)B * ix->cap * 4);
+  L.hist0 = o; o = align256(o + (size_t)B * 4096 * 4);
+  L.hist1 = o; o = align256(o + (size_t)B * 4096 * 4);
+  L.hist2 = o; o = align256(o + (size_t)B * 256 * 4);
+  L.sel = o;   o = align256(o + (size_t)B * sizeof(SelState));
+  L.cand = o;  o = align256(o + (size_t)B * kpmax * 8);
+  L.bnd = o;   o = align256(o + (size_t)B * kBoundCap * 8);
+  L.ekeys = o; o = align256(o + (size_t)B * kpmax * 8);
+  L.total = o;
+  return L;
+}
+
+Batch views(void *base, const Layout &L) {
+  char *p = (char *)base;
+  Batch bt;
+  bt.terms = (QTerm *)(p + L.terms);
+  bt.nt = (uint32_t *)(p + L.nt);
+  bt.keys = (uint32_t *)(p + L.keys);
+  bt.hist0 = (uint32_t *)(p + L.hist0);
+  bt.hist1 = (uint32_t *)(p + L.hist1);
+  bt.hist2 = (uint32_t *)(p + L.hist2);
+  bt.sel = (SelState *)(p + L.sel);
+  bt.cand = (uint64_t *)(p + L.cand);
+  bt.bnd = (uint64_t *)(p + L.bnd);
+  bt.ekeys = (uint64_t *)(p + L.ekeys);
+  return bt;
+}
+
+enum class Stage { kScores, kCandidates, kFull };
+
+struct SearchReq {
+  const uint64_t *q_indptr;
+  const uint32_t *q_idx;
+  const float *q_val;
+  uint32_t n_q, k, kp, kp_min, kp_max;
+  const uint32_t *kp_arr;
+  uint32_t *out_ids;
+  float *out_scores;
+  uint32_t *out_count;
+  float *out_dense;
+  Stage stage;
+};
+
+size_t score_smem(const sinn_index *ix) {
+  return (size_t)ix->T * 4 + 4096 * 4 + (size_t)ix->max_qnnz * (4 + 4 + 4 + 4 * ix->h) + 4;
+}
+
+int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
+  const uint32_t kpmax = r.kp_max;
+  const Layout one = layout_for(ix, 1, kpmax);
+  uint64_t B = std::max<uint64_t>(1, ix->scratch_budget / one.total);
+  B = std::min<uint64_t>(B, r.n_q);
+  B = std::min<uint64_t>(B, 65535);
+  Layout L = layout_for(ix, (uint32_t)B, kpmax);
+  int st = sinn_ensure_scratch(ix, L.total);
+  if (st) return st;
+  Batch bt = views(ix->scratch, L);
+  const size_t ssm = score_smem(ix);
+  CK(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  ScoreArgs sa;
+  sa.tile_off = ix->d_tile_off;
+  sa.tile_post = ix->d_tile_post;
+  sa.U = ix->d_U;
+  sa.L = ix->d_L;
+  sa.pi = ix->d_pi;
+  sa.live = ix->d_live;
+  sa.cap = ix->cap;
+  sa.n = ix->n;
+  sa.h = ix->h;
+  sa.T = ix->T;
+  sa.log2T = ix->log2T;
+  sa.qmax = ix->max_qnnz;
+  RerankArgs ra;
+  ra.fwd_off = ix->d_fwd_off;
+  ra.fwd_nnz = ix->d_fwd_nnz;
+  ra.fwd = ix->d_fwd;
+  ra.qmax = ix->max_qnnz;
+  ra.kpmax = kpmax;
+  ra.per_block = 64;
+  uint32_t tsz = 64;
+  while (tsz < 2 * ix->max_qnnz) tsz <<= 1;
+  const uint32_t tiles = (uint32_t)(ix->cap / ix->T);
+  const uint32_t chunks = (uint32_t)((ix->cap + kChunk - 1) / kChunk);
+  for (uint32_t q0 = 0; q0 < r.n_q; q0 += (uint32_t)B) {
+    const uint32_t nb = (uint32_t)std::min<uint64_t>(B, r.n_q - q0);
+    {
+    SinnPhase ph(ix, s, 0);
+    ix->launches++;
+    k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0, ix->n,
+                                                       ix->max_qnnz, r.kp, r.kp_arr, r.kp_min,
+                                                       r.kp_max, ix->live_count, bt, ix->d_err);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(bt.hist0, 0, (size_t)nb * 4096 * 4, s));
+    CK(cudaMemsetAsync(bt.hist1, 0, (size_t)nb * 4096 * 4, s));
+    CK(cudaMemsetAsync(bt.hist2, 0, (size_t)nb * 256 * 4, s));
+    }
+    {
+      SinnPhase ph(ix, s, 1);
+      ix->launches++;
+      k_score<<<dim3(tiles, nb), kScoreThreads, ssm, s>>>(sa, bt);
+      CK(cudaGetLastError());
+    }
+    if (r.stage == Stage::kScores) {
+      for (uint32_t b = 0; b < nb; ++b) {
+        uint64_t cnt = ix->cap;
+        k_keys_to_scores<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+            bt.keys + (uint64_t)b * ix->cap, cnt, r.out_dense + (uint64_t)(q0 + b) * ix->cap);
+      }
+      CK(cudaGetLastError());
+      continue;
+    }
+    {
+    SinnPhase ph(ix, s, 2);
+    ix->launches += 7;
+    k_pick<<<nb, 128, 0, s>>>(bt, 0);
+    k_hist_level<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, 1);
+    k_pick<<<nb, 128, 0, s>>>(bt, 1);
+    k_hist_level<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, 2);
+    k_pick<<<nb, 128, 0, s>>>(bt, 2);
+    k_compact<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, kpmax);
+    k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, kpmax);
+    CK(cudaGetLastError());
+    }
+    if (r.stage == Stage::kCandidates) {
+      k_cand_out<<<nb, 256, 0, s>>>(bt, kpmax, q0, r.out_ids, r.out_scores, r.out_count);
+      CK(cudaGetLastError());
+      continue;
+    }
+    {
+      SinnPhase ph(ix, s, 3);
+      ix->launches += 2;
+      k_rerank<<<dim3((kpmax + ra.per_block - 1) / ra.per_block, nb), 256, (size_t)tsz * 8,
+                 s>>>(ra, bt);
+      k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
+      CK(cudaGetLastError());
+    }
+  }
+  return SINN_OK;
+}
+
+int check_query_args(sinn_index *ix, const uint64_t *ip, uint32_t n_q) {
+  if (!ix) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!ip) return SINN_EINVAL;
+  return SINN_OK;
+}
+
+}  // namespace
+
+extern "C" int sinn_search(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                           const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                           uint32_t *out_ids, float *out_scores, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = k;
+  r.kp = k_prime;
+  r.kp_min = k;
+  r.kp_max = k_prime;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.stage = Stage::kFull;
+  return run_search(ix, r, (cudaStream_t)stream);
+}
+
+extern "C" int sinn_search_kp(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                              const float *q_values, uint32_t n_q, uint32_t k,
+                              const uint32_t *k_prime, uint32_t k_prime_max, uint32_t *out_ids,
+                              float *out_scores, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k == 0 || k > SINN_MAX_K || k_prime_max < k || !k_prime) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = k;
+  r.kp = k_prime_max;
+  r.kp_arr = k_prime;
+  r.kp_min = k;
+  r.kp_max = k_prime_max;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.stage = Stage::kFull;
+  return run_search(ix, r, (cudaStream_t)stream);
+}
+
+extern "C" int sinn_scores(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                           const float *q_values, uint32_t n_q, float *out, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (n_q == 0) return SINN_OK;
+  if (!out) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = 1;
+  r.kp = 1;
+  r.kp_min = 1;
+  r.kp_max = 1;
+  r.out_dense = out;
+  r.stage = Stage::kScores;
+  return run_search(ix, r, (cudaStream_t)stream);
+}
+
+extern "C" int sinn_candidates(sinn_index *ix, const uint64_t *q_indptr,
+                               const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                               uint32_t k_prime, uint32_t *out_ids, float *out_scores,
+                               uint32_t *out_count, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k_prime == 0) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores || !out_count) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = 1;
+  r.kp = k_prime;
+  r.kp_min = 1;
+  r.kp_max = k_prime;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.out_count = out_count;
+  r.stage = Stage::kCandidates;
+  return run_search(ix, r, (cudaStream_t)stream);
+}
+
+extern "C" int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr,
+                                const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                                uint32_t k, uint32_t k_prime, uint32_t *out_ids,
+                                float *out_scores, void *stream) {
+  if (!ix) return SINN_EINVAL;
+  if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!q_indptr || !out_ids || !out_scores) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t nnz = q_indptr[n_q] - q_indptr[0];
+  if (nnz && (!q_indices || !q_values)) return SINN_EINVAL;
+  const size_t b_ip = align256(((size_t)n_q + 1) * 8), b_ix = align256(nnz * 4),
+               b_v = align256(nnz * 4), b_oi = align256((size_t)n_q * k * 4),
+               b_os = align256((size_t)n_q * k * 4);
+  const size_t need = b_ip + b_ix + b_v + b_oi + b_os;
+  if (need > ix->hstage_size) {
+    if (ix->hstage) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaFree(ix->hstage));
+      ix->hstage = nullptr;
+      ix->hstage_size = 0;
+    }
+    CK(cudaMalloc(&ix->hstage, need));
+    ix->hstage_size = need;
+  }
+  char *p = (char *)ix->hstage;
+  uint64_t *d_ip = (uint64_t *)p;
+  uint32_t *d_ix = (uint32_t *)(p + b_ip);
+  float *d_v = (float *)(p + b_ip + b_ix);
+  uint32_t *d_oi = (uint32_t *)(p + b_ip + b_ix + b_v);
+  float *d_os = (float *)(p + b_ip + b_ix + b_v + b_oi);
+  // row pointers rebased to zero on the device side
+  std::vector<uint64_t> ip(q_indptr, q_indptr + n_q + 1);
+  const uint64_t base = ip[0];
+  bool rebase = base != 0;
+  if (rebase)
+    for (auto &x : ip) x -= base;
+  CK(cudaMemcpyAsync(d_ip, rebase ? ip.data() : q_indptr, ((size_t)n_q + 1) * 8,
+                     cudaMemcpyHostToDevice, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(d_ix, q_indices + base, nnz * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_v, q_values + base, nnz * 4, cudaMemcpyHostToDevice, s));
+  }
+  int st = sinn_search(ix, d_ip, d_ix, d_v, n_q, k, k_prime, d_oi, d_os, stream);
+  if (st) return st;
+  CK(cudaMemcpyAsync(out_ids, d_oi, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(out_scores, d_os, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
+  return sinn_sync(ix, stream);
+}

@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <functional>
+#include <queue>
+#include <vector>
+
+#include "../../include/sinnamon.h"
+
+// ---------------------------------------------------------------- constants
+#define SINN_MAX_H 8
+#define SINN_MAX_K 1024
+#define SINN_TOMB 0x8000u   // tombstone bit of a 16-bit local posting id
+#define SINN_HIST0_BITS 12  // first select level: key bits [31:20]
+#define SINN_HIST1_BITS 12  // second level: key bits [19:8]
+#define SINN_HIST2_BITS 8   // third level: key bits [7:0]
+
+// device error bits (sticky flag)
+#define SINN_DERR_QUERY 1u     // malformed query
+#define SINN_DERR_INTERNAL 2u  // an internal capacity check failed
+#define SINN_DERR_INSERT 4u    // malformed insert batch (validation kernel)
+
+// ------------------------------------------------------------ index object
+struct sinn_index {
+  uint32_t n = 0, m = 0, h = 0;
+  uint32_t T = 0, log2T = 0;  // ids per tile
+  uint64_t seed = 0;
+  uint32_t max_qnnz = 0;
+  uint64_t scratch_budget = 0;
+  int device = 0;
+
+  // ---- device state
+  uint32_t *d_pi = nullptr;        // n*h mappings
+  float *d_U = nullptr;            // m x cap, row-major (row k contiguous over ids)
+  float *d_L = nullptr;            // m x cap
+  uint32_t *d_live = nullptr;      // cap/32 bitmap words
+  uint64_t *d_fwd_off = nullptr;   // cap: offset of each vector in d_fwd
+  uint32_t *d_fwd_nnz = nullptr;   // cap: entries stored (zeros included)
+  uint2 *d_fwd = nullptr;          // vector store pool: (coordinate, value bits)
+  uint64_t fwd_cap = 0, fwd_used = 0;
+  uint32_t *d_tile_off = nullptr;  // tiles_cap x (n+1) offsets into each tile's postings
+  uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
+  uint32_t *d_err = nullptr;       // sticky device error bits
+  uint64_t cap = 0;                // id capacity = tiles_cap * T
+
+  // ---- host mirror
+  std::vector<uint8_t> live;        // per id
+  std::vector<uint32_t> nnz;        // per id: stored entries of the live vector
+  std::priority_queue<uint32_t, std::vector<uint32_t>, std::greater<uint32_t>> free_ids;
+  uint64_t next_id = 0, live_count = 0;
+  std::vector<uint16_t *> tile_post;     // per tile posting array (device)
+  std::vector<uint64_t> tile_post_len;   // postings held (tombstones included)
+  std::vector<uint64_t> tile_nnz;        // sum of nnz over live vectors of the tile
+  std::vector<uint64_t> tile_tombs;      // tombstoned postings per tile
+  uint64_t tombstones = 0;
+
+  // ---- scratch (search and insert), grow-only
+  void *scratch = nullptr;
+  size_t scratch_size = 0;
+  void *iscratch = nullptr;
+  size_t iscratch_size = 0;
+  // pinned host staging
+  void *pinned = nullptr;
+  size_t pinned_size = 0;
+  // device staging for sinn_search_host
+  void *hstage = nullptr;
+  size_t hstage_size = 0;
+
+  // ---- timing (sinn_timing_start/stop)
+  bool tm_on = false;
+  struct Span {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> tm_spans;
+  std::vector<cudaEvent_t> tm_pool;
+  uint64_t launches = 0;
+};
+
+// Brackets one phase with CUDA events when timing is on.
+struct SinnPhase {
+  sinn_index *ix;
+  cudaStream_t s;
+  int phase;
+  cudaEvent_t a = nullptr;
+  SinnPhase(sinn_index *ix_, cudaStream_t s_, int ph);
+  ~SinnPhase();
+};
+
+// host helpers shared across translation units
+int sinn_ensure_scratch(sinn_index *ix, size_t bytes);
+int sinn_ensure_pinned(sinn_index *ix, size_t bytes);
+int sinn_check_cuda(cudaError_t e);
+
+// ---------------------------------------------------------- device helpers
+// Order-preserving map from float to uint32 (for all non-NaN values: a < b as
+// floats iff key(a) < key(b) as unsigned integers).
+__device__ __forceinline__ uint32_t sinn_f2key(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float sinn_key2f(uint32_t k) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ bool sinn_is_live(const uint32_t *live, uint64_t id) {
+  return (__ldg(live + (id >> 5)) >> (id & 31)) & 1u;
+}

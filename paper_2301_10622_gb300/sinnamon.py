@@ -1,0 +1,365 @@
+"""Python binding of the SINNAMON C ABI (include/sinnamon.h).
+
+Argument marshalling only: every step of insertion, deletion and search runs in
+the CUDA library ``libsinnamon.so``.  The functions keep the C names; tensors
+are PyTorch CUDA tensors of the index's device (device pointers of the C ABI)
+unless a name says ``host``.  Unsigned C types travel in signed torch dtypes of
+the same width: indptr int64, coordinates and ids int32 (id 0xFFFFFFFF, the
+padding of short result rows, reads as -1).
+
+Importing this module loads the library and fails loudly if it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE = range(6)
+
+# every symbol declared in include/sinnamon.h
+EXPORTS = [
+    "sinn_create", "sinn_create_ex", "sinn_destroy", "sinn_insert", "sinn_delete",
+    "sinn_search", "sinn_search_kp", "sinn_search_host", "sinn_sync", "sinn_stats",
+    "sinn_strerror", "sinn_hash_table", "sinn_sketch_columns", "sinn_inverted_list",
+    "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
+]
+
+PHASES = ["prep", "score", "select", "rerank", "insert", "delete"]
+
+
+class SinnConfig(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m", C.c_uint32), ("h", C.c_uint32),
+                ("tile_docs", C.c_uint32), ("seed", C.c_uint64), ("capacity_hint", C.c_uint64),
+                ("table", C.c_void_p), ("max_query_nnz", C.c_uint32), ("reserved", C.c_uint32),
+                ("scratch_bytes", C.c_uint64)]
+
+
+class SinnStats(C.Structure):
+    _fields_ = [("live", C.c_uint64), ("capacity", C.c_uint64), ("next_id", C.c_uint64),
+                ("postings", C.c_uint64), ("tombstones", C.c_uint64),
+                ("bytes_lists", C.c_uint64), ("bytes_sketch", C.c_uint64),
+                ("bytes_store", C.c_uint64), ("bytes_scratch", C.c_uint64),
+                ("n", C.c_uint32), ("m", C.c_uint32), ("h", C.c_uint32),
+                ("tile_docs", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SinnTiming(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("spans", C.c_uint64 * 6), ("launches", C.c_uint64)]
+
+    def as_dict(self):
+        return {"ms": {p: self.ms[i] for i, p in enumerate(PHASES)},
+                "spans": {p: int(self.spans[i]) for i, p in enumerate(PHASES)},
+                "launches": int(self.launches)}
+
+
+class SinnError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        msg = _LIB.sinn_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsinnamon.so (raises if it is missing and not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"libsinnamon.so is not built ({path}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+    sig = {
+        "sinn_create": ([u32, u32, u32, C.POINTER(vp)], C.c_int),
+        "sinn_create_ex": ([C.POINTER(SinnConfig), C.POINTER(vp)], C.c_int),
+        "sinn_destroy": ([vp], C.c_int),
+        "sinn_insert": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
+        "sinn_delete": ([vp, vp, u32, vp], C.c_int),
+        "sinn_search": ([vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
+        "sinn_search_kp": ([vp, vp, vp, vp, u32, u32, vp, u32, vp, vp, vp], C.c_int),
+        "sinn_search_host": ([vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
+        "sinn_sync": ([vp, vp], C.c_int),
+        "sinn_stats": ([vp, C.POINTER(SinnStats)], C.c_int),
+        "sinn_strerror": ([C.c_int], C.c_char_p),
+        "sinn_hash_table": ([vp, vp], C.c_int),
+        "sinn_sketch_columns": ([vp, vp, u32, vp, vp, vp], C.c_int),
+        "sinn_inverted_list": ([vp, u32, vp, u64, C.POINTER(u64)], C.c_int),
+        "sinn_scores": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
+        "sinn_candidates": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp], C.c_int),
+        "sinn_timing_start": ([vp], C.c_int),
+        "sinn_timing_stop": ([vp, C.POINTER(SinnTiming)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != SINN_OK:
+        raise SinnError(code, where)
+
+
+def _p(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
+        return C.c_void_p(t.data_ptr()) if t.numel() else C.c_void_p(t.data_ptr() or 0)
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    raise TypeError(type(t))
+
+
+def _s(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t, dtype, device):
+    t = torch.as_tensor(t)
+    if t.dtype != dtype:
+        t = t.to(dtype)
+    return t.to(device).contiguous()
+
+
+# ------------------------------------------------------------ C-named calls
+
+def sinn_create(n: int, m: int, h: int):
+    lib = load()
+    out = C.c_void_p()
+    _check(lib.sinn_create(n, m, h, C.byref(out)), "sinn_create")
+    return out
+
+
+def sinn_create_ex(n: int, m: int, h: int, tile_docs: int = 0, seed: int = 0,
+                   capacity_hint: int = 0, table=None, max_query_nnz: int = 0,
+                   scratch_bytes: int = 0):
+    lib = load()
+    cfg = SinnConfig(n=n, m=m, h=h, tile_docs=tile_docs, seed=seed,
+                     capacity_hint=capacity_hint, max_query_nnz=max_query_nnz,
+                     scratch_bytes=scratch_bytes)
+    keep = None
+    if table is not None:
+        keep = np.ascontiguousarray(np.asarray(table, dtype=np.uint32).reshape(-1))
+        cfg.table = keep.ctypes.data
+    out = C.c_void_p()
+    _check(lib.sinn_create_ex(C.byref(cfg), C.byref(out)), "sinn_create_ex")
+    return out
+
+
+def sinn_destroy(ix):
+    _check(load().sinn_destroy(ix), "sinn_destroy")
+
+
+def sinn_insert(ix, indptr, indices, values, out_ids, stream=None):
+    n_docs = indptr.numel() - 1
+    _check(load().sinn_insert(ix, _p(indptr), _p(indices), _p(values), n_docs, _p(out_ids),
+                              _s(stream)), "sinn_insert")
+    return out_ids
+
+
+def sinn_delete(ix, ids, stream=None):
+    _check(load().sinn_delete(ix, _p(ids), ids.numel(), _s(stream)), "sinn_delete")
+
+
+def sinn_search(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
+                stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_search(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k, k_prime,
+                              _p(out_ids), _p(out_scores), _s(stream)), "sinn_search")
+
+
+def sinn_search_kp(ix, q_indptr, q_indices, q_values, k, k_prime, k_prime_max, out_ids,
+                   out_scores, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_search_kp(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
+                                 _p(k_prime), k_prime_max, _p(out_ids), _p(out_scores),
+                                 _s(stream)), "sinn_search_kp")
+
+
+def sinn_search_host(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
+                     stream=None):
+    """All buffers host (CPU) tensors or numpy arrays; waits for completion."""
+    n_q = (q_indptr.numel() if isinstance(q_indptr, torch.Tensor) else q_indptr.size) - 1
+    _check(load().sinn_search_host(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
+                                   k_prime, _p(out_ids), _p(out_scores), _s(stream)),
+           "sinn_search_host")
+
+
+def sinn_sync(ix, stream=None):
+    _check(load().sinn_sync(ix, _s(stream)), "sinn_sync")
+
+
+def sinn_stats(ix) -> dict:
+    st = SinnStats()
+    _check(load().sinn_stats(ix, C.byref(st)), "sinn_stats")
+    return st.as_dict()
+
+
+def sinn_strerror(code: int) -> str:
+    return load().sinn_strerror(code).decode()
+
+
+def sinn_hash_table(ix, n: int, h: int) -> np.ndarray:
+    out = np.zeros(n * h, np.uint32)
+    _check(load().sinn_hash_table(ix, _p(out)), "sinn_hash_table")
+    return out.reshape(n, h)
+
+
+def sinn_sketch_columns(ix, ids, u_out, l_out, stream=None):
+    _check(load().sinn_sketch_columns(ix, _p(ids), ids.numel(), _p(u_out), _p(l_out),
+                                      _s(stream)), "sinn_sketch_columns")
+
+
+def sinn_inverted_list(ix, coord: int) -> np.ndarray:
+    lib = load()
+    n = C.c_uint64()
+    _check(lib.sinn_inverted_list(ix, coord, None, 0, C.byref(n)), "sinn_inverted_list")
+    out = np.zeros(max(n.value, 1), np.uint32)
+    _check(lib.sinn_inverted_list(ix, coord, _p(out), n.value, C.byref(n)), "sinn_inverted_list")
+    return out[: n.value].copy()
+
+
+def sinn_scores(ix, q_indptr, q_indices, q_values, out, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_scores(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, _p(out),
+                              _s(stream)), "sinn_scores")
+
+
+def sinn_candidates(ix, q_indptr, q_indices, q_values, k_prime, out_ids, out_scores, out_count,
+                    stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_candidates(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k_prime,
+                                  _p(out_ids), _p(out_scores), _p(out_count), _s(stream)),
+           "sinn_candidates")
+
+
+def sinn_timing_start(ix):
+    _check(load().sinn_timing_start(ix), "sinn_timing_start")
+
+
+def sinn_timing_stop(ix) -> dict:
+    t = SinnTiming()
+    _check(load().sinn_timing_stop(ix, C.byref(t)), "sinn_timing_stop")
+    return t.as_dict()
+
+
+# ------------------------------------------------------------- convenience
+
+class Index:
+    """A SINNAMON index on one CUDA device (owns a sinn_index handle)."""
+
+    def __init__(self, n: int, m: int, h: int, device=None, **cfg):
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self._h = sinn_create_ex(n, m, h, **cfg)
+        self.n, self.m, self.h = n, m, h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            sinn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _csr(self, indptr, indices, values):
+        return (_dev(indptr, torch.int64, self.device), _dev(indices, torch.int32, self.device),
+                _dev(values, torch.float32, self.device))
+
+    def insert(self, indptr, indices, values, stream=None) -> torch.Tensor:
+        ip, ix, v = self._csr(indptr, indices, values)
+        out = torch.empty(ip.numel() - 1, dtype=torch.int32, device=self.device)
+        sinn_insert(self._h, ip, ix, v, out, stream)
+        return out
+
+    def delete(self, ids, stream=None):
+        sinn_delete(self._h, _dev(ids, torch.int32, self.device), stream)
+
+    def search(self, indptr, indices, values, k: int, k_prime, k_prime_max: int | None = None,
+               stream=None):
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        ids = torch.empty((nq, k), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=self.device)
+        if isinstance(k_prime, int):
+            sinn_search(self._h, ip, ix, v, k, k_prime, ids, sc, stream)
+        else:
+            kp = _dev(k_prime, torch.int32, self.device)
+            sinn_search_kp(self._h, ip, ix, v, k, kp, int(k_prime_max), ids, sc, stream)
+        return ids, sc
+
+    def scores(self, indptr, indices, values, stream=None) -> torch.Tensor:
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        out = torch.empty((nq, self.stats()["capacity"]), dtype=torch.float32, device=self.device)
+        sinn_scores(self._h, ip, ix, v, out, stream)
+        return out
+
+    def candidates(self, indptr, indices, values, k_prime: int, stream=None):
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        ids = torch.empty((nq, k_prime), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nq, k_prime), dtype=torch.float32, device=self.device)
+        cnt = torch.empty(nq, dtype=torch.int32, device=self.device)
+        sinn_candidates(self._h, ip, ix, v, k_prime, ids, sc, cnt, stream)
+        return ids, sc, cnt
+
+    def sketch_columns(self, ids, stream=None):
+        ids = _dev(ids, torch.int32, self.device)
+        u = torch.empty((ids.numel(), self.m), dtype=torch.float32, device=self.device)
+        l = torch.empty_like(u)
+        sinn_sketch_columns(self._h, ids, u, l, stream)
+        return u, l
+
+    def inverted_list(self, coord: int) -> np.ndarray:
+        return sinn_inverted_list(self._h, coord)
+
+    def hash_table(self) -> np.ndarray:
+        return sinn_hash_table(self._h, self.n, self.h)
+
+    def sync(self, stream=None):
+        sinn_sync(self._h, stream)
+
+    def stats(self) -> dict:
+        return sinn_stats(self._h)
