@@ -484,6 +484,9 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   if (need <= ix->cap) return SINN_OK;
   uint64_t nc = std::max<uint64_t>(ix->cap * 2, need);
   nc = (nc + ix->T - 1) / ix->T * ix->T;
+  const uint64_t max_cap = 65535ull * ix->T;  // tiles index the second grid dimension
+  if (need > max_cap) return SINN_ENOMEM;
+  nc = std::min(nc, max_cap);
   const uint64_t ot = ix->cap / ix->T, nt = nc / ix->T;
   CK(cudaDeviceSynchronize());
   // sketch planes: copy the m rows into the wider layout

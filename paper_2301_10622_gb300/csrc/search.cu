@@ -2,17 +2,26 @@
 //
 // One search launch handles a batch of B queries:
 //   k_qprep      nz(q), sorted by |q_j| descending, ties by j (Alg. 6 lines 1-2)
-//   k_score      grid (tile, query): walks the query's lists inside one tile of
-//                T ids, decodes each posting from the sketch (least upper bound
-//                from U for q_j > 0, greatest lower bound from L for q_j < 0,
-//                Alg. 6 lines 5-12) and accumulates q_j * x~ in shared memory;
-//                writes one order-preserving 32-bit score key per id and a
-//                4096-bin histogram of the keys' top 12 bits
-//   k_pick/k_hist_level/k_compact/k_refine
-//                FindLargest(scores, k') of Alg. 7 line 1 as a radix select
-//                over the keys: find the bin holding the k'-th largest, narrow
-//                it with finer histograms while it is large, collect the keys
-//                above it, then pick the rest of the bin by (score, -id)
+//   k_score_emit grid (query, tile), queries fastest so the blocks resident at
+//                any time share one tile's lists and sketch rows in L2: walks
+//                the query's lists inside one tile of T ids, decodes each
+//                posting from the sketch (least upper bound from U for
+//                q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6
+//                lines 5-12) and accumulates q_j * x~ in shared memory.  Each
+//                block adds its 4096-bin histogram of score keys (top 12
+//                bits) to the query's histogram, and every few tiles one block
+//                turns that histogram into a lower bound on the k'-th best
+//                score: at least k' scores already seen are at or above it.
+//                Only ids at or above the bound are emitted as candidates.
+//   k_pick_list/k_compact_list/k_refine
+//                FindLargest(scores, k') of Alg. 7 line 1 as a radix select:
+//                the complete histogram gives the bin holding the k'-th best;
+//                emitted keys above it are in, the rest of that bin is picked
+//                by (score, -id).
+//   fallback     a query whose emitted list overflows, or whose boundary bin
+//                is huge (massive ties), is rescored densely (one key per id)
+//                and selected with finer histogram levels (k_hist_level) or,
+//                for exact ties beyond the buffer, by id order.
 //   k_rerank     s_v = <q, S.Fetch(v)> for every candidate (Alg. 7 lines 2-3)
 //   k_final      FindLargest({s_v}, k) (Alg. 7 line 4), sorted best first
 // Ties rank the smaller id first: keys carry ~id in their low 32 bits.
@@ -29,9 +38,17 @@
 
 namespace {
 
-constexpr uint32_t kBoundCap = 65536;  // boundary-bin entries kept per query
-constexpr uint32_t kScoreThreads = 256;
-constexpr uint32_t kChunk = 8192;      // keys per block in the dense select passes
+constexpr uint32_t kBoundCap = 65536;   // boundary-bin entries kept per query
+constexpr uint32_t kEmitCap = 131072;   // emitted candidates kept per query
+constexpr uint32_t kScoreThreads = 512;
+constexpr uint32_t kChunk = 8192;       // keys per block in the dense select passes
+constexpr uint32_t kBoundEvery = 4;     // tiles between lower-bound refreshes
+constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
+constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
+// Below this many queries per launch a query's tiles mostly run at the same
+// time, so no tile has finished when the others would emit and the running
+// bound cannot prune: such launches score densely.
+constexpr uint32_t kEmitMinBatch = 32;
 
 enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
 
@@ -44,6 +61,8 @@ struct SelState {
   uint32_t kq;      // candidates wanted: min(k', live)
   uint32_t ncand;   // candidates collected so far
   uint32_t nbnd;    // boundary keys collected
+  uint32_t dense;   // 1: selected from dense keys (fallback), 0: from the emitted list
+  uint32_t pad[3];
 };
 
 struct QTerm {
@@ -62,6 +81,12 @@ struct Batch {  // device scratch views of one launch
   uint64_t *cand;   // B x kpmax
   uint64_t *bnd;    // B x kBoundCap
   uint64_t *ekeys;  // B x kpmax
+  uint64_t *elist;  // B x kEmitCap: emitted (key << 32 | ~id)
+  uint32_t *ecnt;   // B: emitted count (may exceed kEmitCap: overflow)
+  uint32_t *bound;  // B: lower-bound bin of the k'-th best key
+  uint32_t *tdone;  // B: tiles finished
+  uint32_t *flagged;  // B: queries taking the dense fallback
+  uint32_t *nflag;    // 1
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -136,6 +161,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     st.kq = s_bad ? 0u : (uint32_t)(live_count < kp ? live_count : (uint64_t)kp);
     st.ncand = 0;
     st.nbnd = 0;
+    st.dense = 0;
     bt.sel[b] = st;
   }
 }
@@ -152,114 +178,245 @@ struct ScoreArgs {
   const uint32_t *pi;
   const uint32_t *live;
   uint64_t cap;
-  uint32_t n, h, T, log2T, qmax;
+  uint32_t n, h, T, log2T, qmax, tiles;
 };
 
-__global__ void __launch_bounds__(kScoreThreads)
-    k_score(ScoreArgs a, Batch bt) {
-  extern __shared__ uint32_t sm[];
+// Lower-bound bin of the kq-th largest key from a (partial) histogram: the
+// highest bin b with sum_{i >= b} hist[i] >= kq, or 0 if the counts fall short.
+// Counts only grow, so a stale read gives a lower (still valid) bound.
+__device__ uint32_t bound_from_hist(const uint32_t *gh, uint32_t kq, uint32_t *part) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr uint32_t per = 4096 / kScoreThreads;  // thread tid owns the tid-th group from the top
+  const uint32_t top = 4096 - tid * per;
+  uint32_t c[per], s = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < per; ++i) {
+    c[i] = __ldcg(gh + top - 1 - i);
+    s += c[i];
+  }
+  uint32_t x = s;  // inclusive scan over threads (top groups first)
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) part[wid] = x;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t r = 0;
+    for (uint32_t w = 0; w < kScoreThreads / 32; ++w) {
+      uint32_t v = part[w];
+      part[w] = r;
+      r += v;
+    }
+    part[kScoreThreads / 32] = 0;  // result slot
+  }
+  __syncthreads();
+  const uint32_t before = part[wid] + x - s;
+  if (before < kq && before + s >= kq) {
+    uint32_t run = before, bin = top - 1;
+#pragma unroll
+    for (uint32_t i = 0; i < per; ++i) {
+      if (run + c[i] >= kq) {
+        bin = top - 1 - i;
+        break;
+      }
+      run += c[i];
+    }
+    part[kScoreThreads / 32] = bin;
+  }
+  __syncthreads();
+  const uint32_t r = part[kScoreThreads / 32];
+  __syncthreads();
+  return r;
+}
+
+// Decoded value x~ of one posting (Alg. 6 lines 7-11): the least upper bound
+// over the term's h rows of U (q_j > 0) or the greatest lower bound over its
+// rows of L (q_j < 0).  row[o] already points at the tile's slice of the row.
+template <int H>
+__device__ __forceinline__ float decode(const float *const *row, uint32_t h, bool pos, uint32_t d) {
+  float y = __ldg(row[0] + d);
+  const uint32_t hh = H > 0 ? (uint32_t)H : h;
+#pragma unroll
+  for (uint32_t o = 1; o < (H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H); ++o) {
+    if (o >= hh) break;
+    const float z = __ldg(row[o] + d);
+    y = pos ? fminf(y, z) : fmaxf(y, z);
+  }
+  return y;
+}
+
+// Alg. 6 for query slot b over tile t.
+//   Work split: warp w owns the ids [w*T/NW, (w+1)*T/NW) of the tile.  Lists
+//   are sorted by local id, so a binary search finds each term's segment for
+//   each warp; a warp then walks the terms in the order Alg. 6 visits them
+//   (|q_j| descending) and adds q_j * x~ into its own ids with plain
+//   read-modify-writes.  No two warps share an id, so no atomics are needed,
+//   and every score is the fp32 sum of its terms in the paper's order: scores
+//   do not depend on scheduling or on the other queries of the batch.
+//   EMIT: ids whose score key falls at or above the query's running bound are
+//   counted in the histogram and emitted; otherwise (dense) every live id gets
+//   its key written and counted.
+template <bool EMIT, int H>
+__device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t,
+                           uint32_t *sm) {
+  constexpr uint32_t NW = kScoreThreads / 32;
+  constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
   const uint32_t T = a.T;
   float *acc = (float *)sm;                      // T
   uint32_t *hist = sm + T;                       // 4096
-  uint32_t *t_lo = hist + 4096;                  // qmax
-  uint32_t *t_pref = t_lo + a.qmax;              // qmax+1
-  float *t_v = (float *)(t_pref + a.qmax + 1);   // qmax
-  uint32_t *t_bin = (uint32_t *)(t_v + a.qmax);  // qmax*h
-  __shared__ uint32_t part[kScoreThreads / 32 + 1];
+  uint32_t *t_lo = hist + 4096;                  // kTermBatch
+  float *t_v = (float *)(t_lo + kTermBatch);     // kTermBatch
+  uint32_t *t_bin = (uint32_t *)(t_v + kTermBatch);  // kTermBatch * h
+  uint32_t *t_seg = t_bin + kTermBatch * a.h;    // kTermBatch * (NW+1) segment starts
+  __shared__ uint32_t part[NW + 2];
 
-  const uint32_t t = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.nt[b];
   const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
   const uint32_t *off = a.tile_off + (uint64_t)t * (a.n + 1);
   const uint16_t *post = a.tile_post[t];
+  const uint64_t id0 = (uint64_t)t << a.log2T;
+  const uint32_t span = T / NW;
 
   for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
   for (uint32_t i = tid; i < 4096; i += kScoreThreads) hist[i] = 0;
-  for (uint32_t i = tid; i < nt; i += kScoreThreads) {
-    const uint32_t j = terms[i].j;
-    const uint32_t lo = off[j], hi = off[j + 1];
-    t_lo[i] = lo;
-    t_pref[i] = hi - lo;
-    t_v[i] = terms[i].v;
-    for (uint32_t o = 0; o < a.h; ++o) t_bin[i * a.h + o] = a.pi[(uint64_t)j * a.h + o];
-  }
-  __syncthreads();
-  // exclusive prefix of the per-term posting counts (one warp: nt is small)
-  if (tid < 32) {
-    uint32_t run = 0;
-    for (uint32_t base = 0; base < nt; base += 32) {
-      uint32_t i = base + tid;
-      uint32_t v = i < nt ? t_pref[i] : 0, x = v;
-      for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (tid >= (uint32_t)d) x += y;
+  for (uint32_t i0 = 0; i0 < nt; i0 += kTermBatch) {
+    const uint32_t nb = min(kTermBatch, nt - i0);
+    __syncthreads();  // the previous batch is consumed
+    for (uint32_t k = tid; k < nb; k += kScoreThreads) {
+      const uint32_t j = terms[i0 + k].j;
+      const uint32_t lo = off[j], hi = off[j + 1];
+      t_lo[k] = lo;
+      t_v[k] = terms[i0 + k].v;
+      for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
+      t_seg[k * (NW + 1)] = 0;
+      t_seg[k * (NW + 1) + NW] = hi - lo;
+    }
+    __syncthreads();
+    // segment starts: first position whose local id reaches w * span
+    for (uint32_t task = tid; task < nb * (NW - 1); task += kScoreThreads) {
+      const uint32_t k = task / (NW - 1), w = 1 + task % (NW - 1);
+      const uint16_t *lst = post + t_lo[k];
+      uint32_t lo = 0, hi = t_seg[k * (NW + 1) + NW];
+      const uint32_t target = w * span;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)(__ldg(lst + mid) & 0x7FFFu) < target) lo = mid + 1;
+        else hi = mid;
       }
-      if (i < nt) t_pref[i] = run + x - v;
-      run += __shfl_sync(0xFFFFFFFFu, x, 31);
+      t_seg[k * (NW + 1) + w] = lo;
     }
-    if (tid == 0) {
-      t_pref[nt] = run;
-      part[0] = run;
-    }
-  }
-  __syncthreads();
-  const uint32_t P = part[0];
-  const uint64_t id0 = (uint64_t)t << a.log2T;
-
-  // flattened walk: element f belongs to the term i with t_pref[i] <= f < t_pref[i+1]
-  for (uint32_t f0 = tid; f0 < P; f0 += 4 * kScoreThreads) {
-    uint32_t ti[4], d16[4];
+    __syncthreads();
+    for (uint32_t k = 0; k < nb; ++k) {
+      const uint32_t p_beg = t_seg[k * (NW + 1) + wid], p_end = t_seg[k * (NW + 1) + wid + 1];
+      if (p_beg >= p_end) continue;
+      const float v = t_v[k];
+      const bool pos = v > 0.0f;
+      const float *plane = pos ? a.U : a.L;
+      const float *row[HS];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t f = f0 + u * kScoreThreads;
-      ti[u] = 0xFFFFFFFFu;
-      d16[u] = SINN_TOMB;
-      if (f < P) {
-        uint32_t lo = 0, hi = nt;  // last i with t_pref[i] <= f
-        while (hi - lo > 1) {
-          uint32_t mid = (lo + hi) >> 1;
-          if (t_pref[mid] <= f) lo = mid;
-          else hi = mid;
+      for (uint32_t o = 0; o < HS; ++o)
+        if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+      const uint16_t *lst = post + t_lo[k];
+      for (uint32_t p0 = p_beg; p0 < p_end; p0 += 128) {
+        uint32_t d[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+          const uint32_t p = p0 + u * 32 + lane;
+          d[u] = p < p_end ? (uint32_t)__ldg(lst + p) : SINN_TOMB;
         }
-        ti[u] = lo;
-        d16[u] = __ldg(post + t_lo[lo] + (f - t_pref[lo]));
+        float x[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u)
+          x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H>(row, a.h, pos, d[u]);
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u)
+          if (!(d[u] & SINN_TOMB)) acc[d[u]] = fmaf(v, x[u], acc[d[u]]);
       }
     }
-    float x[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      x[u] = 0.0f;
-      if (!(d16[u] & SINN_TOMB)) {
-        const uint32_t i = ti[u];
-        const float v = t_v[i];
-        const float *plane = v > 0.0f ? a.U : a.L;
-        const uint64_t gid = id0 + d16[u];
-        float y = __ldg(plane + (uint64_t)t_bin[i * a.h] * a.cap + gid);
-        for (uint32_t o = 1; o < a.h; ++o) {
-          float z = __ldg(plane + (uint64_t)t_bin[i * a.h + o] * a.cap + gid);
-          y = v > 0.0f ? fminf(y, z) : fmaxf(y, z);
-        }
-        x[u] = y;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (!(d16[u] & SINN_TOMB)) atomicAdd(&acc[d16[u]], t_v[ti[u]] * x[u]);
   }
   __syncthreads();
 
-  // epilogue: one key per id slot of the tile (0 = not live), histogram
-  uint32_t *keys = bt.keys + (uint64_t)b * a.cap + id0;
-  for (uint32_t d = tid; d < T; d += kScoreThreads) {
-    const bool lv = sinn_is_live(a.live, id0 + d);
-    const uint32_t key = lv ? sinn_f2key(acc[d] + 0.0f) : 0u;
-    keys[d] = key;
-    if (lv) atomicAdd(&hist[key >> 20], 1u);
-  }
-  __syncthreads();
   uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
-  for (uint32_t i = tid; i < 4096; i += kScoreThreads)
-    if (hist[i]) atomicAdd(&gh[i], hist[i]);
+  if (!EMIT) {
+    // dense: a key for every id slot (0 = not live) and the full histogram
+    for (uint32_t d = tid; d < T; d += kScoreThreads) {
+      const bool lv = sinn_is_live(a.live, id0 + d);
+      const uint32_t key = sinn_f2key(acc[d] + 0.0f);
+      bt.keys[(uint64_t)b * a.cap + id0 + d] = lv ? key : 0u;
+      const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
+      const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
+      if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
+    }
+    __syncthreads();
+    for (uint32_t k = tid; k < 4096; k += kScoreThreads)
+      if (hist[k]) atomicAdd(&gh[k], hist[k]);
+    return;
+  }
+
+  // EMIT: only ids at or above the running bound matter.  The final boundary
+  // bin is never below any bound used, so the histogram stays exact from the
+  // boundary bin up and every candidate is emitted.
+  if (tid == 0) part[0] = __ldcg(&bt.bound[b]);
+  __syncthreads();
+  const uint32_t lb = part[0];
+  uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
+  const uint32_t *lw = a.live + (id0 >> 5);
+  for (uint32_t d = tid; d < T; d += kScoreThreads) {
+    const bool lv = (__ldg(lw + (d >> 5)) >> (d & 31)) & 1u;
+    const uint32_t key = sinn_f2key(acc[d] + 0.0f);
+    const bool em = lv && (key >> 20) >= lb;
+    if (em) atomicAdd(&hist[key >> 20], 1u);
+    if (__any_sync(0xFFFFFFFFu, em)) {
+      const uint32_t p = warp_append(em, &bt.ecnt[b]);
+      if (em && p < kEmitCap) el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d);
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = (lb & ~31u) + tid; k < 4096; k += kScoreThreads)
+    if (k >= lb && hist[k]) atomicAdd(&gh[k], hist[k]);
+  // refresh the query's bound every kBoundEvery tiles
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) part[NW + 1] = atomicAdd(&bt.tdone[b], 1u);
+  __syncthreads();
+  const uint32_t kq = bt.sel[b].kq;
+  if (part[NW + 1] % kBoundEvery == kBoundEvery - 1 && kq > 0) {
+    const uint32_t nbnd = bound_from_hist(gh, kq, part);
+    if (tid == 0 && nbnd > 0) atomicMax(&bt.bound[b], nbnd);
+  }
+}
+
+template <int H>
+__global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Batch bt) {
+  extern __shared__ uint32_t sm[];
+  score_tile<true, H>(a, bt, blockIdx.x, blockIdx.y, sm);
+}
+
+// Dense scoring of the flagged queries (grid-stride over (query, tile)).
+template <int H>
+__global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, Batch bt) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t nf = *bt.nflag;
+  for (uint64_t w = blockIdx.x; w < (uint64_t)nf * a.tiles; w += gridDim.x) {
+    const uint32_t b = bt.flagged[w / a.tiles], t = (uint32_t)(w % a.tiles);
+    score_tile<false, H>(a, bt, b, t, sm);
+    __syncthreads();
+  }
+}
+
+// Kernels specialised for h = 1 and h = 2 (the common sketch shapes); other h
+// use the general loop.
+struct ScoreKernels {
+  void (*emit)(ScoreArgs, Batch);
+  void (*dense)(ScoreArgs, Batch);
+};
+
+ScoreKernels score_kernels(uint32_t h) {
+  if (h == 1) return {k_score_emit<1>, k_score_dense<1>};
+  if (h == 2) return {k_score_emit<2>, k_score_dense<2>};
+  return {k_score_emit<0>, k_score_dense<0>};
 }
 
 // ------------------------------------------------------------------ select
@@ -305,82 +462,164 @@ __device__ void find_bin(const uint32_t *hist, uint32_t nb, uint32_t rem, uint32
   *out_above = res[1];
 }
 
-__global__ void k_pick(Batch bt, uint32_t level) {
+// Level-0 pick for every query of the batch from its complete histogram.
+// Emitted lists hold every key at or above the final boundary bin (the
+// running bound never exceeds it), so the list path suffices unless the list
+// overflowed or the boundary bin is too large to buffer: then the query is
+// flagged for the dense fallback.
+__global__ void k_pick_list(Batch bt) {
   const uint32_t b = blockIdx.x;
   SelState st = bt.sel[b];
-  if (level == 0) {
-    if (st.kq == 0) return;  // SEL_DONE already
-    st.rem = st.kq;
-  } else if ((level == 1 && st.mode != SEL_L1) || (level == 2 && st.mode != SEL_L2)) {
-    return;
-  }
-  const uint32_t nb = level == 2 ? 256u : 4096u;
-  const uint32_t *h = level == 0 ? bt.hist0 + (uint64_t)b * 4096
-                                 : level == 1 ? bt.hist1 + (uint64_t)b * 4096
-                                              : bt.hist2 + (uint64_t)b * 256;
+  if (st.kq == 0) return;
   uint32_t bin, above;
-  find_bin(h, nb, st.rem, &bin, &above);
+  find_bin(bt.hist0 + (uint64_t)b * 4096, 4096, st.kq, &bin, &above);
   if (threadIdx.x == 0) {
-    const uint32_t digits = level == 2 ? 8u : 12u;
-    st.prefix = (st.prefix << digits) | bin;
-    st.pbits += digits;
-    st.rem -= above;
-    st.cnt = h[bin];
-    if (st.cnt <= kBoundCap) st.mode = SEL_COMPACT;
-    else st.mode = level == 0 ? SEL_L1 : level == 1 ? SEL_L2 : SEL_TIES;
+    const uint32_t cnt = bt.hist0[(uint64_t)b * 4096 + bin];
+    if (bt.ecnt[b] > kEmitCap || cnt > kBoundCap) {
+      bt.flagged[atomicAdd(bt.nflag, 1u)] = b;
+      st.dense = 1;
+      st.mode = SEL_DONE;
+    } else {
+      st.prefix = bin;
+      st.pbits = 12;
+      st.rem = st.kq - above;
+      st.cnt = cnt;
+      st.mode = SEL_COMPACT;
+      st.dense = 0;
+    }
     bt.sel[b] = st;
   }
 }
 
-// Histogram of the next digit over keys matching the current prefix.
-__global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
-  __shared__ uint32_t hist[4096];
-  const uint32_t b = blockIdx.y;
+// Split each emitted list: keys above the boundary bin are candidates, keys in
+// it go to the boundary buffer.
+__global__ void k_compact_list(Batch bt, uint32_t kpmax) {
+  const uint32_t b = blockIdx.x;
   const SelState st = bt.sel[b];
-  if (st.mode != (level == 1 ? SEL_L1 : SEL_L2)) return;
-  const uint32_t nb = level == 1 ? 4096u : 256u;
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  const uint32_t shift_p = 32 - st.pbits;       // 20 or 8
-  const uint32_t shift_d = level == 1 ? 8u : 0u;
-  const uint32_t dmask = nb - 1;
-  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
-  const uint64_t beg = (uint64_t)blockIdx.x * kChunk;
-  const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
-  for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const uint32_t key = keys[i];
-    if (key != 0u && (key >> shift_p) == st.prefix) atomicAdd(&hist[(key >> shift_d) & dmask], 1u);
-  }
-  __syncthreads();
-  uint32_t *gh = level == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
-    if (hist[i]) atomicAdd(&gh[i], hist[i]);
-}
-
-// Collect keys above the boundary bin (certain candidates) and, in COMPACT
-// mode, the keys of the boundary bin itself.
-__global__ void k_compact(Batch bt, uint64_t cap, uint32_t kpmax) {
-  const uint32_t b = blockIdx.y;
-  const SelState st = bt.sel[b];
-  if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) return;
-  const uint32_t shift = 32 - st.pbits;
-  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+  if (st.mode != SEL_COMPACT || st.dense) return;
+  const uint32_t ne = min(bt.ecnt[b], kEmitCap);
+  const uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
   uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
   uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
   uint32_t *ncand = &bt.sel[b].ncand, *nbnd = &bt.sel[b].nbnd;
-  const uint64_t beg = (uint64_t)blockIdx.x * kChunk;
-  const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
-  for (uint64_t i0 = beg; i0 < end; i0 += blockDim.x) {
-    const uint64_t i = i0 + threadIdx.x;
-    const uint32_t key = i < end ? keys[i] : 0u;
-    const uint32_t top = shift == 32 ? 0u : (key >> shift);
-    const bool up = key != 0u && top > st.prefix;
-    const bool eq = key != 0u && top == st.prefix && st.mode == SEL_COMPACT;
-    const uint64_t k64 = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)i;
+  for (uint32_t i0 = 0; i0 < ne; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint64_t k64 = i < ne ? el[i] : 0ull;
+    const uint32_t top = (uint32_t)(k64 >> 52);
+    const bool up = i < ne && top > st.prefix;
+    const bool eq = i < ne && top == st.prefix;
     uint32_t p = warp_append(up, ncand);
     if (up) cand[p] = k64;
     p = warp_append(eq, nbnd);
     if (eq) bnd[p] = k64;
+  }
+}
+
+// Fallback: reset the flagged queries' histogram (their keys are recomputed).
+__global__ void k_fb_reset(Batch bt) {
+  const uint32_t nf = *bt.nflag;
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+    const uint32_t b = bt.flagged[f];
+    for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x) {
+      bt.hist0[(uint64_t)b * 4096 + i] = 0;
+      bt.hist1[(uint64_t)b * 4096 + i] = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) bt.hist2[(uint64_t)b * 256 + i] = 0;
+  }
+}
+
+// Dense-path pick at a level for the flagged queries.
+__global__ void k_pick(Batch bt, uint32_t level) {
+  const uint32_t nf = *bt.nflag;
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+    const uint32_t b = bt.flagged[f];
+    SelState st = bt.sel[b];
+    if (level == 0) {
+      st.rem = st.kq;
+      st.prefix = 0;
+      st.pbits = 0;
+    } else if ((level == 1 && st.mode != SEL_L1) || (level == 2 && st.mode != SEL_L2)) {
+      continue;
+    }
+    const uint32_t nb = level == 2 ? 256u : 4096u;
+    const uint32_t *h = level == 0 ? bt.hist0 + (uint64_t)b * 4096
+                                   : level == 1 ? bt.hist1 + (uint64_t)b * 4096
+                                                : bt.hist2 + (uint64_t)b * 256;
+    uint32_t bin, above;
+    find_bin(h, nb, st.rem, &bin, &above);
+    if (threadIdx.x == 0) {
+      const uint32_t digits = level == 2 ? 8u : 12u;
+      st.prefix = (st.prefix << digits) | bin;
+      st.pbits += digits;
+      st.rem -= above;
+      st.cnt = h[bin];
+      if (st.cnt <= kBoundCap) st.mode = SEL_COMPACT;
+      else st.mode = level == 0 ? SEL_L1 : level == 1 ? SEL_L2 : SEL_TIES;
+      bt.sel[b] = st;
+    }
+    __syncthreads();
+  }
+}
+
+// Histogram of the next digit over dense keys matching the current prefix.
+__global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
+  __shared__ uint32_t hist[4096];
+  const uint32_t nf = *bt.nflag;
+  const uint64_t chunks = (cap + kChunk - 1) / kChunk;
+  const uint32_t nb = level == 1 ? 4096u : 256u;
+  for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
+    const uint32_t b = bt.flagged[w / chunks];
+    const SelState st = bt.sel[b];
+    if (st.mode != (level == 1 ? SEL_L1 : SEL_L2)) continue;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t shift_p = 32 - st.pbits;  // 20 or 8
+    const uint32_t shift_d = level == 1 ? 8u : 0u;
+    const uint32_t dmask = nb - 1;
+    const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+    const uint64_t beg = (w % chunks) * kChunk;
+    const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      const uint32_t key = keys[i];
+      if (key != 0u && (key >> shift_p) == st.prefix)
+        atomicAdd(&hist[(key >> shift_d) & dmask], 1u);
+    }
+    __syncthreads();
+    uint32_t *gh = level == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+      if (hist[i]) atomicAdd(&gh[i], hist[i]);
+    __syncthreads();
+  }
+}
+
+// Dense-path collection: keys above the boundary bin are candidates; in
+// COMPACT mode the boundary bin's keys are buffered too.
+__global__ void k_compact(Batch bt, uint64_t cap, uint32_t kpmax) {
+  const uint32_t nf = *bt.nflag;
+  const uint64_t chunks = (cap + kChunk - 1) / kChunk;
+  for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
+    const uint32_t b = bt.flagged[w / chunks];
+    const SelState st = bt.sel[b];
+    if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) continue;
+    const uint32_t shift = 32 - st.pbits;
+    const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+    uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
+    uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
+    uint32_t *ncand = &bt.sel[b].ncand, *nbnd = &bt.sel[b].nbnd;
+    const uint64_t beg = (w % chunks) * kChunk;
+    const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+    for (uint64_t i0 = beg; i0 < end; i0 += blockDim.x) {
+      const uint64_t i = i0 + threadIdx.x;
+      const uint32_t key = i < end ? keys[i] : 0u;
+      const uint32_t top = shift == 32 ? 0u : (key >> shift);
+      const bool up = key != 0u && top > st.prefix;
+      const bool eq = key != 0u && top == st.prefix && st.mode == SEL_COMPACT;
+      const uint64_t k64 = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)i;
+      uint32_t p = warp_append(up, ncand);
+      if (up) cand[p] = k64;
+      p = warp_append(eq, nbnd);
+      if (eq) bnd[p] = k64;
+    }
   }
 }
 
@@ -624,7 +863,7 @@ __global__ void k_cand_out(Batch bt, uint32_t kpmax, uint32_t q0, uint32_t *out_
 
 // ------------------------------------------------------------- host driver
 struct Layout {
-  size_t terms, nt, keys, hist0, hist1, hist2, sel, cand, bnd, ekeys, total;
+  size_t terms, nt, keys, hist, sel, cand, bnd, ekeys, elist, ctr, flagged, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -632,34 +871,49 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 Layout layout_for(const sinn_index *ix, uint32_t B, uint32_t kpmax) {
   Layout L;
   size_t o = 0;
-  L.terms = o; o = align256(o + (size_t)B * ix->max_qnnz * sizeof(QTerm));
-  L.nt = o;    o = align256(o + (size_t)B * 4);
-  L.keys = o;  o = align256(o + (size_t)B * ix->cap * 4);
-  L.hist0 = o; o = align256(o + (size_t)B * 4096 * 4);
-  L.hist1 = o; o = align256(o + (size_t)B * 4096 * 4);
-  L.hist2 = o; o = align256(o + (size_t)B * 256 * 4);
-  L.sel = o;   o = align256(o + (size_t)B * sizeof(SelState));
-  L.cand = o;  o = align256(o + (size_t)B * kpmax * 8);
-  L.bnd = o;   o = align256(o + (size_t)B * kBoundCap * 8);
-  L.ekeys = o; o = align256(o + (size_t)B * kpmax * 8);
+  L.terms = o;   o = align256(o + (size_t)B * ix->max_qnnz * sizeof(QTerm));
+  L.nt = o;      o = align256(o + (size_t)B * 4);
+  L.keys = o;    o = align256(o + (size_t)B * ix->cap * 4);
+  L.hist = o;    o = align256(o + (size_t)B * (4096 + 4096 + 256) * 4);
+  L.sel = o;     o = align256(o + (size_t)B * sizeof(SelState));
+  L.cand = o;    o = align256(o + (size_t)B * kpmax * 8);
+  L.bnd = o;     o = align256(o + (size_t)B * kBoundCap * 8);
+  L.ekeys = o;   o = align256(o + (size_t)B * kpmax * 8);
+  L.elist = o;   o = align256(o + (size_t)B * kEmitCap * 8);
+  L.ctr = o;     o = align256(o + ((size_t)3 * B + 1) * 4);
+  L.flagged = o; o = align256(o + (size_t)B * 4);
   L.total = o;
   return L;
 }
 
-Batch views(void *base, const Layout &L) {
+Batch views(void *base, const Layout &L, uint32_t B) {
   char *p = (char *)base;
   Batch bt;
   bt.terms = (QTerm *)(p + L.terms);
   bt.nt = (uint32_t *)(p + L.nt);
   bt.keys = (uint32_t *)(p + L.keys);
-  bt.hist0 = (uint32_t *)(p + L.hist0);
-  bt.hist1 = (uint32_t *)(p + L.hist1);
-  bt.hist2 = (uint32_t *)(p + L.hist2);
+  bt.hist0 = (uint32_t *)(p + L.hist);
+  bt.hist1 = bt.hist0 + (size_t)B * 4096;
+  bt.hist2 = bt.hist1 + (size_t)B * 4096;
   bt.sel = (SelState *)(p + L.sel);
   bt.cand = (uint64_t *)(p + L.cand);
   bt.bnd = (uint64_t *)(p + L.bnd);
   bt.ekeys = (uint64_t *)(p + L.ekeys);
+  bt.elist = (uint64_t *)(p + L.elist);
+  bt.ecnt = (uint32_t *)(p + L.ctr);
+  bt.bound = bt.ecnt + B;
+  bt.tdone = bt.bound + B;
+  bt.nflag = bt.tdone + B;
+  bt.flagged = (uint32_t *)(p + L.flagged);
   return bt;
+}
+
+__global__ void k_flag_all(Batch bt, uint32_t nb) {
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    bt.flagged[i] = i;
+    bt.sel[i].dense = 1;
+  }
+  if (threadIdx.x == 0) *bt.nflag = nb;
 }
 
 enum class Stage { kScores, kCandidates, kFull };
@@ -678,7 +932,8 @@ struct SearchReq {
 };
 
 size_t score_smem(const sinn_index *ix) {
-  return (size_t)ix->T * 4 + 4096 * 4 + (size_t)ix->max_qnnz * (4 + 4 + 4 + 4 * ix->h) + 4;
+  return (size_t)ix->T * 4 + 4096 * 4 +
+         (size_t)kTermBatch * (4 + 4 + 4 * ix->h + 4 * (kScoreThreads / 32 + 1));
 }
 
 int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
@@ -690,9 +945,11 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
   Layout L = layout_for(ix, (uint32_t)B, kpmax);
   int st = sinn_ensure_scratch(ix, L.total);
   if (st) return st;
-  Batch bt = views(ix->scratch, L);
+  Batch bt = views(ix->scratch, L, (uint32_t)B);
   const size_t ssm = score_smem(ix);
-  CK(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  const ScoreKernels sk = score_kernels(ix->h);
+  CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   ScoreArgs sa;
   sa.tile_off = ix->d_tile_off;
   sa.tile_post = ix->d_tile_post;
@@ -706,6 +963,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
   sa.T = ix->T;
   sa.log2T = ix->log2T;
   sa.qmax = ix->max_qnnz;
+  sa.tiles = (uint32_t)(ix->cap / ix->T);
   RerankArgs ra;
   ra.fwd_off = ix->d_fwd_off;
   ra.fwd_nnz = ix->d_fwd_nnz;
@@ -715,28 +973,26 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
   ra.per_block = 64;
   uint32_t tsz = 64;
   while (tsz < 2 * ix->max_qnnz) tsz <<= 1;
-  const uint32_t tiles = (uint32_t)(ix->cap / ix->T);
-  const uint32_t chunks = (uint32_t)((ix->cap + kChunk - 1) / kChunk);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  const uint32_t fb_score_blocks = (uint32_t)std::max(1, sms) * 4;
   for (uint32_t q0 = 0; q0 < r.n_q; q0 += (uint32_t)B) {
     const uint32_t nb = (uint32_t)std::min<uint64_t>(B, r.n_q - q0);
     {
-    SinnPhase ph(ix, s, 0);
-    ix->launches++;
-    k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0, ix->n,
-                                                       ix->max_qnnz, r.kp, r.kp_arr, r.kp_min,
-                                                       r.kp_max, ix->live_count, bt, ix->d_err);
-    CK(cudaGetLastError());
-    CK(cudaMemsetAsync(bt.hist0, 0, (size_t)nb * 4096 * 4, s));
-    CK(cudaMemsetAsync(bt.hist1, 0, (size_t)nb * 4096 * 4, s));
-    CK(cudaMemsetAsync(bt.hist2, 0, (size_t)nb * 256 * 4, s));
-    }
-    {
-      SinnPhase ph(ix, s, 1);
+      SinnPhase ph(ix, s, 0);
       ix->launches++;
-      k_score<<<dim3(tiles, nb), kScoreThreads, ssm, s>>>(sa, bt);
+      k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0,
+                                                         ix->n, ix->max_qnnz, r.kp, r.kp_arr,
+                                                         r.kp_min, r.kp_max, ix->live_count, bt,
+                                                         ix->d_err);
       CK(cudaGetLastError());
+      CK(cudaMemsetAsync(bt.hist0, 0, (size_t)B * (4096 + 4096 + 256) * 4, s));
+      CK(cudaMemsetAsync(bt.ecnt, 0, ((size_t)3 * B + 1) * 4, s));
     }
-    if (r.stage == Stage::kScores) {
+    if (r.stage == Stage::kScores) {  // dense keys for every query
+      ix->launches += 3;
+      k_flag_all<<<1, 1024, 0, s>>>(bt, nb);
+      sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
       for (uint32_t b = 0; b < nb; ++b) {
         uint64_t cnt = ix->cap;
         k_keys_to_scores<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
@@ -745,19 +1001,42 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
       CK(cudaGetLastError());
       continue;
     }
+    const bool dense_all = nb < kEmitMinBatch;
     {
-    SinnPhase ph(ix, s, 2);
-    ix->launches += 7;
-    k_pick<<<nb, 128, 0, s>>>(bt, 0);
-    k_hist_level<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, 1);
-    k_pick<<<nb, 128, 0, s>>>(bt, 1);
-    k_hist_level<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, 2);
-    k_pick<<<nb, 128, 0, s>>>(bt, 2);
-    k_compact<<<dim3(chunks, nb), 256, 0, s>>>(bt, ix->cap, kpmax);
-    k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, kpmax);
-    CK(cudaGetLastError());
+      SinnPhase ph(ix, s, 1);
+      if (dense_all) {
+        ix->launches += 2;
+        k_flag_all<<<1, 1024, 0, s>>>(bt, nb);
+        sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
+      } else {
+        ix->launches++;
+        sk.emit<<<dim3(nb, sa.tiles), kScoreThreads, ssm, s>>>(sa, bt);
+      }
+      CK(cudaGetLastError());
+    }
+    {
+      SinnPhase ph(ix, s, 2);
+      if (!dense_all) {
+        // list path, then the dense fallback for flagged queries (no work
+        // when none is flagged)
+        ix->launches += 4;
+        k_pick_list<<<nb, 128, 0, s>>>(bt);
+        k_compact_list<<<nb, 512, 0, s>>>(bt, kpmax);
+        k_fb_reset<<<kFbBlocks, 256, 0, s>>>(bt);
+        sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
+      }
+      ix->launches += 7;
+      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 0);
+      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, 1);
+      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 1);
+      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, 2);
+      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 2);
+      k_compact<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, kpmax);
+      k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, kpmax);
+      CK(cudaGetLastError());
     }
     if (r.stage == Stage::kCandidates) {
+      ix->launches++;
       k_cand_out<<<nb, 256, 0, s>>>(bt, kpmax, q0, r.out_ids, r.out_scores, r.out_count);
       CK(cudaGetLastError());
       continue;

@@ -150,8 +150,10 @@ def test_injective_mapping_scores_are_exact():
 
 @pytest.mark.parametrize("name,n_docs,tile,nq,k,kp", [
     ("tiny", 10_000, 1024, 100, 10, 100),      # the tiny workload at full size
-    ("mixed", 6000, 2048, 25, 10, 500),
+    ("mixed", 6000, 2048, 25, 10, 500),        # small batch: dense scoring
+    ("mixed", 9000, 1024, 48, 10, 500),        # batch: emitted candidates
     ("text", 6000, 4096, 25, 10, 300),
+    ("text", 12000, 1024, 64, 10, 1000),
     ("tiny", 3000, 1024, 10, 1, 1),            # k = k' = 1
     ("tiny", 2500, 1024, 10, 32, 2500),        # k' = |X|: exact top-k
 ])
@@ -209,7 +211,7 @@ def test_streaming_insert_delete_search():
     a reused id never scores through its previous owner's postings."""
     w = synth.scaled(synth.WORKLOADS["mixed"], 0, n=2000)
     pool = synth.make_docs(w, n_docs=9000, seed=5)
-    qs = synth.make_queries(w, n_q=12, seed=6)
+    qs = synth.make_queries(w, n_q=40, seed=6)
     gpu, ora = _pair(w, None, tile_docs=1024)
     rng = np.random.default_rng(0)
     pos = 0
@@ -358,8 +360,9 @@ def test_invalid_inputs_are_rejected_without_change():
         sinnamon.sinn_create(10, 4, 5)
 
 
+@pytest.mark.parametrize("nq", [1, 40])
 @pytest.mark.parametrize("case", ["l1", "l2", "ties"])
-def test_select_levels(case):
+def test_select_levels(case, nq):
     """The k'-th score falls in a bin too large to collect at once, so the
     select narrows it with finer digits (l1, l2) or, for more exact ties than
     the boundary buffer holds, takes the smallest ids in order (ties)."""
@@ -376,13 +379,18 @@ def test_select_levels(case):
     docs = synth.CSR(ip, np.zeros(nd, np.uint32), vals)
     w = synth.scaled(synth.WORKLOADS["tiny"], nd, n=16, m=16)
     gpu, ora = _pair(w, docs, tile_docs=8192)
-    q = synth.CSR(np.array([0, 1], np.uint64), np.array([0], np.uint32),
-                  np.array([1.0], np.float32))
+    # the same query nq times (a batch of 40 takes the emitted-candidate path
+    # and falls back to dense scoring because the boundary bin is huge)
+    q = synth.CSR(np.arange(nq + 1, dtype=np.uint64), np.zeros(nq, np.uint32),
+                  np.ones(nq, np.float32))
     for kp in (1000, 70_000):
         ci, cs, cnt = gpu.candidates(_ip(q), _ix(q), q.values, kp)
         gpu.sync()
-        ref = ora.search(q.indptr, q.indices, q.values, k=10, k_prime=kp, candidates=True)
-        assert int(cnt[0]) == kp
-        assert set(ci.cpu().numpy().astype(np.uint32)[0]) == set(ref["cand_ids"][0])
+        ref = ora.search(q.indptr[:2], q.indices[:1], q.values[:1], k=10, k_prime=kp,
+                         candidates=True)
         gi, gs = gpu.search(_ip(q), _ix(q), q.values, k=10, k_prime=kp)
-        assert list(gi.cpu().numpy().astype(np.uint32)[0]) == list(ref["ids"][0])
+        ci, gi = ci.cpu().numpy().astype(np.uint32), gi.cpu().numpy().astype(np.uint32)
+        for r in range(nq):
+            assert int(cnt[r]) == kp
+            assert set(ci[r]) == set(ref["cand_ids"][0])
+            assert list(gi[r]) == list(ref["ids"][0])
