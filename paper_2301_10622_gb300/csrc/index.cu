@@ -7,11 +7,21 @@
 //                               as the paper stores the sketch matrix)
 //   d_live      cap bits        live ids
 //   d_fwd*      vector store    (coordinate, value) pairs per id
-//   d_tile_off  tiles x (n+1)   per tile t and coordinate j, the postings of
-//                               I[j] with ids in [t*T, (t+1)*T) are
-//                               post_t[off[t][j] .. off[t][j+1]), as 16-bit
-//                               local ids sorted ascending; bit 15 marks a
-//                               deleted (tombstoned) posting.
+//   d_tile_dir  tiles x n uint2 per tile t and coordinate j, the container of
+//                               the postings of I[j] with ids in
+//                               [t*T, (t+1)*T): {start, count} in 16-bit words
+//                               of the tile's storage post_t.  count >= T/2:
+//                               a bitmap of T bits (bit d = local id d; a
+//                               deleted posting's bit is cleared); otherwise a
+//                               sorted array of count 16-bit local ids (bit 15
+//                               marks a deleted posting).  Arrays fill the
+//                               storage from the front, bitmaps from the back
+//                               (T/16-word aligned).  This is the array/bitmap
+//                               split of the Roaring containers the paper
+//                               uses for its lists, per tile of T ids; the
+//                               threshold is set where scoring a bitmap by
+//                               sweeping all T ids costs no more per posting
+//                               than walking an array.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -173,8 +183,9 @@ __device__ uint32_t block_excl_scan(uint32_t *a, uint32_t cnt, uint32_t *smem_pa
 
 // Rebuild the postings of one tile per block from the vector store: for every
 // live id of the tile and each of its non-zero coordinates j, the local id is
-// placed in list (tile, j); lists come out sorted by local id because entries
-// are placed in id order (a stable counting sort by coordinate).  Tombstones
+// placed in container (tile, j).  Array containers come out sorted by local
+// id because entries are placed in id order (a stable counting sort by
+// coordinate); bitmap containers take their bits in any order.  Tombstones
 // disappear: only live vectors contribute.
 //   E     scratch of the block: one (coordinate<<16 | local id) entry per stored
 //         entry of the tile's live vectors, in id order (skipped entries are
@@ -182,7 +193,8 @@ __device__ uint32_t block_excl_scan(uint32_t *a, uint32_t cnt, uint32_t *smem_pa
 //   dpref scratch: T+1 per-id entry offsets into E
 struct RebuildArgs {
   const uint32_t *tiles;      // tile index per block
-  uint16_t *const *new_post;  // posting array per block
+  uint16_t *const *new_post;  // storage per block
+  const uint64_t *post_cap;   // storage size per block (16-bit words, multiple of T/16)
   const uint64_t *e_off;      // offset of each block's E region
   uint64_t *E;
   uint32_t *dpref;            // (T+1) per block
@@ -192,21 +204,31 @@ struct RebuildArgs {
 __global__ void __launch_bounds__(512)
     k_tile_rebuild(RebuildArgs a, const uint32_t *__restrict__ live,
                    const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
-                   const uint2 *__restrict__ fwd, uint32_t *__restrict__ tile_off,
+                   const uint2 *__restrict__ fwd, uint2 *__restrict__ tile_dir,
                    uint16_t **tile_post, uint32_t n, uint32_t T, uint32_t log2T, uint32_t W) {
-  extern __shared__ uint32_t cursor[];  // W coordinate cursors
+  extern __shared__ uint32_t sm[];
+  uint32_t *cursor = sm;                 // W: counts, then array starts / cursors
+  uint32_t *isbm = sm + W;               // W/32: bitmap flags
   __shared__ uint32_t part[33];
+  __shared__ uint32_t s_nbm, s_posts;
+  const uint32_t W16 = T >> 4;           // 16-bit words of one bitmap (T bits)
+  const uint32_t BMIN = T >> 1;          // postings from which a container is a bitmap
   const uint32_t t = a.tiles[blockIdx.x];
   uint16_t *post = a.new_post[blockIdx.x];
+  const uint64_t cap16 = a.post_cap[blockIdx.x];
   uint64_t *E = a.E + a.e_off[blockIdx.x];
   uint32_t *dpref = a.dpref + (uint64_t)blockIdx.x * (T + 1);
-  uint32_t *off = tile_off + (uint64_t)t * (n + 1);
+  uint2 *dir = tile_dir + (uint64_t)t * n;
   const uint64_t id0 = (uint64_t)t << log2T;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 
   // phase 1: entries per id, then offsets into E
   for (uint32_t d = tid; d < T; d += blockDim.x)
     dpref[d] = sinn_is_live(live, id0 + d) ? fwd_nnz[id0 + d] : 0u;
+  if (tid == 0) {
+    s_nbm = 0;
+    s_posts = 0;
+  }
   __syncthreads();
   const uint32_t total = block_excl_scan(dpref, T, part);
   if (tid == 0) dpref[T] = total;
@@ -225,44 +247,89 @@ __global__ void __launch_bounds__(512)
   }
   __syncthreads();
 
-  // phases 3-5 per window of W coordinates
+  // phases 3-7 per window of W coordinates
   uint32_t base = 0;
   for (uint32_t w0 = 0; w0 < n; w0 += W) {
     const uint32_t wn = min(W, n - w0);
     for (uint32_t i = tid; i < wn; i += blockDim.x) cursor[i] = 0;
+    for (uint32_t i = tid; i < (wn + 31) / 32; i += blockDim.x) isbm[i] = 0;
     __syncthreads();
+    // 3: postings per coordinate
     for (uint32_t e = tid; e < total; e += blockDim.x) {
-      uint64_t key = E[e];
-      uint32_t c = (uint32_t)(key >> 16);
+      const uint64_t key = E[e];
+      const uint32_t c = (uint32_t)(key >> 16);
       if (key != ~0ull && c >= w0 && c < w0 + wn) atomicAdd(&cursor[c - w0], 1u);
     }
     __syncthreads();
+    // 4: containers with at least T/2 postings become bitmaps, claimed from
+    //    the back of the storage; they take no array space
+    const uint32_t nbm0 = s_nbm;
+    uint32_t wposts = 0;
+    for (uint32_t i = tid; i < wn; i += blockDim.x) {
+      const uint32_t cnt = cursor[i];
+      wposts += cnt;
+      if (cnt >= BMIN) {
+        const uint32_t k = atomicAdd(&s_nbm, 1u);
+        dir[w0 + i] = make_uint2((uint32_t)(cap16 - (uint64_t)(k + 1) * W16), cnt);
+        atomicOr(&isbm[i >> 5], 1u << (i & 31));
+        cursor[i] = 0;
+      } else if (cnt == 0) {
+        dir[w0 + i] = make_uint2(0u, 0u);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) wposts += __shfl_xor_sync(0xFFFFFFFFu, wposts, o);
+    if (lane == 0 && wposts) atomicAdd(&s_posts, wposts);
+    __syncthreads();
+    {  // zero the bitmaps claimed in this window
+      const uint32_t nbm1 = s_nbm;
+      uint32_t *z = (uint32_t *)(post + (cap16 - (uint64_t)nbm1 * W16));
+      const uint64_t words = (uint64_t)(nbm1 - nbm0) * (W16 / 2);
+      for (uint64_t i = tid; i < words; i += blockDim.x) z[i] = 0u;
+    }
+    // 5: array containers: starts by an exclusive scan of their sizes
     const uint32_t wtot = block_excl_scan(cursor, wn, part);
     for (uint32_t i = tid; i < wn; i += blockDim.x) {
-      cursor[i] += base;
-      off[w0 + i] = cursor[i];
+      if ((isbm[i >> 5] >> (i & 31)) & 1u) continue;
+      const uint32_t st = cursor[i], nx = i + 1 < wn ? cursor[i + 1] : wtot;
+      if (nx > st) dir[w0 + i] = make_uint2(base + st, nx - st);
     }
     __syncthreads();
-    if (wid == 0) {  // stable scatter: entries in id order, lanes in order
+    for (uint32_t i = tid; i < wn; i += blockDim.x) cursor[i] += base;
+    __syncthreads();
+    // 6: bitmap bits, in any order (all threads)
+    for (uint32_t e = tid; e < total; e += blockDim.x) {
+      const uint64_t key = E[e];
+      const uint32_t c = (uint32_t)(key >> 16);
+      if (key == ~0ull || c < w0 || c >= w0 + wn) continue;
+      const uint32_t i = c - w0;
+      if (!((isbm[i >> 5] >> (i & 31)) & 1u)) continue;
+      const uint32_t d = (uint32_t)(key & 0xFFFFu);
+      uint32_t *bm = (uint32_t *)(post + dir[c].x);
+      atomicOr(bm + (d >> 5), 1u << (d & 31));
+    }
+    // 7: array containers: stable scatter by one warp, entries in id order
+    if (wid == 0) {
       const uint32_t lt = (1u << lane) - 1u;
       for (uint32_t e0 = 0; e0 < total; e0 += 128) {
         uint64_t kk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          uint32_t e = e0 + u * 32 + lane;
+          const uint32_t e = e0 + u * 32 + lane;
           kk[u] = e < total ? E[e] : ~0ull;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          uint32_t c = (uint32_t)(kk[u] >> 16);
-          bool ok = kk[u] != ~0ull && c >= w0 && c < w0 + wn;
-          uint32_t okm = __ballot_sync(0xFFFFFFFFu, ok);
+          const uint32_t c = (uint32_t)(kk[u] >> 16);
+          const uint32_t i = c - w0;
+          const bool ok = kk[u] != ~0ull && c >= w0 && c < w0 + wn &&
+                          !((isbm[i >> 5] >> (i & 31)) & 1u);
+          const uint32_t okm = __ballot_sync(0xFFFFFFFFu, ok);
           if (ok) {
-            uint32_t grp = __match_any_sync(okm, c);
-            uint32_t rank = __popc(grp & lt);
-            uint32_t pos = cursor[c - w0];
+            const uint32_t grp = __match_any_sync(okm, c);
+            const uint32_t rank = __popc(grp & lt);
+            const uint32_t pos = cursor[i];
             post[pos + rank] = (uint16_t)(kk[u] & 0xFFFFu);
-            if ((grp >> lane) == 1u) cursor[c - w0] = pos + __popc(grp);
+            if ((grp >> lane) == 1u) cursor[i] = pos + __popc(grp);
           }
           __syncwarp();
         }
@@ -272,19 +339,19 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
   }
   if (tid == 0) {
-    off[n] = base;
     tile_post[t] = post;
-    a.out_len[blockIdx.x] = base;
+    a.out_len[blockIdx.x] = s_posts;
   }
 }
 
 // Sec. 4.3 deletion: for each deleted id, remove it from every list it is in
-// by setting the tombstone bit of its posting (binary search within the
-// sorted tile list), then clear its live bit.  One warp per id.
+// -- clear its bit in a bitmap container, or set the tombstone bit of its
+// posting in an array container (binary search: arrays are sorted) -- then
+// clear its live bit.  One warp per id.
 __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
                             const uint64_t *__restrict__ fwd_off,
                             const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd,
-                            const uint32_t *__restrict__ tile_off, uint16_t *const *tile_post,
+                            const uint2 *__restrict__ tile_dir, uint16_t *const *tile_post,
                             uint32_t *live, uint32_t n, uint32_t log2T, uint32_t *tomb_count,
                             uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
@@ -292,27 +359,36 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
   if (w >= cnt) return;
   const uint32_t id = ids[w];
   const uint32_t t = id >> log2T;
-  const uint16_t d = (uint16_t)(id & ((1u << log2T) - 1u));
-  const uint32_t *off = tile_off + (uint64_t)t * (n + 1);
+  const uint32_t BMIN = (1u << log2T) >> 1;
+  const uint32_t d = id & ((1u << log2T) - 1u);
+  const uint2 *dir = tile_dir + (uint64_t)t * n;
   uint16_t *post = tile_post[t];
   const uint64_t fo = fwd_off[id];
   const uint32_t nz = fwd_nnz[id];
   uint32_t marked = 0;
   for (uint32_t e = lane; e < nz; e += 32) {
-    uint2 pr = fwd[fo + e];
+    const uint2 pr = fwd[fo + e];
     if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
-    uint32_t lo = off[pr.x], hi = off[pr.x + 1];
-    while (lo < hi) {  // first position with local id >= d
-      uint32_t mid = (lo + hi) >> 1;
-      if ((post[mid] & 0x7FFFu) < d) lo = mid + 1;
-      else hi = mid;
-    }
-    if (lo < off[pr.x + 1] && (post[lo] & 0x7FFFu) == d && !(post[lo] & SINN_TOMB)) {
-      post[lo] = (uint16_t)(post[lo] | SINN_TOMB);
-      marked++;
+    const uint2 de = dir[pr.x];
+    bool ok = false;
+    if (de.y >= BMIN) {
+      uint32_t *bm = (uint32_t *)(post + de.x);
+      const uint32_t bit = 1u << (d & 31);
+      ok = (atomicAnd(bm + (d >> 5), ~bit) & bit) != 0u;
     } else {
-      atomicOr(err, SINN_DERR_INTERNAL);
+      uint32_t lo = de.x, hi = de.x + de.y;
+      while (lo < hi) {  // first position with local id >= d
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)(post[mid] & 0x7FFFu) < d) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < de.x + de.y && (uint32_t)(post[lo] & 0x7FFFu) == d && !(post[lo] & SINN_TOMB)) {
+        post[lo] = (uint16_t)(post[lo] | SINN_TOMB);
+        ok = true;
+      }
     }
+    if (ok) marked++;
+    else atomicOr(err, SINN_DERR_INTERNAL);
   }
   for (int s = 16; s > 0; s >>= 1) marked += __shfl_xor_sync(0xFFFFFFFFu, marked, s);
   if (lane == 0) {
@@ -417,7 +493,7 @@ static void release(sinn_index *ix) {
   cudaFree(ix->d_fwd_off);
   cudaFree(ix->d_fwd_nnz);
   cudaFree(ix->d_fwd);
-  cudaFree(ix->d_tile_off);
+  cudaFree(ix->d_tile_dir);
   cudaFree(ix->d_tile_post);
   cudaFree(ix->d_err);
   cudaFree(ix->scratch);
@@ -504,7 +580,7 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   if ((st = realloc_copy(&ix->d_live, ix->cap / 32, nc / 32, true))) return st;
   if ((st = realloc_copy(&ix->d_fwd_off, ix->cap, nc, true))) return st;
   if ((st = realloc_copy(&ix->d_fwd_nnz, ix->cap, nc, true))) return st;
-  if ((st = realloc_copy(&ix->d_tile_off, ot * (ix->n + 1), nt * (ix->n + 1), true))) return st;
+  if ((st = realloc_copy(&ix->d_tile_dir, ot * ix->n, nt * ix->n, true))) return st;
   if ((st = realloc_copy(&ix->d_tile_post, ot, nt, true))) return st;
   ix->cap = nc;
   ix->live.resize(nc, 0);
@@ -513,6 +589,7 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   ix->tile_post_len.resize(nt, 0);
   ix->tile_nnz.resize(nt, 0);
   ix->tile_tombs.resize(nt, 0);
+  ix->tile_post_cap.resize(nt, 0);
   return SINN_OK;
 }
 
@@ -627,66 +704,85 @@ extern "C" int sinn_sync(sinn_index *ix, void *stream) {
 static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s) {
   if (tiles.empty()) return SINN_OK;
   const uint32_t nb = (uint32_t)tiles.size();
-  std::vector<uint64_t> eoff(nb);
+  const uint64_t W16 = ix->T / 16;
+  std::vector<uint64_t> eoff(nb), pcap(nb);
   uint64_t etot = 0;
   for (uint32_t i = 0; i < nb; ++i) {
     eoff[i] = etot;
     etot += ix->tile_nnz[tiles[i]];
+    // containers never need more words than postings; bitmaps sit on T/16-word
+    // boundaries counted from the end
+    pcap[i] = std::max<uint64_t>((ix->tile_nnz[tiles[i]] + W16 - 1) / W16 * W16, W16);
   }
-  // scratch: E, dpref, tiles, ptrs, eoff, out_len
+  // scratch: E, dpref, tiles, ptrs, caps, eoff, out_len
   size_t o_E = 0;
   size_t o_dp = o_E + etot * 8;
   size_t o_tl = (o_dp + (uint64_t)nb * (ix->T + 1) * 4 + 15) / 16 * 16;
   size_t o_pt = (o_tl + nb * 4 + 15) / 16 * 16;
-  size_t o_eo = o_pt + nb * 8;
+  size_t o_pc = o_pt + nb * 8;
+  size_t o_eo = o_pc + nb * 8;
   size_t o_ln = o_eo + nb * 8;
   size_t bytes = o_ln + nb * 4;
   int st = ensure_iscratch(ix, bytes);
   if (st) return st;
   std::vector<uint16_t *> newp(nb);
   for (uint32_t i = 0; i < nb; ++i) {
-    uint32_t t = tiles[i];
-    uint64_t need = std::max<uint64_t>(ix->tile_nnz[t], 1);
-    CK(cudaMallocAsync((void **)&newp[i], need * sizeof(uint16_t), s));
+    const uint32_t t = tiles[i];
+    if (ix->tile_post[t] && ix->tile_post_cap[t] >= pcap[i] &&
+        ix->tile_post_cap[t] <= 2 * pcap[i]) {
+      newp[i] = ix->tile_post[t];  // rebuilt in place: the rebuild reads only the store
+      pcap[i] = ix->tile_post_cap[t];
+    } else {
+      const uint64_t alloc = pcap[i] + pcap[i] / 4 / W16 * W16;  // room to grow
+      CK(cudaMallocAsync((void **)&newp[i], alloc * sizeof(uint16_t), s));
+      pcap[i] = alloc;
+    }
   }
-  size_t hb = nb * 4 + nb * 8 + nb * 8 + nb * 4;
+  size_t hb = nb * (4 + 8 + 8 + 8 + 4);
   CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
   if ((st = sinn_ensure_pinned(ix, hb))) return st;
   char *hp = (char *)ix->pinned;
   memcpy(hp, tiles.data(), nb * 4);
   memcpy(hp + nb * 4, newp.data(), nb * 8);
-  memcpy(hp + nb * 12, eoff.data(), nb * 8);
+  memcpy(hp + nb * 12, pcap.data(), nb * 8);
+  memcpy(hp + nb * 20, eoff.data(), nb * 8);
   char *sp = (char *)ix->iscratch;
   CK(cudaMemcpyAsync(sp + o_tl, hp, nb * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sp + o_pt, hp + nb * 4, nb * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_eo, hp + nb * 12, nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_pc, hp + nb * 12, nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_eo, hp + nb * 20, nb * 8, cudaMemcpyHostToDevice, s));
   RebuildArgs a;
   a.tiles = (const uint32_t *)(sp + o_tl);
   a.new_post = (uint16_t *const *)(sp + o_pt);
+  a.post_cap = (const uint64_t *)(sp + o_pc);
   a.e_off = (const uint64_t *)(sp + o_eo);
   a.E = (uint64_t *)(sp + o_E);
   a.dpref = (uint32_t *)(sp + o_dp);
   a.out_len = (uint32_t *)(sp + o_ln);
   int dev_smem = 0;
   cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device);
-  uint32_t W = std::min<uint32_t>(ix->n, (uint32_t)((dev_smem - 4096) / 4));
-  size_t smem = (size_t)W * 4;
+  // W coordinate cursors + W/32 flag words in dynamic shared memory
+  uint32_t W = (uint32_t)((uint64_t)(dev_smem - 4096) * 32 / 132);
+  W = std::min<uint32_t>(ix->n, W & ~31u);
+  size_t smem = (size_t)W * 4 + (size_t)(W + 31) / 32 * 4;
   CK(cudaFuncSetAttribute(k_tile_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ix->launches++;
   k_tile_rebuild<<<nb, 512, smem, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz, ix->d_fwd,
-                                       ix->d_tile_off, ix->d_tile_post, ix->n, ix->T, ix->log2T,
+                                       ix->d_tile_dir, ix->d_tile_post, ix->n, ix->T, ix->log2T,
                                        W);
   CK(cudaGetLastError());
   for (uint32_t i = 0; i < nb; ++i) {
-    uint32_t t = tiles[i];
-    if (ix->tile_post[t]) CK(cudaFreeAsync(ix->tile_post[t], s));
+    const uint32_t t = tiles[i];
+    if (ix->tile_post[t] && ix->tile_post[t] != newp[i]) CK(cudaFreeAsync(ix->tile_post[t], s));
     ix->tile_post[t] = newp[i];
+    ix->tile_post_cap[t] = pcap[i];
   }
   std::vector<uint32_t> lens(nb);
   CK(cudaMemcpyAsync(hp, sp + o_ln, nb * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   memcpy(lens.data(), hp, nb * 4);
   for (uint32_t i = 0; i < nb; ++i) {
-    uint32_t t = tiles[i];
+    const uint32_t t = tiles[i];
     ix->tile_post_len[t] = lens[i];
     ix->tombstones -= ix->tile_tombs[t];  // a rebuild compacts tombstones away
     ix->tile_tombs[t] = 0;
@@ -764,7 +860,7 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   CK(cudaMemcpyAsync(d_ids, hids, (size_t)n_docs * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_off, hoff, (size_t)n_docs * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(out_ids, d_ids, (size_t)n_docs * 4, cudaMemcpyDeviceToDevice, s));
-  ix->launches += 4;  // store, sketch, live bits, tile rebuild
+  ix->launches += 3;  // store, sketch, live bits (the tile rebuild counts itself)
   k_fwd_write<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, d_ids, d_off,
                                               ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz);
   CK(cudaGetLastError());
@@ -821,7 +917,7 @@ extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, 
   SinnPhase phase(ix, s, 5);
   ix->launches++;
   k_tombstone<<<(n_ids + 7) / 8, 256, 0, s>>>(d_ids, n_ids, ix->d_fwd_off, ix->d_fwd_nnz,
-                                              ix->d_fwd, ix->d_tile_off, ix->d_tile_post,
+                                              ix->d_fwd, ix->d_tile_dir, ix->d_tile_post,
                                               ix->d_live, ix->n, ix->log2T, d_cnt, ix->d_err);
   CK(cudaGetLastError());
   uint32_t *hc = (uint32_t *)ix->pinned;
@@ -852,11 +948,11 @@ extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   uint64_t post = 0, pbytes = 0;
   for (size_t t = 0; t < ix->tile_post.size(); ++t) {
     post += ix->tile_post_len[t];
-    pbytes += ix->tile_post[t] ? std::max<uint64_t>(ix->tile_nnz[t], 1) * 2 : 0;
+    pbytes += ix->tile_post_cap[t] * 2;
   }
   out->postings = post;
   out->tombstones = ix->tombstones;
-  out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)(ix->n + 1) * 4;
+  out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)ix->n * 8;
   out->bytes_sketch = 2ull * ix->m * ix->cap * 4;
   out->bytes_store = ix->fwd_cap * 8 + ix->cap * 12;
   out->bytes_scratch = ix->scratch_size + ix->iscratch_size;
@@ -893,21 +989,28 @@ extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out,
   cudaSetDevice(ix->device);
   CK(cudaDeviceSynchronize());
   const uint64_t nt = ix->cap / ix->T;
-  std::vector<uint32_t> lo(nt), hi(nt);
-  CK(cudaMemcpy2D(lo.data(), 4, ix->d_tile_off + coord, (size_t)(ix->n + 1) * 4, 4, nt,
-                  cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy2D(hi.data(), 4, ix->d_tile_off + coord + 1, (size_t)(ix->n + 1) * 4, 4, nt,
-                  cudaMemcpyDeviceToHost));
+  const uint32_t W16 = ix->T / 16;
+  std::vector<uint2> de(nt);
+  CK(cudaMemcpy2D(de.data(), sizeof(uint2), ix->d_tile_dir + coord, (size_t)ix->n * sizeof(uint2),
+                  sizeof(uint2), nt, cudaMemcpyDeviceToHost));
   uint64_t cnt = 0;
   std::vector<uint16_t> buf;
   for (uint64_t t = 0; t < nt; ++t) {
-    if (hi[t] <= lo[t] || !ix->tile_post[t]) continue;
-    buf.resize(hi[t] - lo[t]);
-    CK(cudaMemcpy(buf.data(), ix->tile_post[t] + lo[t], buf.size() * 2, cudaMemcpyDeviceToHost));
-    for (uint16_t d : buf) {
-      if (d & SINN_TOMB) continue;
+    if (de[t].y == 0 || !ix->tile_post[t]) continue;
+    const bool bitmap = de[t].y >= ix->T / 2;
+    buf.resize(bitmap ? W16 : de[t].y);
+    CK(cudaMemcpy(buf.data(), ix->tile_post[t] + de[t].x, buf.size() * 2, cudaMemcpyDeviceToHost));
+    auto emit = [&](uint32_t d) {
       if (cnt < cap) out[cnt] = (uint32_t)((t << ix->log2T) + d);
       cnt++;
+    };
+    if (bitmap) {
+      for (uint32_t w = 0; w < W16; ++w)
+        for (uint32_t b = 0; b < 16; ++b)
+          if ((buf[w] >> b) & 1u) emit(w * 16 + b);
+    } else {
+      for (uint16_t d : buf)
+        if (!(d & SINN_TOMB)) emit(d);
     }
   }
   *len = cnt;

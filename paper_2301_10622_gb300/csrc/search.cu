@@ -171,7 +171,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
 // that have postings in this tile, then walks the flattened (term, posting)
 // space so every thread stays busy whatever the list lengths.
 struct ScoreArgs {
-  const uint32_t *tile_off;
+  const uint2 *tile_dir;
   uint16_t *const *tile_post;
   const float *U;
   const float *L;
@@ -246,14 +246,17 @@ __device__ __forceinline__ float decode(const float *const *row, uint32_t h, boo
   return y;
 }
 
-// Alg. 6 for query slot b over tile t.
-//   Work split: warp w owns the ids [w*T/NW, (w+1)*T/NW) of the tile.  Lists
-//   are sorted by local id, so a binary search finds each term's segment for
-//   each warp; a warp then walks the terms in the order Alg. 6 visits them
-//   (|q_j| descending) and adds q_j * x~ into its own ids with plain
-//   read-modify-writes.  No two warps share an id, so no atomics are needed,
-//   and every score is the fp32 sum of its terms in the paper's order: scores
-//   do not depend on scheduling or on the other queries of the batch.
+// Alg. 6 for query slot b over tile t.  A query term's postings inside the
+// tile sit in one container: a bitmap of T bits when at least T/2 ids of the
+// tile hold the coordinate, else a sorted array of 16-bit local ids.
+//   Phase 1, bitmap terms: thread tid owns ids tid, tid+512, ... of the tile
+//   and keeps their partial scores in registers; for each term it tests its
+//   ids' bits and adds q_j * x~ for the set ones, reading the term's sketch
+//   row(s) contiguously across the warp.  No atomics; a fixed order.
+//   Phase 2, array terms: their postings are cut into chunks of 32 (one per
+//   lane), numbered in term order; each warp takes a contiguous range of
+//   chunks, so it finds a chunk's term by advancing one pointer, and adds into
+//   shared memory with atomics (two terms may share an id).
 //   EMIT: ids whose score key falls at or above the query's running bound are
 //   counted in the histogram and emitted; otherwise (dense) every live id gets
 //   its key written and counted.
@@ -262,69 +265,147 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
                            uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
   constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
-  const uint32_t T = a.T;
-  float *acc = (float *)sm;                      // T
-  uint32_t *hist = sm + T;                       // 4096
-  uint32_t *t_lo = hist + 4096;                  // kTermBatch
-  float *t_v = (float *)(t_lo + kTermBatch);     // kTermBatch
+  constexpr uint32_t PER = 4;  // register accumulators per thread per pass
+  const uint32_t T = a.T, BMIN = T >> 1;
+  float *acc = (float *)sm;                          // T
+  uint32_t *hist = sm + T;                           // 4096
+  uint32_t *t_start = hist + 4096;                   // kTermBatch
+  uint32_t *t_cnt = t_start + kTermBatch;            // kTermBatch
+  uint32_t *t_cp = t_cnt + kTermBatch;               // kTermBatch+1: chunk prefix (arrays)
+  float *t_v = (float *)(t_cp + kTermBatch + 1);     // kTermBatch
   uint32_t *t_bin = (uint32_t *)(t_v + kTermBatch);  // kTermBatch * h
-  uint32_t *t_seg = t_bin + kTermBatch * a.h;    // kTermBatch * (NW+1) segment starts
   __shared__ uint32_t part[NW + 2];
+  __shared__ uint32_t s_nbm;
+  __shared__ uint8_t t_bl[kTermBatch];  // bitmap terms of the batch, in order
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.nt[b];
   const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
-  const uint32_t *off = a.tile_off + (uint64_t)t * (a.n + 1);
+  const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
   const uint16_t *post = a.tile_post[t];
   const uint64_t id0 = (uint64_t)t << a.log2T;
-  const uint32_t span = T / NW;
 
   for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
   for (uint32_t i = tid; i < 4096; i += kScoreThreads) hist[i] = 0;
   for (uint32_t i0 = 0; i0 < nt; i0 += kTermBatch) {
     const uint32_t nb = min(kTermBatch, nt - i0);
     __syncthreads();  // the previous batch is consumed
+    if (tid == 0) s_nbm = 0;
     for (uint32_t k = tid; k < nb; k += kScoreThreads) {
       const uint32_t j = terms[i0 + k].j;
-      const uint32_t lo = off[j], hi = off[j + 1];
-      t_lo[k] = lo;
+      const uint2 de = dir[j];
+      t_start[k] = de.x;
+      t_cnt[k] = de.y;
+      t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
       t_v[k] = terms[i0 + k].v;
       for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
-      t_seg[k * (NW + 1)] = 0;
-      t_seg[k * (NW + 1) + NW] = hi - lo;
     }
     __syncthreads();
-    // segment starts: first position whose local id reaches w * span
-    for (uint32_t task = tid; task < nb * (NW - 1); task += kScoreThreads) {
-      const uint32_t k = task / (NW - 1), w = 1 + task % (NW - 1);
-      const uint16_t *lst = post + t_lo[k];
-      uint32_t lo = 0, hi = t_seg[k * (NW + 1) + NW];
-      const uint32_t target = w * span;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if ((uint32_t)(__ldg(lst + mid) & 0x7FFFu) < target) lo = mid + 1;
+    if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap count
+      uint32_t run = 0, nbm = 0;
+      for (uint32_t base = 0; base < nb; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t v = i < nb ? t_cp[i] : 0;
+        const uint32_t isb = __ballot_sync(0xFFFFFFFFu, i < nb && t_cnt[i] >= BMIN);
+        if ((isb >> lane) & 1u) t_bl[nbm + __popc(isb & ((1u << lane) - 1u))] = (uint8_t)i;
+        nbm += __popc(isb);
+        uint32_t x = v;
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, dd);
+          if (lane >= (uint32_t)dd) x += y;
+        }
+        if (i < nb) t_cp[i] = run + x - v;
+        run += __shfl_sync(0xFFFFFFFFu, x, 31);
+      }
+      if (lane == 0) {
+        t_cp[nb] = run;
+        part[0] = run;
+        s_nbm = nbm;
+      }
+    }
+    __syncthreads();
+    const uint32_t C = part[0];
+    // phase 1: bitmap terms (listed in t_bl, in term order)
+    const uint32_t nbm = s_nbm;
+    if (nbm > 0) {
+      for (uint32_t g0 = 0; g0 < T; g0 += kScoreThreads * PER) {
+        float r[PER];
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+          const uint32_t d = g0 + q * kScoreThreads + tid;
+          r[q] = d < T ? acc[d] : 0.0f;
+        }
+        for (uint32_t kk = 0; kk < nbm; ++kk) {
+          const uint32_t k = t_bl[kk];
+          const float v = t_v[k];
+          const bool pos = v > 0.0f;
+          const float *plane = pos ? a.U : a.L;
+          const float *row[HS];
+#pragma unroll
+          for (uint32_t o = 0; o < HS; ++o)
+            if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+          const uint32_t *bm = (const uint32_t *)(post + t_start[k]);
+          uint32_t wv[PER];
+          float xv[PER];
+#pragma unroll
+          for (uint32_t q = 0; q < PER; ++q) {  // both loads issue together
+            const uint32_t d = min(g0 + q * kScoreThreads + tid, T - 1);
+            wv[q] = __ldg(bm + (d >> 5));
+            xv[q] = decode<H>(row, a.h, pos, d);
+          }
+#pragma unroll
+          for (uint32_t q = 0; q < PER; ++q) {
+            const uint32_t d = g0 + q * kScoreThreads + tid;
+            if (d < T && ((wv[q] >> (d & 31)) & 1u)) r[q] = fmaf(v, xv[q], r[q]);
+          }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+          const uint32_t d = g0 + q * kScoreThreads + tid;
+          if (d < T) acc[d] = r[q];
+        }
+      }
+      __syncthreads();
+    }
+    // phase 2: array terms
+    const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
+    const uint32_t c_end = (uint32_t)((uint64_t)C * (wid + 1) / NW);
+    if (c_beg < c_end) {
+      uint32_t i = 0, hi = nb;  // term of c_beg: last i with t_cp[i] <= c_beg
+      while (hi - i > 1) {
+        const uint32_t mid = (i + hi) >> 1;
+        if (t_cp[mid] <= c_beg) i = mid;
         else hi = mid;
       }
-      t_seg[k * (NW + 1) + w] = lo;
-    }
-    __syncthreads();
-    for (uint32_t k = 0; k < nb; ++k) {
-      const uint32_t p_beg = t_seg[k * (NW + 1) + wid], p_end = t_seg[k * (NW + 1) + wid + 1];
-      if (p_beg >= p_end) continue;
-      const float v = t_v[k];
-      const bool pos = v > 0.0f;
-      const float *plane = pos ? a.U : a.L;
+      uint32_t c_start = 0, c_next = 0, lo = 0, len = 0;
+      float v = 0.0f;
+      bool pos = true;
       const float *row[HS];
+      auto load_term = [&]() {
+        c_start = t_cp[i];
+        c_next = t_cp[i + 1];
+        lo = t_start[i];
+        len = t_cnt[i];
+        v = t_v[i];
+        pos = v > 0.0f;
+        const float *plane = pos ? a.U : a.L;
 #pragma unroll
-      for (uint32_t o = 0; o < HS; ++o)
-        if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
-      const uint16_t *lst = post + t_lo[k];
-      for (uint32_t p0 = p_beg; p0 < p_end; p0 += 128) {
+        for (uint32_t o = 0; o < HS; ++o)
+          if (o < a.h) row[o] = plane + (uint64_t)t_bin[i * a.h + o] * a.cap + id0;
+      };
+      load_term();
+      for (uint32_t c = c_beg; c < c_end;) {
+        while (c >= c_next) {
+          ++i;
+          load_term();
+        }
+        const uint32_t nck = min(min(4u, c_end - c), c_next - c);
+        const uint32_t p0 = (c - c_start) * 32 + lane;
         uint32_t d[4];
 #pragma unroll
         for (uint32_t u = 0; u < 4; ++u) {
-          const uint32_t p = p0 + u * 32 + lane;
-          d[u] = p < p_end ? (uint32_t)__ldg(lst + p) : SINN_TOMB;
+          const uint32_t p = p0 + u * 32;
+          d[u] = (u < nck && p < len) ? (uint32_t)__ldg(post + lo + p) : SINN_TOMB;
         }
         float x[4];
 #pragma unroll
@@ -332,7 +413,8 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
           x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H>(row, a.h, pos, d[u]);
 #pragma unroll
         for (uint32_t u = 0; u < 4; ++u)
-          if (!(d[u] & SINN_TOMB)) acc[d[u]] = fmaf(v, x[u], acc[d[u]]);
+          if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], v * x[u]);
+        c += nck;
       }
     }
   }
@@ -932,8 +1014,7 @@ struct SearchReq {
 };
 
 size_t score_smem(const sinn_index *ix) {
-  return (size_t)ix->T * 4 + 4096 * 4 +
-         (size_t)kTermBatch * (4 + 4 + 4 * ix->h + 4 * (kScoreThreads / 32 + 1));
+  return (size_t)ix->T * 4 + 4096 * 4 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
 }
 
 int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
@@ -951,7 +1032,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
   CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   ScoreArgs sa;
-  sa.tile_off = ix->d_tile_off;
+  sa.tile_dir = ix->d_tile_dir;
   sa.tile_post = ix->d_tile_post;
   sa.U = ix->d_U;
   sa.L = ix->d_L;

@@ -41,7 +41,8 @@ struct sinn_index {
   uint32_t *d_fwd_nnz = nullptr;   // cap: entries stored (zeros included)
   uint2 *d_fwd = nullptr;          // vector store pool: (coordinate, value bits)
   uint64_t fwd_cap = 0, fwd_used = 0;
-  uint32_t *d_tile_off = nullptr;  // tiles_cap x (n+1) offsets into each tile's postings
+  uint2 *d_tile_dir = nullptr;     // tiles_cap x n containers {start, count} per tile
+                                   // (count >= T/16: bitmap of T bits, else sorted array)
   uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
   uint32_t *d_err = nullptr;       // sticky device error bits
   uint64_t cap = 0;                // id capacity = tiles_cap * T
@@ -53,6 +54,7 @@ struct sinn_index {
   uint64_t next_id = 0, live_count = 0;
   std::vector<uint16_t *> tile_post;     // per tile posting array (device)
   std::vector<uint64_t> tile_post_len;   // postings held (tombstones included)
+  std::vector<uint64_t> tile_post_cap;   // storage words allocated per tile
   std::vector<uint64_t> tile_nnz;        // sum of nnz over live vectors of the tile
   std::vector<uint64_t> tile_tombs;      // tombstoned postings per tile
   uint64_t tombstones = 0;
