@@ -48,6 +48,7 @@ extern "C" {
 #define SINN_ENOMEM 3    /* device or host allocation failed */
 #define SINN_ECUDA 4     /* a CUDA runtime call failed */
 #define SINN_EDEVICE 5   /* a kernel reported an error (see sinn_sync) */
+#define SINN_ESCRATCH 6  /* sinn_search_noalloc: one query needs more than its fixed scratch */
 
 typedef struct sinn_index sinn_index; /* opaque; owned by the library */
 
@@ -133,6 +134,25 @@ int sinn_search_kp(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_i
 int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
                      const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
                      uint32_t *out_ids, float *out_scores, void *stream);
+
+/* sinn_search without any allocation, for callers that cannot allocate
+ * device memory while they search (a memory budget fixed in advance, or a
+ * serving path that must not enter the allocator, which can synchronise the
+ * device or fail when memory is fragmented).  The paper has no counterpart:
+ * this is a deployment variant of the same search.
+ * Arguments and results are exactly those of sinn_search.  The scratch is a
+ * fixed 64 MiB device array inside the library, present on every device that
+ * loads it until the library is unloaded.  Queries are processed in groups
+ * that fit it; SINN_ESCRATCH if even one query does not fit (one query needs
+ * about 4 bytes per id slot of the index plus 1.6 MB).  The first call on a
+ * device looks the array's address up, so make that first call before any
+ * stream capture.  Every call on a device shares the array and overwrites
+ * what the last call left there: calls that overlap on the GPU (on different
+ * streams, or for different indexes of the same device) race, so order them.
+ * The call itself allocates nothing and records no timing events. */
+int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                        const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                        uint32_t *out_ids, float *out_scores, void *stream);
 
 /* Wait for the stream, then return and clear the sticky device error
  * (SINN_OK if none; SINN_EINVAL for a malformed query; SINN_EDEVICE for an

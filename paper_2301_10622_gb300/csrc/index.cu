@@ -676,6 +676,7 @@ extern "C" const char *sinn_strerror(int code) {
     case SINN_ENOMEM: return "out of memory";
     case SINN_ECUDA: return "CUDA runtime error";
     case SINN_EDEVICE: return "device-side error";
+    case SINN_ESCRATCH: return "request needs more than the fixed no-allocation scratch";
     default: return "unknown error";
   }
 }

@@ -1017,16 +1017,27 @@ size_t score_smem(const sinn_index *ix) {
   return (size_t)ix->T * 4 + 4096 * 4 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
 }
 
-int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s) {
+// Scratch supplied by the caller instead of the index's own (grown) buffer.
+struct FixedScratch {
+  void *base;
+  size_t bytes;
+};
+
+int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
+               const FixedScratch *fixed = nullptr) {
   const uint32_t kpmax = r.kp_max;
   const Layout one = layout_for(ix, 1, kpmax);
-  uint64_t B = std::max<uint64_t>(1, ix->scratch_budget / one.total);
+  const uint64_t budget = fixed ? fixed->bytes : ix->scratch_budget;
+  uint64_t B = std::max<uint64_t>(1, budget / one.total);
   B = std::min<uint64_t>(B, r.n_q);
   B = std::min<uint64_t>(B, 65535);
   Layout L = layout_for(ix, (uint32_t)B, kpmax);
-  int st = sinn_ensure_scratch(ix, L.total);
-  if (st) return st;
-  Batch bt = views(ix->scratch, L, (uint32_t)B);
+  if (fixed && L.total > fixed->bytes) return SINN_ESCRATCH;
+  if (!fixed) {
+    int st = sinn_ensure_scratch(ix, L.total);
+    if (st) return st;
+  }
+  Batch bt = views(fixed ? fixed->base : ix->scratch, L, (uint32_t)B);
   const size_t ssm = score_smem(ix);
   const ScoreKernels sk = score_kernels(ix->h);
   CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
@@ -1289,4 +1300,70 @@ extern "C" int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr,
   CK(cudaMemcpyAsync(out_ids, d_oi, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(out_scores, d_os, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
   return sinn_sync(ix, stream);
+}
+
+// ------------------------------------------------ search without allocation
+// Some callers cannot allocate device memory while they search: code running
+// inside a memory budget that was fixed up front, or a host whose allocator
+// must not be entered on its serving path (an allocation may synchronise the
+// device or fail under fragmentation).  sinn_search_noalloc serves them: its
+// scratch is this file-scope device array, which exists on every device that
+// loads the library for as long as the library stays loaded, so the call
+// itself never allocates.  All calls on one device share it.
+constexpr size_t kNoAllocBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// The array's device address, looked up once per device (with that device
+// current).  In host code the array's name is only a host-side stand-in.
+int noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kMaxDevices) return SINN_ECUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return SINN_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SINN_OK;
+}
+}  // namespace
+
+extern "C" int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr,
+                                   const uint32_t *q_indices, const float *q_values,
+                                   uint32_t n_q, uint32_t k, uint32_t k_prime, uint32_t *out_ids,
+                                   float *out_scores, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  FixedScratch fx;
+  if ((st = noalloc_scratch(ix->device, &fx.base))) return st;
+  fx.bytes = kNoAllocBytes;
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = k;
+  r.kp = k_prime;
+  r.kp_min = k;
+  r.kp_max = k_prime;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.stage = Stage::kFull;
+  // phase timing records events; keep this call free of any resource creation
+  const bool tm = ix->tm_on;
+  ix->tm_on = false;
+  st = run_search(ix, r, (cudaStream_t)stream, &fx);
+  ix->tm_on = tm;
+  return st;
 }

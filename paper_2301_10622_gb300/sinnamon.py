@@ -22,7 +22,7 @@ from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
-SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE = range(6)
+SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH = range(7)
 
 # every symbol declared in include/sinnamon.h
 EXPORTS = [
@@ -30,6 +30,7 @@ EXPORTS = [
     "sinn_search", "sinn_search_kp", "sinn_search_host", "sinn_sync", "sinn_stats",
     "sinn_strerror", "sinn_hash_table", "sinn_sketch_columns", "sinn_inverted_list",
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
+    "sinn_search_noalloc",
 ]
 
 PHASES = ["prep", "score", "select", "rerank", "insert", "delete"]
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = False):
         "sinn_scores": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
         "sinn_candidates": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp], C.c_int),
         "sinn_timing_start": ([vp], C.c_int),
+        "sinn_search_noalloc": ([vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
         "sinn_timing_stop": ([vp, C.POINTER(SinnTiming)], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -202,6 +204,16 @@ def sinn_search_kp(ix, q_indptr, q_indices, q_values, k, k_prime, k_prime_max, o
     _check(load().sinn_search_kp(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
                                  _p(k_prime), k_prime_max, _p(out_ids), _p(out_scores),
                                  _s(stream)), "sinn_search_kp")
+
+
+def sinn_search_noalloc(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
+                        stream=None):
+    """sinn_search with its scratch in the library's fixed device array: no
+    allocation happens during the call (for callers that cannot allocate)."""
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_search_noalloc(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
+                                      k_prime, _p(out_ids), _p(out_scores), _s(stream)),
+           "sinn_search_noalloc")
 
 
 def sinn_search_host(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
