@@ -1,0 +1,656 @@
+// Learned per-query k' (the paper's Sec. 5.3 / Sec. 7 suggestion that k' be
+// chosen per query from the expected approximation error): query features,
+// a 2-hidden-layer MLP with BF16 tensor-core GEMMs (FP32 accumulation), its
+// training step (pinball loss, Adam) and a search that uses its prediction.
+//
+// GEMMs use mma.sync.m16n8k16 (bf16 inputs, fp32 accumulators) on 64x64
+// tiles staged through shared memory; operands are read through arbitrary
+// (row, column) strides, so the same kernel computes X W^T, dY W and dY^T X.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "../../include/sinnamon_kprime.h"
+#include "sinn_internal.cuh"
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) return sinn_check_cuda(e_); \
+  } while (0)
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+struct GemmArgs {
+  // C[m][n] = alpha * sum_k A(m,k) B(n,k) (+ bias[n]) (ReLU) ; A, B bf16
+  const __nv_bfloat16 *A;
+  int64_t sam, sak;
+  const __nv_bfloat16 *B;
+  int64_t sbn, sbk;
+  int M, N, K;
+  float alpha;
+  const float *bias;        // nullable, per n
+  int relu;                 // 1: max(0, .)
+  float *C;                 // nullable fp32 out, row stride ldc
+  int64_t ldc;
+  __nv_bfloat16 *Cb;        // nullable bf16 out, row stride ldcb
+  int64_t ldcb;
+  const float *mask;        // nullable: multiply by (mask[m*ldm+n] > 0)
+  int64_t ldm;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// 4 warps; warp w computes rows [32*(w/2), +32) x cols [32*(w%2), +32) of the tile
+__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
+  __shared__ __nv_bfloat16 As[BM][BK + 8];
+  __shared__ __nv_bfloat16 Bs[BN][BK + 8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (w >> 1) * 32, wn = (w & 1) * 32;
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 128) {
+      const int r = e / BK, c = e % BK;
+      const int m = m0 + r, k = k0 + c;
+      As[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+      const int n = n0 + r;
+      Bs[r][c] = (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
+    }
+    __syncthreads();
+    uint32_t af[2][4], bf[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = wm + i * 16 + gid;
+      af[i][0] = pack_bf16(As[r][tig * 2], As[r][tig * 2 + 1]);
+      af[i][1] = pack_bf16(As[r + 8][tig * 2], As[r + 8][tig * 2 + 1]);
+      af[i][2] = pack_bf16(As[r][tig * 2 + 8], As[r][tig * 2 + 9]);
+      af[i][3] = pack_bf16(As[r + 8][tig * 2 + 8], As[r + 8][tig * 2 + 9]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = wn + j * 8 + gid;
+      bf[j][0] = pack_bf16(Bs[n][tig * 2], Bs[n][tig * 2 + 1]);
+      bf[j][1] = pack_bf16(Bs[n][tig * 2 + 8], Bs[n][tig * 2 + 9]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+            : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]),
+              "r"(bf[j][1]));
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
+        if (m >= g.M || n >= g.N) continue;
+        float v = g.alpha * acc[i][j][r];
+        if (g.bias) v += g.bias[n];
+        if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) v = 0.0f;
+        if (g.relu) v = fmaxf(v, 0.0f);
+        if (g.C) g.C[m * g.ldc + n] = v;
+        if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(v);
+      }
+}
+
+void gemm(const GemmArgs &g, cudaStream_t s) {
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+  k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+}
+
+// Features -> normalised bf16 inputs (padded to K columns with zeros).
+__global__ void k_normalise(const float *X, uint32_t B, uint32_t nin, uint32_t kpad,
+                            const float *mean, const float *inv_std, __nv_bfloat16 *Xb) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)B * kpad) return;
+  const uint32_t r = (uint32_t)(i / kpad), c = (uint32_t)(i % kpad);
+  const float v = c < nin ? (X[(uint64_t)r * nin + c] - mean[c]) * inv_std[c] : 0.0f;
+  Xb[i] = __float2bfloat16(v);
+}
+
+// y[r] = sum_c H[r][c] w[c] + b (one warp per row), fp32.
+__global__ void k_head(const float *H, uint32_t B, uint32_t hdim, const float *w, const float *b,
+                       float *y) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= B) return;
+  float s = 0.0f;
+  for (uint32_t c = lane; c < hdim; c += 32) s = fmaf(H[r * hdim + c], w[c], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) y[r] = s + b[0];
+}
+
+// Pinball loss at quantile tau: dL/dy = (1[t < y] - tau) / B; also the loss.
+__global__ void k_pinball(const float *y, const float *t, uint32_t B, float tau, float *dy,
+                          float *loss) {
+  __shared__ float part[32];
+  float l = 0.0f;
+  for (uint32_t i = threadIdx.x; i < B; i += blockDim.x) {
+    const float u = t[i] - y[i];
+    l += u >= 0.0f ? tau * u : (tau - 1.0f) * u;
+    dy[i] = ((u < 0.0f ? 1.0f : 0.0f) - tau) / (float)B;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) s += part[w];
+    if (loss) *loss = s / (float)B;
+  }
+}
+
+// dH2[r][c] = dy[r] w3[c] masked by Z2 > 0 (as fp32 and bf16); dw3[c] and
+// db3 are reduced by k_colsum.
+__global__ void k_head_back(const float *dy, const float *w3, const float *H2, uint32_t B,
+                            uint32_t hdim, float *dZ2, __nv_bfloat16 *dZ2b) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)B * hdim) return;
+  const uint32_t r = (uint32_t)(i / hdim), c = (uint32_t)(i % hdim);
+  const float v = H2[i] > 0.0f ? dy[r] * w3[c] : 0.0f;
+  dZ2[i] = v;
+  dZ2b[i] = __float2bfloat16(v);
+}
+
+// out[c] = sum_r X[r][c] * (s ? s[r] : 1) over rows (column sums), fp32.
+__global__ void k_colsum(const float *X, const float *s, uint32_t B, uint32_t cols, float *out) {
+  const uint32_t c = blockIdx.x * blockDim.y + threadIdx.y;
+  if (c >= cols) return;
+  float a = 0.0f;
+  for (uint32_t r = threadIdx.x; r < B; r += 32) a += X[(uint64_t)r * cols + c] * (s ? s[r] : 1.0f);
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+  if (threadIdx.x == 0) out[c] = a;
+}
+
+__global__ void k_sum(const float *x, uint32_t n, float *out) {
+  __shared__ float part[32];
+  float a = 0.0f;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) s += part[w];
+    *out = s;
+  }
+}
+
+// Adam on all parameters (flat), then refresh the bf16 copies.
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, uint64_t n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float a = b1 * m1[i] + (1.0f - b1) * gi;
+  const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// bf16 copies of W1 (hid x kpad, zero-padded columns), W2 (hid x hid) and
+// W2^T (for dH1 = dZ2 W2 as a row-major-by-row operand).
+__global__ void k_weights_bf16(const float *W1, const float *W2, uint32_t nin, uint32_t kpad,
+                               uint32_t hid, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b,
+                               __nv_bfloat16 *W2tb) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < (uint64_t)hid * kpad) {
+    const uint32_t r = (uint32_t)(i / kpad), c = (uint32_t)(i % kpad);
+    W1b[i] = __float2bfloat16(c < nin ? W1[(uint64_t)r * nin + c] : 0.0f);
+  }
+  if (i < (uint64_t)hid * hid) {
+    const uint32_t r = (uint32_t)(i / hid), c = (uint32_t)(i % hid);
+    W2b[i] = __float2bfloat16(W2[i]);
+    W2tb[(uint64_t)c * hid + r] = __float2bfloat16(W2[i]);
+  }
+}
+
+// Per-query features: nnz, L1, L2 of the non-zeros, then log2(1 + |I[j]|)
+// for the 16 terms of largest |q_j| (ties by j), 0 where fewer.  |I[j]| is
+// summed over the tiles' containers (tombstones included).
+__global__ void k_features(const uint64_t *__restrict__ ip, const uint32_t *__restrict__ idx,
+                           const float *__restrict__ val, uint32_t n, const uint2 *tile_dir,
+                           uint32_t tiles, float *out) {
+  const uint32_t q = blockIdx.x, tid = threadIdx.x;
+  __shared__ uint32_t sj[SINN_KP_TOP];
+  __shared__ float red[3][32];
+  __shared__ uint32_t s_top;
+  const uint64_t s = ip[q], e = ip[q + 1];
+  float c0 = 0.0f, l1 = 0.0f, l2 = 0.0f;
+  for (uint64_t p = s + tid; p < e; p += blockDim.x) {
+    const float v = val[p];
+    if (v == 0.0f || !isfinite(v) || idx[p] >= n) continue;
+    c0 += 1.0f;
+    l1 += fabsf(v);
+    l2 += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, o);
+    l1 += __shfl_xor_sync(0xFFFFFFFFu, l1, o);
+    l2 += __shfl_xor_sync(0xFFFFFFFFu, l2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = c0;
+    red[1][tid >> 5] = l1;
+    red[2][tid >> 5] = l2;
+  }
+  if (tid == 0) s_top = 0;
+  __syncthreads();
+  // top terms by rank counting (|v| desc, j asc)
+  for (uint64_t p = s + tid; p < e; p += blockDim.x) {
+    const float v = val[p];
+    const uint32_t j = idx[p];
+    if (v == 0.0f || !isfinite(v) || j >= n) continue;
+    uint32_t r = 0;
+    for (uint64_t t = s; t < e && r < SINN_KP_TOP; ++t) {
+      const float w = val[t];
+      if (w == 0.0f || !isfinite(w) || idx[t] >= n) continue;
+      r += (fabsf(w) > fabsf(v)) || (fabsf(w) == fabsf(v) && idx[t] < j);
+    }
+    if (r < SINN_KP_TOP) {
+      sj[r] = j;
+      atomicMax(&s_top, r + 1);
+    }
+  }
+  __syncthreads();
+  float *o = out + (uint64_t)q * SINN_KP_FEATURES;
+  if (tid == 0) {
+    float a = 0.0f, b = 0.0f, c = 0.0f;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+    }
+    o[0] = log2f(1.0f + a);
+    o[1] = b;
+    o[2] = sqrtf(c);
+  }
+  // list lengths: warp w sums term w over tiles
+  const uint32_t lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (uint32_t r = wid; r < SINN_KP_TOP; r += nw) {
+    float f = 0.0f;
+    if (r < s_top) {
+      uint64_t cnt = 0;
+      for (uint32_t t = lane; t < tiles; t += 32) cnt += tile_dir[(uint64_t)t * n + sj[r]].y;
+      for (int s2 = 16; s2 > 0; s2 >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, s2);
+      f = log2f(1.0f + (float)cnt);
+    }
+    if (lane == 0) o[3 + r] = f;
+  }
+}
+
+// k'[q] = clamp(ceil(2^y[q]), lo, hi)
+__global__ void k_kprime(const float *y, uint32_t B, uint32_t lo, uint32_t hi, uint32_t *kp) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const float v = exp2f(fminf(fmaxf(y[i], 0.0f), 31.0f));
+  kp[i] = min(max((uint32_t)ceilf(v), lo), hi);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ model
+struct sinn_mlp {
+  uint32_t nin = 0, hid = 0, kpad = 0;
+  int device = 0;
+  uint64_t nparams = 0;
+  float *d_p = nullptr;   // flat params: W1 (hid x nin), b1, W2 (hid x hid), b2, w3, b3
+  float *d_g = nullptr;   // gradients, same layout
+  float *d_m1 = nullptr, *d_m2 = nullptr;
+  float *d_mean = nullptr, *d_istd = nullptr;
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2tb = nullptr;
+  uint64_t steps = 0;
+  // activations (grow-only)
+  uint32_t cap = 0;
+  void *act = nullptr;
+  bool bf16_fresh = false;
+};
+
+namespace {
+
+struct Views {
+  float *W1, *b1, *W2, *b2, *w3, *b3;
+};
+
+Views views(sinn_mlp *m, float *base) {
+  Views v;
+  v.W1 = base;
+  v.b1 = v.W1 + (uint64_t)m->hid * m->nin;
+  v.W2 = v.b1 + m->hid;
+  v.b2 = v.W2 + (uint64_t)m->hid * m->hid;
+  v.w3 = v.b2 + m->hid;
+  v.b3 = v.w3 + m->hid;
+  return v;
+}
+
+struct Acts {
+  __nv_bfloat16 *Xb, *H1b, *dZ2b, *dZ1b;
+  float *Z1, *H2, *y, *dy, *dZ2, *dH1, *loss;
+};
+
+int ensure_acts(sinn_mlp *m, uint32_t B, Acts *a) {
+  if (B > m->cap) {
+    if (m->act) {
+      CK(cudaDeviceSynchronize());
+      CK(cudaFree(m->act));
+      m->act = nullptr;
+    }
+    const uint32_t c = std::max<uint32_t>(B, 1024);
+    const size_t bytes = (size_t)c * (m->kpad * 2 + m->hid * 2 * 3 + m->hid * 4 * 4 + 16) + 1024;
+    CK(cudaMalloc(&m->act, bytes));
+    m->cap = c;
+  }
+  char *p = (char *)m->act;
+  const size_t c = m->cap;
+  auto take = [&](size_t bytes) {
+    char *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  a->Xb = (__nv_bfloat16 *)take(c * m->kpad * 2);
+  a->H1b = (__nv_bfloat16 *)take(c * m->hid * 2);
+  a->dZ2b = (__nv_bfloat16 *)take(c * m->hid * 2);
+  a->dZ1b = (__nv_bfloat16 *)take(c * m->hid * 2);
+  a->Z1 = (float *)take(c * m->hid * 4);
+  a->H2 = (float *)take(c * m->hid * 4);
+  a->dZ2 = (float *)take(c * m->hid * 4);
+  a->dH1 = (float *)take(c * m->hid * 4);
+  a->y = (float *)take(c * 4);
+  a->dy = (float *)take(c * 4);
+  a->loss = (float *)take(64);
+  return SINN_OK;
+}
+
+int refresh_bf16(sinn_mlp *m, cudaStream_t s) {
+  if (m->bf16_fresh) return SINN_OK;
+  Views v = views(m, m->d_p);
+  const uint64_t n = std::max<uint64_t>((uint64_t)m->hid * m->kpad, (uint64_t)m->hid * m->hid);
+  k_weights_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v.W1, v.W2, m->nin, m->kpad, m->hid,
+                                                            m->W1b, m->W2b, m->W2tb);
+  CK(cudaGetLastError());
+  m->bf16_fresh = true;
+  return SINN_OK;
+}
+
+// Forward through the network for B rows of raw features X; leaves the
+// activations in a (needed by the backward pass).
+int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s) {
+  int st = refresh_bf16(m, s);
+  if (st) return st;
+  Views v = views(m, m->d_p);
+  const uint64_t nx = (uint64_t)B * m->kpad;
+  k_normalise<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(X, B, m->nin, m->kpad, m->d_mean,
+                                                          m->d_istd, a.Xb);
+  GemmArgs g{};
+  // Z1 = X W1^T + b1 ; H1 = relu(Z1)
+  g.A = a.Xb; g.sam = m->kpad; g.sak = 1;
+  g.B = m->W1b; g.sbn = m->kpad; g.sbk = 1;
+  g.M = (int)B; g.N = (int)m->hid; g.K = (int)m->kpad; g.alpha = 1.0f;
+  g.bias = v.b1; g.relu = 0; g.C = a.Z1; g.ldc = m->hid; g.Cb = nullptr;
+  gemm(g, s);
+  GemmArgs r = g;  // H1 (bf16) = relu(Z1)
+  r.relu = 1; r.C = nullptr; r.Cb = a.H1b; r.ldcb = m->hid;
+  gemm(r, s);
+  // H2 = relu(H1 W2^T + b2)
+  GemmArgs g2{};
+  g2.A = a.H1b; g2.sam = m->hid; g2.sak = 1;
+  g2.B = m->W2b; g2.sbn = m->hid; g2.sbk = 1;
+  g2.M = (int)B; g2.N = (int)m->hid; g2.K = (int)m->hid; g2.alpha = 1.0f;
+  g2.bias = v.b2; g2.relu = 1; g2.C = a.H2; g2.ldc = m->hid;
+  gemm(g2, s);
+  k_head<<<(B + 7) / 8, 256, 0, s>>>(a.H2, B, m->hid, v.w3, v.b3, a.y);
+  CK(cudaGetLastError());
+  return SINN_OK;
+}
+
+// Gradients of the mean pinball loss into m->d_g.
+int backward(sinn_mlp *m, const float *t, uint32_t B, float tau, Acts &a, cudaStream_t s) {
+  Views v = views(m, m->d_p);
+  Views gv = views(m, m->d_g);
+  k_pinball<<<1, 1024, 0, s>>>(a.y, t, B, tau, a.dy, a.loss);
+  // head: dw3 = H2^T dy ; db3 = sum dy ; dZ2 = dy w3 * 1[H2 > 0]
+  k_colsum<<<(m->hid + 7) / 8, dim3(32, 8), 0, s>>>(a.H2, a.dy, B, m->hid, gv.w3);
+  k_sum<<<1, 1024, 0, s>>>(a.dy, B, gv.b3);
+  const uint64_t nh = (uint64_t)B * m->hid;
+  k_head_back<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(a.dy, v.w3, a.H2, B, m->hid, a.dZ2,
+                                                          a.dZ2b);
+  // dW2 = dZ2^T H1 (hid x hid, reduction over rows) ; db2 = colsum dZ2
+  GemmArgs g{};
+  g.A = a.dZ2b; g.sam = 1; g.sak = m->hid;       // A(n_out, r) = dZ2[r][n_out]
+  g.B = a.H1b; g.sbn = 1; g.sbk = m->hid;        // B(n_in, r) = H1[r][n_in]
+  g.M = (int)m->hid; g.N = (int)m->hid; g.K = (int)B; g.alpha = 1.0f;
+  g.C = gv.W2; g.ldc = m->hid;
+  gemm(g, s);
+  k_colsum<<<(m->hid + 7) / 8, dim3(32, 8), 0, s>>>(a.dZ2, nullptr, B, m->hid, gv.b2);
+  // dH1 = dZ2 W2 (B x hid) masked by Z1 > 0 -> dZ1 ; B(n, k) = W2[k][n] = W2t[n][k]
+  GemmArgs h{};
+  h.A = a.dZ2b; h.sam = m->hid; h.sak = 1;
+  h.B = m->W2tb; h.sbn = m->hid; h.sbk = 1;
+  h.M = (int)B; h.N = (int)m->hid; h.K = (int)m->hid; h.alpha = 1.0f;
+  h.mask = a.Z1; h.ldm = m->hid;
+  h.C = a.dH1; h.ldc = m->hid; h.Cb = a.dZ1b; h.ldcb = m->hid;
+  gemm(h, s);
+  // dW1 = dZ1^T X (hid x nin) ; db1 = colsum dZ1
+  GemmArgs w{};
+  w.A = a.dZ1b; w.sam = 1; w.sak = m->hid;
+  w.B = a.Xb; w.sbn = 1; w.sbk = m->kpad;
+  w.M = (int)m->hid; w.N = (int)m->nin; w.K = (int)B; w.alpha = 1.0f;
+  w.C = gv.W1; w.ldc = m->nin;
+  gemm(w, s);
+  k_colsum<<<(m->hid + 7) / 8, dim3(32, 8), 0, s>>>(a.dH1, nullptr, B, m->hid, gv.b1);
+  CK(cudaGetLastError());
+  return SINN_OK;
+}
+
+uint64_t splitmix_next(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, sinn_mlp **out) {
+  if (!out || n_in == 0 || hidden == 0 || hidden > 4096 || n_in > 1024) return SINN_EINVAL;
+  *out = nullptr;
+  sinn_mlp *m = new (std::nothrow) sinn_mlp();
+  if (!m) return SINN_ENOMEM;
+  cudaGetDevice(&m->device);
+  m->nin = n_in;
+  m->hid = hidden;
+  m->kpad = (n_in + 15) / 16 * 16;
+  m->nparams = (uint64_t)hidden * n_in + hidden + (uint64_t)hidden * hidden + hidden + hidden + 1;
+  std::vector<float> p(m->nparams, 0.0f), ones(n_in, 1.0f), zeros(n_in, 0.0f);
+  uint64_t s = seed ? seed : 0x5151;
+  auto uni = [&](float bound) {  // uniform in [-bound, bound]
+    const double u = (double)(splitmix_next(s) >> 11) * (1.0 / 9007199254740992.0);
+    return (float)((2.0 * u - 1.0) * bound);
+  };
+  Views v = views(m, p.data());
+  for (uint64_t i = 0; i < (uint64_t)hidden * n_in; ++i) v.W1[i] = uni(sqrtf(6.0f / n_in));
+  for (uint64_t i = 0; i < (uint64_t)hidden * hidden; ++i) v.W2[i] = uni(sqrtf(6.0f / hidden));
+  for (uint32_t i = 0; i < hidden; ++i) v.w3[i] = uni(sqrtf(3.0f / hidden));
+  int st = SINN_OK;
+  auto fail = [&](int e) {
+    sinn_mlp_destroy(m);
+    return e;
+  };
+  const size_t pb = m->nparams * 4;
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_p, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_g, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_m1, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_m2, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_mean, n_in * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->d_istd, n_in * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->W1b, (size_t)hidden * m->kpad * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->W2b, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&m->W2tb, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemcpy(m->d_p, p.data(), pb, cudaMemcpyHostToDevice))))
+    return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(m->d_g, 0, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(m->d_m1, 0, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(m->d_m2, 0, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemcpy(m->d_mean, zeros.data(), n_in * 4, cudaMemcpyHostToDevice))))
+    return fail(st);
+  if ((st = sinn_check_cuda(cudaMemcpy(m->d_istd, ones.data(), n_in * 4, cudaMemcpyHostToDevice))))
+    return fail(st);
+  *out = m;
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_destroy(sinn_mlp *m) {
+  if (!m) return SINN_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  cudaFree(m->d_p);
+  cudaFree(m->d_g);
+  cudaFree(m->d_m1);
+  cudaFree(m->d_m2);
+  cudaFree(m->d_mean);
+  cudaFree(m->d_istd);
+  cudaFree(m->W1b);
+  cudaFree(m->W2b);
+  cudaFree(m->W2tb);
+  cudaFree(m->act);
+  delete m;
+  return SINN_OK;
+}
+
+extern "C" uint64_t sinn_mlp_num_params(sinn_mlp *m) { return m ? m->nparams : 0; }
+
+extern "C" int sinn_mlp_params(sinn_mlp *m, float *host_out, int which) {
+  if (!m || !host_out) return SINN_EINVAL;
+  cudaSetDevice(m->device);
+  const float *src = which == 0 ? m->d_p : m->d_g;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(host_out, src, m->nparams * 4, cudaMemcpyDeviceToHost));
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_set_params(sinn_mlp *m, const float *host_in) {
+  if (!m || !host_in) return SINN_EINVAL;
+  cudaSetDevice(m->device);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(m->d_p, host_in, m->nparams * 4, cudaMemcpyHostToDevice));
+  m->bf16_fresh = false;
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_set_normalizer(sinn_mlp *m, const float *mean, const float *stdev) {
+  if (!m || !mean || !stdev) return SINN_EINVAL;
+  std::vector<float> is(m->nin);
+  for (uint32_t i = 0; i < m->nin; ++i) is[i] = stdev[i] > 0.0f ? 1.0f / stdev[i] : 1.0f;
+  cudaSetDevice(m->device);
+  CK(cudaMemcpy(m->d_mean, mean, m->nin * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->d_istd, is.data(), m->nin * 4, cudaMemcpyHostToDevice));
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_forward(sinn_mlp *m, const float *X, uint32_t B, float *y, void *stream) {
+  if (!m || (B && (!X || !y))) return SINN_EINVAL;
+  if (B == 0) return SINN_OK;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Acts a;
+  int st = ensure_acts(m, B, &a);
+  if (st) return st;
+  if ((st = forward(m, X, B, a, s))) return st;
+  CK(cudaMemcpyAsync(y, a.y, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_grad(sinn_mlp *m, const float *X, const float *t, uint32_t B, float tau,
+                             float *grad_out, float *loss_out, void *stream) {
+  if (!m || B == 0 || !X || !t || tau <= 0.0f || tau >= 1.0f) return SINN_EINVAL;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Acts a;
+  int st = ensure_acts(m, B, &a);
+  if (st) return st;
+  if ((st = forward(m, X, B, a, s))) return st;
+  if ((st = backward(m, t, B, tau, a, s))) return st;
+  if (grad_out) CK(cudaMemcpyAsync(grad_out, m->d_g, m->nparams * 4, cudaMemcpyDeviceToDevice, s));
+  if (loss_out) CK(cudaMemcpyAsync(loss_out, a.loss, 4, cudaMemcpyDeviceToDevice, s));
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_train_step(sinn_mlp *m, const float *X, const float *t, uint32_t B,
+                                   float tau, float lr, float *loss_out, void *stream) {
+  int st = sinn_mlp_grad(m, X, t, B, tau, nullptr, loss_out, stream);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  m->steps++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, (float)m->steps), c2 = 1.0f - powf(b2, (float)m->steps);
+  k_adam<<<(unsigned)((m->nparams + 255) / 256), 256, 0, s>>>(m->d_p, m->d_g, m->d_m1, m->d_m2,
+                                                            m->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  CK(cudaGetLastError());
+  m->bf16_fresh = false;
+  return SINN_OK;
+}
+
+extern "C" int sinn_kp_features(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                                const float *q_values, uint32_t n_q, float *out, void *stream) {
+  if (!ix || (n_q && (!q_indptr || !out))) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  cudaSetDevice(ix->device);
+  k_features<<<n_q, 256, 0, (cudaStream_t)stream>>>(q_indptr, q_indices, q_values, ix->n,
+                                                    ix->d_tile_dir, (uint32_t)(ix->cap / ix->T),
+                                                    out);
+  CK(cudaGetLastError());
+  return SINN_OK;
+}
+
+extern "C" int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
+                                   const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                                   uint32_t k, uint32_t k_prime_min, uint32_t k_prime_max,
+                                   uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
+                                   void *stream) {
+  if (!ix || !m || m->nin != SINN_KP_FEATURES) return SINN_EINVAL;
+  if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // features, prediction and k' live in the model's activation buffer tail
+  Acts a;
+  int st = ensure_acts(m, n_q, &a);
+  if (st) return st;
+  float *feat = a.dH1;                     // n_q x 19 <= n_q x hid floats
+  uint32_t *kp = (uint32_t *)a.dZ2;        // n_q
+  if (m->hid < SINN_KP_FEATURES) return SINN_EINVAL;
+  if ((st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream))) return st;
+  if ((st = forward(m, feat, n_q, a, s))) return st;
+  k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
+  CK(cudaGetLastError());
+  ix->launches += 8;
+  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
+  return sinn_search_kp(ix, q_indptr, q_indices, q_values, n_q, k, kp, k_prime_max, out_ids,
+                        out_scores, stream);
+}

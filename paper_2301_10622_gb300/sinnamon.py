@@ -31,7 +31,13 @@ EXPORTS = [
     "sinn_strerror", "sinn_hash_table", "sinn_sketch_columns", "sinn_inverted_list",
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
     "sinn_search_noalloc",
+    # sinnamon_kprime.h
+    "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
+    "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
+    "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned",
 ]
+
+KP_FEATURES = 19
 
 PHASES = ["prep", "score", "select", "rerank", "insert", "delete"]
 
@@ -111,6 +117,18 @@ def load(build_if_missing: bool = False):
         "sinn_candidates": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp], C.c_int),
         "sinn_timing_start": ([vp], C.c_int),
         "sinn_search_noalloc": ([vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
+        "sinn_kp_features": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
+        "sinn_mlp_create": ([u32, u32, u64, C.POINTER(vp)], C.c_int),
+        "sinn_mlp_destroy": ([vp], C.c_int),
+        "sinn_mlp_num_params": ([vp], u64),
+        "sinn_mlp_params": ([vp, vp, C.c_int], C.c_int),
+        "sinn_mlp_set_params": ([vp, vp], C.c_int),
+        "sinn_mlp_set_normalizer": ([vp, vp, vp], C.c_int),
+        "sinn_mlp_forward": ([vp, vp, u32, vp, vp], C.c_int),
+        "sinn_mlp_grad": ([vp, vp, vp, u32, C.c_float, vp, vp, vp], C.c_int),
+        "sinn_mlp_train_step": ([vp, vp, vp, u32, C.c_float, C.c_float, vp, vp], C.c_int),
+        "sinn_search_learned": ([vp, vp, vp, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp],
+                                C.c_int),
         "sinn_timing_stop": ([vp, C.POINTER(SinnTiming)], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -283,6 +301,89 @@ def sinn_timing_stop(ix) -> dict:
     return t.as_dict()
 
 
+def sinn_kp_features(ix, q_indptr, q_indices, q_values, out, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_kp_features(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, _p(out),
+                                   _s(stream)), "sinn_kp_features")
+
+
+def sinn_search_learned(ix, mlp, q_indptr, q_indices, q_values, k, kp_min, kp_max, out_ids,
+                        out_scores, out_kprime=None, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_search_learned(ix, mlp, _p(q_indptr), _p(q_indices), _p(q_values), n_q,
+                                      k, kp_min, kp_max, _p(out_ids), _p(out_scores),
+                                      _p(out_kprime), _s(stream)), "sinn_search_learned")
+
+
+class MLP:
+    """The k' network (sinn_mlp): n_in -> hidden -> hidden -> 1."""
+
+    def __init__(self, n_in: int = KP_FEATURES, hidden: int = 256, seed: int = 0x5151,
+                 device=None):
+        lib = load()
+        self.device = torch.device(device or "cuda")
+        out = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.sinn_mlp_create(n_in, hidden, seed, C.byref(out)), "sinn_mlp_create")
+        self._h, self.n_in, self.hidden = out, n_in, hidden
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sinn_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(load().sinn_mlp_num_params(self._h))
+
+    def params(self, which: int = 0) -> np.ndarray:
+        out = np.zeros(self.num_params, np.float32)
+        _check(load().sinn_mlp_params(self._h, _p(out), which), "sinn_mlp_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(load().sinn_mlp_set_params(self._h, _p(p)), "sinn_mlp_set_params")
+
+    def set_normalizer(self, mean, std):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(std, dtype=np.float32)
+        _check(load().sinn_mlp_set_normalizer(self._h, _p(m), _p(s)), "sinn_mlp_set_normalizer")
+
+    def forward(self, X, stream=None) -> torch.Tensor:
+        X = _dev(X, torch.float32, self.device)
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=self.device)
+        _check(load().sinn_mlp_forward(self._h, _p(X), X.shape[0], _p(y), _s(stream)),
+               "sinn_mlp_forward")
+        return y
+
+    def grad(self, X, t, tau: float, stream=None):
+        X = _dev(X, torch.float32, self.device)
+        t = _dev(t, torch.float32, self.device)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _check(load().sinn_mlp_grad(self._h, _p(X), _p(t), X.shape[0], tau, _p(g), _p(loss),
+                                    _s(stream)), "sinn_mlp_grad")
+        return g, loss
+
+    def train_step(self, X, t, tau: float, lr: float, stream=None) -> torch.Tensor:
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _check(load().sinn_mlp_train_step(self._h, _p(X), _p(t), X.shape[0], tau, lr, _p(loss),
+                                          _s(stream)), "sinn_mlp_train_step")
+        return loss
+
+
 # ------------------------------------------------------------- convenience
 
 class Index:
@@ -369,6 +470,23 @@ class Index:
 
     def hash_table(self) -> np.ndarray:
         return sinn_hash_table(self._h, self.n, self.h)
+
+    def kp_features(self, indptr, indices, values, stream=None) -> torch.Tensor:
+        ip, ix, v = self._csr(indptr, indices, values)
+        out = torch.empty((ip.numel() - 1, KP_FEATURES), dtype=torch.float32, device=self.device)
+        sinn_kp_features(self._h, ip, ix, v, out, stream)
+        return out
+
+    def search_learned(self, mlp, indptr, indices, values, k: int, kp_min: int, kp_max: int,
+                       stream=None):
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        ids = torch.empty((nq, k), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=self.device)
+        kp = torch.empty(nq, dtype=torch.int32, device=self.device)
+        sinn_search_learned(self._h, mlp.handle, ip, ix, v, k, kp_min, kp_max, ids, sc, kp,
+                            stream)
+        return ids, sc, kp
 
     def sync(self, stream=None):
         sinn_sync(self._h, stream)

@@ -1,0 +1,146 @@
+"""The learned per-query k': CUDA network forward/gradient against the FP64
+reference, features against their definition, labels against the oracle,
+and what the trained network gains over a fixed k'."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+from paper_2301_10622_gb300 import kprime, sinnamon, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _blocks(n_in, hid):
+    sizes = [hid * n_in, hid, hid * hid, hid, hid, 1]
+    return np.cumsum([0] + sizes)
+
+
+@pytest.mark.parametrize("B", [300, 64, 1])
+def test_network_forward_and_gradient_match_fp64(B):
+    """GEMMs run in bf16 with fp32 accumulation: outputs and each parameter
+    block's gradient agree with the FP64 reference to bf16 accuracy."""
+    n_in, hid = sinnamon.KP_FEATURES, 256
+    net = sinnamon.MLP(n_in, hid, seed=3)
+    rng = np.random.default_rng(B)
+    X = rng.normal(2.0, 3.0, (B, n_in)).astype(np.float32)
+    t = rng.normal(0.5, 1.0, B).astype(np.float32)
+    mean, std = X.mean(0), X.std(0) + 1e-3
+    if B == 1:
+        mean, std = np.zeros(n_in, np.float32), np.ones(n_in, np.float32)
+    net.set_normalizer(mean, std)
+    p = net.params()
+    y = net.forward(X).cpu().numpy()
+    y_ref, _ = omlp.forward(p, X, mean.astype(np.float64), std.astype(np.float64), n_in, hid)
+    scale = np.abs(y_ref).max() + 1e-3
+    assert np.max(np.abs(y - y_ref)) <= 2e-2 * scale
+    g, loss = net.grad(X, t, 0.9)
+    g = g.cpu().numpy()
+    g_ref, l_ref = omlp.grad(p, X, t, 0.9, mean.astype(np.float64), std.astype(np.float64),
+                             n_in, hid)
+    assert abs(float(loss.item()) - l_ref) <= 2e-2 * abs(l_ref) + 1e-4
+    cut = _blocks(n_in, hid)
+    for a, b in zip(cut[:-1], cut[1:]):
+        ga, gr = g[a:b], g_ref[a:b]
+        nr = np.linalg.norm(gr)
+        if nr < 1e-9:
+            assert np.linalg.norm(ga) < 1e-6
+            continue
+        cos = float(ga @ gr / (np.linalg.norm(ga) * nr))
+        assert cos > 0.995, (a, b, cos)
+        assert np.linalg.norm(ga - gr) <= 5e-2 * nr, (a, b)
+
+
+def test_training_reduces_the_loss():
+    net = sinnamon.MLP(sinnamon.KP_FEATURES, 64, seed=1)
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.normal(0, 1, (2048, sinnamon.KP_FEATURES)).astype(np.float32)).cuda()
+    w = rng.normal(0, 1, sinnamon.KP_FEATURES).astype(np.float32)
+    t = (X.cpu().numpy() @ w).astype(np.float32)
+    t = torch.from_numpy(t).cuda()
+    first = float(net.train_step(X, t, 0.5, 1e-2).item())
+    for _ in range(200):
+        last = float(net.train_step(X, t, 0.5, 1e-2).item())
+    assert last < 0.2 * first
+
+
+def test_features_match_their_definition():
+    w = synth.scaled(synth.WORKLOADS["text"], 5000, n=3000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=40)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=1024)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    ix.delete(np.arange(0, 5000, 7, dtype=np.int32))  # tombstones still count
+    F = ix.kp_features(qs.indptr.astype(np.int64), qs.indices.astype(np.int32),
+                       qs.values).cpu().numpy()
+    lens = np.bincount(docs.indices[docs.values != 0], minlength=w.n)
+    for r in range(qs.rows):
+        i, v = qs.row(r)
+        keep = v != 0
+        i, v = i[keep], v[keep].astype(np.float64)
+        assert abs(F[r, 0] - np.log2(1 + i.size)) < 1e-5
+        assert abs(F[r, 1] - np.abs(v).sum()) < 1e-4 * (1 + np.abs(v).sum())
+        assert abs(F[r, 2] - np.sqrt((v * v).sum())) < 1e-4 * (1 + np.sqrt((v * v).sum()))
+        order = np.lexsort((i, -np.abs(v)))[:16]
+        want = np.zeros(16)
+        want[:order.size] = np.log2(1 + lens[i[order]])
+        np.testing.assert_allclose(F[r, 3:], want, rtol=1e-5, atol=1e-5)
+
+
+def test_labels_match_the_oracle():
+    """The 9th smallest approximate rank of the exact top 10, from the GPU's
+    own scores, equals the same quantity from the FP64 oracle (up to fp32
+    near-ties in the approximate order)."""
+    w = synth.scaled(synth.WORKLOADS["text"], 20000, n=5000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=60)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=2048)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    kp, cert, ex_ids = kprime.labels(ix, qs, cap=20000)
+    assert cert.all()  # every live id is a candidate here
+    ora = oracle.OracleIndex(w.n, w.m, w.h)
+    ora.insert(docs.indptr, docs.indices, docs.values)
+    ex = ora.exact_topk(qs.indptr, qs.indices, qs.values, k=10)
+    agree = 0
+    for r in range(qs.rows):
+        qi, qv = qs.row(r)
+        approx = ora.scores(qi, qv)
+        order = np.lexsort((np.arange(approx.size), -approx))
+        rank = np.empty(approx.size, np.int64)
+        rank[order] = np.arange(1, approx.size + 1)
+        want = np.sort(rank[ex["ids"][r].astype(np.int64)])[8]
+        agree += int(kp[r] == want)
+        assert abs(kp[r] - want) <= max(3, 0.02 * want), (r, kp[r], want)
+        assert len(set(ex_ids[r]) & set(ex["ids"][r].astype(np.int64))) >= 9
+    assert agree >= 0.9 * qs.rows
+
+
+def test_learned_kprime_beats_fixed_kprime():
+    """Trained on the method's own labels, the network keeps recall@10 >= 0.9
+    with a much smaller mean k' than the fixed fallback of 1000."""
+    w = synth.scaled(synth.WORKLOADS["text"], 100_000)
+    docs = synth.make_docs(w)
+    train_q = synth.make_queries(w, n_q=4000, seed=3000)
+    test_q = synth.make_queries(w, n_q=400, seed=3001)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=4096)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    kp_train, cert, _ = kprime.labels(ix, train_q, cap=20000)
+    assert cert.mean() > 0.95
+    net = kprime.train(ix, train_q, kp_train, epochs=40, batch=1024)
+    _, _, ex_test = kprime.labels(ix, test_q, cap=20000)
+    res = kprime.evaluate(ix, net, test_q, ex_test, fixed=1000)
+    assert res["recall_learned"] >= 0.9, res
+    assert res["mean_kprime_learned"] < 0.5 * res["fixed_kprime"], res
+    # the learned search equals sinn_search_kp at the k' it chose
+    ip, ii = test_q.indptr.astype(np.int64), test_q.indices.astype(np.int32)
+    ids_l, sc_l, kps = ix.search_learned(net, ip, ii, test_q.values, 10, 10, 20000)
+    ids_k, sc_k = ix.search(ip, ii, test_q.values, k=10, k_prime=kps.cpu().numpy(),
+                            k_prime_max=20000)
+    assert np.array_equal(ids_l.cpu().numpy(), ids_k.cpu().numpy())
