@@ -3,9 +3,12 @@
 
 One step = one pass of the whole path over one batch of synthetic input:
 delete D live vectors (Sec. 4.3), insert D new ones (Alg. 5; they reuse the
-freed ids), then search a batch of Q queries (Alg. 6 + Alg. 7).  The metric is
-queries/s (Q per step); recall@10 against the FP64 exact top-10 is measured on
-the same index and reported beside it.
+freed ids), then search a batch of Q queries (Alg. 6 + Alg. 7) with k' chosen
+per query by the learned network (trained before timing on the method's own
+labels; --fixed-kprime uses k' = 1000 instead).  The metric is queries/s (Q
+per step); recall@10 against the FP64 exact top-10 is measured on the same
+index and reported beside it, as are the plain baseline (one query per call,
+fixed k') and the batched fixed-k' search.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -28,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "queries/s at recall@10>=0.9 (batched search, fixed k'=1000 fallback)"
+METRIC = "queries/s at recall@10>=0.9 (batched search with learned per-query k')"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -309,6 +312,22 @@ def run_ours(args):
     log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
     cap, tiles = st["capacity"], st["capacity"] // st["tile_docs"]
 
+    # the learned k' (trained before timing, on labels the method generates)
+    mlp, kp_info = None, None
+    if not args.fixed_kprime:
+        from paper_2301_10622_gb300 import kprime, synth
+        t0 = time.time()
+        tq = cached(f"{w.name}_train_{args.train_queries}", lambda: synth.make_queries(
+            w, n_q=args.train_queries, seed=3000))
+        kp_train, cert, _ = kprime.labels(ix, tq, k=k, cap=args.kp_cap)
+        mlp = kprime.train(ix, tq, kp_train, k=k, epochs=args.epochs)
+        kp_info = {"train_queries": tq.rows, "label_cap": args.kp_cap, "search_cap": args.kp_max,
+                   "certified_labels": float(cert.mean()),
+                   "label_median": float(np.median(kp_train)),
+                   "label_p90": float(np.percentile(kp_train, 90)),
+                   "train_seconds": time.time() - t0}
+        log(f"k' network trained: {kp_info}")
+
     # device-resident step inputs
     g_qip = torch.from_numpy(qs.indptr.astype(np.int64)).to(dev)
     g_qix = torch.from_numpy(qs.indices.astype(np.int32)).to(dev)
@@ -327,15 +346,23 @@ def run_ours(args):
                       torch.from_numpy(p.indices.astype(np.int32)).to(dev),
                       torch.from_numpy(p.values).to(dev), p))
     new_ids = torch.empty(args.churn, dtype=torch.int32, device=dev)
+    out_kp = torch.empty(qs.rows, dtype=torch.int32, device=dev)
     h = ix.handle
     executed = []
+
+    def search(qip, qix, qv, oids, osc):
+        if mlp is None:
+            sinnamon.sinn_search(h, qip, qix, qv, k, kp, oids, osc)
+        else:
+            sinnamon.sinn_search_learned(h, mlp.handle, qip, qix, qv, k, k, args.kp_max, oids,
+                                         osc, out_kp)
 
     def step(si):
         executed.append(si)
         sinnamon.sinn_delete(h, dels[si])
         ip, ii, vv, _ = parts[si]
         sinnamon.sinn_insert(h, ip, ii, vv, new_ids)
-        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, out_ids, out_sc)
+        search(g_qip, g_qix, g_qv, out_ids, out_sc)
 
     for si in range(args.warmup):
         step(si)
@@ -393,8 +420,13 @@ def run_ours(args):
                        torch.from_numpy(p.indices.astype(np.int32)).pin_memory(),
                        torch.from_numpy(p.values).pin_memory(),
                        torch.from_numpy(dels[si + nsteps].cpu().numpy()).pin_memory())
-        qidx_pin = torch.from_numpy(qs.indices).pin_memory()
+        qidx_pin = torch.from_numpy(qs.indices.view(np.int32)).pin_memory()
         qval_pin = torch.from_numpy(qs.values).pin_memory()
+        qip_pin = torch.from_numpy(qs.indptr.astype(np.int64)).pin_memory()
+        e_ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
+        e_sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
+        ids_pin = torch.empty((qs.rows, k), dtype=torch.int32).pin_memory()
+        sc_pin = torch.empty((qs.rows, k), dtype=torch.float32).pin_memory()
         hid_pin = torch.empty(args.churn, dtype=torch.int32).pin_memory()
         torch.cuda.synchronize()
         e_times = []
@@ -408,8 +440,16 @@ def run_ours(args):
                                 pvv.to(dev, non_blocking=True))
             sinnamon.sinn_insert(h, d_ip, d_ii, d_vv, new_ids)
             hid_pin.copy_(new_ids, non_blocking=True)
-            sinnamon.sinn_search_host(h, h_qip, qidx_pin.numpy(), qval_pin.numpy(), k, kp,
-                                      h_ids, h_sc)
+            if mlp is None:
+                sinnamon.sinn_search_host(h, h_qip, qidx_pin.numpy(), qval_pin.numpy(), k, kp,
+                                          h_ids, h_sc)
+            else:
+                e_ip = qip_pin.to(dev, non_blocking=True)
+                e_ix = qidx_pin.to(dev, non_blocking=True)
+                e_v = qval_pin.to(dev, non_blocking=True)
+                search(e_ip, e_ix.view(torch.int32), e_v, e_ids, e_sc)
+                ids_pin.copy_(e_ids, non_blocking=True)
+                sc_pin.copy_(e_sc, non_blocking=True)
             torch.cuda.synchronize()
             e_times.append(time.perf_counter() - t0)
         e2e_s = float(np.median(e_times))
@@ -446,13 +486,29 @@ def run_ours(args):
         extras["plain"] = {"qps": npl / plain_s, "p50_ms": float(np.percentile(lat, 50)),
                            "p99_ms": float(np.percentile(lat, 99)), "queries": npl}
 
-        # batched latency and recall on the (post-churn) index vs a fresh oracle
+        # batched latency (learned, as timed) and the batched fixed-k' search
         ev0.record()
-        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, out_ids, out_sc)
+        search(g_qip, g_qix, g_qv, out_ids, out_sc)
         ev1.record()
         torch.cuda.synchronize()
         extras["batched"] = {"qps": value / world, "batch_ms": ev0.elapsed_time(ev1),
                              "p50_ms": ev0.elapsed_time(ev1), "p99_ms": ev0.elapsed_time(ev1)}
+        fx_ids = torch.empty_like(out_ids)
+        fx_sc = torch.empty_like(out_sc)
+        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids, fx_sc)
+        torch.cuda.synchronize()
+        ev0.record()
+        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids, fx_sc)
+        ev1.record()
+        torch.cuda.synchronize()
+        extras["batched_fixed_kprime"] = {"qps": qs.rows / (ev0.elapsed_time(ev1) / 1000.0),
+                                          "k_prime": kp}
+        if mlp is not None:
+            kps = out_kp.float()
+            extras["learned_kprime"] = dict(kp_info, mean=float(kps.mean().item()),
+                                            p50=float(kps.median().item()),
+                                            p90=float(kps.quantile(0.9).item()),
+                                            max=float(kps.max().item()))
         if not args.skip_oracle:
             import oracle
             oracle.build()
@@ -463,8 +519,12 @@ def run_ours(args):
             samp = qs.slice(0, nr)
             gids = out_ids.cpu().numpy()[:nr]
             extras["recall_at_10"] = recall_at_10(ora, samp, gids, os.cpu_count() or 1)
+            extras["recall_at_10_fixed_kprime"] = recall_at_10(
+                ora, samp, fx_ids.cpu().numpy()[:nr], os.cpu_count() or 1)
             extras["recall_queries"] = nr
             extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
+        if args.serve_seconds > 0:
+            extras["serving"] = run_serving(args, w, ix, qs, docs.rows, mlp, k, kp)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -482,14 +542,43 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "recall_at_10": extras.get("recall_at_10"),
         "recall_queries": extras.get("recall_queries"),
+        "recall_at_10_fixed_kprime": extras.get("recall_at_10_fixed_kprime"),
         "plain": extras.get("plain"),
         "batched": extras.get("batched"),
+        "batched_fixed_kprime": extras.get("batched_fixed_kprime"),
+        "learned_kprime": extras.get("learned_kprime"),
+        "serving": extras.get("serving"),
         "phases_ms_per_step": {p: v / args.steps for p, v in tm["ms"].items()},
         "index": st,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_serving(args, w, ix, qs, n_live, mlp, k, kp):
+    """Continuous-batching serving on the bench's index after the timed steps:
+    Poisson arrivals of inserts, deletes and queries (rates per second) for
+    a fixed wall time; every id below n_live is live at this point (each
+    step re-inserted as many vectors as it deleted, into the freed ids)."""
+    from paper_2301_10622_gb300 import serving, synth
+    r_ins, r_del, r_q = (float(x) for x in args.serve_rates.split(","))
+    n_pool = int(r_ins * args.serve_seconds * 1.1) + 64
+    spool = cached(f"{w.name}_serve_{n_pool}", lambda: synth.make_docs(w, n_docs=n_pool,
+                                                                       seed=5001))
+    reqs = serving.poisson_stream(args.serve_seconds, {"insert": r_ins, "delete": r_del,
+                                                       "query": r_q}, spool.rows, qs.rows)
+    srv = serving.Server(ix, qs, spool, np.arange(n_live), slots=args.serve_slots,
+                         slot_bytes=int(args.serve_slot_gb * (1 << 30)), k=k, k_prime=kp,
+                         mlp=mlp, kp_max=args.kp_max, mutation_delay=args.serve_delay)
+    stats, results, _ = srv.serve(reqs, max_wall=3 * args.serve_seconds + 5)
+    stats.update({"rates_per_s": {"insert": r_ins, "delete": r_del, "query": r_q},
+                  "seconds": args.serve_seconds, "start_docs": n_live,
+                  "learned_kprime": mlp is not None, "mutation_delay_s": args.serve_delay,
+                  "mean_kprime": float(np.mean([v[2] for v in results.values()]))
+                  if results else None})
+    log(f"serving: {stats}")
+    return stats
 
 
 def reconstruct(docs, parts, dels, executed):
@@ -543,6 +632,17 @@ def main():
     ap.add_argument("--recall-queries", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-oracle", action="store_true")
+    ap.add_argument("--fixed-kprime", action="store_true")
+    ap.add_argument("--train-queries", type=int, default=20000)
+    ap.add_argument("--kp-cap", type=int, default=20000)
+    ap.add_argument("--kp-max", type=int, default=4096)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rates", default="20000,2000,5000",
+                    help="inserts,deletes,queries per second")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slot-gb", type=float, default=1.0)
+    ap.add_argument("--serve-delay", type=float, default=0.005)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -154,6 +154,25 @@ int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr, const uint32_t
                         const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
                         uint32_t *out_ids, float *out_scores, void *stream);
 
+/* ---- Search contexts: concurrent searches of one index ------------------
+ * A context owns the device scratch of one search, so searches in different
+ * contexts may run at the same time on different streams (a search only
+ * reads the index).  Inserts and deletes of the index must be ordered
+ * against every search in flight (they change the index in place).
+ * scratch_bytes >= 1 MiB; sinn_ctx_query_bytes gives the scratch one query
+ * needs at a given k'; a search processes as many queries at a time as fit
+ * (SINN_ESCRATCH if one does not). */
+typedef struct sinn_ctx sinn_ctx;
+int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx **out);
+int sinn_ctx_destroy(sinn_ctx *c);
+uint64_t sinn_ctx_query_bytes(sinn_ctx *c, uint32_t k_prime_max);
+
+/* sinn_search (k_prime == NULL: k' = k_prime_max for every query) or
+ * sinn_search_kp (device k_prime[n_q]) on the context's scratch. */
+int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint32_t *q_indices,
+                    const float *q_values, uint32_t n_q, uint32_t k, const uint32_t *k_prime,
+                    uint32_t k_prime_max, uint32_t *out_ids, float *out_scores, void *stream);
+
 /* Wait for the stream, then return and clear the sticky device error
  * (SINN_OK if none; SINN_EINVAL for a malformed query; SINN_EDEVICE for an
  * internal kernel error). */

@@ -78,6 +78,21 @@ int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
                         uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
                         void *stream);
 
+/* Device bytes of the activation buffer sinn_search_learned_ctx needs for
+ * n_q queries. */
+uint64_t sinn_mlp_act_bytes(sinn_mlp *m, uint32_t rows);
+
+/* sinn_search_learned on a search context (sinnamon.h), with the network's
+ * activations in the caller's device buffer act[act_bytes] so that several
+ * contexts can use one network at once.  The network must not be trained
+ * while such searches run. */
+int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m, void *act,
+                            uint64_t act_bytes, const uint64_t *q_indptr,
+                            const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                            uint32_t k, uint32_t k_prime_min, uint32_t k_prime_max,
+                            uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

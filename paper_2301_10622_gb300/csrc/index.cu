@@ -10,7 +10,7 @@
 //   d_tile_dir  tiles x n uint2 per tile t and coordinate j, the container of
 //                               the postings of I[j] with ids in
 //                               [t*T, (t+1)*T): {start, count} in 16-bit words
-//                               of the tile's storage post_t.  count >= T/2:
+//                               of the tile's storage post_t.  count >= T/4:
 //                               a bitmap of T bits (bit d = local id d; a
 //                               deleted posting's bit is cleared); otherwise a
 //                               sorted array of count 16-bit local ids (bit 15
@@ -20,8 +20,9 @@
 //                               split of the Roaring containers the paper
 //                               uses for its lists, per tile of T ids; the
 //                               threshold is set where scoring a bitmap by
-//                               sweeping all T ids costs no more per posting
-//                               than walking an array.
+//                               sweeping all T ids (4 ids per 16-byte load)
+//                               costs no more per posting than walking an
+//                               array.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -143,204 +144,196 @@ __global__ void k_set_live(const uint32_t *__restrict__ ids, uint32_t cnt, uint3
   else atomicAnd(&live[id >> 5], ~(1u << (id & 31)));
 }
 
-// Block-wide exclusive scan of a[0..cnt) in place (any memory space), returning
-// the total.  Every thread of the block must call it.  Uses smem_part
-// (blockDim.x/32 + 1 words).
-__device__ uint32_t block_excl_scan(uint32_t *a, uint32_t cnt, uint32_t *smem_part) {
-  const uint32_t nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t per = (cnt + nt - 1) / nt;
-  const uint32_t b = min(cnt, tid * per), e = min(cnt, b + per);
-  uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += a[i];
-  uint32_t x = s;
+// Block-wide exclusive scan of one value per thread; *total receives the
+// sum.  Every thread of the block must call it; part holds 33 words.
+__device__ uint32_t block_scan_value(uint32_t x, uint32_t *part, uint32_t *total) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = x;
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-    if (lane >= (uint32_t)d) x += y;
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= (uint32_t)d) inc += y;
   }
-  if (lane == 31) smem_part[wid] = x;
+  if (lane == 31) part[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    uint32_t nw = nt >> 5;
-    uint32_t v = lane < nw ? smem_part[lane] : 0, z = v;
+    const uint32_t v = lane < nw ? part[lane] : 0u;
+    uint32_t z = v;
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, d);
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, d);
       if (lane >= (uint32_t)d) z += y;
     }
-    if (lane < nw) smem_part[lane] = z - v;  // exclusive warp offsets
-    if (lane == nw - 1) smem_part[32] = z;   // total
+    if (lane < nw) part[lane] = z - v;
+    if (lane == 31) part[32] = z;
   }
   __syncthreads();
-  uint32_t run = smem_part[wid] + x - s;
-  for (uint32_t i = b; i < e; ++i) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
-  }
-  uint32_t total = smem_part[32];
+  const uint32_t r = part[wid] + inc - x;
+  *total = part[32];
   __syncthreads();
-  return total;
+  return r;
 }
 
-// Rebuild the postings of one tile per block from the vector store: for every
-// live id of the tile and each of its non-zero coordinates j, the local id is
-// placed in container (tile, j).  Array containers come out sorted by local
-// id because entries are placed in id order (a stable counting sort by
-// coordinate); bitmap containers take their bits in any order.  Tombstones
-// disappear: only live vectors contribute.
-//   E     scratch of the block: one (coordinate<<16 | local id) entry per stored
-//         entry of the tile's live vectors, in id order (skipped entries are
-//         all-ones)
-//   dpref scratch: T+1 per-id entry offsets into E
+// Rebuild of the postings of a group of tiles from the vector store, in four
+// passes.  For every live id of a tile and each of its non-zero coordinates
+// j, the tile-local id lands in container (tile, j): a bitmap of T bits when
+// the tile has at least T >> SINN_BITMAP_SHIFT postings of j, else an array
+// of 16-bit local ids in ascending order.  Tombstones disappear: only live
+// vectors contribute.
+//   count   one warp per id slot: postings per (tile, coordinate)
+//   plan    one block per tile: container kinds, array starts by a scan in
+//           coordinate order, bitmap slots from the back of the storage in
+//           the same order; the directory is written and the bitmaps zeroed
+//   scatter one warp per id slot: bitmap bits, array slots by atomic cursors
+//   sort    one warp per (tile, coordinate): each array is put in ascending
+//           order through a bitmap of the tile's local ids
 struct RebuildArgs {
-  const uint32_t *tiles;      // tile index per block
-  uint16_t *const *new_post;  // storage per block
-  const uint64_t *post_cap;   // storage size per block (16-bit words, multiple of T/16)
-  const uint64_t *e_off;      // offset of each block's E region
-  uint64_t *E;
-  uint32_t *dpref;            // (T+1) per block
-  uint32_t *out_len;          // postings written per block
+  const uint32_t *tiles;      // tile per group entry
+  uint16_t *const *new_post;  // storage per group entry
+  const uint64_t *post_cap;   // storage size per entry (16-bit words, multiple of T/16)
+  uint32_t *cnt;              // n per entry: counts, then array cursors
+  uint32_t *out_len;          // postings per entry
+  uint32_t nb, n, T, log2T;
 };
 
-__global__ void __launch_bounds__(512)
-    k_tile_rebuild(RebuildArgs a, const uint32_t *__restrict__ live,
-                   const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
-                   const uint2 *__restrict__ fwd, uint2 *__restrict__ tile_dir,
-                   uint16_t **tile_post, uint32_t n, uint32_t T, uint32_t log2T, uint32_t W) {
-  extern __shared__ uint32_t sm[];
-  uint32_t *cursor = sm;                 // W: counts, then array starts / cursors
-  uint32_t *isbm = sm + W;               // W/32: bitmap flags
+__global__ void __launch_bounds__(256)
+    k_rb_count(RebuildArgs a, const uint32_t *__restrict__ live,
+               const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
+               const uint2 *__restrict__ fwd) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+       w < (uint64_t)a.nb * a.T; w += nwarps) {
+    const uint32_t i = (uint32_t)(w >> a.log2T), d = (uint32_t)(w & (a.T - 1));
+    const uint64_t id = ((uint64_t)a.tiles[i] << a.log2T) + d;
+    if (!sinn_is_live(live, id)) continue;
+    const uint64_t fo = fwd_off[id];
+    const uint32_t nz = fwd_nnz[id];
+    uint32_t *cnt = a.cnt + (uint64_t)i * a.n;
+    for (uint32_t e = lane; e < nz; e += 32) {
+      const uint2 pr = fwd[fo + e];
+      if ((pr.y & 0x7FFFFFFFu) != 0u) atomicAdd(&cnt[pr.x], 1u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_rb_plan(RebuildArgs a, uint2 *__restrict__ tile_dir, uint16_t **tile_post, uint32_t *err) {
   __shared__ uint32_t part[33];
-  __shared__ uint32_t s_nbm, s_posts;
-  const uint32_t W16 = T >> 4;           // 16-bit words of one bitmap (T bits)
-  const uint32_t BMIN = T >> 1;          // postings from which a container is a bitmap
-  const uint32_t t = a.tiles[blockIdx.x];
-  uint16_t *post = a.new_post[blockIdx.x];
-  const uint64_t cap16 = a.post_cap[blockIdx.x];
-  uint64_t *E = a.E + a.e_off[blockIdx.x];
-  uint32_t *dpref = a.dpref + (uint64_t)blockIdx.x * (T + 1);
+  const uint32_t i = blockIdx.x, t = a.tiles[i], n = a.n;
+  const uint32_t W16 = a.T >> 4, BMIN = a.T >> SINN_BITMAP_SHIFT;
+  uint16_t *post = a.new_post[i];
+  const uint64_t cap16 = a.post_cap[i];
+  uint32_t *cnt = a.cnt + (uint64_t)i * n;
   uint2 *dir = tile_dir + (uint64_t)t * n;
-  const uint64_t id0 = (uint64_t)t << log2T;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-
-  // phase 1: entries per id, then offsets into E
-  for (uint32_t d = tid; d < T; d += blockDim.x)
-    dpref[d] = sinn_is_live(live, id0 + d) ? fwd_nnz[id0 + d] : 0u;
-  if (tid == 0) {
-    s_nbm = 0;
-    s_posts = 0;
+  // each thread owns a contiguous run of coordinates
+  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+  const uint32_t c0 = min(n, threadIdx.x * per), c1 = min(n, c0 + per);
+  uint32_t sa = 0, sb = 0, st = 0;
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t v = cnt[c];
+    st += v;
+    if (v >= BMIN) sb++;
+    else sa += v;
   }
-  __syncthreads();
-  const uint32_t total = block_excl_scan(dpref, T, part);
-  if (tid == 0) dpref[T] = total;
-  __syncthreads();
-
-  // phase 2: fill E in id order (one warp per id)
-  for (uint32_t d = wid; d < T; d += nw) {
-    const uint32_t c0 = dpref[d], c1 = dpref[d + 1];
-    if (c1 == c0) continue;
-    const uint64_t fo = fwd_off[id0 + d];
-    for (uint32_t e = lane; e < c1 - c0; e += 32) {
-      uint2 pr = fwd[fo + e];
-      bool nz = (pr.y & 0x7FFFFFFFu) != 0u;
-      E[c0 + e] = nz ? (((uint64_t)pr.x << 16) | d) : ~0ull;
+  uint32_t tot_a, tot_b, tot_t;
+  uint32_t run_a = block_scan_value(sa, part, &tot_a);
+  uint32_t run_b = block_scan_value(sb, part, &tot_b);
+  (void)block_scan_value(st, part, &tot_t);
+  if ((uint64_t)tot_a + (uint64_t)tot_b * W16 > cap16) {  // cannot happen if sized right
+    if (threadIdx.x == 0) atomicOr(err, SINN_DERR_INTERNAL);
+    return;
+  }
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t v = cnt[c];
+    if (v == 0) {
+      dir[c] = make_uint2(0u, 0u);
+    } else if (v >= BMIN) {
+      dir[c] = make_uint2((uint32_t)(cap16 - (uint64_t)(run_b + 1) * W16), v);
+      run_b++;
+    } else {
+      dir[c] = make_uint2(run_a, v);
+      cnt[c] = run_a;
+      run_a += v;
     }
   }
-  __syncthreads();
-
-  // phases 3-7 per window of W coordinates
-  uint32_t base = 0;
-  for (uint32_t w0 = 0; w0 < n; w0 += W) {
-    const uint32_t wn = min(W, n - w0);
-    for (uint32_t i = tid; i < wn; i += blockDim.x) cursor[i] = 0;
-    for (uint32_t i = tid; i < (wn + 31) / 32; i += blockDim.x) isbm[i] = 0;
-    __syncthreads();
-    // 3: postings per coordinate
-    for (uint32_t e = tid; e < total; e += blockDim.x) {
-      const uint64_t key = E[e];
-      const uint32_t c = (uint32_t)(key >> 16);
-      if (key != ~0ull && c >= w0 && c < w0 + wn) atomicAdd(&cursor[c - w0], 1u);
-    }
-    __syncthreads();
-    // 4: containers with at least T/2 postings become bitmaps, claimed from
-    //    the back of the storage; they take no array space
-    const uint32_t nbm0 = s_nbm;
-    uint32_t wposts = 0;
-    for (uint32_t i = tid; i < wn; i += blockDim.x) {
-      const uint32_t cnt = cursor[i];
-      wposts += cnt;
-      if (cnt >= BMIN) {
-        const uint32_t k = atomicAdd(&s_nbm, 1u);
-        dir[w0 + i] = make_uint2((uint32_t)(cap16 - (uint64_t)(k + 1) * W16), cnt);
-        atomicOr(&isbm[i >> 5], 1u << (i & 31));
-        cursor[i] = 0;
-      } else if (cnt == 0) {
-        dir[w0 + i] = make_uint2(0u, 0u);
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) wposts += __shfl_xor_sync(0xFFFFFFFFu, wposts, o);
-    if (lane == 0 && wposts) atomicAdd(&s_posts, wposts);
-    __syncthreads();
-    {  // zero the bitmaps claimed in this window
-      const uint32_t nbm1 = s_nbm;
-      uint32_t *z = (uint32_t *)(post + (cap16 - (uint64_t)nbm1 * W16));
-      const uint64_t words = (uint64_t)(nbm1 - nbm0) * (W16 / 2);
-      for (uint64_t i = tid; i < words; i += blockDim.x) z[i] = 0u;
-    }
-    // 5: array containers: starts by an exclusive scan of their sizes
-    const uint32_t wtot = block_excl_scan(cursor, wn, part);
-    for (uint32_t i = tid; i < wn; i += blockDim.x) {
-      if ((isbm[i >> 5] >> (i & 31)) & 1u) continue;
-      const uint32_t st = cursor[i], nx = i + 1 < wn ? cursor[i + 1] : wtot;
-      if (nx > st) dir[w0 + i] = make_uint2(base + st, nx - st);
-    }
-    __syncthreads();
-    for (uint32_t i = tid; i < wn; i += blockDim.x) cursor[i] += base;
-    __syncthreads();
-    // 6: bitmap bits, in any order (all threads)
-    for (uint32_t e = tid; e < total; e += blockDim.x) {
-      const uint64_t key = E[e];
-      const uint32_t c = (uint32_t)(key >> 16);
-      if (key == ~0ull || c < w0 || c >= w0 + wn) continue;
-      const uint32_t i = c - w0;
-      if (!((isbm[i >> 5] >> (i & 31)) & 1u)) continue;
-      const uint32_t d = (uint32_t)(key & 0xFFFFu);
-      uint32_t *bm = (uint32_t *)(post + dir[c].x);
-      atomicOr(bm + (d >> 5), 1u << (d & 31));
-    }
-    // 7: array containers: stable scatter by one warp, entries in id order
-    if (wid == 0) {
-      const uint32_t lt = (1u << lane) - 1u;
-      for (uint32_t e0 = 0; e0 < total; e0 += 128) {
-        uint64_t kk[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t e = e0 + u * 32 + lane;
-          kk[u] = e < total ? E[e] : ~0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t c = (uint32_t)(kk[u] >> 16);
-          const uint32_t i = c - w0;
-          const bool ok = kk[u] != ~0ull && c >= w0 && c < w0 + wn &&
-                          !((isbm[i >> 5] >> (i & 31)) & 1u);
-          const uint32_t okm = __ballot_sync(0xFFFFFFFFu, ok);
-          if (ok) {
-            const uint32_t grp = __match_any_sync(okm, c);
-            const uint32_t rank = __popc(grp & lt);
-            const uint32_t pos = cursor[i];
-            post[pos + rank] = (uint16_t)(kk[u] & 0xFFFFu);
-            if ((grp >> lane) == 1u) cursor[i] = pos + __popc(grp);
-          }
-          __syncwarp();
-        }
-      }
-    }
-    base += wtot;
-    __syncthreads();
-  }
-  if (tid == 0) {
+  uint32_t *z = (uint32_t *)(post + (cap16 - (uint64_t)tot_b * W16));
+  const uint64_t words = (uint64_t)tot_b * (W16 / 2);
+  for (uint64_t k = threadIdx.x; k < words; k += blockDim.x) z[k] = 0u;
+  if (threadIdx.x == 0) {
+    a.out_len[i] = tot_t;
     tile_post[t] = post;
-    a.out_len[blockIdx.x] = s_posts;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_rb_scatter(RebuildArgs a, const uint32_t *__restrict__ live,
+                 const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
+                 const uint2 *__restrict__ fwd, const uint2 *__restrict__ tile_dir) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t BMIN = a.T >> SINN_BITMAP_SHIFT;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+       w < (uint64_t)a.nb * a.T; w += nwarps) {
+    const uint32_t i = (uint32_t)(w >> a.log2T), d = (uint32_t)(w & (a.T - 1));
+    const uint32_t t = a.tiles[i];
+    const uint64_t id = ((uint64_t)t << a.log2T) + d;
+    if (!sinn_is_live(live, id)) continue;
+    const uint64_t fo = fwd_off[id];
+    const uint32_t nz = fwd_nnz[id];
+    uint32_t *cur = a.cnt + (uint64_t)i * a.n;
+    const uint2 *dir = tile_dir + (uint64_t)t * a.n;
+    uint16_t *post = a.new_post[i];
+    for (uint32_t e = lane; e < nz; e += 32) {
+      const uint2 pr = fwd[fo + e];
+      if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
+      const uint2 de = dir[pr.x];
+      if (de.y >= BMIN) {
+        atomicOr((uint32_t *)(post + de.x) + (d >> 5), 1u << (d & 31));
+      } else {
+        post[atomicAdd(&cur[pr.x], 1u)] = (uint16_t)d;
+      }
+    }
+  }
+}
+
+// Dynamic shared memory: T/32 words per warp.
+__global__ void __launch_bounds__(256)
+    k_rb_sort(RebuildArgs a, const uint2 *__restrict__ tile_dir) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t lane = threadIdx.x & 31, words = a.T >> 5, wpl = words >> 5;
+  const uint32_t BMIN = a.T >> SINN_BITMAP_SHIFT;
+  uint32_t *bm = sm + (threadIdx.x >> 5) * words;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+       w < (uint64_t)a.nb * a.n; w += nwarps) {
+    const uint32_t i = (uint32_t)(w / a.n), c = (uint32_t)(w % a.n);
+    const uint2 de = tile_dir[(uint64_t)a.tiles[i] * a.n + c];
+    if (de.y < 2 || de.y >= BMIN) continue;  // warp-uniform
+    uint16_t *seg = a.new_post[i] + de.x;
+    for (uint32_t j = lane; j < words; j += 32) bm[j] = 0u;
+    __syncwarp();
+    for (uint32_t e = lane; e < de.y; e += 32) {
+      const uint32_t d = seg[e] & 0x7FFFu;
+      atomicOr(&bm[d >> 5], 1u << (d & 31));
+    }
+    __syncwarp();
+    const uint32_t w0 = lane * wpl;
+    uint32_t mine = 0;
+    for (uint32_t j = 0; j < wpl; ++j) mine += __popc(bm[w0 + j]);
+    uint32_t inc = mine;
+    for (int s = 1; s < 32; s <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, s);
+      if (lane >= (uint32_t)s) inc += y;
+    }
+    uint32_t pos = inc - mine;
+    for (uint32_t j = 0; j < wpl; ++j) {
+      uint32_t bits = bm[w0 + j];
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        seg[pos++] = (uint16_t)(((w0 + j) << 5) + b);
+        bits &= bits - 1;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -359,7 +352,7 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
   if (w >= cnt) return;
   const uint32_t id = ids[w];
   const uint32_t t = id >> log2T;
-  const uint32_t BMIN = (1u << log2T) >> 1;
+  const uint32_t BMIN = (1u << log2T) >> SINN_BITMAP_SHIFT;
   const uint32_t d = id & ((1u << log2T) - 1u);
   const uint2 *dir = tile_dir + (uint64_t)t * n;
   uint16_t *post = tile_post[t];
@@ -701,29 +694,21 @@ extern "C" int sinn_sync(sinn_index *ix, void *stream) {
   return SINN_OK;
 }
 
-// Rebuild the postings of the given tiles (sorted, unique) from the store.
-static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s) {
-  if (tiles.empty()) return SINN_OK;
-  const uint32_t nb = (uint32_t)tiles.size();
+// Rebuild the postings of a group of tiles (sorted, unique) from the store.
+static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cudaStream_t s) {
   const uint64_t W16 = ix->T / 16;
-  std::vector<uint64_t> eoff(nb), pcap(nb);
-  uint64_t etot = 0;
-  for (uint32_t i = 0; i < nb; ++i) {
-    eoff[i] = etot;
-    etot += ix->tile_nnz[tiles[i]];
+  std::vector<uint64_t> pcap(nb);
+  for (uint32_t i = 0; i < nb; ++i)
     // containers never need more words than postings; bitmaps sit on T/16-word
     // boundaries counted from the end
     pcap[i] = std::max<uint64_t>((ix->tile_nnz[tiles[i]] + W16 - 1) / W16 * W16, W16);
-  }
-  // scratch: E, dpref, tiles, ptrs, caps, eoff, out_len
-  size_t o_E = 0;
-  size_t o_dp = o_E + etot * 8;
-  size_t o_tl = (o_dp + (uint64_t)nb * (ix->T + 1) * 4 + 15) / 16 * 16;
-  size_t o_pt = (o_tl + nb * 4 + 15) / 16 * 16;
-  size_t o_pc = o_pt + nb * 8;
-  size_t o_eo = o_pc + nb * 8;
-  size_t o_ln = o_eo + nb * 8;
-  size_t bytes = o_ln + nb * 4;
+  // scratch: counts, tiles, storage pointers, storage sizes, lengths
+  const size_t o_cn = 0;
+  const size_t o_tl = o_cn + (size_t)nb * ix->n * 4;
+  const size_t o_pt = (o_tl + (size_t)nb * 4 + 15) / 16 * 16;
+  const size_t o_pc = o_pt + (size_t)nb * 8;
+  const size_t o_ln = o_pc + (size_t)nb * 8;
+  const size_t bytes = o_ln + (size_t)nb * 4;
   int st = ensure_iscratch(ix, bytes);
   if (st) return st;
   std::vector<uint16_t *> newp(nb);
@@ -739,38 +724,40 @@ static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cud
       pcap[i] = alloc;
     }
   }
-  size_t hb = nb * (4 + 8 + 8 + 8 + 4);
+  const size_t hb = (size_t)nb * (4 + 8 + 8 + 4);
   CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
   if ((st = sinn_ensure_pinned(ix, hb))) return st;
   char *hp = (char *)ix->pinned;
-  memcpy(hp, tiles.data(), nb * 4);
-  memcpy(hp + nb * 4, newp.data(), nb * 8);
-  memcpy(hp + nb * 12, pcap.data(), nb * 8);
-  memcpy(hp + nb * 20, eoff.data(), nb * 8);
+  memcpy(hp, tiles, (size_t)nb * 4);
+  memcpy(hp + (size_t)nb * 4, newp.data(), (size_t)nb * 8);
+  memcpy(hp + (size_t)nb * 12, pcap.data(), (size_t)nb * 8);
   char *sp = (char *)ix->iscratch;
-  CK(cudaMemcpyAsync(sp + o_tl, hp, nb * 4, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_pt, hp + nb * 4, nb * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_pc, hp + nb * 12, nb * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_eo, hp + nb * 20, nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_tl, hp, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_pt, hp + (size_t)nb * 4, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + o_pc, hp + (size_t)nb * 12, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(sp + o_cn, 0, (size_t)nb * ix->n * 4, s));
   RebuildArgs a;
   a.tiles = (const uint32_t *)(sp + o_tl);
   a.new_post = (uint16_t *const *)(sp + o_pt);
   a.post_cap = (const uint64_t *)(sp + o_pc);
-  a.e_off = (const uint64_t *)(sp + o_eo);
-  a.E = (uint64_t *)(sp + o_E);
-  a.dpref = (uint32_t *)(sp + o_dp);
+  a.cnt = (uint32_t *)(sp + o_cn);
   a.out_len = (uint32_t *)(sp + o_ln);
-  int dev_smem = 0;
-  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device);
-  // W coordinate cursors + W/32 flag words in dynamic shared memory
-  uint32_t W = (uint32_t)((uint64_t)(dev_smem - 4096) * 32 / 132);
-  W = std::min<uint32_t>(ix->n, W & ~31u);
-  size_t smem = (size_t)W * 4 + (size_t)(W + 31) / 32 * 4;
-  CK(cudaFuncSetAttribute(k_tile_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ix->launches++;
-  k_tile_rebuild<<<nb, 512, smem, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz, ix->d_fwd,
-                                       ix->d_tile_dir, ix->d_tile_post, ix->n, ix->T, ix->log2T,
-                                       W);
+  a.nb = nb;
+  a.n = ix->n;
+  a.T = ix->T;
+  a.log2T = ix->log2T;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  const uint64_t cap_blocks = (uint64_t)std::max(1, sms) * 32;
+  const uint64_t slot_blocks = std::min<uint64_t>(((uint64_t)nb * ix->T + 7) / 8, cap_blocks);
+  const uint64_t pair_blocks = std::min<uint64_t>(((uint64_t)nb * ix->n + 7) / 8, cap_blocks);
+  ix->launches += 4;
+  k_rb_count<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
+                                                   ix->d_fwd);
+  k_rb_plan<<<nb, 1024, 0, s>>>(a, ix->d_tile_dir, ix->d_tile_post, ix->d_err);
+  k_rb_scatter<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
+                                                     ix->d_fwd, ix->d_tile_dir);
+  k_rb_sort<<<(unsigned)pair_blocks, 256, (size_t)8 * (ix->T / 32) * 4, s>>>(a, ix->d_tile_dir);
   CK(cudaGetLastError());
   for (uint32_t i = 0; i < nb; ++i) {
     const uint32_t t = tiles[i];
@@ -779,14 +766,29 @@ static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cud
     ix->tile_post_cap[t] = pcap[i];
   }
   std::vector<uint32_t> lens(nb);
-  CK(cudaMemcpyAsync(hp, sp + o_ln, nb * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp, sp + o_ln, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  memcpy(lens.data(), hp, nb * 4);
+  memcpy(lens.data(), hp, (size_t)nb * 4);
   for (uint32_t i = 0; i < nb; ++i) {
     const uint32_t t = tiles[i];
     ix->tile_post_len[t] = lens[i];
     ix->tombstones -= ix->tile_tombs[t];  // a rebuild compacts tombstones away
     ix->tile_tombs[t] = 0;
+  }
+  return SINN_OK;
+}
+
+// Rebuild the postings of the given tiles (sorted, unique), in groups whose
+// per-coordinate counts fit 1 GiB of scratch.
+static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s) {
+  if (tiles.empty()) return SINN_OK;
+  const uint64_t per = (uint64_t)ix->n * 4;
+  const uint32_t g = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>(tiles.size(), (1ull << 30) / per));
+  for (size_t g0 = 0; g0 < tiles.size(); g0 += g) {
+    const uint32_t nb = (uint32_t)std::min<size_t>(g, tiles.size() - g0);
+    int st = rebuild_group(ix, tiles.data() + g0, nb, s);
+    if (st) return st;
   }
   return SINN_OK;
 }
@@ -998,7 +1000,7 @@ extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out,
   std::vector<uint16_t> buf;
   for (uint64_t t = 0; t < nt; ++t) {
     if (de[t].y == 0 || !ix->tile_post[t]) continue;
-    const bool bitmap = de[t].y >= ix->T / 2;
+    const bool bitmap = de[t].y >= (ix->T >> SINN_BITMAP_SHIFT);
     buf.resize(bitmap ? W16 : de[t].y);
     CK(cudaMemcpy(buf.data(), ix->tile_post[t] + de[t].x, buf.size() * 2, cudaMemcpyDeviceToHost));
     auto emit = [&](uint32_t d) {

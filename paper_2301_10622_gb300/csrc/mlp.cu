@@ -354,20 +354,15 @@ struct Acts {
   float *Z1, *H2, *y, *dy, *dZ2, *dH1, *loss;
 };
 
-int ensure_acts(sinn_mlp *m, uint32_t B, Acts *a) {
-  if (B > m->cap) {
-    if (m->act) {
-      CK(cudaDeviceSynchronize());
-      CK(cudaFree(m->act));
-      m->act = nullptr;
-    }
-    const uint32_t c = std::max<uint32_t>(B, 1024);
-    const size_t bytes = (size_t)c * (m->kpad * 2 + m->hid * 2 * 3 + m->hid * 4 * 4 + 16) + 1024;
-    CK(cudaMalloc(&m->act, bytes));
-    m->cap = c;
-  }
-  char *p = (char *)m->act;
-  const size_t c = m->cap;
+// Carve activation buffers for up to cap rows from base (see acts_bytes).
+size_t acts_bytes(const sinn_mlp *m, size_t c) {
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  return r(c * m->kpad * 2) + 3 * r(c * m->hid * 2) + 4 * r(c * m->hid * 4) + 2 * r(c * 4) +
+         r(64);
+}
+
+void carve_acts(const sinn_mlp *m, void *base, size_t c, Acts *a) {
+  char *p = (char *)base;
   auto take = [&](size_t bytes) {
     char *q = p;
     p += (bytes + 255) / 256 * 256;
@@ -384,6 +379,20 @@ int ensure_acts(sinn_mlp *m, uint32_t B, Acts *a) {
   a->y = (float *)take(c * 4);
   a->dy = (float *)take(c * 4);
   a->loss = (float *)take(64);
+}
+
+int ensure_acts(sinn_mlp *m, uint32_t B, Acts *a) {
+  if (B > m->cap) {
+    if (m->act) {
+      CK(cudaDeviceSynchronize());
+      CK(cudaFree(m->act));
+      m->act = nullptr;
+    }
+    const uint32_t c = std::max<uint32_t>(B, 1024);
+    CK(cudaMalloc(&m->act, acts_bytes(m, c)));
+    m->cap = c;
+  }
+  carve_acts(m, m->act, m->cap, a);
   return SINN_OK;
 }
 
@@ -653,4 +662,44 @@ extern "C" int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *
   if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
   return sinn_search_kp(ix, q_indptr, q_indices, q_values, n_q, k, kp, k_prime_max, out_ids,
                         out_scores, stream);
+}
+
+// sinn_search_learned on a context: the network's activations come from a
+// caller buffer (act, act_bytes) so concurrent contexts share one model.
+struct sinn_ctx;
+extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint32_t *q_indices,
+                               const float *q_values, uint32_t n_q, uint32_t k,
+                               const uint32_t *k_prime, uint32_t k_prime_max, uint32_t *out_ids,
+                               float *out_scores, void *stream);
+
+extern "C" uint64_t sinn_mlp_act_bytes(sinn_mlp *m, uint32_t rows) {
+  return m ? acts_bytes(m, rows) + (uint64_t)rows * (SINN_KP_FEATURES * 4 + 4) + 512 : 0;
+}
+
+extern "C" int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m, void *act,
+                                       uint64_t act_bytes, const uint64_t *q_indptr,
+                                       const uint32_t *q_indices, const float *q_values,
+                                       uint32_t n_q, uint32_t k, uint32_t k_prime_min,
+                                       uint32_t k_prime_max, uint32_t *out_ids, float *out_scores,
+                                       uint32_t *out_kprime, void *stream) {
+  if (!c || !ix || !m || !act || m->nin != SINN_KP_FEATURES) return SINN_EINVAL;
+  if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (act_bytes < sinn_mlp_act_bytes(m, n_q)) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Acts a;
+  carve_acts(m, act, n_q, &a);
+  char *tail = (char *)act + acts_bytes(m, n_q);
+  float *feat = (float *)tail;
+  uint32_t *kp = (uint32_t *)(tail + ((size_t)n_q * SINN_KP_FEATURES * 4 + 255) / 256 * 256);
+  int st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream);
+  if (st) return st;
+  if ((st = refresh_bf16(m, s))) return st;
+  if ((st = forward(m, feat, n_q, a, s))) return st;
+  k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
+  CK(cudaGetLastError());
+  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
+  return sinn_search_ctx(c, q_indptr, q_indices, q_values, n_q, k, kp, k_prime_max, out_ids,
+                         out_scores, stream);
 }

@@ -44,6 +44,7 @@ constexpr uint32_t kScoreThreads = 512;
 constexpr uint32_t kChunk = 8192;       // keys per block in the dense select passes
 constexpr uint32_t kBoundEvery = 4;     // tiles between lower-bound refreshes
 constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
+constexpr uint32_t kRerankBlocks = 8;   // re-rank blocks per query (8 warps each)
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
 // Below this many queries per launch a query's tiles mostly run at the same
 // time, so no tile has finished when the others would emit and the running
@@ -246,27 +247,46 @@ __device__ __forceinline__ float decode(const float *const *row, uint32_t h, boo
   return y;
 }
 
+// Sketch values of 4 consecutive ids (16-byte aligned: rows start on tile
+// boundaries): least upper bound over the rows for q_j > 0, greatest lower
+// bound for q_j < 0 (Alg. 6 lines 7-11).
+template <int H>
+__device__ __forceinline__ float4 decode4(const float *const *row, uint32_t h, bool pos,
+                                          uint32_t d0) {
+  float4 y = __ldg((const float4 *)(row[0] + d0));
+  const uint32_t hh = H > 0 ? (uint32_t)H : h;
+#pragma unroll
+  for (uint32_t o = 1; o < (H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H); ++o) {
+    if (o >= hh) break;
+    const float4 z = __ldg((const float4 *)(row[o] + d0));
+    if (pos) {
+      y.x = fminf(y.x, z.x); y.y = fminf(y.y, z.y); y.z = fminf(y.z, z.z); y.w = fminf(y.w, z.w);
+    } else {
+      y.x = fmaxf(y.x, z.x); y.y = fmaxf(y.y, z.y); y.z = fmaxf(y.z, z.z); y.w = fmaxf(y.w, z.w);
+    }
+  }
+  return y;
+}
+
 // Alg. 6 for query slot b over tile t.  A query term's postings inside the
-// tile sit in one container: a bitmap of T bits when at least T/2 ids of the
-// tile hold the coordinate, else a sorted array of 16-bit local ids.
-//   Phase 1, bitmap terms: thread tid owns ids tid, tid+512, ... of the tile
-//   and keeps their partial scores in registers; for each term it tests its
-//   ids' bits and adds q_j * x~ for the set ones, reading the term's sketch
-//   row(s) contiguously across the warp.  No atomics; a fixed order.
-//   Phase 2, array terms: their postings are cut into chunks of 32 (one per
+// tile sit in one container: a bitmap of T bits when at least a quarter of
+// the tile's ids hold the coordinate, else a sorted array of 16-bit local ids.
+//   Array terms first: their postings are cut into chunks of 32 (one per
 //   lane), numbered in term order; each warp takes a contiguous range of
-//   chunks, so it finds a chunk's term by advancing one pointer, and adds into
-//   shared memory with atomics (two terms may share an id).
-//   EMIT: ids whose score key falls at or above the query's running bound are
-//   counted in the histogram and emitted; otherwise (dense) every live id gets
-//   its key written and counted.
+//   chunks (so it finds a chunk's term by advancing one pointer) and adds
+//   q_j * x~ into shared memory with atomics (two terms may share an id).
+//   Bitmap terms next: thread t owns the 4 consecutive ids 4t..4t+3 of each
+//   2048-id slice, holds their partial scores in registers and, per term,
+//   reads one bitmap word and one 16-byte group of sketch values; no atomics.
+//   The epilogue runs on those registers: ids whose score key reaches the
+//   query's running bound are counted in the histogram and emitted (EMIT), or
+//   every live id's key is written and counted (dense).
 template <bool EMIT, int H>
 __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t,
                            uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
   constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
-  constexpr uint32_t PER = 4;  // register accumulators per thread per pass
-  const uint32_t T = a.T, BMIN = T >> 1;
+  const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT;
   float *acc = (float *)sm;                          // T
   uint32_t *hist = sm + T;                           // 4096
   uint32_t *t_start = hist + 4096;                   // kTermBatch
@@ -275,7 +295,7 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
   float *t_v = (float *)(t_cp + kTermBatch + 1);     // kTermBatch
   uint32_t *t_bin = (uint32_t *)(t_v + kTermBatch);  // kTermBatch * h
   __shared__ uint32_t part[NW + 2];
-  __shared__ uint32_t s_nbm;
+  __shared__ uint32_t s_nbm, s_lb;
   __shared__ uint8_t t_bl[kTermBatch];  // bitmap terms of the batch, in order
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -284,11 +304,17 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
   const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
   const uint16_t *post = a.tile_post[t];
   const uint64_t id0 = (uint64_t)t << a.log2T;
+  uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
+  uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
 
   for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
   for (uint32_t i = tid; i < 4096; i += kScoreThreads) hist[i] = 0;
-  for (uint32_t i0 = 0; i0 < nt; i0 += kTermBatch) {
-    const uint32_t nb = min(kTermBatch, nt - i0);
+  if (tid == 0) s_lb = EMIT ? __ldcg(&bt.bound[b]) : 0u;
+  const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
+  for (uint32_t bi = 0; bi < nbatch; ++bi) {
+    const uint32_t i0 = bi * kTermBatch;
+    const uint32_t nb = nt > i0 ? min(kTermBatch, nt - i0) : 0u;
+    const bool last = bi + 1 == nbatch;
     __syncthreads();  // the previous batch is consumed
     if (tid == 0) s_nbm = 0;
     for (uint32_t k = tid; k < nb; k += kScoreThreads) {
@@ -301,7 +327,7 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
       for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
     }
     __syncthreads();
-    if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap count
+    if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap list
       uint32_t run = 0, nbm = 0;
       for (uint32_t base = 0; base < nb; base += 32) {
         const uint32_t i = base + lane;
@@ -324,50 +350,8 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
       }
     }
     __syncthreads();
+    // array terms
     const uint32_t C = part[0];
-    // phase 1: bitmap terms (listed in t_bl, in term order)
-    const uint32_t nbm = s_nbm;
-    if (nbm > 0) {
-      for (uint32_t g0 = 0; g0 < T; g0 += kScoreThreads * PER) {
-        float r[PER];
-#pragma unroll
-        for (uint32_t q = 0; q < PER; ++q) {
-          const uint32_t d = g0 + q * kScoreThreads + tid;
-          r[q] = d < T ? acc[d] : 0.0f;
-        }
-        for (uint32_t kk = 0; kk < nbm; ++kk) {
-          const uint32_t k = t_bl[kk];
-          const float v = t_v[k];
-          const bool pos = v > 0.0f;
-          const float *plane = pos ? a.U : a.L;
-          const float *row[HS];
-#pragma unroll
-          for (uint32_t o = 0; o < HS; ++o)
-            if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
-          const uint32_t *bm = (const uint32_t *)(post + t_start[k]);
-          uint32_t wv[PER];
-          float xv[PER];
-#pragma unroll
-          for (uint32_t q = 0; q < PER; ++q) {  // both loads issue together
-            const uint32_t d = min(g0 + q * kScoreThreads + tid, T - 1);
-            wv[q] = __ldg(bm + (d >> 5));
-            xv[q] = decode<H>(row, a.h, pos, d);
-          }
-#pragma unroll
-          for (uint32_t q = 0; q < PER; ++q) {
-            const uint32_t d = g0 + q * kScoreThreads + tid;
-            if (d < T && ((wv[q] >> (d & 31)) & 1u)) r[q] = fmaf(v, xv[q], r[q]);
-          }
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < PER; ++q) {
-          const uint32_t d = g0 + q * kScoreThreads + tid;
-          if (d < T) acc[d] = r[q];
-        }
-      }
-      __syncthreads();
-    }
-    // phase 2: array terms
     const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
     const uint32_t c_end = (uint32_t)((uint64_t)C * (wid + 1) / NW);
     if (c_beg < c_end) {
@@ -417,10 +401,53 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
         c += nck;
       }
     }
+    __syncthreads();
+    // bitmap terms, then (last batch) the epilogue, from registers
+    const uint32_t nbm = s_nbm;
+    const uint32_t lb = s_lb;
+    for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
+      const uint32_t d0 = g0 + 4 * tid;
+      const bool in = d0 < T;
+      float4 r = in ? *(const float4 *)(acc + d0) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (uint32_t kk = 0; kk < nbm && in; ++kk) {
+        const uint32_t k = t_bl[kk];
+        const float v = t_v[k];
+        const bool pos = v > 0.0f;
+        const float *plane = pos ? a.U : a.L;
+        const float *row[HS];
+#pragma unroll
+        for (uint32_t o = 0; o < HS; ++o)
+          if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+        const uint32_t w = __ldg((const uint32_t *)(post + t_start[k]) + (d0 >> 5));
+        const float4 x = decode4<H>(row, a.h, pos, d0);
+        const uint32_t bits = w >> (d0 & 31);
+        if (bits & 1u) r.x = fmaf(v, x.x, r.x);
+        if (bits & 2u) r.y = fmaf(v, x.y, r.y);
+        if (bits & 4u) r.z = fmaf(v, x.z, r.z);
+        if (bits & 8u) r.w = fmaf(v, x.w, r.w);
+      }
+      if (!last || !EMIT) {
+        if (in) *(float4 *)(acc + d0) = r;
+        continue;
+      }
+      // EMIT epilogue: ids at or above the running bound count and are emitted
+      const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
+      const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t key = sinn_f2key(rv[q] + 0.0f);
+        const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
+        if (em) atomicAdd(&hist[key >> 20], 1u);
+        if (__any_sync(0xFFFFFFFFu, em)) {
+          const uint32_t p = warp_append(em, &bt.ecnt[b]);
+          if (em && p < kEmitCap)
+            el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
+        }
+      }
+    }
   }
   __syncthreads();
 
-  uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
   if (!EMIT) {
     // dense: a key for every id slot (0 = not live) and the full histogram
     for (uint32_t d = tid; d < T; d += kScoreThreads) {
@@ -436,29 +463,13 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
       if (hist[k]) atomicAdd(&gh[k], hist[k]);
     return;
   }
-
-  // EMIT: only ids at or above the running bound matter.  The final boundary
-  // bin is never below any bound used, so the histogram stays exact from the
-  // boundary bin up and every candidate is emitted.
-  if (tid == 0) part[0] = __ldcg(&bt.bound[b]);
-  __syncthreads();
-  const uint32_t lb = part[0];
-  uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
-  const uint32_t *lw = a.live + (id0 >> 5);
-  for (uint32_t d = tid; d < T; d += kScoreThreads) {
-    const bool lv = (__ldg(lw + (d >> 5)) >> (d & 31)) & 1u;
-    const uint32_t key = sinn_f2key(acc[d] + 0.0f);
-    const bool em = lv && (key >> 20) >= lb;
-    if (em) atomicAdd(&hist[key >> 20], 1u);
-    if (__any_sync(0xFFFFFFFFu, em)) {
-      const uint32_t p = warp_append(em, &bt.ecnt[b]);
-      if (em && p < kEmitCap) el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d);
-    }
-  }
-  __syncthreads();
+  // EMIT: the final boundary bin is never below any bound used, so the
+  // histogram stays exact from the boundary bin up and every candidate is
+  // emitted.  Merge the tile's counts, then refresh the query's bound every
+  // kBoundEvery tiles.
+  const uint32_t lb = s_lb;
   for (uint32_t k = (lb & ~31u) + tid; k < 4096; k += kScoreThreads)
     if (k >= lb && hist[k]) atomicAdd(&gh[k], hist[k]);
-  // refresh the query's bound every kBoundEvery tiles
   __threadfence();
   __syncthreads();
   if (tid == 0) part[NW + 1] = atomicAdd(&bt.tdone[b], 1u);
@@ -644,10 +655,10 @@ __global__ void k_pick(Batch bt, uint32_t level) {
 }
 
 // Histogram of the next digit over dense keys matching the current prefix.
-__global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
+__global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t level) {
   __shared__ uint32_t hist[4096];
   const uint32_t nf = *bt.nflag;
-  const uint64_t chunks = (cap + kChunk - 1) / kChunk;
+  const uint64_t chunks = (span + kChunk - 1) / kChunk;
   const uint32_t nb = level == 1 ? 4096u : 256u;
   for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / chunks];
@@ -660,7 +671,7 @@ __global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
     const uint32_t dmask = nb - 1;
     const uint32_t *keys = bt.keys + (uint64_t)b * cap;
     const uint64_t beg = (w % chunks) * kChunk;
-    const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+    const uint64_t end = (beg + kChunk < span) ? beg + kChunk : span;
     for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
       const uint32_t key = keys[i];
       if (key != 0u && (key >> shift_p) == st.prefix)
@@ -676,9 +687,9 @@ __global__ void k_hist_level(Batch bt, uint64_t cap, uint32_t level) {
 
 // Dense-path collection: keys above the boundary bin are candidates; in
 // COMPACT mode the boundary bin's keys are buffered too.
-__global__ void k_compact(Batch bt, uint64_t cap, uint32_t kpmax) {
+__global__ void k_compact(Batch bt, uint64_t cap, uint64_t span, uint32_t kpmax) {
   const uint32_t nf = *bt.nflag;
-  const uint64_t chunks = (cap + kChunk - 1) / kChunk;
+  const uint64_t chunks = (span + kChunk - 1) / kChunk;
   for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / chunks];
     const SelState st = bt.sel[b];
@@ -689,7 +700,7 @@ __global__ void k_compact(Batch bt, uint64_t cap, uint32_t kpmax) {
     uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
     uint32_t *ncand = &bt.sel[b].ncand, *nbnd = &bt.sel[b].nbnd;
     const uint64_t beg = (w % chunks) * kChunk;
-    const uint64_t end = (beg + kChunk < cap) ? beg + kChunk : cap;
+    const uint64_t end = (beg + kChunk < span) ? beg + kChunk : span;
     for (uint64_t i0 = beg; i0 < end; i0 += blockDim.x) {
       const uint64_t i = i0 + threadIdx.x;
       const uint32_t key = i < end ? keys[i] : 0u;
@@ -753,7 +764,8 @@ __device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
 
 // Rest of the boundary bin: the rem best of its keys (COMPACT), or in TIES
 // mode the rem smallest ids whose key equals the boundary value exactly.
-__global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint32_t kpmax) {
+__global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t span,
+                                                uint32_t kpmax) {
   const uint32_t b = blockIdx.x;
   __shared__ SelState st;
   __shared__ uint32_t s_base, wsum[16];
@@ -782,9 +794,9 @@ __global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint32_t
   if (threadIdx.x == 0) s_base = 0;
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint64_t i0 = 0; i0 < cap && s_base < st.rem; i0 += blockDim.x) {
+  for (uint64_t i0 = 0; i0 < span && s_base < st.rem; i0 += blockDim.x) {
     const uint64_t i = i0 + threadIdx.x;
-    const bool m = i < cap && keys[i] == tau;
+    const bool m = i < span && keys[i] == tau;
     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, m);
     if (lane == 0) wsum[wid] = __popc(bal);
     __syncthreads();
@@ -810,7 +822,7 @@ struct RerankArgs {
   const uint64_t *fwd_off;
   const uint32_t *fwd_nnz;
   const uint2 *fwd;
-  uint32_t qmax, kpmax, per_block;
+  uint32_t qmax, kpmax;
 };
 
 __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
@@ -824,8 +836,7 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
   extern __shared__ uint32_t hs[];
   const uint32_t b = blockIdx.y;
   const uint32_t kq = bt.sel[b].kq;
-  const uint32_t c0 = blockIdx.x * a.per_block;
-  if (c0 >= kq) return;
+  if (blockIdx.x * (blockDim.x >> 5) >= kq) return;
   const uint32_t nt = bt.nt[b];
   uint32_t tsz = 64;
   while (tsz < 2 * nt) tsz <<= 1;
@@ -844,8 +855,7 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint64_t *cand = bt.cand + (uint64_t)b * a.kpmax;
   uint64_t *ek = bt.ekeys + (uint64_t)b * a.kpmax;
-  const uint32_t c1 = min(kq, c0 + a.per_block);
-  for (uint32_t c = c0 + wid; c < c1; c += nw) {
+  for (uint32_t c = blockIdx.x * nw + wid; c < kq; c += gridDim.x * nw) {
     const uint32_t id = ~(uint32_t)cand[c];
     const uint64_t fo = a.fwd_off[id];
     const uint32_t nz = a.fwd_nnz[id];
@@ -1055,14 +1065,18 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   sa.T = ix->T;
   sa.log2T = ix->log2T;
   sa.qmax = ix->max_qnnz;
-  sa.tiles = (uint32_t)(ix->cap / ix->T);
+  // ids at or above next_id were never assigned: search covers the tiles
+  // below it (the keys keep the capacity as their row stride)
+  const uint64_t used_tiles =
+      std::max<uint64_t>(1, std::min<uint64_t>(ix->cap / ix->T, (ix->next_id + ix->T - 1) / ix->T));
+  const uint64_t span = r.stage == Stage::kScores ? ix->cap : used_tiles * ix->T;
+  sa.tiles = (uint32_t)(span / ix->T);
   RerankArgs ra;
   ra.fwd_off = ix->d_fwd_off;
   ra.fwd_nnz = ix->d_fwd_nnz;
   ra.fwd = ix->d_fwd;
   ra.qmax = ix->max_qnnz;
   ra.kpmax = kpmax;
-  ra.per_block = 64;
   uint32_t tsz = 64;
   while (tsz < 2 * ix->max_qnnz) tsz <<= 1;
   int sms = 0;
@@ -1119,12 +1133,12 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       }
       ix->launches += 7;
       k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 0);
-      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, 1);
+      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, 1);
       k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 1);
-      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, 2);
+      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, 2);
       k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 2);
-      k_compact<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, kpmax);
-      k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, kpmax);
+      k_compact<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, kpmax);
+      k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, span, kpmax);
       CK(cudaGetLastError());
     }
     if (r.stage == Stage::kCandidates) {
@@ -1136,8 +1150,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     {
       SinnPhase ph(ix, s, 3);
       ix->launches += 2;
-      k_rerank<<<dim3((kpmax + ra.per_block - 1) / ra.per_block, nb), 256, (size_t)tsz * 8,
-                 s>>>(ra, bt);
+      k_rerank<<<dim3(std::min<uint32_t>(kRerankBlocks, (kpmax + 7) / 8), nb), 256,
+                 (size_t)tsz * 8, s>>>(ra, bt);
       k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
       CK(cudaGetLastError());
     }
@@ -1366,4 +1380,76 @@ extern "C" int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr,
   st = run_search(ix, r, (cudaStream_t)stream, &fx);
   ix->tm_on = tm;
   return st;
+}
+
+// ------------------------------------------------------- search contexts
+// A context owns the scratch of one in-flight search, so several searches of
+// the same index can run at once on different streams (the index itself is
+// only read by a search).  Mutations must still be ordered against them.
+struct sinn_ctx {
+  sinn_index *ix = nullptr;
+  void *scratch = nullptr;
+  size_t bytes = 0;
+};
+
+extern "C" int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx **out) {
+  if (!ix || !out || scratch_bytes < (1u << 20)) return SINN_EINVAL;
+  *out = nullptr;
+  sinn_ctx *c = new (std::nothrow) sinn_ctx();
+  if (!c) return SINN_ENOMEM;
+  cudaSetDevice(ix->device);
+  if (cudaMalloc(&c->scratch, scratch_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete c;
+    return SINN_ENOMEM;
+  }
+  c->ix = ix;
+  c->bytes = scratch_bytes;
+  *out = c;
+  return SINN_OK;
+}
+
+extern "C" int sinn_ctx_destroy(sinn_ctx *c) {
+  if (!c) return SINN_OK;
+  cudaSetDevice(c->ix->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->scratch);
+  delete c;
+  return SINN_OK;
+}
+
+extern "C" uint64_t sinn_ctx_query_bytes(sinn_ctx *c, uint32_t k_prime_max) {
+  if (!c || k_prime_max == 0) return 0;
+  return layout_for(c->ix, 1, k_prime_max).total;
+}
+
+// sinn_search / sinn_search_kp on a context's scratch (k_prime may be NULL:
+// fixed k' = k_prime_max).
+extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint32_t *q_indices,
+                               const float *q_values, uint32_t n_q, uint32_t k,
+                               const uint32_t *k_prime, uint32_t k_prime_max, uint32_t *out_ids,
+                               float *out_scores, void *stream) {
+  if (!c) return SINN_EINVAL;
+  sinn_index *ix = c->ix;
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k == 0 || k > SINN_MAX_K || k_prime_max < k) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  FixedScratch fx{c->scratch, c->bytes};
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = k;
+  r.kp = k_prime_max;
+  r.kp_arr = k_prime;
+  r.kp_min = k;
+  r.kp_max = k_prime_max;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.stage = Stage::kFull;
+  return run_search(ix, r, (cudaStream_t)stream, &fx);
 }

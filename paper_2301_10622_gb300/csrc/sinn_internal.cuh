@@ -17,6 +17,10 @@
 #define SINN_HIST0_BITS 12  // first select level: key bits [31:20]
 #define SINN_HIST1_BITS 12  // second level: key bits [19:8]
 #define SINN_HIST2_BITS 8   // third level: key bits [7:0]
+// A tile's container of one coordinate is a bitmap of T bits once it holds
+// at least T >> SINN_BITMAP_SHIFT postings (a quarter of the tile), else a
+// sorted array of 16-bit local ids.
+#define SINN_BITMAP_SHIFT 2
 
 // device error bits (sticky flag)
 #define SINN_DERR_QUERY 1u     // malformed query

@@ -30,11 +30,13 @@ EXPORTS = [
     "sinn_search", "sinn_search_kp", "sinn_search_host", "sinn_sync", "sinn_stats",
     "sinn_strerror", "sinn_hash_table", "sinn_sketch_columns", "sinn_inverted_list",
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
-    "sinn_search_noalloc",
+    "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
+    "sinn_search_ctx",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
-    "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned",
+    "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned", "sinn_mlp_act_bytes",
+    "sinn_search_learned_ctx",
 ]
 
 KP_FEATURES = 19
@@ -118,6 +120,13 @@ def load(build_if_missing: bool = False):
         "sinn_timing_start": ([vp], C.c_int),
         "sinn_search_noalloc": ([vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
         "sinn_kp_features": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
+        "sinn_ctx_create": ([vp, u64, C.POINTER(vp)], C.c_int),
+        "sinn_ctx_destroy": ([vp], C.c_int),
+        "sinn_ctx_query_bytes": ([vp, u32], u64),
+        "sinn_search_ctx": ([vp, vp, vp, vp, u32, u32, vp, u32, vp, vp, vp], C.c_int),
+        "sinn_mlp_act_bytes": ([vp, u32], u64),
+        "sinn_search_learned_ctx": ([vp, vp, vp, vp, u64, vp, vp, vp, u32, u32, u32, u32, vp, vp,
+                                     vp, vp], C.c_int),
         "sinn_mlp_create": ([u32, u32, u64, C.POINTER(vp)], C.c_int),
         "sinn_mlp_destroy": ([vp], C.c_int),
         "sinn_mlp_num_params": ([vp], u64),
@@ -313,6 +322,54 @@ def sinn_search_learned(ix, mlp, q_indptr, q_indices, q_values, k, kp_min, kp_ma
     _check(load().sinn_search_learned(ix, mlp, _p(q_indptr), _p(q_indices), _p(q_values), n_q,
                                       k, kp_min, kp_max, _p(out_ids), _p(out_scores),
                                       _p(out_kprime), _s(stream)), "sinn_search_learned")
+
+
+class Context:
+    """A search context (sinn_ctx): scratch for one in-flight search, so that
+    searches of one index can overlap on different streams."""
+
+    def __init__(self, index: "Index", scratch_bytes: int, mlp=None, max_queries: int = 0):
+        lib = load()
+        out = C.c_void_p()
+        with torch.cuda.device(index.device):
+            _check(lib.sinn_ctx_create(index.handle, scratch_bytes, C.byref(out)),
+                   "sinn_ctx_create")
+        self._h, self.index, self.mlp = out, index, mlp
+        self.act = None
+        if mlp is not None and max_queries:
+            nbytes = int(lib.sinn_mlp_act_bytes(mlp.handle, max_queries))
+            self.act = torch.empty(nbytes, dtype=torch.uint8, device=index.device)
+            self.act_rows = max_queries
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sinn_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query_bytes(self, k_prime_max: int) -> int:
+        return int(load().sinn_ctx_query_bytes(self._h, k_prime_max))
+
+    def search(self, q_indptr, q_indices, q_values, k, k_prime_max, out_ids, out_scores,
+               k_prime=None, stream=None):
+        n_q = q_indptr.numel() - 1
+        _check(load().sinn_search_ctx(self._h, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
+                                      _p(k_prime), k_prime_max, _p(out_ids), _p(out_scores),
+                                      _s(stream)), "sinn_search_ctx")
+
+    def search_learned(self, q_indptr, q_indices, q_values, k, kp_min, kp_max, out_ids,
+                       out_scores, out_kprime=None, stream=None):
+        n_q = q_indptr.numel() - 1
+        assert self.act is not None and n_q <= self.act_rows
+        _check(load().sinn_search_learned_ctx(
+            self._h, self.index.handle, self.mlp.handle, _p(self.act), self.act.numel(),
+            _p(q_indptr), _p(q_indices), _p(q_values), n_q, k, kp_min, kp_max, _p(out_ids),
+            _p(out_scores), _p(out_kprime), _s(stream)), "sinn_search_learned_ctx")
 
 
 class MLP:
