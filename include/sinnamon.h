@@ -181,6 +181,41 @@ int sinn_sync(sinn_index *ix, void *stream);
 /* Fill *out with the counters above (host). */
 int sinn_stats(sinn_index *ix, sinn_stats_t *out);
 
+/* ---- Launch tuning (the paper has no counterpart: these are GPU launch
+ * parameters; results do not depend on them beyond fp32 summation order) -- */
+
+/* Run-time launch parameters of the search.  Defaults come with the index;
+ * sinn_autotune chooses them by timing. */
+typedef struct sinn_tuning {
+  uint32_t bound_every;      /* scored tiles between refreshes of a query's running
+                                k'-th bound, 1..64 (default 4) */
+  uint32_t emit_min_batch;   /* launches of fewer queries score densely instead of
+                                emitting candidates, 1..65535 (default 32) */
+  uint32_t max_batch;        /* cap on queries per internal launch, 0 = as many as the
+                                scratch holds (default 0) */
+  uint32_t rerank_blocks;    /* re-rank blocks per query, 1..64 (default 8) */
+  uint32_t dense_blocks_per_sm; /* grid of the dense scoring kernel per SM, 1..32
+                                   (default 4) */
+  uint32_t tiles_per_block;  /* tiles one block of the batched scoring kernel covers,
+                                1..64 (default 4) */
+  uint32_t reserved[2];      /* zero */
+} sinn_tuning;
+
+/* Current tuning of the index into *out (host). */
+int sinn_get_tuning(sinn_index *ix, sinn_tuning *out);
+
+/* Set the tuning; SINN_EINVAL (and no change) if a field is out of range. */
+int sinn_set_tuning(sinn_index *ix, const sinn_tuning *t);
+
+/* Choose the tuning by timing sinn_search on a sample of queries (device
+ * CSR as in sinn_search, at least 1 query) with k and k_prime: coordinate
+ * descent over the fields above, each candidate timed with CUDA events on
+ * `stream` (best of `reps` runs, 1..8).  Leaves the fastest tuning set and
+ * copies it to *out (host, may be NULL).  Synchronises the stream. */
+int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                  const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                  uint32_t reps, sinn_tuning *out, void *stream);
+
 /* Per-phase device timing, for benchmarks.  Phases: 0 query preparation,
  * 1 scoring (Alg. 6), 2 top-k' selection (Alg. 7 line 1), 3 re-rank and
  * top-k (Alg. 7 lines 2-4), 4 insert (Alg. 5), 5 delete (Sec. 4.3). */

@@ -42,14 +42,8 @@ constexpr uint32_t kBoundCap = 65536;   // boundary-bin entries kept per query
 constexpr uint32_t kEmitCap = 131072;   // emitted candidates kept per query
 constexpr uint32_t kScoreThreads = 512;
 constexpr uint32_t kChunk = 8192;       // keys per block in the dense select passes
-constexpr uint32_t kBoundEvery = 4;     // tiles between lower-bound refreshes
 constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
-constexpr uint32_t kRerankBlocks = 8;   // re-rank blocks per query (8 warps each)
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
-// Below this many queries per launch a query's tiles mostly run at the same
-// time, so no tile has finished when the others would emit and the running
-// bound cannot prune: such launches score densely.
-constexpr uint32_t kEmitMinBatch = 32;
 
 enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
 
@@ -180,19 +174,24 @@ struct ScoreArgs {
   const uint32_t *live;
   uint64_t cap;
   uint32_t n, h, T, log2T, qmax, tiles;
+  uint32_t bound_every;  // tiles between refreshes of the running bound
+  uint32_t tpb;          // tiles per block of the batched kernel
 };
 
 // Lower-bound bin of the kq-th largest key from a (partial) histogram: the
 // highest bin b with sum_{i >= b} hist[i] >= kq, or 0 if the counts fall short.
-// Counts only grow, so a stale read gives a lower (still valid) bound.
-__device__ uint32_t bound_from_hist(const uint32_t *gh, uint32_t kq, uint32_t *part) {
+// Counts only grow, so a stale read gives a lower (still valid) bound.  Only
+// bins at or above lb (the bound already known) are read: a new bound below
+// it would not raise it.
+__device__ uint32_t bound_from_hist(const uint32_t *gh, uint32_t kq, uint32_t lb,
+                                   uint32_t *part) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr uint32_t per = 4096 / kScoreThreads;  // thread tid owns the tid-th group from the top
   const uint32_t top = 4096 - tid * per;
   uint32_t c[per], s = 0;
 #pragma unroll
   for (uint32_t i = 0; i < per; ++i) {
-    c[i] = __ldcg(gh + top - 1 - i);
+    c[i] = top - 1 - i >= lb ? __ldcg(gh + top - 1 - i) : 0u;
     s += c[i];
   }
   uint32_t x = s;  // inclusive scan over threads (top groups first)
@@ -268,9 +267,10 @@ __device__ __forceinline__ float4 decode4(const float *const *row, uint32_t h, b
   return y;
 }
 
-// Alg. 6 for query slot b over tile t.  A query term's postings inside the
-// tile sit in one container: a bitmap of T bits when at least a quarter of
-// the tile's ids hold the coordinate, else a sorted array of 16-bit local ids.
+// Alg. 6 for query slot b over tiles [t_beg, t_end).  A query term's postings
+// inside a tile sit in one container: a bitmap of T bits when at least a
+// quarter of the tile's ids hold the coordinate, else a sorted array of 16-bit
+// local ids.  Per tile:
 //   Array terms first: their postings are cut into chunks of 32 (one per
 //   lane), numbered in term order; each warp takes a contiguous range of
 //   chunks (so it finds a chunk's term by advancing one pointer) and adds
@@ -281,9 +281,11 @@ __device__ __forceinline__ float4 decode4(const float *const *row, uint32_t h, b
 //   The epilogue runs on those registers: ids whose score key reaches the
 //   query's running bound are counted in the histogram and emitted (EMIT), or
 //   every live id's key is written and counted (dense).
+// The histogram covers all the block's tiles: it is cleared, merged into the
+// query's global histogram and used to refresh the bound once per block.
 template <bool EMIT, int H>
-__device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t,
-                           uint32_t *sm) {
+__device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
+                            uint32_t t_end, uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
   constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
   const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT;
@@ -301,190 +303,199 @@ __device__ void score_tile(const ScoreArgs &a, const Batch &bt, uint32_t b, uint
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.nt[b];
   const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
-  const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
-  const uint16_t *post = a.tile_post[t];
-  const uint64_t id0 = (uint64_t)t << a.log2T;
   uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
   uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
 
-  for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
-  for (uint32_t i = tid; i < 4096; i += kScoreThreads) hist[i] = 0;
   if (tid == 0) s_lb = EMIT ? __ldcg(&bt.bound[b]) : 0u;
+  __syncthreads();
+  // keys below the bound are neither counted nor emitted: their bins stay
+  // untouched
+  const uint32_t lb = s_lb, h0 = lb & ~31u;
+  for (uint32_t i = h0 + tid; i < 4096; i += kScoreThreads) hist[i] = 0;
   const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
-  for (uint32_t bi = 0; bi < nbatch; ++bi) {
-    const uint32_t i0 = bi * kTermBatch;
-    const uint32_t nb = nt > i0 ? min(kTermBatch, nt - i0) : 0u;
-    const bool last = bi + 1 == nbatch;
-    __syncthreads();  // the previous batch is consumed
-    if (tid == 0) s_nbm = 0;
-    for (uint32_t k = tid; k < nb; k += kScoreThreads) {
-      const uint32_t j = terms[i0 + k].j;
-      const uint2 de = dir[j];
-      t_start[k] = de.x;
-      t_cnt[k] = de.y;
-      t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
-      t_v[k] = terms[i0 + k].v;
-      for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
-    }
-    __syncthreads();
-    if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap list
-      uint32_t run = 0, nbm = 0;
-      for (uint32_t base = 0; base < nb; base += 32) {
-        const uint32_t i = base + lane;
-        const uint32_t v = i < nb ? t_cp[i] : 0;
-        const uint32_t isb = __ballot_sync(0xFFFFFFFFu, i < nb && t_cnt[i] >= BMIN);
-        if ((isb >> lane) & 1u) t_bl[nbm + __popc(isb & ((1u << lane) - 1u))] = (uint8_t)i;
-        nbm += __popc(isb);
-        uint32_t x = v;
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, dd);
-          if (lane >= (uint32_t)dd) x += y;
+  for (uint32_t t = t_beg; t < t_end; ++t) {
+    const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
+    const uint16_t *post = a.tile_post[t];
+    const uint64_t id0 = (uint64_t)t << a.log2T;
+    __syncthreads();  // the previous tile's epilogue is done with acc
+    for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
+    for (uint32_t bi = 0; bi < nbatch; ++bi) {
+      const uint32_t i0 = bi * kTermBatch;
+      const uint32_t nb = nt > i0 ? min(kTermBatch, nt - i0) : 0u;
+      const bool last = bi + 1 == nbatch;
+      __syncthreads();  // the previous batch is consumed
+      if (tid == 0) s_nbm = 0;
+      for (uint32_t k = tid; k < nb; k += kScoreThreads) {
+        const uint32_t j = terms[i0 + k].j;
+        const uint2 de = dir[j];
+        t_start[k] = de.x;
+        t_cnt[k] = de.y;
+        t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
+        t_v[k] = terms[i0 + k].v;
+        for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
+      }
+      __syncthreads();
+      if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap list
+        uint32_t run = 0, nbm = 0;
+        for (uint32_t base = 0; base < nb; base += 32) {
+          const uint32_t i = base + lane;
+          const uint32_t v = i < nb ? t_cp[i] : 0;
+          const uint32_t isb = __ballot_sync(0xFFFFFFFFu, i < nb && t_cnt[i] >= BMIN);
+          if ((isb >> lane) & 1u) t_bl[nbm + __popc(isb & ((1u << lane) - 1u))] = (uint8_t)i;
+          nbm += __popc(isb);
+          uint32_t x = v;
+          for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, dd);
+            if (lane >= (uint32_t)dd) x += y;
+          }
+          if (i < nb) t_cp[i] = run + x - v;
+          run += __shfl_sync(0xFFFFFFFFu, x, 31);
         }
-        if (i < nb) t_cp[i] = run + x - v;
-        run += __shfl_sync(0xFFFFFFFFu, x, 31);
-      }
-      if (lane == 0) {
-        t_cp[nb] = run;
-        part[0] = run;
-        s_nbm = nbm;
-      }
-    }
-    __syncthreads();
-    // array terms
-    const uint32_t C = part[0];
-    const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
-    const uint32_t c_end = (uint32_t)((uint64_t)C * (wid + 1) / NW);
-    if (c_beg < c_end) {
-      uint32_t i = 0, hi = nb;  // term of c_beg: last i with t_cp[i] <= c_beg
-      while (hi - i > 1) {
-        const uint32_t mid = (i + hi) >> 1;
-        if (t_cp[mid] <= c_beg) i = mid;
-        else hi = mid;
-      }
-      uint32_t c_start = 0, c_next = 0, lo = 0, len = 0;
-      float v = 0.0f;
-      bool pos = true;
-      const float *row[HS];
-      auto load_term = [&]() {
-        c_start = t_cp[i];
-        c_next = t_cp[i + 1];
-        lo = t_start[i];
-        len = t_cnt[i];
-        v = t_v[i];
-        pos = v > 0.0f;
-        const float *plane = pos ? a.U : a.L;
-#pragma unroll
-        for (uint32_t o = 0; o < HS; ++o)
-          if (o < a.h) row[o] = plane + (uint64_t)t_bin[i * a.h + o] * a.cap + id0;
-      };
-      load_term();
-      for (uint32_t c = c_beg; c < c_end;) {
-        while (c >= c_next) {
-          ++i;
-          load_term();
+        if (lane == 0) {
+          t_cp[nb] = run;
+          part[0] = run;
+          s_nbm = nbm;
         }
-        const uint32_t nck = min(min(4u, c_end - c), c_next - c);
-        const uint32_t p0 = (c - c_start) * 32 + lane;
-        uint32_t d[4];
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
-          const uint32_t p = p0 + u * 32;
-          d[u] = (u < nck && p < len) ? (uint32_t)__ldg(post + lo + p) : SINN_TOMB;
-        }
-        float x[4];
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u)
-          x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H>(row, a.h, pos, d[u]);
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u)
-          if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], v * x[u]);
-        c += nck;
       }
-    }
-    __syncthreads();
-    // bitmap terms, then (last batch) the epilogue, from registers
-    const uint32_t nbm = s_nbm;
-    const uint32_t lb = s_lb;
-    for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
-      const uint32_t d0 = g0 + 4 * tid;
-      const bool in = d0 < T;
-      float4 r = in ? *(const float4 *)(acc + d0) : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (uint32_t kk = 0; kk < nbm && in; ++kk) {
-        const uint32_t k = t_bl[kk];
-        const float v = t_v[k];
-        const bool pos = v > 0.0f;
-        const float *plane = pos ? a.U : a.L;
+      __syncthreads();
+      // array terms
+      const uint32_t C = part[0];
+      const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
+      const uint32_t c_end = (uint32_t)((uint64_t)C * (wid + 1) / NW);
+      if (c_beg < c_end) {
+        uint32_t i = 0, hi = nb;  // term of c_beg: last i with t_cp[i] <= c_beg
+        while (hi - i > 1) {
+          const uint32_t mid = (i + hi) >> 1;
+          if (t_cp[mid] <= c_beg) i = mid;
+          else hi = mid;
+        }
+        uint32_t c_start = 0, c_next = 0, lo = 0, len = 0;
+        float v = 0.0f;
+        bool pos = true;
         const float *row[HS];
+        auto load_term = [&]() {
+          c_start = t_cp[i];
+          c_next = t_cp[i + 1];
+          lo = t_start[i];
+          len = t_cnt[i];
+          v = t_v[i];
+          pos = v > 0.0f;
+          const float *plane = pos ? a.U : a.L;
 #pragma unroll
-        for (uint32_t o = 0; o < HS; ++o)
-          if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
-        const uint32_t w = __ldg((const uint32_t *)(post + t_start[k]) + (d0 >> 5));
-        const float4 x = decode4<H>(row, a.h, pos, d0);
-        const uint32_t bits = w >> (d0 & 31);
-        if (bits & 1u) r.x = fmaf(v, x.x, r.x);
-        if (bits & 2u) r.y = fmaf(v, x.y, r.y);
-        if (bits & 4u) r.z = fmaf(v, x.z, r.z);
-        if (bits & 8u) r.w = fmaf(v, x.w, r.w);
-      }
-      if (!last || !EMIT) {
-        if (in) *(float4 *)(acc + d0) = r;
-        continue;
-      }
-      // EMIT epilogue: ids at or above the running bound count and are emitted
-      const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
-      const float rv[4] = {r.x, r.y, r.z, r.w};
+          for (uint32_t o = 0; o < HS; ++o)
+            if (o < a.h) row[o] = plane + (uint64_t)t_bin[i * a.h + o] * a.cap + id0;
+        };
+        load_term();
+        for (uint32_t c = c_beg; c < c_end;) {
+          while (c >= c_next) {
+            ++i;
+            load_term();
+          }
+          const uint32_t nck = min(min(4u, c_end - c), c_next - c);
+          const uint32_t p0 = (c - c_start) * 32 + lane;
+          uint32_t d[4];
 #pragma unroll
-      for (uint32_t q = 0; q < 4; ++q) {
-        const uint32_t key = sinn_f2key(rv[q] + 0.0f);
-        const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
-        if (em) atomicAdd(&hist[key >> 20], 1u);
-        if (__any_sync(0xFFFFFFFFu, em)) {
-          const uint32_t p = warp_append(em, &bt.ecnt[b]);
-          if (em && p < kEmitCap)
-            el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
+          for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t p = p0 + u * 32;
+            d[u] = (u < nck && p < len) ? (uint32_t)__ldg(post + lo + p) : SINN_TOMB;
+          }
+          float x[4];
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u)
+            x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H>(row, a.h, pos, d[u]);
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u)
+            if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], v * x[u]);
+          c += nck;
         }
+      }
+      __syncthreads();
+      // bitmap terms, then (last batch) the epilogue, from registers
+      const uint32_t nbm = s_nbm;
+      for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
+        const uint32_t d0 = g0 + 4 * tid;
+        const bool in = d0 < T;
+        float4 r = in ? *(const float4 *)(acc + d0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t kk = 0; kk < nbm && in; ++kk) {
+          const uint32_t k = t_bl[kk];
+          const float v = t_v[k];
+          const bool pos = v > 0.0f;
+          const float *plane = pos ? a.U : a.L;
+          const float *row[HS];
+#pragma unroll
+          for (uint32_t o = 0; o < HS; ++o)
+            if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+          const uint32_t w = __ldg((const uint32_t *)(post + t_start[k]) + (d0 >> 5));
+          const float4 x = decode4<H>(row, a.h, pos, d0);
+          const uint32_t bits = w >> (d0 & 31);
+          if (bits & 1u) r.x = fmaf(v, x.x, r.x);
+          if (bits & 2u) r.y = fmaf(v, x.y, r.y);
+          if (bits & 4u) r.z = fmaf(v, x.z, r.z);
+          if (bits & 8u) r.w = fmaf(v, x.w, r.w);
+        }
+        if (!last || !EMIT) {
+          if (in) *(float4 *)(acc + d0) = r;
+          continue;
+        }
+        // EMIT epilogue: ids at or above the running bound count and are emitted
+        const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
+        const float rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+          const uint32_t key = sinn_f2key(rv[q] + 0.0f);
+          const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
+          if (em) atomicAdd(&hist[key >> 20], 1u);
+          if (__any_sync(0xFFFFFFFFu, em)) {
+            const uint32_t p = warp_append(em, &bt.ecnt[b]);
+            if (em && p < kEmitCap)
+              el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
+          }
+        }
+      }
+    }
+    if (!EMIT) {
+      // dense: a key for every id slot of the tile (0 = not live), counted
+      __syncthreads();
+      for (uint32_t d = tid; d < T; d += kScoreThreads) {
+        const bool lv = sinn_is_live(a.live, id0 + d);
+        const uint32_t key = sinn_f2key(acc[d] + 0.0f);
+        bt.keys[(uint64_t)b * a.cap + id0 + d] = lv ? key : 0u;
+        const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
+        if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
       }
     }
   }
   __syncthreads();
-
   if (!EMIT) {
-    // dense: a key for every id slot (0 = not live) and the full histogram
-    for (uint32_t d = tid; d < T; d += kScoreThreads) {
-      const bool lv = sinn_is_live(a.live, id0 + d);
-      const uint32_t key = sinn_f2key(acc[d] + 0.0f);
-      bt.keys[(uint64_t)b * a.cap + id0 + d] = lv ? key : 0u;
-      const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
-      const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
-      if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
-    }
-    __syncthreads();
     for (uint32_t k = tid; k < 4096; k += kScoreThreads)
       if (hist[k]) atomicAdd(&gh[k], hist[k]);
     return;
   }
   // EMIT: the final boundary bin is never below any bound used, so the
   // histogram stays exact from the boundary bin up and every candidate is
-  // emitted.  Merge the tile's counts, then refresh the query's bound every
-  // kBoundEvery tiles.
-  const uint32_t lb = s_lb;
-  for (uint32_t k = (lb & ~31u) + tid; k < 4096; k += kScoreThreads)
+  // emitted.  Merge the block's counts, then refresh the query's bound each
+  // time the tiles done cross a multiple of bound_every.
+  for (uint32_t k = h0 + tid; k < 4096; k += kScoreThreads)
     if (k >= lb && hist[k]) atomicAdd(&gh[k], hist[k]);
   __threadfence();
   __syncthreads();
-  if (tid == 0) part[NW + 1] = atomicAdd(&bt.tdone[b], 1u);
+  if (tid == 0) part[NW + 1] = atomicAdd(&bt.tdone[b], t_end - t_beg);
   __syncthreads();
   const uint32_t kq = bt.sel[b].kq;
-  if (part[NW + 1] % kBoundEvery == kBoundEvery - 1 && kq > 0) {
-    const uint32_t nbnd = bound_from_hist(gh, kq, part);
+  const uint32_t done0 = part[NW + 1], done1 = done0 + (t_end - t_beg);
+  if (done1 / a.bound_every > done0 / a.bound_every && kq > 0) {
+    const uint32_t nbnd = bound_from_hist(gh, kq, lb, part);
     if (tid == 0 && nbnd > 0) atomicMax(&bt.bound[b], nbnd);
   }
 }
 
+// Grid (query, group of tiles_per_block tiles), queries fastest.
 template <int H>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Batch bt) {
   extern __shared__ uint32_t sm[];
-  score_tile<true, H>(a, bt, blockIdx.x, blockIdx.y, sm);
+  const uint32_t t0 = blockIdx.y * a.tpb;
+  score_tiles<true, H>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
 }
 
 // Dense scoring of the flagged queries (grid-stride over (query, tile)).
@@ -494,7 +505,7 @@ __global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, B
   const uint32_t nf = *bt.nflag;
   for (uint64_t w = blockIdx.x; w < (uint64_t)nf * a.tiles; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / a.tiles], t = (uint32_t)(w % a.tiles);
-    score_tile<false, H>(a, bt, b, t, sm);
+    score_tiles<false, H>(a, bt, b, t, t + 1, sm);
     __syncthreads();
   }
 }
@@ -568,7 +579,9 @@ __global__ void k_pick_list(Batch bt) {
   find_bin(bt.hist0 + (uint64_t)b * 4096, 4096, st.kq, &bin, &above);
   if (threadIdx.x == 0) {
     const uint32_t cnt = bt.hist0[(uint64_t)b * 4096 + bin];
-    if (bt.ecnt[b] > kEmitCap || cnt > kBoundCap) {
+    // the dense fallback also takes a histogram short of kq keys (not
+    // expected: every live id at or above the running bound is counted)
+    if (bt.ecnt[b] > kEmitCap || cnt > kBoundCap || above + cnt < st.kq) {
       bt.flagged[atomicAdd(bt.nflag, 1u)] = b;
       st.dense = 1;
       st.mode = SEL_DONE;
@@ -602,9 +615,9 @@ __global__ void k_compact_list(Batch bt, uint32_t kpmax) {
     const bool up = i < ne && top > st.prefix;
     const bool eq = i < ne && top == st.prefix;
     uint32_t p = warp_append(up, ncand);
-    if (up) cand[p] = k64;
+    if (up && p < kpmax) cand[p] = k64;
     p = warp_append(eq, nbnd);
-    if (eq) bnd[p] = k64;
+    if (eq && p < kBoundCap) bnd[p] = k64;
   }
 }
 
@@ -709,9 +722,9 @@ __global__ void k_compact(Batch bt, uint64_t cap, uint64_t span, uint32_t kpmax)
       const bool eq = key != 0u && top == st.prefix && st.mode == SEL_COMPACT;
       const uint64_t k64 = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)i;
       uint32_t p = warp_append(up, ncand);
-      if (up) cand[p] = k64;
+      if (up && p < kpmax) cand[p] = k64;
       p = warp_append(eq, nbnd);
-      if (eq) bnd[p] = k64;
+      if (eq && p < kBoundCap) bnd[p] = k64;
     }
   }
 }
@@ -784,7 +797,7 @@ __global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t
       const uint64_t k = i < nb ? bnd[i] : 0ull;
       const bool take = i < nb && (k & msk) >= pre;
       const uint32_t p = warp_append(take, ncand);
-      if (take) cand[p] = k;
+      if (take && p < kpmax) cand[p] = k;
     }
     return;
   }
@@ -805,7 +818,7 @@ __global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t
     before += __popc(bal & lanemask_lt());
     if (m && before < st.rem) {
       const uint32_t p = atomicAdd(ncand, 1u);
-      cand[p] = ((uint64_t)tau << 32) | (uint32_t)~(uint32_t)i;
+      if (p < kpmax) cand[p] = ((uint64_t)tau << 32) | (uint32_t)~(uint32_t)i;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -822,8 +835,18 @@ struct RerankArgs {
   const uint64_t *fwd_off;
   const uint32_t *fwd_nnz;
   const uint2 *fwd;
+  uint64_t cap;
+  uint32_t *err;
   uint32_t qmax, kpmax;
 };
+
+// Candidates a query's selection produced.  Equal to kq by construction (the
+// histogram is exact from the boundary bin up); the minimum keeps every later
+// read inside what was written even if that ever failed, and the re-rank
+// raises the internal-error flag then.
+__device__ __forceinline__ uint32_t n_selected(const SelState &st, uint32_t kpmax) {
+  return min(min(st.kq, st.ncand), kpmax);
+}
 
 __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
   return (c * 0x9E3779B1u) >> 7 & mask;
@@ -835,7 +858,9 @@ __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
 __global__ void k_rerank(RerankArgs a, Batch bt) {
   extern __shared__ uint32_t hs[];
   const uint32_t b = blockIdx.y;
-  const uint32_t kq = bt.sel[b].kq;
+  const SelState st = bt.sel[b];
+  const uint32_t kq = n_selected(st, a.kpmax);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st.ncand != st.kq) atomicOr(a.err, SINN_DERR_INTERNAL);
   if (blockIdx.x * (blockDim.x >> 5) >= kq) return;
   const uint32_t nt = bt.nt[b];
   uint32_t tsz = 64;
@@ -857,6 +882,13 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
   uint64_t *ek = bt.ekeys + (uint64_t)b * a.kpmax;
   for (uint32_t c = blockIdx.x * nw + wid; c < kq; c += gridDim.x * nw) {
     const uint32_t id = ~(uint32_t)cand[c];
+    if (id >= a.cap) {  // cannot happen: selected keys carry live ids
+      if (lane == 0) {
+        ek[c] = 0ull;
+        atomicOr(a.err, SINN_DERR_INTERNAL);
+      }
+      continue;
+    }
     const uint64_t fo = a.fwd_off[id];
     const uint32_t nz = a.fwd_nnz[id];
     float s = 0.0f;
@@ -886,7 +918,7 @@ __global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32
   __shared__ uint64_t sk[SINN_MAX_K];
   __shared__ uint32_t s_cnt;
   const uint32_t b = blockIdx.x;
-  const uint32_t kq = bt.sel[b].kq;
+  const uint32_t kq = n_selected(bt.sel[b], kpmax);
   const uint32_t r = min(k, kq);
   const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
   uint64_t pre = 0, msk = 0;
@@ -895,7 +927,10 @@ __global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kq; i += blockDim.x) {
     const uint64_t key = ek[i];
-    if ((key & msk) >= pre) sk[atomicAdd(&s_cnt, 1u)] = key;
+    if ((key & msk) >= pre) {
+      const uint32_t p = atomicAdd(&s_cnt, 1u);
+      if (p < SINN_MAX_K) sk[p] = key;
+    }
   }
   for (uint32_t i = r + threadIdx.x; i < SINN_MAX_K; i += blockDim.x) sk[i] = 0ull;
   __syncthreads();
@@ -938,7 +973,7 @@ __global__ void k_keys_to_scores(const uint32_t *__restrict__ keys, uint64_t cnt
 __global__ void k_cand_out(Batch bt, uint32_t kpmax, uint32_t q0, uint32_t *out_ids,
                            float *out_scores, uint32_t *out_count) {
   const uint32_t b = blockIdx.x;
-  const uint32_t kq = bt.sel[b].kq;
+  const uint32_t kq = n_selected(bt.sel[b], kpmax);
   const uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
   const uint64_t ob = (uint64_t)(q0 + b) * kpmax;
   for (uint32_t i = threadIdx.x; i < kpmax; i += blockDim.x) {
@@ -1041,6 +1076,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   uint64_t B = std::max<uint64_t>(1, budget / one.total);
   B = std::min<uint64_t>(B, r.n_q);
   B = std::min<uint64_t>(B, 65535);
+  if (ix->tune.max_batch) B = std::min<uint64_t>(B, ix->tune.max_batch);
   Layout L = layout_for(ix, (uint32_t)B, kpmax);
   if (fixed && L.total > fixed->bytes) return SINN_ESCRATCH;
   if (!fixed) {
@@ -1071,17 +1107,21 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       std::max<uint64_t>(1, std::min<uint64_t>(ix->cap / ix->T, (ix->next_id + ix->T - 1) / ix->T));
   const uint64_t span = r.stage == Stage::kScores ? ix->cap : used_tiles * ix->T;
   sa.tiles = (uint32_t)(span / ix->T);
+  sa.bound_every = ix->tune.bound_every;
+  sa.tpb = ix->tune.tiles_per_block;
   RerankArgs ra;
   ra.fwd_off = ix->d_fwd_off;
   ra.fwd_nnz = ix->d_fwd_nnz;
   ra.fwd = ix->d_fwd;
   ra.qmax = ix->max_qnnz;
   ra.kpmax = kpmax;
+  ra.cap = ix->cap;
+  ra.err = ix->d_err;
   uint32_t tsz = 64;
   while (tsz < 2 * ix->max_qnnz) tsz <<= 1;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  const uint32_t fb_score_blocks = (uint32_t)std::max(1, sms) * 4;
+  const uint32_t fb_score_blocks = (uint32_t)std::max(1, sms) * ix->tune.dense_blocks_per_sm;
   for (uint32_t q0 = 0; q0 < r.n_q; q0 += (uint32_t)B) {
     const uint32_t nb = (uint32_t)std::min<uint64_t>(B, r.n_q - q0);
     {
@@ -1107,7 +1147,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       CK(cudaGetLastError());
       continue;
     }
-    const bool dense_all = nb < kEmitMinBatch;
+    const bool dense_all = nb < ix->tune.emit_min_batch;
     {
       SinnPhase ph(ix, s, 1);
       if (dense_all) {
@@ -1116,7 +1156,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
         sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
       } else {
         ix->launches++;
-        sk.emit<<<dim3(nb, sa.tiles), kScoreThreads, ssm, s>>>(sa, bt);
+        sk.emit<<<dim3(nb, (sa.tiles + sa.tpb - 1) / sa.tpb), kScoreThreads, ssm, s>>>(sa, bt);
       }
       CK(cudaGetLastError());
     }
@@ -1150,7 +1190,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     {
       SinnPhase ph(ix, s, 3);
       ix->launches += 2;
-      k_rerank<<<dim3(std::min<uint32_t>(kRerankBlocks, (kpmax + 7) / 8), nb), 256,
+      k_rerank<<<dim3(std::min<uint32_t>(ix->tune.rerank_blocks, (kpmax + 7) / 8), nb), 256,
                  (size_t)tsz * 8, s>>>(ra, bt);
       k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
       CK(cudaGetLastError());
@@ -1452,4 +1492,100 @@ extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint
   r.out_scores = out_scores;
   r.stage = Stage::kFull;
   return run_search(ix, r, (cudaStream_t)stream, &fx);
+}
+
+// ------------------------------------------------------------------ tuning
+
+static bool tuning_ok(const sinn_tuning &t) {
+  return t.bound_every >= 1 && t.bound_every <= 64 && t.emit_min_batch >= 1 &&
+         t.emit_min_batch <= 65535 && t.rerank_blocks >= 1 && t.rerank_blocks <= 64 &&
+         t.dense_blocks_per_sm >= 1 && t.dense_blocks_per_sm <= 32 && t.tiles_per_block >= 1 &&
+         t.tiles_per_block <= 64;
+}
+
+extern "C" int sinn_get_tuning(sinn_index *ix, sinn_tuning *out) {
+  if (!ix || !out) return SINN_EINVAL;
+  *out = ix->tune;
+  return SINN_OK;
+}
+
+extern "C" int sinn_set_tuning(sinn_index *ix, const sinn_tuning *t) {
+  if (!ix || !t || !tuning_ok(*t)) return SINN_EINVAL;
+  ix->tune = *t;
+  memset(ix->tune.reserved, 0, sizeof(ix->tune.reserved));
+  return SINN_OK;
+}
+
+// Coordinate descent: each field in turn takes the candidate value with the
+// shortest search time (a change must gain 1% to be kept).
+extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                             const float *q_values, uint32_t n_q, uint32_t k, uint32_t k_prime,
+                             uint32_t reps, sinn_tuning *out, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (n_q == 0 || reps == 0 || reps > 8 || k == 0 || k > SINN_MAX_K || k_prime < k)
+    return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *ids = nullptr;
+  float *sc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaMalloc(&ids, (size_t)n_q * k * 4));
+  CK(cudaMalloc(&sc, (size_t)n_q * k * 4));
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto run = [&](float *ms) -> int {
+    float best = 3.4e38f;
+    for (uint32_t r = 0; r < reps; ++r) {
+      CK(cudaEventRecord(e0, s));
+      int q = sinn_search(ix, q_indptr, q_indices, q_values, n_q, k, k_prime, ids, sc, stream);
+      if (q) return q;
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.0f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return SINN_OK;
+  };
+  const sinn_tuning start = ix->tune;
+  float best_ms = 0.0f;
+  st = run(&best_ms);  // warm-up: scratch grows here
+  if (!st) st = run(&best_ms);
+  sinn_tuning best = ix->tune;
+  struct Field {
+    uint32_t sinn_tuning::*f;
+    uint32_t vals[6];
+  };
+  const Field fields[] = {
+      {&sinn_tuning::max_batch, {0, 256, 512, 1024, 2048, 4096}},
+      {&sinn_tuning::bound_every, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::rerank_blocks, {2, 4, 8, 16, 32, 64}},
+      {&sinn_tuning::dense_blocks_per_sm, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::emit_min_batch, {4, 8, 16, 32, 64, 128}},
+      {&sinn_tuning::tiles_per_block, {1, 2, 4, 8, 16, 32}},
+  };
+  for (const Field &fd : fields) {
+    if (st) break;
+    for (uint32_t v : fd.vals) {
+      if (v == best.*fd.f) continue;
+      if (fd.f == &sinn_tuning::max_batch && v >= n_q) continue;  // same as unlimited
+      ix->tune = best;
+      ix->tune.*fd.f = v;
+      float ms = 0.0f;
+      if ((st = run(&ms))) break;
+      if (ms < 0.99f * best_ms) {
+        best_ms = ms;
+        best = ix->tune;
+      }
+    }
+  }
+  ix->tune = st ? start : best;
+  if (out) *out = ix->tune;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(ids);
+  cudaFree(sc);
+  return st;
 }

@@ -35,6 +35,12 @@ struct sinn_index {
   uint32_t max_qnnz = 0;
   uint64_t scratch_budget = 0;
   int device = 0;
+  // Search launch parameters.  Defaults: refresh the running bound every 4
+  // tiles; launches of fewer than 32 queries score densely (their tiles run
+  // at about the same time, so the bound could not prune); batches as large
+  // as the scratch allows; 8 re-rank blocks per query; 4 dense blocks per SM;
+  // 4 tiles per block of the batched scoring kernel.
+  sinn_tuning tune{4, 32, 0, 8, 4, 4, {0, 0}};
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings

@@ -31,7 +31,7 @@ EXPORTS = [
     "sinn_strerror", "sinn_hash_table", "sinn_sketch_columns", "sinn_inverted_list",
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
     "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
-    "sinn_search_ctx",
+    "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
@@ -70,6 +70,18 @@ class SinnTiming(C.Structure):
         return {"ms": {p: self.ms[i] for i, p in enumerate(PHASES)},
                 "spans": {p: int(self.spans[i]) for i, p in enumerate(PHASES)},
                 "launches": int(self.launches)}
+
+
+class SinnTuning(C.Structure):
+    _fields_ = [("bound_every", C.c_uint32), ("emit_min_batch", C.c_uint32),
+                ("max_batch", C.c_uint32), ("rerank_blocks", C.c_uint32),
+                ("dense_blocks_per_sm", C.c_uint32), ("tiles_per_block", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
+    FIELDS = ["bound_every", "emit_min_batch", "max_batch", "rerank_blocks",
+              "dense_blocks_per_sm", "tiles_per_block"]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f in self.FIELDS}
 
 
 class SinnError(RuntimeError):
@@ -139,6 +151,10 @@ def load(build_if_missing: bool = False):
         "sinn_search_learned": ([vp, vp, vp, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp],
                                 C.c_int),
         "sinn_timing_stop": ([vp, C.POINTER(SinnTiming)], C.c_int),
+        "sinn_get_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
+        "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
+        "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
+                          C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -307,6 +323,30 @@ def sinn_timing_start(ix):
 def sinn_timing_stop(ix) -> dict:
     t = SinnTiming()
     _check(load().sinn_timing_stop(ix, C.byref(t)), "sinn_timing_stop")
+    return t.as_dict()
+
+
+def sinn_get_tuning(ix) -> dict:
+    t = SinnTuning()
+    _check(load().sinn_get_tuning(ix, C.byref(t)), "sinn_get_tuning")
+    return t.as_dict()
+
+
+def sinn_set_tuning(ix, **fields):
+    t = SinnTuning()
+    _check(load().sinn_get_tuning(ix, C.byref(t)), "sinn_get_tuning")
+    for f, v in fields.items():
+        if f not in SinnTuning.FIELDS:
+            raise KeyError(f)
+        setattr(t, f, int(v))
+    _check(load().sinn_set_tuning(ix, C.byref(t)), "sinn_set_tuning")
+
+
+def sinn_autotune(ix, q_indptr, q_indices, q_values, k, k_prime, reps=2, stream=None) -> dict:
+    t = SinnTuning()
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_autotune(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k, k_prime,
+                                reps, C.byref(t), _s(stream)), "sinn_autotune")
     return t.as_dict()
 
 
@@ -544,6 +584,17 @@ class Index:
         sinn_search_learned(self._h, mlp.handle, ip, ix, v, k, kp_min, kp_max, ids, sc, kp,
                             stream)
         return ids, sc, kp
+
+    def tuning(self) -> dict:
+        return sinn_get_tuning(self._h)
+
+    def set_tuning(self, **fields):
+        sinn_set_tuning(self._h, **fields)
+
+    def autotune(self, indptr, indices, values, k: int, k_prime: int, reps: int = 2,
+                 stream=None) -> dict:
+        ip, ix, v = self._csr(indptr, indices, values)
+        return sinn_autotune(self._h, ip, ix, v, k, k_prime, reps, stream)
 
     def sync(self, stream=None):
         sinn_sync(self._h, stream)

@@ -1,0 +1,88 @@
+"""Launch tuning: every tuning returns the same results (the launch
+parameters change only the fp32 summation order and the batching), invalid
+tunings are rejected, and the autotuner leaves a valid, faster-or-equal
+configuration in place."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2301_10622_gb300 import sinnamon, synth  # noqa: E402
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def setup():
+    w = synth.scaled(synth.WORKLOADS["text"], 30000, n=8000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=400)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=2048)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    q = (qs.indptr.astype(np.int64), qs.indices.astype(np.int32), qs.values)
+    yield ix, q
+    ix.close()
+
+
+def _same(a, b):
+    (ia, sa), (ib, sb) = a, b
+    scale = np.maximum(np.abs(sa).max(axis=1, keepdims=True), 1e-30)
+    assert np.all(np.abs(sa.astype(np.float64) - sb) <= REL * scale)
+    diff = ia != ib
+    assert np.all(np.abs(sa[diff].astype(np.float64) - sb[diff]) <= REL * scale.repeat(
+        ia.shape[1], axis=1)[diff])
+
+
+def _run(ix, q, kp=300):
+    ids, sc = ix.search(*q, k=10, k_prime=kp)
+    return ids.cpu().numpy(), sc.cpu().numpy()
+
+
+@pytest.mark.parametrize("fields", [
+    dict(max_batch=7), dict(max_batch=33, bound_every=1), dict(bound_every=64),
+    dict(emit_min_batch=1, max_batch=40), dict(emit_min_batch=65535),
+    dict(rerank_blocks=1), dict(rerank_blocks=64, dense_blocks_per_sm=1),
+    dict(dense_blocks_per_sm=32, emit_min_batch=500), dict(tiles_per_block=1),
+    dict(tiles_per_block=3, bound_every=5), dict(tiles_per_block=64, bound_every=1)])
+def test_every_tuning_gives_the_same_results(setup, fields):
+    ix, q = setup
+    base = ix.tuning()
+    want = _run(ix, q)
+    try:
+        ix.set_tuning(**fields)
+        assert all(ix.tuning()[f] == v for f, v in fields.items())
+        _same(want, _run(ix, q))
+    finally:
+        ix.set_tuning(**base)
+
+
+@pytest.mark.parametrize("field,value", [("bound_every", 0), ("bound_every", 65),
+                                          ("emit_min_batch", 0), ("rerank_blocks", 0),
+                                          ("rerank_blocks", 65), ("dense_blocks_per_sm", 0),
+                                          ("dense_blocks_per_sm", 33), ("tiles_per_block", 0),
+                                          ("tiles_per_block", 65)])
+def test_invalid_tuning_is_rejected(setup, field, value):
+    ix, _ = setup
+    before = ix.tuning()
+    with pytest.raises(sinnamon.SinnError):
+        ix.set_tuning(**{field: value})
+    assert ix.tuning() == before
+
+
+def test_autotune_picks_a_valid_tuning(setup):
+    ix, q = setup
+    want = _run(ix, q)
+    t = ix.autotune(*q, k=10, k_prime=300, reps=1)
+    assert t == ix.tuning()
+    assert 1 <= t["bound_every"] <= 64 and 1 <= t["rerank_blocks"] <= 64
+    assert 1 <= t["dense_blocks_per_sm"] <= 32 and 1 <= t["emit_min_batch"] <= 65535
+    assert 1 <= t["tiles_per_block"] <= 64
+    _same(want, _run(ix, q))
