@@ -57,7 +57,7 @@ typedef struct sinn_config {
   uint32_t n;              /* dimensionality; coordinates are [0, n) */
   uint32_t m;              /* sketch bins per side (U and L have m rows each), m <= 4096 */
   uint32_t h;              /* number of random mappings pi_o: [n] -> [m], 1 <= h <= min(m, 8) */
-  uint32_t tile_docs;      /* ids per tile T: power of two in [1024, 32768]; 0 -> 4096 */
+  uint32_t tile_docs;      /* ids per tile T: power of two in [1024, 16384]; 0 -> 4096 */
   uint64_t seed;           /* seed of the mappings; 0 -> 0x5151 */
   uint64_t capacity_hint;  /* id slots to reserve up front; 0 -> one tile */
   const uint32_t *table;   /* optional host table[n*h] with table[j*h+o] = pi_o(j) < m;
@@ -193,7 +193,8 @@ typedef struct sinn_tuning {
                                 emitting candidates, 1..65535 (default 32) */
   uint32_t max_batch;        /* cap on queries per internal launch, 0 = as many as the
                                 scratch holds (default 0) */
-  uint32_t rerank_blocks;    /* re-rank blocks per query, 1..64 (default 8) */
+  uint32_t rerank_blocks;    /* re-rank blocks per query, 1..1024, or 0 (default) for
+                                one per 64 candidates of the largest k' */
   uint32_t dense_blocks_per_sm; /* grid of the dense scoring kernel per SM, 1..32
                                    (default 4) */
   uint32_t tiles_per_block;  /* tiles one block of the batched scoring kernel covers,

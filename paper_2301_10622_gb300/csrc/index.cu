@@ -603,7 +603,7 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   const uint32_t n = cfg->n, m = cfg->m, h = cfg->h;
   if (n == 0 || m == 0 || h == 0 || h > m || h > SINN_MAX_H || m > 4096) return SINN_EINVAL;
   uint32_t T = cfg->tile_docs ? cfg->tile_docs : 4096;
-  if (T < 1024 || T > 32768 || (T & (T - 1))) return SINN_EINVAL;
+  if (T < 1024 || T > 16384 || (T & (T - 1))) return SINN_EINVAL;
   if (cfg->table)
     for (uint64_t t = 0; t < (uint64_t)n * h; ++t)
       if (cfg->table[t] >= m) return SINN_EINVAL;

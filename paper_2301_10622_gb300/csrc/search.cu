@@ -43,6 +43,7 @@ constexpr uint32_t kEmitCap = 131072;   // emitted candidates kept per query
 constexpr uint32_t kScoreThreads = 512;
 constexpr uint32_t kChunk = 8192;       // keys per block in the dense select passes
 constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
+constexpr uint32_t kBmGroups = 2;       // 4-id groups per thread a bitmap term pass holds
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
 
 enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
@@ -289,8 +290,9 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   constexpr uint32_t NW = kScoreThreads / 32;
   constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
   const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT;
-  float *acc = (float *)sm;                          // T
-  uint32_t *hist = sm + T;                           // 4096
+  float *acc = (float *)sm;                          // T: array terms (atomics)
+  float *bacc = acc + T;                             // T: bitmap terms (owner only)
+  uint32_t *hist = sm + 2 * T;                       // 4096
   uint32_t *t_start = hist + 4096;                   // kTermBatch
   uint32_t *t_cnt = t_start + kTermBatch;            // kTermBatch
   uint32_t *t_cp = t_cnt + kTermBatch;               // kTermBatch+1: chunk prefix (arrays)
@@ -317,25 +319,28 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
     const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
     const uint16_t *post = a.tile_post[t];
     const uint64_t id0 = (uint64_t)t << a.log2T;
-    __syncthreads();  // the previous tile's epilogue is done with acc
-    for (uint32_t d = tid; d < T; d += kScoreThreads) acc[d] = 0.0f;
+    __syncthreads();  // the previous tile's epilogue is done with acc and bacc
+    for (uint32_t d = 4 * tid; d < T; d += 4 * kScoreThreads) {
+      *(float4 *)(acc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
+      *(float4 *)(bacc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (uint32_t bi = 0; bi < nbatch; ++bi) {
       const uint32_t i0 = bi * kTermBatch;
       const uint32_t nb = nt > i0 ? min(kTermBatch, nt - i0) : 0u;
-      const bool last = bi + 1 == nbatch;
-      __syncthreads();  // the previous batch is consumed
-      if (tid == 0) s_nbm = 0;
-      for (uint32_t k = tid; k < nb; k += kScoreThreads) {
-        const uint32_t j = terms[i0 + k].j;
-        const uint2 de = dir[j];
-        t_start[k] = de.x;
-        t_cnt[k] = de.y;
-        t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
-        t_v[k] = terms[i0 + k].v;
-        for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
-      }
-      __syncthreads();
-      if (wid == 0) {  // exclusive prefix of the array chunk counts; bitmap list
+      if (bi > 0) __syncthreads();  // the previous batch is consumed
+      if (wid == 0) {
+        // stage the batch's terms, then the exclusive prefix of the array
+        // chunk counts and the list of bitmap terms
+        for (uint32_t k = lane; k < nb; k += 32) {
+          const uint32_t j = terms[i0 + k].j;
+          const uint2 de = dir[j];
+          t_start[k] = de.x;
+          t_cnt[k] = de.y;
+          t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
+          t_v[k] = terms[i0 + k].v;
+          for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
+        }
+        __syncwarp();
         uint32_t run = 0, nbm = 0;
         for (uint32_t base = 0; base < nb; base += 32) {
           const uint32_t i = base + lane;
@@ -358,6 +363,46 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
         }
       }
       __syncthreads();
+      // bitmap terms: thread tid owns ids 4*tid + 4*kScoreThreads*g .. +3;
+      // their partial sums go to bacc, which only the owner touches, so the
+      // array terms need not wait for them
+      const uint32_t nbm = s_nbm;
+      for (uint32_t g0 = 0; g0 < T && nbm > 0; g0 += 4 * kScoreThreads * kBmGroups) {
+        float4 r[kBmGroups];
+#pragma unroll
+        for (uint32_t g = 0; g < kBmGroups; ++g) {
+          const uint32_t d0 = g0 + g * 4 * kScoreThreads + 4 * tid;
+          r[g] = d0 < T ? *(const float4 *)(bacc + d0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (uint32_t kk = 0; kk < nbm; ++kk) {
+          const uint32_t k = t_bl[kk];
+          const float v = t_v[k];
+          const bool pos = v > 0.0f;
+          const float *plane = pos ? a.U : a.L;
+          const float *row[HS];
+#pragma unroll
+          for (uint32_t o = 0; o < HS; ++o)
+            if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+          const uint32_t *bm = (const uint32_t *)(post + t_start[k]);
+#pragma unroll
+          for (uint32_t g = 0; g < kBmGroups; ++g) {
+            const uint32_t d0 = g0 + g * 4 * kScoreThreads + 4 * tid;
+            if (d0 < T) {
+              const uint32_t bits = __ldg(bm + (d0 >> 5)) >> (d0 & 31);
+              const float4 x = decode4<H>(row, a.h, pos, d0);
+              if (bits & 1u) r[g].x = fmaf(v, x.x, r[g].x);
+              if (bits & 2u) r[g].y = fmaf(v, x.y, r[g].y);
+              if (bits & 4u) r[g].z = fmaf(v, x.z, r[g].z);
+              if (bits & 8u) r[g].w = fmaf(v, x.w, r[g].w);
+            }
+          }
+        }
+#pragma unroll
+        for (uint32_t g = 0; g < kBmGroups; ++g) {
+          const uint32_t d0 = g0 + g * 4 * kScoreThreads + 4 * tid;
+          if (d0 < T) *(float4 *)(bacc + d0) = r[g];
+        }
+      }
       // array terms
       const uint32_t C = part[0];
       const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
@@ -409,37 +454,21 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           c += nck;
         }
       }
-      __syncthreads();
-      // bitmap terms, then (last batch) the epilogue, from registers
-      const uint32_t nbm = s_nbm;
-      for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
-        const uint32_t d0 = g0 + 4 * tid;
-        const bool in = d0 < T;
-        float4 r = in ? *(const float4 *)(acc + d0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t kk = 0; kk < nbm && in; ++kk) {
-          const uint32_t k = t_bl[kk];
-          const float v = t_v[k];
-          const bool pos = v > 0.0f;
-          const float *plane = pos ? a.U : a.L;
-          const float *row[HS];
-#pragma unroll
-          for (uint32_t o = 0; o < HS; ++o)
-            if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
-          const uint32_t w = __ldg((const uint32_t *)(post + t_start[k]) + (d0 >> 5));
-          const float4 x = decode4<H>(row, a.h, pos, d0);
-          const uint32_t bits = w >> (d0 & 31);
-          if (bits & 1u) r.x = fmaf(v, x.x, r.x);
-          if (bits & 2u) r.y = fmaf(v, x.y, r.y);
-          if (bits & 4u) r.z = fmaf(v, x.z, r.z);
-          if (bits & 8u) r.w = fmaf(v, x.w, r.w);
-        }
-        if (!last || !EMIT) {
-          if (in) *(float4 *)(acc + d0) = r;
-          continue;
-        }
-        // EMIT epilogue: ids at or above the running bound count and are emitted
-        const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
-        const float rv[4] = {r.x, r.y, r.z, r.w};
+    }
+    __syncthreads();  // the array terms' atomics are complete
+    // epilogue, 4 consecutive ids per thread: score = array part + bitmap part
+    for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
+      const uint32_t d0 = g0 + 4 * tid;
+      const bool in = d0 < T;
+      float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in) {
+        const float4 x = *(const float4 *)(acc + d0), y = *(const float4 *)(bacc + d0);
+        sa = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+      }
+      const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
+      const float rv[4] = {sa.x, sa.y, sa.z, sa.w};
+      if (EMIT) {
+        // ids at or above the running bound count and are emitted
 #pragma unroll
         for (uint32_t q = 0; q < 4; ++q) {
           const uint32_t key = sinn_f2key(rv[q] + 0.0f);
@@ -451,18 +480,20 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
               el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
           }
         }
-      }
-    }
-    if (!EMIT) {
-      // dense: a key for every id slot of the tile (0 = not live), counted
-      __syncthreads();
-      for (uint32_t d = tid; d < T; d += kScoreThreads) {
-        const bool lv = sinn_is_live(a.live, id0 + d);
-        const uint32_t key = sinn_f2key(acc[d] + 0.0f);
-        bt.keys[(uint64_t)b * a.cap + id0 + d] = lv ? key : 0u;
-        const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
-        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
-        if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
+      } else {
+        // dense: a key for every id slot (0 = not live), counted
+        uint32_t kv[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+          const bool lv = (lwv >> q) & 1u;
+          const uint32_t key = sinn_f2key(rv[q] + 0.0f);
+          kv[q] = lv ? key : 0u;
+          const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
+          const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
+          if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
+        }
+        if (in)
+          *(uint4 *)(bt.keys + (uint64_t)b * a.cap + id0 + d0) = make_uint4(kv[0], kv[1], kv[2], kv[3]);
       }
     }
   }
@@ -892,20 +923,31 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
     const uint64_t fo = a.fwd_off[id];
     const uint32_t nz = a.fwd_nnz[id];
     float s = 0.0f;
-    for (uint32_t e = lane; e < nz; e += 32) {
-      const uint2 pr = __ldg(a.fwd + fo + e);
-      uint32_t h = hslot(pr.x, mask);
-      float qv = 0.0f;
-      while (true) {
-        uint32_t kk = hk[h];
-        if (kk == pr.x) {
-          qv = hv[h];
-          break;
-        }
-        if (kk == 0xFFFFFFFFu) break;
-        h = (h + 1) & mask;
+    // four entries per lane in flight, then their look-ups; the sum keeps
+    // the entries' order within each lane
+    for (uint32_t e0 = 0; e0 < nz; e0 += 128) {
+      uint2 pr[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t e = e0 + u * 32 + lane;
+        pr[u] = e < nz ? __ldg(a.fwd + fo + e) : make_uint2(0xFFFFFFFFu, 0u);
       }
-      s = fmaf(qv, __uint_as_float(pr.y), s);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        if (pr[u].x == 0xFFFFFFFFu) continue;
+        uint32_t h = hslot(pr[u].x, mask);
+        float qv = 0.0f;
+        while (true) {
+          const uint32_t kk = hk[h];
+          if (kk == pr[u].x) {
+            qv = hv[h];
+            break;
+          }
+          if (kk == 0xFFFFFFFFu) break;
+          h = (h + 1) & mask;
+        }
+        s = fmaf(qv, __uint_as_float(pr[u].y), s);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     if (lane == 0) ek[c] = ((uint64_t)sinn_f2key(s + 0.0f) << 32) | (uint32_t)~id;
@@ -1059,7 +1101,7 @@ struct SearchReq {
 };
 
 size_t score_smem(const sinn_index *ix) {
-  return (size_t)ix->T * 4 + 4096 * 4 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
+  return (size_t)ix->T * 8 + 4096 * 4 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
 }
 
 // Scratch supplied by the caller instead of the index's own (grown) buffer.
@@ -1190,7 +1232,9 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     {
       SinnPhase ph(ix, s, 3);
       ix->launches += 2;
-      k_rerank<<<dim3(std::min<uint32_t>(ix->tune.rerank_blocks, (kpmax + 7) / 8), nb), 256,
+      // blocks per query: the tuning's count, or (0) about 64 candidates each
+      const uint32_t rb = ix->tune.rerank_blocks ? ix->tune.rerank_blocks : (kpmax + 63) / 64;
+      k_rerank<<<dim3(std::min<uint32_t>(rb, (kpmax + 7) / 8), nb), 256,
                  (size_t)tsz * 8, s>>>(ra, bt);
       k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
       CK(cudaGetLastError());
@@ -1498,7 +1542,7 @@ extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint
 
 static bool tuning_ok(const sinn_tuning &t) {
   return t.bound_every >= 1 && t.bound_every <= 64 && t.emit_min_batch >= 1 &&
-         t.emit_min_batch <= 65535 && t.rerank_blocks >= 1 && t.rerank_blocks <= 64 &&
+         t.emit_min_batch <= 65535 && t.rerank_blocks <= 1024 &&
          t.dense_blocks_per_sm >= 1 && t.dense_blocks_per_sm <= 32 && t.tiles_per_block >= 1 &&
          t.tiles_per_block <= 64;
 }
@@ -1561,7 +1605,7 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   const Field fields[] = {
       {&sinn_tuning::max_batch, {0, 256, 512, 1024, 2048, 4096}},
       {&sinn_tuning::bound_every, {1, 2, 4, 8, 16, 32}},
-      {&sinn_tuning::rerank_blocks, {2, 4, 8, 16, 32, 64}},
+      {&sinn_tuning::rerank_blocks, {0, 4, 16, 64, 256, 1024}},
       {&sinn_tuning::dense_blocks_per_sm, {1, 2, 4, 8, 16, 32}},
       {&sinn_tuning::emit_min_batch, {4, 8, 16, 32, 64, 128}},
       {&sinn_tuning::tiles_per_block, {1, 2, 4, 8, 16, 32}},

@@ -38,9 +38,10 @@ struct sinn_index {
   // Search launch parameters.  Defaults: refresh the running bound every 4
   // tiles; launches of fewer than 32 queries score densely (their tiles run
   // at about the same time, so the bound could not prune); batches as large
-  // as the scratch allows; 8 re-rank blocks per query; 4 dense blocks per SM;
-  // 4 tiles per block of the batched scoring kernel.
-  sinn_tuning tune{4, 32, 0, 8, 4, 4, {0, 0}};
+  // as the scratch allows; re-rank blocks per query sized to k' (about 64
+  // candidates each); 4 dense blocks per SM; 4 tiles per block of the
+  // batched scoring kernel.
+  sinn_tuning tune{4, 32, 0, 0, 4, 4, {0, 0}};
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings

@@ -49,7 +49,7 @@ def _run(ix, q, kp=300):
 @pytest.mark.parametrize("fields", [
     dict(max_batch=7), dict(max_batch=33, bound_every=1), dict(bound_every=64),
     dict(emit_min_batch=1, max_batch=40), dict(emit_min_batch=65535),
-    dict(rerank_blocks=1), dict(rerank_blocks=64, dense_blocks_per_sm=1),
+    dict(rerank_blocks=1), dict(rerank_blocks=1024, dense_blocks_per_sm=1), dict(rerank_blocks=0),
     dict(dense_blocks_per_sm=32, emit_min_batch=500), dict(tiles_per_block=1),
     dict(tiles_per_block=3, bound_every=5), dict(tiles_per_block=64, bound_every=1)])
 def test_every_tuning_gives_the_same_results(setup, fields):
@@ -65,8 +65,8 @@ def test_every_tuning_gives_the_same_results(setup, fields):
 
 
 @pytest.mark.parametrize("field,value", [("bound_every", 0), ("bound_every", 65),
-                                          ("emit_min_batch", 0), ("rerank_blocks", 0),
-                                          ("rerank_blocks", 65), ("dense_blocks_per_sm", 0),
+                                          ("emit_min_batch", 0), ("rerank_blocks", 1025),
+                                          ("dense_blocks_per_sm", 0),
                                           ("dense_blocks_per_sm", 33), ("tiles_per_block", 0),
                                           ("tiles_per_block", 65)])
 def test_invalid_tuning_is_rejected(setup, field, value):
@@ -82,7 +82,7 @@ def test_autotune_picks_a_valid_tuning(setup):
     want = _run(ix, q)
     t = ix.autotune(*q, k=10, k_prime=300, reps=1)
     assert t == ix.tuning()
-    assert 1 <= t["bound_every"] <= 64 and 1 <= t["rerank_blocks"] <= 64
+    assert 1 <= t["bound_every"] <= 64 and 0 <= t["rerank_blocks"] <= 1024
     assert 1 <= t["dense_blocks_per_sm"] <= 32 and 1 <= t["emit_min_batch"] <= 65535
     assert 1 <= t["tiles_per_block"] <= 64
     _same(want, _run(ix, q))

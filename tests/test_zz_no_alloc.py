@@ -67,7 +67,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch(built):
     sinnamon, synth = built
     # 20M id slots need ~80 MB of score keys for a single query: more than the
     # fixed 64 MiB scratch
-    ix = sinnamon.Index(64, 8, 1, tile_docs=32768, capacity_hint=20_000_000)
+    ix = sinnamon.Index(64, 8, 1, tile_docs=16384, capacity_hint=20_000_000)
     ip = torch.tensor([0, 1], dtype=torch.int64, device=ix.device)
     ii = torch.tensor([3], dtype=torch.int32, device=ix.device)
     vv = torch.tensor([1.0], dtype=torch.float32, device=ix.device)
