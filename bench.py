@@ -357,12 +357,35 @@ def run_ours(args):
             sinnamon.sinn_search_learned(h, mlp.handle, qip, qix, qv, k, k, args.kp_max, oids,
                                          osc, out_kp)
 
+    # launch tuning chosen by the autotuner on a sample of the step's queries
+    tuning = None
+    if not args.no_autotune:
+        t0 = time.time()
+        sq = qs.slice(0, min(qs.rows, 2000))
+        tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
+                             k, kp, reps=2)
+        log(f"autotuned in {time.time() - t0:.1f}s: {tuning}")
+    tuning = ix.tuning()
+    # the step's search as one recorded CUDA graph, replayed every step
+    plan = None
+    if not args.no_graph:
+        plan = (sinnamon.Plan(ix, g_qip, g_qix, g_qv, k, kp, scratch_bytes=args.scratch_gb << 30)
+                if mlp is None else
+                sinnamon.Plan(ix, g_qip, g_qix, g_qv, k, args.kp_max, mlp=mlp, k_prime_min=k,
+                              scratch_bytes=args.scratch_gb << 30))
+        out_ids, out_sc = plan.out_ids, plan.out_scores
+        if mlp is not None:
+            out_kp = plan.out_kprime
+
     def step(si):
         executed.append(si)
         sinnamon.sinn_delete(h, dels[si])
         ip, ii, vv, _ = parts[si]
         sinnamon.sinn_insert(h, ip, ii, vv, new_ids)
-        search(g_qip, g_qix, g_qv, out_ids, out_sc)
+        if plan is not None:
+            plan.run()
+        else:
+            search(g_qip, g_qix, g_qv, out_ids, out_sc)
 
     for si in range(args.warmup):
         step(si)
@@ -488,11 +511,15 @@ def run_ours(args):
 
         # batched latency (learned, as timed) and the batched fixed-k' search
         ev0.record()
-        search(g_qip, g_qix, g_qv, out_ids, out_sc)
+        if plan is not None:
+            plan.run()
+        else:
+            search(g_qip, g_qix, g_qv, out_ids, out_sc)
         ev1.record()
         torch.cuda.synchronize()
         extras["batched"] = {"qps": value / world, "batch_ms": ev0.elapsed_time(ev1),
-                             "p50_ms": ev0.elapsed_time(ev1), "p99_ms": ev0.elapsed_time(ev1)}
+                             "p50_ms": ev0.elapsed_time(ev1), "p99_ms": ev0.elapsed_time(ev1),
+                             "plan_recordings": plan.recordings if plan is not None else None}
         fx_ids = torch.empty_like(out_ids)
         fx_sc = torch.empty_like(out_sc)
         sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids, fx_sc)
@@ -534,7 +561,9 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": config_dict(args, w, docs, qs, T),
+        "config": dict(config_dict(args, w, docs, qs, T), tuning=tuning,
+                       search_launch=("one recorded CUDA graph per step (sinn_plan)"
+                                      if plan is not None else "direct launches")),
         "roofline": roof,
         "cpu_baseline": extras.get("cpu_baseline"),
         "e2e": extras.get("e2e"),
@@ -637,6 +666,8 @@ def main():
     ap.add_argument("--kp-cap", type=int, default=20000)
     ap.add_argument("--kp-max", type=int, default=4096)
     ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--no-graph", action="store_true", help="launch the search directly")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rates", default="20000,2000,5000",
                     help="inserts,deletes,queries per second")

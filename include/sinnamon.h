@@ -199,7 +199,10 @@ typedef struct sinn_tuning {
                                    (default 4) */
   uint32_t tiles_per_block;  /* tiles one block of the batched scoring kernel covers,
                                 1..64 (default 4) */
-  uint32_t reserved[2];      /* zero */
+  uint32_t persistent_blocks_per_sm; /* 0 (default): one block per (query, tile group);
+                                        1..4: that many resident blocks per SM take
+                                        (query, tile group) items from a counter */
+  uint32_t reserved[1];      /* zero */
 } sinn_tuning;
 
 /* Current tuning of the index into *out (host). */

@@ -406,6 +406,8 @@ __global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
   l_out[i] = L[(uint64_t)k * cap + id];
 }
 
+__global__ void k_store_u64(uint64_t *dst, uint64_t v) { *dst = v; }
+
 // ------------------------------------------------------------- host side
 
 static cudaEvent_t tm_event(sinn_index *ix) {
@@ -419,17 +421,26 @@ static cudaEvent_t tm_event(sinn_index *ix) {
   return e;
 }
 
+// Inside a stream capture an event must be recorded as an external event to
+// become a node that records at every replay.
+static void tm_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
+
 SinnPhase::SinnPhase(sinn_index *ix_, cudaStream_t s_, int ph) : ix(ix_), s(s_), phase(ph) {
   if (ix->tm_on) {
     a = tm_event(ix);
-    cudaEventRecord(a, s);
+    tm_record(a, s);
   }
 }
 
 SinnPhase::~SinnPhase() {
   if (a) {
     cudaEvent_t b = tm_event(ix);
-    cudaEventRecord(b, s);
+    tm_record(b, s);
     ix->tm_spans.push_back({phase, a, b});
   }
 }
@@ -442,6 +453,10 @@ extern "C" int sinn_timing_start(sinn_index *ix) {
     ix->tm_pool.push_back(sp.b);
   }
   ix->tm_spans.clear();
+  for (int p = 0; p < SINN_PHASES; ++p) {
+    ix->tm_acc_ms[p] = 0.0;
+    ix->tm_acc_spans[p] = 0;
+  }
   ix->launches = 0;
   ix->tm_on = true;
   return SINN_OK;
@@ -464,6 +479,10 @@ extern "C" int sinn_timing_stop(sinn_index *ix, sinn_timing_t *out) {
     ix->tm_pool.push_back(sp.b);
   }
   ix->tm_spans.clear();
+  for (int p = 0; p < SINN_PHASES; ++p) {
+    out->ms[p] += ix->tm_acc_ms[p];
+    out->spans[p] += ix->tm_acc_spans[p];
+  }
   out->launches = ix->launches;
   return SINN_OK;
 }
@@ -489,6 +508,7 @@ static void release(sinn_index *ix) {
   cudaFree(ix->d_tile_dir);
   cudaFree(ix->d_tile_post);
   cudaFree(ix->d_err);
+  cudaFree(ix->d_live_count);
   cudaFree(ix->scratch);
   cudaFree(ix->iscratch);
   cudaFree(ix->hstage);
@@ -576,6 +596,7 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   if ((st = realloc_copy(&ix->d_tile_dir, ot * ix->n, nt * ix->n, true))) return st;
   if ((st = realloc_copy(&ix->d_tile_post, ot, nt, true))) return st;
   ix->cap = nc;
+  ix->shape_version++;
   ix->live.resize(nc, 0);
   ix->nnz.resize(nc, 0);
   ix->tile_post.resize(nt, nullptr);
@@ -594,6 +615,7 @@ static int grow_store(sinn_index *ix, uint64_t need) {
   int st = realloc_copy(&ix->d_fwd, ix->fwd_used, nc, false);
   if (st) return st;
   ix->fwd_cap = nc;
+  ix->shape_version++;
   return SINN_OK;
 }
 
@@ -641,6 +663,8 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
     return fail(st);
   if ((st = sinn_check_cuda(cudaMalloc(&ix->d_err, sizeof(uint32_t) * 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_err, 0, sizeof(uint32_t) * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_live_count, sizeof(uint64_t))))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(ix->d_live_count, 0, sizeof(uint64_t))))) return fail(st);
   uint64_t hint = std::max<uint64_t>(cfg->capacity_hint, T);
   if ((st = grow_capacity(ix, hint))) return fail(st);
   *out = ix;
@@ -846,6 +870,7 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
     if ((st = grow_capacity(ix, max_id + 1))) return st;
     if ((st = grow_store(ix, ix->fwd_used + total))) return st;
     ix->free_ids = fq;
+    if ((nid + ix->T - 1) / ix->T != (ix->next_id + ix->T - 1) / ix->T) ix->shape_version++;
     ix->next_id = nid;
   }
   // offsets in the store, staged with the ids
@@ -884,6 +909,9 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
     ix->live_count++;
     tiles.push_back(id >> ix->log2T);
   }
+  ix->launches++;
+  k_store_u64<<<1, 1, 0, s>>>(ix->d_live_count, ix->live_count);
+  CK(cudaGetLastError());
   std::sort(tiles.begin(), tiles.end());
   tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
   if ((st = rebuild_tiles(ix, tiles, s))) return st;
@@ -937,6 +965,9 @@ extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, 
     ix->live_count--;
     ix->free_ids.push(id);
   }
+  ix->launches++;
+  k_store_u64<<<1, 1, 0, s>>>(ix->d_live_count, ix->live_count);
+  CK(cudaGetLastError());
   uint32_t bits = 0;
   if ((st = read_and_clear_err(ix, s, &bits))) return st;
   return bits ? SINN_EDEVICE : SINN_OK;

@@ -486,6 +486,10 @@ uint64_t splitmix_next(uint64_t &s) {
 
 }  // namespace
 
+// The network's bf16 weight copies made current (no work when they are);
+// used by recorded searches, which replay a graph without this check.
+int sinn_mlp_refresh(sinn_mlp *m, cudaStream_t s) { return refresh_bf16(m, s); }
+
 extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, sinn_mlp **out) {
   if (!out || n_in == 0 || hidden == 0 || hidden > 4096 || n_in > 1024) return SINN_EINVAL;
   *out = nullptr;

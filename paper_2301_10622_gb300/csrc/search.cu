@@ -104,7 +104,8 @@ __device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t *counter) {
 __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *__restrict__ q_idx,
                         const float *__restrict__ q_val, uint32_t q0, uint32_t n, uint32_t qmax,
                         uint32_t kp_scalar, const uint32_t *__restrict__ kp_arr, uint32_t kp_min,
-                        uint32_t kp_max, uint64_t live_count, Batch bt, uint32_t *err) {
+                        uint32_t kp_max, const uint64_t *live_count, Batch bt,
+                        uint32_t *err) {
   extern __shared__ uint32_t sq[];
   uint32_t *sj = sq;                  // qmax
   float *sv = (float *)(sq + qmax);   // qmax
@@ -154,7 +155,8 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     st.pbits = 0;
     st.rem = 0;
     st.cnt = 0;
-    st.kq = s_bad ? 0u : (uint32_t)(live_count < kp ? live_count : (uint64_t)kp);
+    const uint64_t lc = *live_count;
+    st.kq = s_bad ? 0u : (uint32_t)(lc < kp ? lc : (uint64_t)kp);
     st.ncand = 0;
     st.nbnd = 0;
     st.dense = 0;
@@ -529,6 +531,26 @@ __global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Ba
   score_tiles<true, H>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
 }
 
+// The same work as k_score_emit from a fixed grid of blocks: each block takes
+// (query, group) items from a counter in the same query-fastest order until
+// none is left.
+template <int H>
+__global__ void __launch_bounds__(kScoreThreads, 4)
+    k_score_emit_persistent(ScoreArgs a, Batch bt, uint32_t nb, unsigned long long *next) {
+  extern __shared__ uint32_t sm[];
+  __shared__ unsigned long long s_item;
+  const uint64_t groups = (a.tiles + a.tpb - 1) / a.tpb, total = groups * nb;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1ull);
+    __syncthreads();
+    const uint64_t item = s_item;
+    __syncthreads();  // every thread has read the item before the next draw
+    if (item >= total) break;
+    const uint32_t b = (uint32_t)(item % nb), t0 = (uint32_t)(item / nb) * a.tpb;
+    score_tiles<true, H>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
+  }
+}
+
 // Dense scoring of the flagged queries (grid-stride over (query, tile)).
 template <int H>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, Batch bt) {
@@ -546,12 +568,13 @@ __global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, B
 struct ScoreKernels {
   void (*emit)(ScoreArgs, Batch);
   void (*dense)(ScoreArgs, Batch);
+  void (*persistent)(ScoreArgs, Batch, uint32_t, unsigned long long *);
 };
 
 ScoreKernels score_kernels(uint32_t h) {
-  if (h == 1) return {k_score_emit<1>, k_score_dense<1>};
-  if (h == 2) return {k_score_emit<2>, k_score_dense<2>};
-  return {k_score_emit<0>, k_score_dense<0>};
+  if (h == 1) return {k_score_emit<1>, k_score_dense<1>, k_score_emit_persistent<1>};
+  if (h == 2) return {k_score_emit<2>, k_score_dense<2>, k_score_emit_persistent<2>};
+  return {k_score_emit<0>, k_score_dense<0>, k_score_emit_persistent<0>};
 }
 
 // ------------------------------------------------------------------ select
@@ -1049,7 +1072,7 @@ Layout layout_for(const sinn_index *ix, uint32_t B, uint32_t kpmax) {
   L.bnd = o;     o = align256(o + (size_t)B * kBoundCap * 8);
   L.ekeys = o;   o = align256(o + (size_t)B * kpmax * 8);
   L.elist = o;   o = align256(o + (size_t)B * kEmitCap * 8);
-  L.ctr = o;     o = align256(o + ((size_t)3 * B + 1) * 4);
+  L.ctr = o;     o = align256(o + ((size_t)3 * B + 4) * 4);
   L.flagged = o; o = align256(o + (size_t)B * 4);
   L.total = o;
   return L;
@@ -1130,6 +1153,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   const ScoreKernels sk = score_kernels(ix->h);
   CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  CK(cudaFuncSetAttribute(sk.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   ScoreArgs sa;
   sa.tile_dir = ix->d_tile_dir;
   sa.tile_post = ix->d_tile_post;
@@ -1171,11 +1195,11 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       ix->launches++;
       k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0,
                                                          ix->n, ix->max_qnnz, r.kp, r.kp_arr,
-                                                         r.kp_min, r.kp_max, ix->live_count, bt,
+                                                         r.kp_min, r.kp_max, ix->d_live_count, bt,
                                                          ix->d_err);
       CK(cudaGetLastError());
       CK(cudaMemsetAsync(bt.hist0, 0, (size_t)B * (4096 + 4096 + 256) * 4, s));
-      CK(cudaMemsetAsync(bt.ecnt, 0, ((size_t)3 * B + 1) * 4, s));
+      CK(cudaMemsetAsync(bt.ecnt, 0, ((size_t)3 * B + 4) * 4, s));
     }
     if (r.stage == Stage::kScores) {  // dense keys for every query
       ix->launches += 3;
@@ -1198,7 +1222,15 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
         sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
       } else {
         ix->launches++;
-        sk.emit<<<dim3(nb, (sa.tiles + sa.tpb - 1) / sa.tpb), kScoreThreads, ssm, s>>>(sa, bt);
+        if (ix->tune.persistent_blocks_per_sm) {
+          // 8-byte aligned work counter after the nflag word
+          unsigned long long *next =
+              (unsigned long long *)(((uintptr_t)(bt.nflag + 1) + 7) & ~(uintptr_t)7);
+          sk.persistent<<<(unsigned)sms * ix->tune.persistent_blocks_per_sm, kScoreThreads, ssm,
+                          s>>>(sa, bt, nb, next);
+        } else {
+          sk.emit<<<dim3(nb, (sa.tiles + sa.tpb - 1) / sa.tpb), kScoreThreads, ssm, s>>>(sa, bt);
+        }
       }
       CK(cudaGetLastError());
     }
@@ -1544,7 +1576,7 @@ static bool tuning_ok(const sinn_tuning &t) {
   return t.bound_every >= 1 && t.bound_every <= 64 && t.emit_min_batch >= 1 &&
          t.emit_min_batch <= 65535 && t.rerank_blocks <= 1024 &&
          t.dense_blocks_per_sm >= 1 && t.dense_blocks_per_sm <= 32 && t.tiles_per_block >= 1 &&
-         t.tiles_per_block <= 64;
+         t.tiles_per_block <= 64 && t.persistent_blocks_per_sm <= 4;
 }
 
 extern "C" int sinn_get_tuning(sinn_index *ix, sinn_tuning *out) {
@@ -1557,6 +1589,7 @@ extern "C" int sinn_set_tuning(sinn_index *ix, const sinn_tuning *t) {
   if (!ix || !t || !tuning_ok(*t)) return SINN_EINVAL;
   ix->tune = *t;
   memset(ix->tune.reserved, 0, sizeof(ix->tune.reserved));
+  ix->shape_version++;
   return SINN_OK;
 }
 
@@ -1600,19 +1633,21 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   sinn_tuning best = ix->tune;
   struct Field {
     uint32_t sinn_tuning::*f;
-    uint32_t vals[6];
+    uint32_t n, vals[6];
   };
   const Field fields[] = {
-      {&sinn_tuning::max_batch, {0, 256, 512, 1024, 2048, 4096}},
-      {&sinn_tuning::bound_every, {1, 2, 4, 8, 16, 32}},
-      {&sinn_tuning::rerank_blocks, {0, 4, 16, 64, 256, 1024}},
-      {&sinn_tuning::dense_blocks_per_sm, {1, 2, 4, 8, 16, 32}},
-      {&sinn_tuning::emit_min_batch, {4, 8, 16, 32, 64, 128}},
-      {&sinn_tuning::tiles_per_block, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::max_batch, 6, {0, 256, 512, 1024, 2048, 4096}},
+      {&sinn_tuning::tiles_per_block, 6, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::persistent_blocks_per_sm, 3, {0, 2, 4}},
+      {&sinn_tuning::bound_every, 6, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::rerank_blocks, 6, {0, 4, 16, 64, 256, 1024}},
+      {&sinn_tuning::dense_blocks_per_sm, 6, {1, 2, 4, 8, 16, 32}},
+      {&sinn_tuning::emit_min_batch, 6, {4, 8, 16, 32, 64, 128}},
   };
   for (const Field &fd : fields) {
     if (st) break;
-    for (uint32_t v : fd.vals) {
+    for (uint32_t vi = 0; vi < fd.n; ++vi) {
+      const uint32_t v = fd.vals[vi];
       if (v == best.*fd.f) continue;
       if (fd.f == &sinn_tuning::max_batch && v >= n_q) continue;  // same as unlimited
       ix->tune = best;
@@ -1626,6 +1661,7 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
     }
   }
   ix->tune = st ? start : best;
+  ix->shape_version++;
   if (out) *out = ix->tune;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

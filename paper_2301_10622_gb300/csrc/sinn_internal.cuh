@@ -40,8 +40,8 @@ struct sinn_index {
   // at about the same time, so the bound could not prune); batches as large
   // as the scratch allows; re-rank blocks per query sized to k' (about 64
   // candidates each); 4 dense blocks per SM; 4 tiles per block of the
-  // batched scoring kernel.
-  sinn_tuning tune{4, 32, 0, 0, 4, 4, {0, 0}};
+  // batched scoring kernel, one block per item.
+  sinn_tuning tune{4, 32, 0, 0, 4, 4, 0, {0}};
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings
@@ -53,9 +53,10 @@ struct sinn_index {
   uint2 *d_fwd = nullptr;          // vector store pool: (coordinate, value bits)
   uint64_t fwd_cap = 0, fwd_used = 0;
   uint2 *d_tile_dir = nullptr;     // tiles_cap x n containers {start, count} per tile
-                                   // (count >= T/16: bitmap of T bits, else sorted array)
+                                   // (count >= T/4: bitmap of T bits, else sorted array)
   uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
   uint32_t *d_err = nullptr;       // sticky device error bits
+  uint64_t *d_live_count = nullptr;  // live_count, kept on the device for the searches
   uint64_t cap = 0;                // id capacity = tiles_cap * T
 
   // ---- host mirror
@@ -69,6 +70,9 @@ struct sinn_index {
   std::vector<uint64_t> tile_nnz;        // sum of nnz over live vectors of the tile
   std::vector<uint64_t> tile_tombs;      // tombstoned postings per tile
   uint64_t tombstones = 0;
+  // Bumped whenever a recorded search (sinn_plan) would go stale: device
+  // arrays reallocated, the tiles in use or the tuning changed.
+  uint64_t shape_version = 0;
 
   // ---- scratch (search and insert), grow-only
   void *scratch = nullptr;
@@ -90,6 +94,8 @@ struct sinn_index {
   };
   std::vector<Span> tm_spans;
   std::vector<cudaEvent_t> tm_pool;
+  double tm_acc_ms[SINN_PHASES] = {};      // phases timed inside replayed graphs
+  uint64_t tm_acc_spans[SINN_PHASES] = {};
   uint64_t launches = 0;
 };
 

@@ -37,6 +37,8 @@ EXPORTS = [
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
     "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned", "sinn_mlp_act_bytes",
     "sinn_search_learned_ctx",
+    # sinnamon_plan.h
+    "sinn_plan_create", "sinn_plan_run", "sinn_plan_recordings", "sinn_plan_destroy",
 ]
 
 KP_FEATURES = 19
@@ -76,9 +78,9 @@ class SinnTuning(C.Structure):
     _fields_ = [("bound_every", C.c_uint32), ("emit_min_batch", C.c_uint32),
                 ("max_batch", C.c_uint32), ("rerank_blocks", C.c_uint32),
                 ("dense_blocks_per_sm", C.c_uint32), ("tiles_per_block", C.c_uint32),
-                ("reserved", C.c_uint32 * 2)]
+                ("persistent_blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 1)]
     FIELDS = ["bound_every", "emit_min_batch", "max_batch", "rerank_blocks",
-              "dense_blocks_per_sm", "tiles_per_block"]
+              "dense_blocks_per_sm", "tiles_per_block", "persistent_blocks_per_sm"]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f in self.FIELDS}
@@ -151,6 +153,11 @@ def load(build_if_missing: bool = False):
         "sinn_search_learned": ([vp, vp, vp, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp],
                                 C.c_int),
         "sinn_timing_stop": ([vp, C.POINTER(SinnTiming)], C.c_int),
+        "sinn_plan_create": ([vp, vp, vp, vp, vp, vp, u32, u32, u32, u32, vp, vp, vp, u64,
+                              C.POINTER(vp)], C.c_int),
+        "sinn_plan_run": ([vp, vp], C.c_int),
+        "sinn_plan_recordings": ([vp], u64),
+        "sinn_plan_destroy": ([vp], C.c_int),
         "sinn_get_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
@@ -410,6 +417,56 @@ class Context:
             self._h, self.index.handle, self.mlp.handle, _p(self.act), self.act.numel(),
             _p(q_indptr), _p(q_indices), _p(q_values), n_q, k, kp_min, kp_max, _p(out_ids),
             _p(out_scores), _p(out_kprime), _s(stream)), "sinn_search_learned_ctx")
+
+
+class Plan:
+    """A recorded search (sinn_plan): one CUDA graph replayed per run over
+    fixed device buffers.  The query tensors given are kept and read at
+    every run, so new queries are written into them in place (same shapes).
+    k_prime: None (every query takes k_prime_max) or a device uint32 tensor
+    of per-query k'; with mlp the network chooses k' in [k_prime_min,
+    k_prime_max]."""
+
+    def __init__(self, index: "Index", q_indptr, q_indices, q_values, k: int, k_prime_max: int,
+                 k_prime=None, mlp=None, k_prime_min: int | None = None,
+                 scratch_bytes: int = 1 << 30):
+        lib = load()
+        dev = index.device
+        self.index, self.mlp = index, mlp
+        self.q_indptr, self.q_indices, self.q_values = q_indptr, q_indices, q_values
+        self.k_prime = k_prime
+        n_q = q_indptr.numel() - 1
+        self.out_ids = torch.empty((n_q, k), dtype=torch.int32, device=dev)
+        self.out_scores = torch.empty((n_q, k), dtype=torch.float32, device=dev)
+        self.out_kprime = torch.empty(n_q, dtype=torch.int32, device=dev) if mlp else None
+        out = C.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.sinn_plan_create(index.handle, mlp.handle if mlp else None, _p(q_indptr),
+                                        _p(q_indices), _p(q_values), _p(k_prime), n_q, k,
+                                        k_prime_min if k_prime_min is not None else k,
+                                        k_prime_max, _p(self.out_ids), _p(self.out_scores),
+                                        _p(self.out_kprime), scratch_bytes, C.byref(out)),
+                   "sinn_plan_create")
+        self._h = out
+
+    def run(self, stream=None):
+        _check(load().sinn_plan_run(self._h, _s(stream)), "sinn_plan_run")
+        return self.out_ids, self.out_scores
+
+    @property
+    def recordings(self) -> int:
+        return int(load().sinn_plan_recordings(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sinn_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MLP:

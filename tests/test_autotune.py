@@ -51,7 +51,9 @@ def _run(ix, q, kp=300):
     dict(emit_min_batch=1, max_batch=40), dict(emit_min_batch=65535),
     dict(rerank_blocks=1), dict(rerank_blocks=1024, dense_blocks_per_sm=1), dict(rerank_blocks=0),
     dict(dense_blocks_per_sm=32, emit_min_batch=500), dict(tiles_per_block=1),
-    dict(tiles_per_block=3, bound_every=5), dict(tiles_per_block=64, bound_every=1)])
+    dict(tiles_per_block=3, bound_every=5), dict(tiles_per_block=64, bound_every=1),
+    dict(persistent_blocks_per_sm=4), dict(persistent_blocks_per_sm=1, tiles_per_block=2,
+                                           max_batch=50)])
 def test_every_tuning_gives_the_same_results(setup, fields):
     ix, q = setup
     base = ix.tuning()
@@ -68,7 +70,8 @@ def test_every_tuning_gives_the_same_results(setup, fields):
                                           ("emit_min_batch", 0), ("rerank_blocks", 1025),
                                           ("dense_blocks_per_sm", 0),
                                           ("dense_blocks_per_sm", 33), ("tiles_per_block", 0),
-                                          ("tiles_per_block", 65)])
+                                          ("tiles_per_block", 65),
+                                          ("persistent_blocks_per_sm", 5)])
 def test_invalid_tuning_is_rejected(setup, field, value):
     ix, _ = setup
     before = ix.tuning()
