@@ -39,6 +39,21 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def job_throughput(elapsed_s: float, units: float, device=None):
+    """Whole-job throughput of replicas: every rank's units over the slowest
+    rank's time (MAX over ranks; one process without a process group).
+    Returns (units/s, slowest elapsed seconds)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if world > 1:
+        t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+        dist.barrier()
+    return world * units / elapsed_s, elapsed_s
+
+
 # ----------------------------------------------------------------- inputs
 
 def cached(name, fn):
@@ -405,12 +420,7 @@ def run_ours(args):
         tm = sinnamon.sinn_timing_stop(h)
     ix.sync()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        dist.barrier()
-    value = world * qs.rows * args.steps / elapsed
+    value, elapsed = job_throughput(elapsed, qs.rows * args.steps, dev)
     ms_step = 1000 * elapsed / args.steps
 
     # roofline of the scoring kernel (live CUDA-event durations from the library)

@@ -7,8 +7,10 @@
  * real vectors that changes online (Sec. 1: insertions and deletions arrive
  * while queries run).  The index keeps, on one GPU:
  *   - an inverted index I: coordinate -> ids of the vectors non-zero there
- *     (Alg. 5 line 2), stored per tile of T consecutive ids as sorted 16-bit
- *     local ids; a deleted posting is tombstoned in place (Sec. 4.3);
+ *     (Alg. 5 line 2), stored per tile of T consecutive ids as a container
+ *     of 16-bit local ids: a sorted array, or a T-bit bitmap when at least
+ *     a quarter of the tile holds the coordinate; a deleted posting is
+ *     tombstoned in place (Sec. 4.3);
  *   - the sketch matrix [U; L] (Alg. 5): 2m rows of fp32 over all id slots,
  *     row-major, so one query coordinate reads a fixed set of h rows;
  *   - the vector store S that Alg. 7 re-ranks from (Fig. 1): each vector's

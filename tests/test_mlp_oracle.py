@@ -32,3 +32,21 @@ def test_gradient_matches_finite_differences():
         num[i] = (lp - lm) / (2 * eps)
     # the loss is piecewise linear: compare where no residual changes sign
     np.testing.assert_allclose(g, num, rtol=1e-5, atol=1e-7)
+
+
+def test_forward_hand_worked_example():
+    """2 -> 2 -> 2 -> 1 with non-symmetric weights, worked by hand:
+    x = (3, 5), mean (1, 2), std (2, 3) -> standardised (1, 1);
+    Z1 = W1 x + b1 = (1+2+0.5, 3-4-1) = (3.5, -2) -> H1 = (3.5, 0);
+    Z2 = W2 H1 + b2 = (3.5, 7+1) -> H2 = (3.5, 8);
+    y = w3 . H2 + b3 = 7 - 4 + 0.25 = 3.25."""
+    W1 = [[1.0, 2.0], [3.0, -4.0]]
+    b1 = [0.5, -1.0]
+    W2 = [[1.0, -1.0], [2.0, 0.5]]
+    b2 = [0.0, 1.0]
+    w3 = [2.0, -0.5]
+    b3 = [0.25]
+    p = np.concatenate([np.ravel(W1), b1, np.ravel(W2), b2, w3, b3])
+    y, _ = omlp.forward(p, np.array([[3.0, 5.0]]), np.array([1.0, 2.0]),
+                        np.array([2.0, 3.0]), 2, 2)
+    assert abs(y[0] - 3.25) < 1e-15
