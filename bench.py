@@ -262,10 +262,10 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def measured_traffic(launches, queries):
+def measured_traffic(launches, queries, docs):
     """DRAM bytes per scoring launch from the committed ncu summary, scaled to
     this run's queries per launch; None if the kernel source changed since the
-    counters were taken."""
+    counters were taken or the index is not the size they were taken on."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "k_score_emit_text.md")
     src = os.path.join(ROOT, "paper_2301_10622_gb300", "csrc", "search.cu")
@@ -274,9 +274,12 @@ def measured_traffic(launches, queries):
         want = text.split("source_sha256_16:")[1].split()[0]
         per_launch = float(text.split("traffic_bytes_per_launch:")[1].split()[0])
         q_launch = float(text.split("queries_per_launch:")[1].split()[0])
+        p_docs = int(text.split("docs_in_index:")[1].split()[0])
     except (OSError, IndexError, ValueError):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != want or launches == 0:
+        return None
+    if p_docs != docs:
         return None
     return per_launch * (queries / launches) / q_launch
 
@@ -430,7 +433,7 @@ def run_ours(args):
     achieved = alg_bytes / (score_ms / 1000.0) / 1e9 if score_ms > 0 else None
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = measured_traffic(tm["spans"]["score"], qs.rows * args.steps)
+    traffic = measured_traffic(tm["spans"]["score"], qs.rows * args.steps, docs.rows)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "effective": True,
