@@ -85,11 +85,17 @@ def _load():
         lib.orc_doc.argtypes = [vp, C.c_uint32, u32p, f64p]
         lib.orc_scores.restype = C.c_int
         lib.orc_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p, vp]
+        lib.orc_scores_anytime.restype = C.c_int
+        lib.orc_scores_anytime.argtypes = [vp, u32p, f32p, C.c_uint32, C.c_uint64, f64p, vp]
         lib.orc_exact_scores.restype = C.c_int
         lib.orc_exact_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p, vp]
         lib.orc_search.restype = C.c_int
         lib.orc_search.argtypes = [vp, u64p, u32p, f32p, C.c_uint32, C.c_uint32, C.c_uint32,
                                    u32p, f64p, vp, vp, vp, u32p, C.c_uint32]
+        lib.orc_search_anytime.restype = C.c_int
+        lib.orc_search_anytime.argtypes = [vp, u64p, u32p, f32p, C.c_uint32, C.c_uint32,
+                                           C.c_uint32, C.c_uint64, u32p, f64p, vp, vp, vp,
+                                           u32p, C.c_uint32]
         lib.orc_exact_topk.restype = C.c_int
         lib.orc_exact_topk.argtypes = [vp, u64p, u32p, f32p, C.c_uint32, C.c_uint32, u32p,
                                        f64p, vp, u32p, C.c_uint32]
@@ -228,12 +234,14 @@ class OracleIndex:
             raise OracleError(st)
 
     # ---- queries
-    def scores(self, qi, qv, with_magnitude: bool = False):
+    def scores(self, qi, qv, with_magnitude: bool = False, budget: int = 0):
+        """Alg. 6 scores of every id slot; budget > 0: the anytime break after
+        the term at which the postings visited reach the budget."""
         qi = np.ascontiguousarray(qi, dtype=np.uint32)
         qv = np.ascontiguousarray(qv, dtype=np.float32)
         out = np.zeros(max(self.n_slots, 1), np.float64)
         mag = np.zeros(max(self.n_slots, 1), np.float64) if with_magnitude else None
-        st = self._lib.orc_scores(self._p, qi, qv, qi.size, out, _ptr(mag))
+        st = self._lib.orc_scores_anytime(self._p, qi, qv, qi.size, budget, out, _ptr(mag))
         if st:
             raise OracleError(st)
         out = out[: self.n_slots]
@@ -251,7 +259,7 @@ class OracleIndex:
         return (out, mag[: self.n_slots]) if with_magnitude else out
 
     def search(self, indptr, indices, values, k: int, k_prime: int, threads: int = 1,
-               candidates: bool = False):
+               candidates: bool = False, budget: int = 0):
         """Alg. 6 + Alg. 7.  Returns dict with ids/scores [nq, k] and, when
         asked, cand_ids/cand_scores/cand_mag [nq, k'] (approximate scores)."""
         ip, ix, vv = _csr(indptr, indices, values)
@@ -264,8 +272,8 @@ class OracleIndex:
             ci = np.full((max(nq, 1), k_prime), 0xFFFFFFFF, np.uint32)
             cs = np.full((max(nq, 1), k_prime), -np.inf, np.float64)
             cm = np.zeros((max(nq, 1), k_prime), np.float64)
-        st = self._lib.orc_search(self._p, ip, ix, vv, nq, k, k_prime, ids, sc, _ptr(ci),
-                                  _ptr(cs), _ptr(cm), cnt, threads)
+        st = self._lib.orc_search_anytime(self._p, ip, ix, vv, nq, k, k_prime, budget, ids, sc,
+                                          _ptr(ci), _ptr(cs), _ptr(cm), cnt, threads)
         if st:
             raise OracleError(st)
         res = {"ids": ids[:nq], "scores": sc[:nq], "count": cnt[:nq]}

@@ -22,9 +22,15 @@
  *   orc_delete               -- Sec. 4.3 (remove i from every I[j], leave
  *                               column i of the sketch as it is, free id i).
  *   orc_scores               -- Alg. 6 (scoring), T = infinity.
+ *   orc_scores_anytime       -- Alg. 6 with a time budget, read as postings:
+ *                               terms run in Alg. 6 order and the loop breaks
+ *                               after the first term at which the postings
+ *                               visited so far reach the budget (the check
+ *                               at the end of the term loop).
  *   find_largest             -- Alg. 3 (FindLargest, binary heap).
  *   orc_search               -- Alg. 7 (ranking: top-k' by approximate score,
- *                               exact re-rank from the vector store, top-k).
+ *                               exact re-rank from the vector store, top-k);
+ *                               orc_search_anytime scores with a budget.
  *   orc_exact_*              -- Eq. 2 (MIPS) by brute force over the store.
  *   orc_linscan_*            -- Alg. 1 / Alg. 2 (LinScan), exact.
  *
@@ -448,14 +454,32 @@ static void alg6_scores(const orc_index *ix, const orc_qterm *terms, uint32_t nt
   }
 }
 
-int orc_scores(const orc_index *ix, const uint32_t *qi, const float *qv, uint32_t qnnz,
-               double *scores, double *mag) {
+/* The anytime break of Alg. 6 with the budget counted in postings: the
+ * number of sorted terms scored.  Budget 0 means T = infinity. */
+static uint32_t anytime_terms(const orc_index *ix, const orc_qterm *terms, uint32_t nt,
+                              uint64_t budget) {
+  if (budget == 0) return nt;
+  uint64_t visited = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    visited += ix->lists[terms[t].j].len;
+    if (visited >= budget) return t + 1; /* break after this term */
+  }
+  return nt;
+}
+
+int orc_scores_anytime(const orc_index *ix, const uint32_t *qi, const float *qv, uint32_t qnnz,
+                       uint64_t budget, double *scores, double *mag) {
   if (validate_query(ix, qi, qv, qnnz)) return ORC_EINVAL;
   orc_qterm *terms = (orc_qterm *)malloc((qnnz ? qnnz : 1) * sizeof(orc_qterm));
   uint32_t nt = query_terms(qi, qv, qnnz, terms);
-  alg6_scores(ix, terms, nt, scores, mag);
+  alg6_scores(ix, terms, anytime_terms(ix, terms, nt, budget), scores, mag);
   free(terms);
   return ORC_OK;
+}
+
+int orc_scores(const orc_index *ix, const uint32_t *qi, const float *qv, uint32_t qnnz,
+               double *scores, double *mag) {
+  return orc_scores_anytime(ix, qi, qv, qnnz, 0, scores, mag);
 }
 
 /* ---- Alg. 3: FindLargest with a binary heap -----------------------------
@@ -590,15 +614,15 @@ static void ws_free(orc_ws *w) {
  * min(k', live) candidates V of Alg. 7 line 1 in rank order, with their
  * approximate scores and magnitudes. */
 static uint32_t search_one(const orc_index *ix, orc_ws *w, const uint32_t *qi, const float *qv,
-                           uint32_t qnnz, uint32_t k, uint32_t kp, uint32_t *out_ids,
-                           double *out_scores, uint32_t *cand_ids, double *cand_scores,
-                           double *cand_mag) {
+                           uint32_t qnnz, uint32_t k, uint32_t kp, uint64_t budget,
+                           uint32_t *out_ids, double *out_scores, uint32_t *cand_ids,
+                           double *cand_scores, double *cand_mag) {
   if (qnnz > w->terms_cap) {
     w->terms_cap = qnnz;
     w->terms = (orc_qterm *)xrealloc(w->terms, qnnz * sizeof(orc_qterm));
   }
   uint32_t nt = query_terms(qi, qv, qnnz, w->terms);
-  alg6_scores(ix, w->terms, nt, w->scores, w->mag);
+  alg6_scores(ix, w->terms, anytime_terms(ix, w->terms, nt, budget), w->scores, w->mag);
 
   /* Alg. 7 line 1: V = FindLargest(scores, k') over the live ids. */
   uint32_t cnt = 0;
@@ -661,6 +685,7 @@ typedef struct {
   const uint32_t *indices;
   const float *values;
   uint32_t q0, q1, k, kp, mode;
+  uint64_t budget;
   uint32_t *out_ids;
   double *out_scores;
   uint32_t *cand_ids;
@@ -680,7 +705,8 @@ static void *run_job(void *arg) {
     uint32_t qn = (uint32_t)(jb->indptr[q + 1] - jb->indptr[q]);
     uint32_t r;
     if (jb->mode == 0) {
-      r = search_one(jb->ix, &w, qi, qv, qn, jb->k, jb->kp, jb->out_ids + (size_t)q * jb->k,
+      r = search_one(jb->ix, &w, qi, qv, qn, jb->k, jb->kp, jb->budget,
+                     jb->out_ids + (size_t)q * jb->k,
                      jb->out_scores + (size_t)q * jb->k,
                      jb->cand_ids ? jb->cand_ids + (size_t)q * jb->kp : NULL,
                      jb->cand_scores ? jb->cand_scores + (size_t)q * jb->kp : NULL,
@@ -724,14 +750,17 @@ static int run_batch(orc_job proto, uint32_t n_q, uint32_t n_threads) {
   return ORC_OK;
 }
 
-/* SINNAMON retrieval (Alg. 6 + Alg. 7) for a CSR batch of queries. */
-int orc_search(const orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
-               const float *values, uint32_t n_q, uint32_t k, uint32_t kp, uint32_t *out_ids,
-               double *out_scores, uint32_t *cand_ids, double *cand_scores, double *cand_mag,
-               uint32_t *out_count, uint32_t n_threads) {
+/* SINNAMON retrieval (Alg. 6 with the anytime budget, then Alg. 7) for a
+ * CSR batch of queries; budget 0 means T = infinity. */
+int orc_search_anytime(const orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                       const float *values, uint32_t n_q, uint32_t k, uint32_t kp,
+                       uint64_t budget, uint32_t *out_ids, double *out_scores,
+                       uint32_t *cand_ids, double *cand_scores, double *cand_mag,
+                       uint32_t *out_count, uint32_t n_threads) {
   if (k == 0 || kp < k) return ORC_EINVAL;
   orc_job jb;
   memset(&jb, 0, sizeof(jb));
+  jb.budget = budget;
   jb.ix = ix;
   jb.indptr = indptr;
   jb.indices = indices;
@@ -746,6 +775,15 @@ int orc_search(const orc_index *ix, const uint64_t *indptr, const uint32_t *indi
   jb.cand_mag = cand_mag;
   jb.out_count = out_count;
   return run_batch(jb, n_q, n_threads);
+}
+
+/* SINNAMON retrieval (Alg. 6 + Alg. 7), T = infinity. */
+int orc_search(const orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
+               const float *values, uint32_t n_q, uint32_t k, uint32_t kp, uint32_t *out_ids,
+               double *out_scores, uint32_t *cand_ids, double *cand_scores, double *cand_mag,
+               uint32_t *out_count, uint32_t n_threads) {
+  return orc_search_anytime(ix, indptr, indices, values, n_q, k, kp, 0, out_ids, out_scores,
+                            cand_ids, cand_scores, cand_mag, out_count, n_threads);
 }
 
 /* Exact MIPS (Eq. 2) by brute force, for a CSR batch of queries. */

@@ -412,3 +412,47 @@ def test_invalid_inputs_leave_index_unchanged():
     with pytest.raises(oracle.OracleError):
         ix.search(*_csr([([1], [1.0])]), k=2, k_prime=1)
     assert ix.live_count == 2
+
+
+# ----------------------------------------------------------------- anytime
+
+def test_worked_example_anytime_budget():
+    """Alg. 6's break "if time budget T exhausted", with T counted in postings:
+    hand-worked partial scores after each term of the worked example."""
+    g = _gold()
+    c = g["cases"][0]
+    ix = oracle.OracleIndex(g["n"], g["m"], c["h"], table=np.array(c["table"]))
+    ix.insert(*_csr([(d["idx"], d["val"]) for d in c["docs"]]))
+    q = c["query"]
+    for case in c["anytime"]["cases"]:
+        assert list(ix.scores(q["idx"], q["val"], budget=case["budget"])) == case["scores"]
+    qc = _csr([(q["idx"], q["val"])])
+    for s in c["anytime"]["search"]:
+        r = ix.search(*qc, k=s["k"], k_prime=s["k_prime"], budget=s["budget"])
+        assert list(r["ids"][0]) == s["ids"] and list(r["scores"][0]) == s["scores"]
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_anytime_scores_bound_the_processed_coordinates(h):
+    """With a budget the scores are upper bounds of the inner product over the
+    coordinates processed (Sec. 4.2's remark on the anytime variant), and the
+    processed coordinates are a prefix of Alg. 6's order chosen by the
+    budget; budget 0 is T = infinity."""
+    ix, docs, ids = _random_index(300, 16, h, 400, 24, seed=21 + h)
+    qs = _random_queries(300, 20, 12, seed=7)
+    lens = np.array([ix.inverted_list(j).size for j in range(300)])
+    for r in range(qs.rows):
+        qi, qv = qs.row(r)
+        keep = qv != 0
+        qi, qv = qi[keep], qv[keep]
+        order = np.lexsort((qi, -np.abs(qv.astype(np.float64))))
+        cum = np.cumsum(lens[qi[order]])
+        for budget in (1, int(cum[len(cum) // 2]), int(cum[-1]) + 1):
+            t = min(int(np.searchsorted(cum, budget)) + 1, len(cum))
+            sel = np.sort(order[:t])  # coordinates ascending, as CSR wants
+            a = ix.scores(qi, qv, budget=budget)
+            a_prefix = ix.scores(qi[sel], qv[sel])       # same terms, T = infinity
+            np.testing.assert_array_equal(a, a_prefix)
+            e = ix.exact_scores(qi[sel], qv[sel])
+            assert np.all(a >= e - 1e-12 * (1 + np.abs(e)))
+        np.testing.assert_array_equal(ix.scores(qi, qv, budget=0), ix.scores(qi, qv))
