@@ -563,6 +563,9 @@ def run_ours(args):
                 ora, samp, fx_ids.cpu().numpy()[:nr], os.cpu_count() or 1)
             extras["recall_queries"] = nr
             extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
+        if not args.skip_variants:
+            extras.update(run_variants(args, w, docs, ix, (g_qip, g_qix, g_qv), qs, k, kp,
+                                       float(P.mean()), ora if not args.skip_oracle else None))
         if args.serve_seconds > 0:
             extras["serving"] = run_serving(args, w, ix, qs, docs.rows, mlp, k, kp)
     if world > 1:
@@ -590,12 +593,61 @@ def run_ours(args):
         "batched_fixed_kprime": extras.get("batched_fixed_kprime"),
         "learned_kprime": extras.get("learned_kprime"),
         "serving": extras.get("serving"),
+        "anytime": extras.get("anytime"),
+        "sinnamon_plus": extras.get("sinnamon_plus"),
         "phases_ms_per_step": {p: v / args.steps for p, v in tm["ms"].items()},
         "index": st,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora):
+    """The paper's variants, untimed extras: Alg. 6 with an anytime budget
+    (half and a quarter of the mean postings per query) on the bench's
+    index, and a SINNAMON+ index (U only) of the original collection; each
+    searched with fixed k' as one batch."""
+    import torch
+    from paper_2301_10622_gb300 import sinnamon
+    out = {}
+
+    def timed(index):
+        ids = torch.empty((qs.rows, k), dtype=torch.int32, device=q[0].device)
+        sc = torch.empty((qs.rows, k), dtype=torch.float32, device=q[0].device)
+        sinnamon.sinn_search(index.handle, *q, k, kp, ids, sc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sinnamon.sinn_search(index.handle, *q, k, kp, ids, sc)
+        e1.record()
+        torch.cuda.synchronize()
+        return qs.rows / (e0.elapsed_time(e1) / 1000.0), ids
+
+    nr = min(args.recall_queries, qs.rows)
+    runs = []
+    for frac in (0.5, 0.25):
+        budget = int(mean_postings * frac)
+        ix.set_budget(budget)
+        qps, ids = timed(ix)
+        rec = (recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1)
+               if ora is not None else None)
+        runs.append({"budget_postings": budget, "fraction_of_mean_postings": frac,
+                     "qps": qps, "k_prime": kp, "recall_at_10": rec})
+    ix.set_budget(0)
+    out["anytime"] = runs
+    plus = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=args.tile_docs,
+                          capacity_hint=docs.rows, scratch_bytes=args.scratch_gb << 30,
+                          flags=sinnamon.SINN_FLAG_NONNEG)
+    for a in range(0, docs.rows, 200_000):
+        part = docs.slice(a, min(docs.rows, a + 200_000))
+        plus.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+    qps, _ = timed(plus)
+    out["sinnamon_plus"] = {"qps": qps, "k_prime": kp, "docs": docs.rows,
+                            "bytes_sketch": plus.stats()["bytes_sketch"],
+                            "bytes_sketch_full": ix.stats()["bytes_sketch"]}
+    plus.close()
+    log(f"variants: {out}")
+    return out
 
 
 def run_serving(args, w, ix, qs, n_live, mlp, k, kp):
@@ -681,6 +733,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--no-graph", action="store_true", help="launch the search directly")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rates", default="20000,2000,5000",
                     help="inserts,deletes,queries per second")

@@ -54,6 +54,13 @@ extern "C" {
 
 typedef struct sinn_index sinn_index; /* opaque; owned by the library */
 
+/* SINNAMON+ (the Sec. 4.1 note on the non-negative orthant): only the upper
+ * sketch U is kept.  Inserts with a negative value are rejected (EINVAL) and
+ * queries with a negative value are malformed (their row is padded and the
+ * device error set); on non-negative data the results equal SINNAMON's,
+ * which never reads L for positive query entries. */
+#define SINN_FLAG_NONNEG 1u
+
 /* Index parameters.  Zero fields take the defaults noted. */
 typedef struct sinn_config {
   uint32_t n;              /* dimensionality; coordinates are [0, n) */
@@ -66,7 +73,7 @@ typedef struct sinn_config {
                               NULL -> pi_o(j) = mix64(seed ^ (o+1)*0x9E3779B97F4A7C15 ^ j) mod m,
                               mix64 being SplitMix64's output function */
   uint32_t max_query_nnz;  /* largest query non-zero count sinn_search accepts; 0 -> 1024 */
-  uint32_t reserved;
+  uint32_t flags;          /* 0 or SINN_FLAG_NONNEG */
   uint64_t scratch_bytes;  /* device scratch budget of one search launch; 0 -> 4 GiB */
 } sinn_config;
 
@@ -183,6 +190,16 @@ int sinn_sync(sinn_index *ix, void *stream);
 /* Fill *out with the counters above (host). */
 int sinn_stats(sinn_index *ix, sinn_stats_t *out);
 
+/* Alg. 6's anytime budget T, counted in postings (the scoring time is
+ * proportional to them): each query's terms run in Alg. 6 order and scoring
+ * stops after the first term at which the live postings of the lists scored
+ * so far reach the budget.  0 (the default) is T = infinity.  Applies to
+ * every later search, candidate and score call of the index. */
+int sinn_set_budget(sinn_index *ix, uint64_t postings);
+
+/* The current budget (0 = none); 0 for a NULL index. */
+uint64_t sinn_get_budget(sinn_index *ix);
+
 /* ---- Launch tuning (the paper has no counterpart: these are GPU launch
  * parameters; results do not depend on them beyond fp32 summation order) -- */
 
@@ -249,7 +266,8 @@ int sinn_hash_table(sinn_index *ix, uint32_t *table);
 
 /* Sketch columns of the given ids (Alg. 5's u and l): ids device
  * uint32[n_ids]; u_out, l_out device float[n_ids*m], row r = column ids[r].
- * A deleted id yields its stale column (Sec. 4.3 leaves it in place). */
+ * A deleted id yields its stale column (Sec. 4.3 leaves it in place).
+ * l_out may be NULL; it must be NULL for a SINNAMON+ index (EINVAL). */
 int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, float *u_out,
                         float *l_out, void *stream);
 

@@ -56,7 +56,7 @@ static uint64_t lib_mix64(uint64_t z) {
 __global__ void k_validate_csr(const uint64_t *__restrict__ indptr,
                                const uint32_t *__restrict__ indices,
                                const float *__restrict__ values, uint32_t rows, uint32_t n,
-                               uint32_t *err, uint32_t bit) {
+                               uint32_t *err, uint32_t bit, int nonneg) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (w >= rows) return;
@@ -65,7 +65,7 @@ __global__ void k_validate_csr(const uint64_t *__restrict__ indptr,
   for (uint64_t p = s + lane; p < e; p += 32) {
     uint32_t c = indices[p];
     float v = values[p];
-    if (c >= n || !isfinite(v)) bad = true;
+    if (c >= n || !isfinite(v) || (nonneg && v < 0.0f)) bad = true;
     if (p > s && indices[p - 1] >= c) bad = true;
   }
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, bit);
@@ -77,13 +77,16 @@ __global__ void k_fwd_write(const uint64_t *__restrict__ indptr,
                             const float *__restrict__ values, uint32_t rows,
                             const uint32_t *__restrict__ ids, const uint64_t *__restrict__ offs,
                             uint2 *__restrict__ fwd, uint64_t *__restrict__ fwd_off,
-                            uint32_t *__restrict__ fwd_nnz) {
+                            uint32_t *__restrict__ fwd_nnz, uint32_t *__restrict__ coord_len) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (w >= rows) return;
   const uint64_t s = indptr[w], e = indptr[w + 1], o = offs[w];
-  for (uint64_t p = s + lane; p < e; p += 32)
-    fwd[o + (p - s)] = make_uint2(indices[p], __float_as_uint(values[p]));
+  for (uint64_t p = s + lane; p < e; p += 32) {
+    const float v = values[p];
+    fwd[o + (p - s)] = make_uint2(indices[p], __float_as_uint(v));
+    if (v != 0.0f) atomicAdd(&coord_len[indices[p]], 1u);  // |I[j]| grows
+  }
   if (lane == 0) {
     fwd_off[ids[w]] = o;
     fwd_nnz[ids[w]] = (uint32_t)(e - s);
@@ -131,7 +134,7 @@ __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__
     uint32_t k = t / g_cnt, g = t % g_cnt;
     uint64_t id = ids[r0 + g];
     U[(uint64_t)k * cap + id] = sinn_key2f(uk[g * m + k]);
-    L[(uint64_t)k * cap + id] = sinn_key2f(lk[g * m + k]);
+    if (L) L[(uint64_t)k * cap + id] = sinn_key2f(lk[g * m + k]);  // no L plane: SINNAMON+
   }
 }
 
@@ -346,7 +349,7 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
                             const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd,
                             const uint2 *__restrict__ tile_dir, uint16_t *const *tile_post,
                             uint32_t *live, uint32_t n, uint32_t log2T, uint32_t *tomb_count,
-                            uint32_t *err) {
+                            uint32_t *coord_len, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (w >= cnt) return;
@@ -380,7 +383,10 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
         ok = true;
       }
     }
-    if (ok) marked++;
+    if (ok) {
+      marked++;
+      atomicSub(&coord_len[pr.x], 1u);  // |I[j]| shrinks
+    }
     else atomicOr(err, SINN_DERR_INTERNAL);
   }
   for (int s = 16; s > 0; s >>= 1) marked += __shfl_xor_sync(0xFFFFFFFFu, marked, s);
@@ -399,11 +405,11 @@ __global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
   uint64_t id = ids[r];
   if (id >= cap) {  // no storage for this id: report NaN
     u_out[i] = __int_as_float(0x7FC00000);
-    l_out[i] = __int_as_float(0x7FC00000);
+    if (l_out) l_out[i] = __int_as_float(0x7FC00000);
     return;
   }
   u_out[i] = U[(uint64_t)k * cap + id];
-  l_out[i] = L[(uint64_t)k * cap + id];
+  if (l_out) l_out[i] = L[(uint64_t)k * cap + id];
 }
 
 __global__ void k_store_u64(uint64_t *dst, uint64_t v) { *dst = v; }
@@ -509,6 +515,7 @@ static void release(sinn_index *ix) {
   cudaFree(ix->d_tile_post);
   cudaFree(ix->d_err);
   cudaFree(ix->d_live_count);
+  cudaFree(ix->d_coord_len);
   cudaFree(ix->scratch);
   cudaFree(ix->iscratch);
   cudaFree(ix->hstage);
@@ -579,7 +586,8 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   const uint64_t ot = ix->cap / ix->T, nt = nc / ix->T;
   CK(cudaDeviceSynchronize());
   // sketch planes: copy the m rows into the wider layout
-  for (int plane = 0; plane < 2; ++plane) {
+  const int planes = (ix->flags & SINN_FLAG_NONNEG) ? 1 : 2;  // SINNAMON+: U only
+  for (int plane = 0; plane < planes; ++plane) {
     float **pp = plane ? &ix->d_L : &ix->d_U;
     float *q = nullptr;
     CK(cudaMalloc(&q, (uint64_t)ix->m * nc * sizeof(float)));
@@ -626,6 +634,7 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   if (n == 0 || m == 0 || h == 0 || h > m || h > SINN_MAX_H || m > 4096) return SINN_EINVAL;
   uint32_t T = cfg->tile_docs ? cfg->tile_docs : 4096;
   if (T < 1024 || T > 16384 || (T & (T - 1))) return SINN_EINVAL;
+  if (cfg->flags & ~SINN_FLAG_NONNEG) return SINN_EINVAL;
   if (cfg->table)
     for (uint64_t t = 0; t < (uint64_t)n * h; ++t)
       if (cfg->table[t] >= m) return SINN_EINVAL;
@@ -639,6 +648,7 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   ix->log2T = 0;
   while ((1u << ix->log2T) < T) ix->log2T++;
   ix->seed = cfg->seed ? cfg->seed : 0x5151ULL;
+  ix->flags = cfg->flags;
   ix->max_qnnz = cfg->max_query_nnz ? cfg->max_query_nnz : 1024;
   ix->scratch_budget = cfg->scratch_bytes ? cfg->scratch_bytes : (4ULL << 30);
   std::vector<uint32_t> tab((uint64_t)n * h);
@@ -665,6 +675,8 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   if ((st = sinn_check_cuda(cudaMemset(ix->d_err, 0, sizeof(uint32_t) * 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMalloc(&ix->d_live_count, sizeof(uint64_t))))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_live_count, 0, sizeof(uint64_t))))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_coord_len, (size_t)n * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(ix->d_coord_len, 0, (size_t)n * 4)))) return fail(st);
   uint64_t hint = std::max<uint64_t>(cfg->capacity_hint, T);
   if ((st = grow_capacity(ix, hint))) return fail(st);
   *out = ix;
@@ -845,7 +857,8 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
     ix->launches++;
     uint32_t bits = 0;
     k_validate_csr<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, ix->n,
-                                                    ix->d_err, SINN_DERR_INSERT);
+                                                    ix->d_err, SINN_DERR_INSERT,
+                                                    (ix->flags & SINN_FLAG_NONNEG) ? 1 : 0);
     CK(cudaGetLastError());
     if ((st = read_and_clear_err(ix, s, &bits))) return st;
     if (bits & SINN_DERR_INSERT) return SINN_EINVAL;
@@ -890,7 +903,8 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   CK(cudaMemcpyAsync(out_ids, d_ids, (size_t)n_docs * 4, cudaMemcpyDeviceToDevice, s));
   ix->launches += 3;  // store, sketch, live bits (the tile rebuild counts itself)
   k_fwd_write<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, d_ids, d_off,
-                                              ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz);
+                                              ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz,
+                                              ix->d_coord_len);
   CK(cudaGetLastError());
   uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(32, 6144 / ix->m));
   k_sketch<<<(n_docs + G - 1) / G, 256, (size_t)2 * G * ix->m * 4, s>>>(
@@ -949,7 +963,8 @@ extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, 
   ix->launches++;
   k_tombstone<<<(n_ids + 7) / 8, 256, 0, s>>>(d_ids, n_ids, ix->d_fwd_off, ix->d_fwd_nnz,
                                               ix->d_fwd, ix->d_tile_dir, ix->d_tile_post,
-                                              ix->d_live, ix->n, ix->log2T, d_cnt, ix->d_err);
+                                              ix->d_live, ix->n, ix->log2T, d_cnt,
+                                              ix->d_coord_len, ix->d_err);
   CK(cudaGetLastError());
   uint32_t *hc = (uint32_t *)ix->pinned;
   CK(cudaMemcpyAsync(hc, d_cnt, (size_t)n_ids * 4, cudaMemcpyDeviceToHost, s));
@@ -987,7 +1002,7 @@ extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   out->postings = post;
   out->tombstones = ix->tombstones;
   out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)ix->n * 8;
-  out->bytes_sketch = 2ull * ix->m * ix->cap * 4;
+  out->bytes_sketch = (ix->d_L ? 2ull : 1ull) * ix->m * ix->cap * 4;
   out->bytes_store = ix->fwd_cap * 8 + ix->cap * 12;
   out->bytes_scratch = ix->scratch_size + ix->iscratch_size;
   out->n = ix->n;
@@ -1006,7 +1021,7 @@ extern "C" int sinn_hash_table(sinn_index *ix, uint32_t *table) {
 
 extern "C" int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t n_ids,
                                    float *u_out, float *l_out, void *stream) {
-  if (!ix || (n_ids && (!ids || !u_out || !l_out))) return SINN_EINVAL;
+  if (!ix || (n_ids && (!ids || !u_out)) || (l_out && !ix->d_L)) return SINN_EINVAL;
   if (n_ids == 0) return SINN_OK;
   cudaSetDevice(ix->device);
   cudaStream_t s = (cudaStream_t)stream;

@@ -68,7 +68,8 @@ struct QTerm {
 
 struct Batch {  // device scratch views of one launch
   QTerm *terms;     // B x qmax
-  uint32_t *nt;     // B
+  uint32_t *nt;     // B: query terms (the re-rank uses them all)
+  uint32_t *ns;     // B: terms scored (fewer under an anytime budget)
   uint32_t *keys;   // B x cap
   uint32_t *hist0;  // B x 4096
   uint32_t *hist1;  // B x 4096
@@ -105,6 +106,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
                         const float *__restrict__ q_val, uint32_t q0, uint32_t n, uint32_t qmax,
                         uint32_t kp_scalar, const uint32_t *__restrict__ kp_arr, uint32_t kp_min,
                         uint32_t kp_max, const uint64_t *live_count, Batch bt,
+                        const uint32_t *__restrict__ coord_len, uint64_t budget, int nonneg,
                         uint32_t *err) {
   extern __shared__ uint32_t sq[];
   uint32_t *sj = sq;                  // qmax
@@ -121,7 +123,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     for (uint64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
       uint32_t c = q_idx[p];
       float v = q_val[p];
-      bool bad = c >= n || !isfinite(v) || (p > s && q_idx[p - 1] >= c);
+      bool bad = c >= n || !isfinite(v) || (p > s && q_idx[p - 1] >= c) || (nonneg && v < 0.0f);
       if (bad) atomicOr(&s_bad, 1u);
       if (v != 0.0f && !bad) {
         uint32_t slot = atomicAdd(&s_cnt, 1u);
@@ -145,9 +147,24 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     out[r].j = ji;
     out[r].v = sv[i];
   }
+  if (budget) __syncthreads();  // thread 0 reads the sorted terms
   if (threadIdx.x == 0) {
+    // Alg. 6's anytime break, the budget counted in postings: score the terms
+    // up to the first one at which the postings visited reach the budget (the
+    // re-rank still takes every term: Alg. 7's exact inner product)
+    uint32_t scored = cnt;
+    if (budget) {
+      uint64_t visited = 0;
+      scored = 0;
+      while (scored < cnt) {
+        visited += coord_len[out[scored].j];
+        ++scored;
+        if (visited >= budget) break;
+      }
+    }
     if (s_bad) atomicOr(err, SINN_DERR_QUERY);
     bt.nt[b] = cnt;
+    bt.ns[b] = scored;
     uint32_t kp = kp_arr ? min(max(kp_arr[q], kp_min), kp_max) : kp_scalar;
     SelState st;
     st.mode = SEL_DONE;
@@ -305,7 +322,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   __shared__ uint8_t t_bl[kTermBatch];  // bitmap terms of the batch, in order
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t nt = bt.nt[b];
+  const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
   const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
   uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
   uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
@@ -1064,7 +1081,7 @@ Layout layout_for(const sinn_index *ix, uint32_t B, uint32_t kpmax) {
   Layout L;
   size_t o = 0;
   L.terms = o;   o = align256(o + (size_t)B * ix->max_qnnz * sizeof(QTerm));
-  L.nt = o;      o = align256(o + (size_t)B * 4);
+  L.nt = o;      o = align256(o + (size_t)B * 8);
   L.keys = o;    o = align256(o + (size_t)B * ix->cap * 4);
   L.hist = o;    o = align256(o + (size_t)B * (4096 + 4096 + 256) * 4);
   L.sel = o;     o = align256(o + (size_t)B * sizeof(SelState));
@@ -1083,6 +1100,7 @@ Batch views(void *base, const Layout &L, uint32_t B) {
   Batch bt;
   bt.terms = (QTerm *)(p + L.terms);
   bt.nt = (uint32_t *)(p + L.nt);
+  bt.ns = bt.nt + B;
   bt.keys = (uint32_t *)(p + L.keys);
   bt.hist0 = (uint32_t *)(p + L.hist);
   bt.hist1 = bt.hist0 + (size_t)B * 4096;
@@ -1196,6 +1214,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0,
                                                          ix->n, ix->max_qnnz, r.kp, r.kp_arr,
                                                          r.kp_min, r.kp_max, ix->d_live_count, bt,
+                                                         ix->d_coord_len, ix->budget,
+                                                         (ix->flags & SINN_FLAG_NONNEG) ? 1 : 0,
                                                          ix->d_err);
       CK(cudaGetLastError());
       CK(cudaMemsetAsync(bt.hist0, 0, (size_t)B * (4096 + 4096 + 256) * 4, s));
@@ -1669,3 +1689,14 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   cudaFree(sc);
   return st;
 }
+
+// ------------------------------------------------------------------ anytime
+
+extern "C" int sinn_set_budget(sinn_index *ix, uint64_t postings) {
+  if (!ix) return SINN_EINVAL;
+  if (ix->budget != postings) ix->shape_version++;  // recorded searches bake it in
+  ix->budget = postings;
+  return SINN_OK;
+}
+
+extern "C" uint64_t sinn_get_budget(sinn_index *ix) { return ix ? ix->budget : 0; }

@@ -35,6 +35,8 @@ struct sinn_index {
   uint32_t max_qnnz = 0;
   uint64_t scratch_budget = 0;
   int device = 0;
+  uint32_t flags = 0;        // SINN_FLAG_NONNEG: no L plane (SINNAMON+)
+  uint64_t budget = 0;       // Alg. 6 anytime budget in postings, 0 = none
   // Search launch parameters.  Defaults: refresh the running bound every 4
   // tiles; launches of fewer than 32 queries score densely (their tiles run
   // at about the same time, so the bound could not prune); batches as large
@@ -57,6 +59,7 @@ struct sinn_index {
   uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
   uint32_t *d_err = nullptr;       // sticky device error bits
   uint64_t *d_live_count = nullptr;  // live_count, kept on the device for the searches
+  uint32_t *d_coord_len = nullptr;   // n: live postings per coordinate, |I[j]|
   uint64_t cap = 0;                // id capacity = tiles_cap * T
 
   // ---- host mirror

@@ -23,6 +23,7 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH = range(7)
+SINN_FLAG_NONNEG = 1
 
 # every symbol declared in include/sinnamon.h
 EXPORTS = [
@@ -32,6 +33,7 @@ EXPORTS = [
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
     "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
     "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
+    "sinn_set_budget", "sinn_get_budget",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
@@ -49,7 +51,7 @@ PHASES = ["prep", "score", "select", "rerank", "insert", "delete"]
 class SinnConfig(C.Structure):
     _fields_ = [("n", C.c_uint32), ("m", C.c_uint32), ("h", C.c_uint32),
                 ("tile_docs", C.c_uint32), ("seed", C.c_uint64), ("capacity_hint", C.c_uint64),
-                ("table", C.c_void_p), ("max_query_nnz", C.c_uint32), ("reserved", C.c_uint32),
+                ("table", C.c_void_p), ("max_query_nnz", C.c_uint32), ("flags", C.c_uint32),
                 ("scratch_bytes", C.c_uint64)]
 
 
@@ -159,6 +161,8 @@ def load(build_if_missing: bool = False):
         "sinn_plan_recordings": ([vp], u64),
         "sinn_plan_destroy": ([vp], C.c_int),
         "sinn_get_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
+        "sinn_set_budget": ([vp, u64], C.c_int),
+        "sinn_get_budget": ([vp], u64),
         "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
                           C.c_int),
@@ -212,11 +216,11 @@ def sinn_create(n: int, m: int, h: int):
 
 def sinn_create_ex(n: int, m: int, h: int, tile_docs: int = 0, seed: int = 0,
                    capacity_hint: int = 0, table=None, max_query_nnz: int = 0,
-                   scratch_bytes: int = 0):
+                   scratch_bytes: int = 0, flags: int = 0):
     lib = load()
     cfg = SinnConfig(n=n, m=m, h=h, tile_docs=tile_docs, seed=seed,
                      capacity_hint=capacity_hint, max_query_nnz=max_query_nnz,
-                     scratch_bytes=scratch_bytes)
+                     scratch_bytes=scratch_bytes, flags=flags)
     keep = None
     if table is not None:
         keep = np.ascontiguousarray(np.asarray(table, dtype=np.uint32).reshape(-1))
@@ -548,6 +552,7 @@ class Index:
         with torch.cuda.device(self.device):
             self._h = sinn_create_ex(n, m, h, **cfg)
         self.n, self.m, self.h = n, m, h
+        self.nonneg = bool(cfg.get("flags", 0) & SINN_FLAG_NONNEG)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -613,11 +618,20 @@ class Index:
         return ids, sc, cnt
 
     def sketch_columns(self, ids, stream=None):
+        """Columns of U and L (L is None for a SINNAMON+ index)."""
         ids = _dev(ids, torch.int32, self.device)
         u = torch.empty((ids.numel(), self.m), dtype=torch.float32, device=self.device)
-        l = torch.empty_like(u)
+        l = None if self.nonneg else torch.empty_like(u)
         sinn_sketch_columns(self._h, ids, u, l, stream)
         return u, l
+
+    def set_budget(self, postings: int):
+        """Alg. 6's anytime budget in postings (0 = none)."""
+        _check(load().sinn_set_budget(self._h, int(postings)), "sinn_set_budget")
+
+    @property
+    def budget(self) -> int:
+        return int(load().sinn_get_budget(self._h))
 
     def inverted_list(self, coord: int) -> np.ndarray:
         return sinn_inverted_list(self._h, coord)

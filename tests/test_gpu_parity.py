@@ -41,20 +41,23 @@ def _pair(w, docs, tile_docs=1024, table=None, seed=0x5151, **cfg):
     return gpu, ora
 
 
-def _check_search(gpu, ora, qs, k, kp):
+def _check_search(gpu, ora, qs, k, kp, budget=0):
+    """The GPU index's search (with its own anytime budget, if any) against
+    the oracle's at the same budget."""
     gi, gs = gpu.search(_ip(qs), _ix(qs), qs.values, k=k, k_prime=kp)
     gpu.sync()
     ci, cs, cnt = gpu.candidates(_ip(qs), _ix(qs), qs.values, kp)
     gi, gs = gi.cpu().numpy().astype(np.uint32), gs.cpu().numpy()
     ci, cs, cnt = ci.cpu().numpy().astype(np.uint32), cs.cpu().numpy(), cnt.cpu().numpy()
-    ref = ora.search(qs.indptr, qs.indices, qs.values, k=k, k_prime=kp, candidates=True)
+    ref = ora.search(qs.indptr, qs.indices, qs.values, k=k, k_prime=kp, candidates=True,
+                     budget=budget)
     live = ora.live_mask()
     swaps = 0
     for r in range(qs.rows):
         qi, qv = qs.row(r)
         kq = min(kp, int(live.sum()))
         assert cnt[r] == kq
-        approx, amag = ora.scores(qi, qv, with_magnitude=True)
+        approx, amag = ora.scores(qi, qv, with_magnitude=True, budget=budget)
         exact, emag = ora.exact_scores(qi, qv, with_magnitude=True)
         # candidate approximate scores agree with the oracle's Alg. 6 scores
         for i, s in zip(ci[r][:kq], cs[r][:kq]):
