@@ -83,6 +83,8 @@ def _load():
         lib.orc_doc_nnz.restype = C.c_uint32
         lib.orc_doc_nnz.argtypes = [vp, C.c_uint32]
         lib.orc_doc.argtypes = [vp, C.c_uint32, u32p, f64p]
+        lib.orc_set_sketch_bf16.restype = C.c_int
+        lib.orc_set_sketch_bf16.argtypes = [vp, C.c_int]
         lib.orc_scores.restype = C.c_int
         lib.orc_scores.argtypes = [vp, u32p, f32p, C.c_uint32, f64p, vp]
         lib.orc_scores_anytime.restype = C.c_int
@@ -146,7 +148,8 @@ class OracleError(RuntimeError):
 class OracleIndex:
     """A SINNAMON index held by the CPU oracle (FP64)."""
 
-    def __init__(self, n: int, m: int, h: int, seed: int = 0x5151, table=None):
+    def __init__(self, n: int, m: int, h: int, seed: int = 0x5151, table=None,
+                 sketch_bf16: bool = False):
         lib = _load()
         self.n, self.m, self.h = n, m, h
         if table is None:
@@ -159,6 +162,8 @@ class OracleIndex:
         if not self._p:
             raise OracleError(EINVAL)
         self._lib = lib
+        if sketch_bf16 and lib.orc_set_sketch_bf16(self._p, 1):
+            raise OracleError(EINVAL)
 
     def close(self):
         if getattr(self, "_p", None):

@@ -18,7 +18,11 @@
  *                               mix64(seed ^ ((o+1)*G) ^ j) mod m, where mix64
  *                               is the output function of SplitMix64 (Steele,
  *                               Lea, Flood, OOPSLA 2014) and G its gamma.
- *   orc_insert               -- Alg. 5 (indexing) + id reuse of Sec. 4.3.
+ *   orc_insert               -- Alg. 5 (indexing) + id reuse of Sec. 4.3;
+ *                               with orc_set_sketch_bf16 the bins are stored
+ *                               as bfloat16 (Sec. 4.1 notes), U rounded up
+ *                               and L rounded down (a reading: bounds stay
+ *                               bounds).
  *   orc_delete               -- Sec. 4.3 (remove i from every I[j], leave
  *                               column i of the sketch as it is, free id i).
  *   orc_scores               -- Alg. 6 (scoring), T = infinity.
@@ -79,6 +83,7 @@ typedef struct {
 
 typedef struct orc_index {
   uint32_t n, m, h;
+  int sketch_bf16; /* bins stored as bfloat16: U rounded up, L rounded down */
   uint32_t *pi; /* n*h: pi[j*h + o] */
   /* per id slot */
   uint32_t n_slots, cap_slots; /* n_slots = next fresh id */
@@ -94,6 +99,29 @@ typedef struct orc_index {
   /* inverted index I: coordinate -> ascending list of ids */
   orc_plist *lists;
 } orc_index;
+
+/* bfloat16 storage of a sketch bin (the paper stores sketches as bfloat16,
+ * Sec. 4.1 notes).  bfloat16 values are the floats whose 16 low bits are
+ * zero.  Reading taken: an upper bin takes the least bfloat16 >= its value
+ * and a lower bin the greatest bfloat16 <= it, so decoded values stay upper
+ * / lower bounds (Thm. 1 keeps holding).  x is a float value (or +-inf). */
+static double bf16_round(double x, int up) {
+  float f = (float)x;
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  uint32_t t = b & 0xFFFF0000u; /* toward zero */
+  float tf;
+  memcpy(&tf, &t, 4);
+  if (tf == f) return x;        /* representable */
+  /* toward zero is up for a negative value and down for a positive one */
+  int toward_zero_ok = (f < 0.0f) ? up : !up;
+  if (!toward_zero_ok) t += 0x10000u; /* one bfloat16 step away from zero */
+  memcpy(&tf, &t, 4);
+  return (double)tf;
+}
+
+/* Store bins as bfloat16 from now on (only on an empty index). */
+int orc_set_sketch_bf16(orc_index *ix, int on);
 
 static void *xrealloc(void *p, size_t bytes) {
   void *q = realloc(p, bytes ? bytes : 1);
@@ -160,6 +188,12 @@ void orc_destroy(orc_index *ix) {
   free(ix->doc_nnz);
   free(ix->free_heap);
   free(ix);
+}
+
+int orc_set_sketch_bf16(orc_index *ix, int on) {
+  if (ix->n_slots) return ORC_EINVAL;
+  ix->sketch_bf16 = on ? 1 : 0;
+  return ORC_OK;
 }
 
 void orc_hash_table(const orc_index *ix, uint32_t *out) {
@@ -334,6 +368,11 @@ int orc_insert(orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
         if (v < l[k]) l[k] = v;
       }
     }
+    if (ix->sketch_bf16)
+      for (uint32_t k = 0; k < ix->m; ++k) {
+        u[k] = bf16_round(u[k], 1);
+        l[k] = bf16_round(l[k], 0);
+      }
     ix->live[id] = 1;
     ix->live_count++;
   }

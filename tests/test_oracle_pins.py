@@ -456,3 +456,53 @@ def test_anytime_scores_bound_the_processed_coordinates(h):
             e = ix.exact_scores(qi[sel], qv[sel])
             assert np.all(a >= e - 1e-12 * (1 + np.abs(e)))
         np.testing.assert_array_equal(ix.scores(qi, qv, budget=0), ix.scores(qi, qv))
+
+
+# -------------------------------------------------------- bfloat16 sketch
+
+def test_bf16_sketch_hand_values():
+    """bfloat16 bins (Sec. 4.1 notes), U rounded up and L rounded down:
+    1 + 2^-20 lies between the bfloat16 neighbours 1 and 1 + 2^-7."""
+    x = np.float32(1.0 + 2.0 ** -20)
+    tab = np.array([[0], [0], [1]], np.uint32)                  # n = 3, m = 2
+    ix = oracle.OracleIndex(3, 2, 1, table=tab, sketch_bf16=True)
+    ix.insert(*_csr([([0, 2], [x, 3.0]), ([0, 1], [-x, 0.5]), ([2], [-0.1])]))
+    u, l = ix.sketch_column(0)
+    assert list(u) == [1.0078125, 3.0] and list(l) == [1.0, 3.0]
+    u, l = ix.sketch_column(1)                                  # bin 0: {-x, 0.5}
+    assert list(u) == [0.5, -np.inf] and list(l) == [-1.0078125, np.inf]
+    u, l = ix.sketch_column(2)                                  # -0.1 in bin 1
+    f = np.float32(-0.1).view(np.uint32)
+    lo = np.uint32((f & 0xFFFF0000) + 0x10000).view(np.float32)  # away from zero
+    hi = np.uint32(f & 0xFFFF0000).view(np.float32)               # toward zero
+    assert u[1] == hi and l[1] == lo and lo < -0.1 < hi
+    # scores read the rounded bins: q = (1, 0, 1) on doc 0 -> u_0 + u_1
+    assert ix.scores([0, 2], [1.0, 1.0])[0] == 1.0078125 + 3.0
+
+
+@pytest.mark.parametrize("h", [1, 2])
+def test_bf16_sketch_is_the_directed_rounding_and_keeps_theorem1(h):
+    """Each bin is the fp32 bin rounded to bfloat16 in its direction: a
+    bfloat16 value on the right side with no bfloat16 value in between; and
+    the scores stay upper bounds of the inner products."""
+    full, docs, ids = _random_index(300, 16, h, 200, 24, seed=31 + h)
+    bf = oracle.OracleIndex(300, 16, h, seed=31 + h, sketch_bf16=True)
+    bf.insert(docs.indptr, docs.indices, docs.values)
+    for i in range(0, 200, 7):
+        for a, b, up in zip(full.sketch_column(i), bf.sketch_column(i), (True, False)):
+            fin = np.isfinite(a)
+            assert np.array_equal(a[~fin], b[~fin])
+            a32, b32 = a[fin].astype(np.float32), b[fin].astype(np.float32)
+            assert np.all(b32.view(np.uint32) & 0xFFFF == 0)        # representable
+            assert np.all(b32 >= a32) if up else np.all(b32 <= a32)
+            # the next bfloat16 toward a is past a
+            bits = b32.view(np.uint32).astype(np.int64)
+            step = np.where((b32 > 0) == up, -0x10000, 0x10000)
+            nb = (bits + step).astype(np.uint32).view(np.float32)
+            moved = b32 != a32
+            assert np.all((nb[moved] < a32[moved]) if up else (nb[moved] > a32[moved]))
+    qs = _random_queries(300, 20, 12, seed=8)
+    for r in range(qs.rows):
+        qi, qv = qs.row(r)
+        a, e = bf.scores(qi, qv), bf.exact_scores(qi, qv)
+        assert np.all(a >= e - 1e-12 * (1 + np.abs(e)))
