@@ -595,6 +595,7 @@ def run_ours(args):
         "serving": extras.get("serving"),
         "anytime": extras.get("anytime"),
         "sinnamon_plus": extras.get("sinnamon_plus"),
+        "bf16_sketch": extras.get("bf16_sketch"),
         "phases_ms_per_step": {p: v / args.steps for p, v in tm["ms"].items()},
         "index": st,
     }
@@ -646,6 +647,23 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora):
                             "bytes_sketch": plus.stats()["bytes_sketch"],
                             "bytes_sketch_full": ix.stats()["bytes_sketch"]}
     plus.close()
+    # bfloat16 bins (upper rounded up, lower down) on the original collection
+    bf = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=args.tile_docs,
+                        capacity_hint=docs.rows, scratch_bytes=args.scratch_gb << 30,
+                        flags=sinnamon.SINN_FLAG_BF16_SKETCH)
+    for a in range(0, docs.rows, 200_000):
+        part = docs.slice(a, min(docs.rows, a + 200_000))
+        bf.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+    qps, ids = timed(bf)
+    rec = None
+    if ora is not None:  # recall against the original collection's exact top-10
+        import oracle
+        o0 = oracle_index(w, docs)
+        rec = recall_at_10(o0, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1)
+        o0.close()
+    out["bf16_sketch"] = {"qps": qps, "k_prime": kp, "docs": docs.rows, "recall_at_10": rec,
+                          "bytes_sketch": bf.stats()["bytes_sketch"]}
+    bf.close()
     log(f"variants: {out}")
     return out
 

@@ -61,6 +61,14 @@ typedef struct sinn_index sinn_index; /* opaque; owned by the library */
  * which never reads L for positive query entries. */
 #define SINN_FLAG_NONNEG 1u
 
+/* bfloat16 sketch (the paper stores sketches as bfloat16, Sec. 4.1 notes):
+ * U and L take 2 bytes per bin instead of 4.  An upper bin holds the least
+ * bfloat16 at or above its value and a lower bin the greatest at or below,
+ * so decoded values remain upper / lower bounds (Thm. 1 holds); scores are
+ * sums of those rounded values, so candidates can differ from the fp32
+ * sketch's.  sinn_sketch_columns returns the rounded values as floats. */
+#define SINN_FLAG_BF16_SKETCH 2u
+
 /* Index parameters.  Zero fields take the defaults noted. */
 typedef struct sinn_config {
   uint32_t n;              /* dimensionality; coordinates are [0, n) */
@@ -73,7 +81,7 @@ typedef struct sinn_config {
                               NULL -> pi_o(j) = mix64(seed ^ (o+1)*0x9E3779B97F4A7C15 ^ j) mod m,
                               mix64 being SplitMix64's output function */
   uint32_t max_query_nnz;  /* largest query non-zero count sinn_search accepts; 0 -> 1024 */
-  uint32_t flags;          /* 0 or SINN_FLAG_NONNEG */
+  uint32_t flags;          /* 0 or SINN_FLAG_NONNEG | SINN_FLAG_BF16_SKETCH */
   uint64_t scratch_bytes;  /* device scratch budget of one search launch; 0 -> 4 GiB */
 } sinn_config;
 

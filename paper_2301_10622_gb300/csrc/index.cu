@@ -101,8 +101,8 @@ __global__ void k_fwd_write(const uint64_t *__restrict__ indptr,
 __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__restrict__ indices,
                          const float *__restrict__ values, uint32_t rows,
                          const uint32_t *__restrict__ ids, const uint32_t *__restrict__ pi,
-                         uint32_t m, uint32_t h, uint64_t cap, uint32_t G, float *__restrict__ U,
-                         float *__restrict__ L) {
+                         uint32_t m, uint32_t h, uint64_t cap, uint32_t G, void *__restrict__ U,
+                         void *__restrict__ L, int bf16) {
   extern __shared__ uint32_t sk[];
   uint32_t *uk = sk;          // G*m
   uint32_t *lk = sk + G * m;  // G*m
@@ -133,8 +133,15 @@ __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__
   for (uint32_t t = threadIdx.x; t < g_cnt * m; t += blockDim.x) {
     uint32_t k = t / g_cnt, g = t % g_cnt;
     uint64_t id = ids[r0 + g];
-    U[(uint64_t)k * cap + id] = sinn_key2f(uk[g * m + k]);
-    if (L) L[(uint64_t)k * cap + id] = sinn_key2f(lk[g * m + k]);  // no L plane: SINNAMON+
+    const uint64_t at = (uint64_t)k * cap + id;
+    const float u = sinn_key2f(uk[g * m + k]), l = sinn_key2f(lk[g * m + k]);
+    if (bf16) {  // bounds stay bounds: U rounds up, L rounds down
+      ((uint16_t *)U)[at] = sinn_bf16_dir(u, true);
+      if (L) ((uint16_t *)L)[at] = sinn_bf16_dir(l, false);
+    } else {
+      ((float *)U)[at] = u;
+      if (L) ((float *)L)[at] = l;  // no L plane: SINNAMON+
+    }
   }
 }
 
@@ -397,8 +404,9 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
 }
 
 __global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
-                                 const float *__restrict__ U, const float *__restrict__ L,
-                                 uint32_t m, uint64_t cap, float *u_out, float *l_out) {
+                                 const void *__restrict__ U, const void *__restrict__ L,
+                                 uint32_t m, uint64_t cap, int bf16, float *u_out,
+                                 float *l_out) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= (uint64_t)cnt * m) return;
   uint32_t r = (uint32_t)(i / m), k = (uint32_t)(i % m);
@@ -408,8 +416,9 @@ __global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
     if (l_out) l_out[i] = __int_as_float(0x7FC00000);
     return;
   }
-  u_out[i] = U[(uint64_t)k * cap + id];
-  if (l_out) l_out[i] = L[(uint64_t)k * cap + id];
+  const uint64_t at = (uint64_t)k * cap + id;
+  u_out[i] = bf16 ? sinn_bf16_f(((const uint16_t *)U)[at]) : ((const float *)U)[at];
+  if (l_out) l_out[i] = bf16 ? sinn_bf16_f(((const uint16_t *)L)[at]) : ((const float *)L)[at];
 }
 
 __global__ void k_store_u64(uint64_t *dst, uint64_t v) { *dst = v; }
@@ -588,12 +597,12 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   // sketch planes: copy the m rows into the wider layout
   const int planes = (ix->flags & SINN_FLAG_NONNEG) ? 1 : 2;  // SINNAMON+: U only
   for (int plane = 0; plane < planes; ++plane) {
-    float **pp = plane ? &ix->d_L : &ix->d_U;
-    float *q = nullptr;
-    CK(cudaMalloc(&q, (uint64_t)ix->m * nc * sizeof(float)));
+    void **pp = plane ? &ix->d_L : &ix->d_U;
+    void *q = nullptr;
+    const size_t e = ix->sk_elem;
+    CK(cudaMalloc(&q, (uint64_t)ix->m * nc * e));
     if (*pp && ix->cap)
-      CK(cudaMemcpy2D(q, nc * sizeof(float), *pp, ix->cap * sizeof(float), ix->cap * sizeof(float),
-                      ix->m, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy2D(q, nc * e, *pp, ix->cap * e, ix->cap * e, ix->m, cudaMemcpyDeviceToDevice));
     if (*pp) CK(cudaFree(*pp));
     *pp = q;
   }
@@ -634,7 +643,7 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   if (n == 0 || m == 0 || h == 0 || h > m || h > SINN_MAX_H || m > 4096) return SINN_EINVAL;
   uint32_t T = cfg->tile_docs ? cfg->tile_docs : 4096;
   if (T < 1024 || T > 16384 || (T & (T - 1))) return SINN_EINVAL;
-  if (cfg->flags & ~SINN_FLAG_NONNEG) return SINN_EINVAL;
+  if (cfg->flags & ~(SINN_FLAG_NONNEG | SINN_FLAG_BF16_SKETCH)) return SINN_EINVAL;
   if (cfg->table)
     for (uint64_t t = 0; t < (uint64_t)n * h; ++t)
       if (cfg->table[t] >= m) return SINN_EINVAL;
@@ -649,6 +658,7 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
   while ((1u << ix->log2T) < T) ix->log2T++;
   ix->seed = cfg->seed ? cfg->seed : 0x5151ULL;
   ix->flags = cfg->flags;
+  ix->sk_elem = (cfg->flags & SINN_FLAG_BF16_SKETCH) ? 2 : 4;
   ix->max_qnnz = cfg->max_query_nnz ? cfg->max_query_nnz : 1024;
   ix->scratch_budget = cfg->scratch_bytes ? cfg->scratch_bytes : (4ULL << 30);
   std::vector<uint32_t> tab((uint64_t)n * h);
@@ -909,7 +919,7 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(32, 6144 / ix->m));
   k_sketch<<<(n_docs + G - 1) / G, 256, (size_t)2 * G * ix->m * 4, s>>>(
       indptr, indices, values, n_docs, d_ids, ix->d_pi, ix->m, ix->h, ix->cap, G, ix->d_U,
-      ix->d_L);
+      ix->d_L, ix->sk_elem == 2 ? 1 : 0);
   CK(cudaGetLastError());
   k_set_live<<<(n_docs + 255) / 256, 256, 0, s>>>(d_ids, n_docs, ix->d_live, 1);
   CK(cudaGetLastError());
@@ -1002,7 +1012,7 @@ extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   out->postings = post;
   out->tombstones = ix->tombstones;
   out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)ix->n * 8;
-  out->bytes_sketch = (ix->d_L ? 2ull : 1ull) * ix->m * ix->cap * 4;
+  out->bytes_sketch = (ix->d_L ? 2ull : 1ull) * ix->m * ix->cap * ix->sk_elem;
   out->bytes_store = ix->fwd_cap * 8 + ix->cap * 12;
   out->bytes_scratch = ix->scratch_size + ix->iscratch_size;
   out->n = ix->n;
@@ -1027,7 +1037,9 @@ extern "C" int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t
   cudaStream_t s = (cudaStream_t)stream;
   uint64_t tot = (uint64_t)n_ids * ix->m;
   k_gather_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ids, n_ids, ix->d_U, ix->d_L,
-                                                                  ix->m, ix->cap, u_out, l_out);
+                                                                  ix->m, ix->cap,
+                                                                  ix->sk_elem == 2 ? 1 : 0,
+                                                                  u_out, l_out);
   CK(cudaGetLastError());
   return SINN_OK;
 }

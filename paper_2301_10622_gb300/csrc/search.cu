@@ -188,8 +188,8 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
 struct ScoreArgs {
   const uint2 *tile_dir;
   uint16_t *const *tile_post;
-  const float *U;
-  const float *L;
+  const void *U;  // sketch planes: fp32 or bfloat16 bits (S below)
+  const void *L;
   const uint32_t *pi;
   const uint32_t *live;
   uint64_t cap;
@@ -253,14 +253,23 @@ __device__ uint32_t bound_from_hist(const uint32_t *gh, uint32_t kq, uint32_t lb
 // Decoded value x~ of one posting (Alg. 6 lines 7-11): the least upper bound
 // over the term's h rows of U (q_j > 0) or the greatest lower bound over its
 // rows of L (q_j < 0).  row[o] already points at the tile's slice of the row.
-template <int H>
-__device__ __forceinline__ float decode(const float *const *row, uint32_t h, bool pos, uint32_t d) {
-  float y = __ldg(row[0] + d);
+__device__ __forceinline__ float sk_load(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float sk_load(const uint16_t *p) { return sinn_bf16_f(__ldg(p)); }
+__device__ __forceinline__ float4 sk_load4(const float *p) { return __ldg((const float4 *)p); }
+__device__ __forceinline__ float4 sk_load4(const uint16_t *p) {
+  const uint2 v = __ldg((const uint2 *)p);  // 4 bins, 8-byte aligned
+  return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
+                     __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+}
+
+template <int H, typename S>
+__device__ __forceinline__ float decode(const S *const *row, uint32_t h, bool pos, uint32_t d) {
+  float y = sk_load(row[0] + d);
   const uint32_t hh = H > 0 ? (uint32_t)H : h;
 #pragma unroll
   for (uint32_t o = 1; o < (H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H); ++o) {
     if (o >= hh) break;
-    const float z = __ldg(row[o] + d);
+    const float z = sk_load(row[o] + d);
     y = pos ? fminf(y, z) : fmaxf(y, z);
   }
   return y;
@@ -269,15 +278,15 @@ __device__ __forceinline__ float decode(const float *const *row, uint32_t h, boo
 // Sketch values of 4 consecutive ids (16-byte aligned: rows start on tile
 // boundaries): least upper bound over the rows for q_j > 0, greatest lower
 // bound for q_j < 0 (Alg. 6 lines 7-11).
-template <int H>
-__device__ __forceinline__ float4 decode4(const float *const *row, uint32_t h, bool pos,
+template <int H, typename S>
+__device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool pos,
                                           uint32_t d0) {
-  float4 y = __ldg((const float4 *)(row[0] + d0));
+  float4 y = sk_load4(row[0] + d0);
   const uint32_t hh = H > 0 ? (uint32_t)H : h;
 #pragma unroll
   for (uint32_t o = 1; o < (H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H); ++o) {
     if (o >= hh) break;
-    const float4 z = __ldg((const float4 *)(row[o] + d0));
+    const float4 z = sk_load4(row[o] + d0);
     if (pos) {
       y.x = fminf(y.x, z.x); y.y = fminf(y.y, z.y); y.z = fminf(y.z, z.z); y.w = fminf(y.w, z.w);
     } else {
@@ -303,7 +312,7 @@ __device__ __forceinline__ float4 decode4(const float *const *row, uint32_t h, b
 //   every live id's key is written and counted (dense).
 // The histogram covers all the block's tiles: it is cleared, merged into the
 // query's global histogram and used to refresh the bound once per block.
-template <bool EMIT, int H>
+template <bool EMIT, int H, typename S>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
@@ -397,8 +406,8 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           const uint32_t k = t_bl[kk];
           const float v = t_v[k];
           const bool pos = v > 0.0f;
-          const float *plane = pos ? a.U : a.L;
-          const float *row[HS];
+          const S *plane = (const S *)(pos ? a.U : a.L);
+          const S *row[HS];
 #pragma unroll
           for (uint32_t o = 0; o < HS; ++o)
             if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
@@ -408,7 +417,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
             const uint32_t d0 = g0 + g * 4 * kScoreThreads + 4 * tid;
             if (d0 < T) {
               const uint32_t bits = __ldg(bm + (d0 >> 5)) >> (d0 & 31);
-              const float4 x = decode4<H>(row, a.h, pos, d0);
+              const float4 x = decode4<H, S>(row, a.h, pos, d0);
               if (bits & 1u) r[g].x = fmaf(v, x.x, r[g].x);
               if (bits & 2u) r[g].y = fmaf(v, x.y, r[g].y);
               if (bits & 4u) r[g].z = fmaf(v, x.z, r[g].z);
@@ -436,7 +445,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
         uint32_t c_start = 0, c_next = 0, lo = 0, len = 0;
         float v = 0.0f;
         bool pos = true;
-        const float *row[HS];
+        const S *row[HS];
         auto load_term = [&]() {
           c_start = t_cp[i];
           c_next = t_cp[i + 1];
@@ -444,7 +453,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           len = t_cnt[i];
           v = t_v[i];
           pos = v > 0.0f;
-          const float *plane = pos ? a.U : a.L;
+          const S *plane = (const S *)(pos ? a.U : a.L);
 #pragma unroll
           for (uint32_t o = 0; o < HS; ++o)
             if (o < a.h) row[o] = plane + (uint64_t)t_bin[i * a.h + o] * a.cap + id0;
@@ -466,7 +475,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           float x[4];
 #pragma unroll
           for (uint32_t u = 0; u < 4; ++u)
-            x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H>(row, a.h, pos, d[u]);
+            x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H, S>(row, a.h, pos, d[u]);
 #pragma unroll
           for (uint32_t u = 0; u < 4; ++u)
             if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], v * x[u]);
@@ -541,17 +550,17 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
 }
 
 // Grid (query, group of tiles_per_block tiles), queries fastest.
-template <int H>
+template <int H, typename S>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Batch bt) {
   extern __shared__ uint32_t sm[];
   const uint32_t t0 = blockIdx.y * a.tpb;
-  score_tiles<true, H>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
+  score_tiles<true, H, S>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
 }
 
 // The same work as k_score_emit from a fixed grid of blocks: each block takes
 // (query, group) items from a counter in the same query-fastest order until
 // none is left.
-template <int H>
+template <int H, typename S>
 __global__ void __launch_bounds__(kScoreThreads, 4)
     k_score_emit_persistent(ScoreArgs a, Batch bt, uint32_t nb, unsigned long long *next) {
   extern __shared__ uint32_t sm[];
@@ -564,18 +573,18 @@ __global__ void __launch_bounds__(kScoreThreads, 4)
     __syncthreads();  // every thread has read the item before the next draw
     if (item >= total) break;
     const uint32_t b = (uint32_t)(item % nb), t0 = (uint32_t)(item / nb) * a.tpb;
-    score_tiles<true, H>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
+    score_tiles<true, H, S>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
   }
 }
 
 // Dense scoring of the flagged queries (grid-stride over (query, tile)).
-template <int H>
+template <int H, typename S>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, Batch bt) {
   extern __shared__ uint32_t sm[];
   const uint32_t nf = *bt.nflag;
   for (uint64_t w = blockIdx.x; w < (uint64_t)nf * a.tiles; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / a.tiles], t = (uint32_t)(w % a.tiles);
-    score_tiles<false, H>(a, bt, b, t, t + 1, sm);
+    score_tiles<false, H, S>(a, bt, b, t, t + 1, sm);
     __syncthreads();
   }
 }
@@ -588,10 +597,16 @@ struct ScoreKernels {
   void (*persistent)(ScoreArgs, Batch, uint32_t, unsigned long long *);
 };
 
-ScoreKernels score_kernels(uint32_t h) {
-  if (h == 1) return {k_score_emit<1>, k_score_dense<1>, k_score_emit_persistent<1>};
-  if (h == 2) return {k_score_emit<2>, k_score_dense<2>, k_score_emit_persistent<2>};
-  return {k_score_emit<0>, k_score_dense<0>, k_score_emit_persistent<0>};
+template <typename S>
+ScoreKernels score_kernels_for(uint32_t h) {
+  if (h == 1) return {k_score_emit<1, S>, k_score_dense<1, S>, k_score_emit_persistent<1, S>};
+  if (h == 2) return {k_score_emit<2, S>, k_score_dense<2, S>, k_score_emit_persistent<2, S>};
+  return {k_score_emit<0, S>, k_score_dense<0, S>, k_score_emit_persistent<0, S>};
+}
+
+// Sketch bins as fp32 or as bfloat16 bits.
+ScoreKernels score_kernels(uint32_t h, bool bf16) {
+  return bf16 ? score_kernels_for<uint16_t>(h) : score_kernels_for<float>(h);
 }
 
 // ------------------------------------------------------------------ select
@@ -1168,7 +1183,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   }
   Batch bt = views(fixed ? fixed->base : ix->scratch, L, (uint32_t)B);
   const size_t ssm = score_smem(ix);
-  const ScoreKernels sk = score_kernels(ix->h);
+  const ScoreKernels sk = score_kernels(ix->h, ix->sk_elem == 2);
   CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));

@@ -47,8 +47,9 @@ struct sinn_index {
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings
-  float *d_U = nullptr;            // m x cap, row-major (row k contiguous over ids)
-  float *d_L = nullptr;            // m x cap
+  void *d_U = nullptr;             // m x cap, row-major (row k contiguous over ids):
+  void *d_L = nullptr;             //   fp32, or bfloat16 bits with SINN_FLAG_BF16_SKETCH
+  uint32_t sk_elem = 4;            // bytes per sketch bin
   uint32_t *d_live = nullptr;      // cap/32 bitmap words
   uint64_t *d_fwd_off = nullptr;   // cap: offset of each vector in d_fwd
   uint32_t *d_fwd_nnz = nullptr;   // cap: entries stored (zeros included)
@@ -128,6 +129,21 @@ __device__ __forceinline__ float sinn_key2f(uint32_t k) {
   uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
   return __uint_as_float(b);
 }
+
+// bfloat16 bins: the floats whose 16 low bits are zero.  An upper bin takes
+// the least bfloat16 at or above x, a lower bin the greatest at or below it
+// (toward zero is up for a negative x and down for a positive one).
+__device__ __forceinline__ uint16_t sinn_bf16_dir(float x, bool up) {
+  const uint32_t b = __float_as_uint(x);
+  uint32_t t = b >> 16;
+  if (b & 0xFFFFu) {
+    const bool toward_zero_ok = (b >> 31) ? up : !up;
+    if (!toward_zero_ok) t += 1u;  // one bfloat16 step away from zero
+  }
+  return (uint16_t)t;
+}
+
+__device__ __forceinline__ float sinn_bf16_f(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
 __device__ __forceinline__ bool sinn_is_live(const uint32_t *live, uint64_t id) {
   return (__ldg(live + (id >> 5)) >> (id & 31)) & 1u;
 }

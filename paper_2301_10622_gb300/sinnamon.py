@@ -24,6 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH = range(7)
 SINN_FLAG_NONNEG = 1
+SINN_FLAG_BF16_SKETCH = 2
 
 # every symbol declared in include/sinnamon.h
 EXPORTS = [

@@ -1,7 +1,8 @@
 """The paper's variants on the GPU against the oracle: SINNAMON+ (the Sec.
-4.1 note: non-negative data, no lower sketch L) and Alg. 6's anytime budget
+4.1 note: non-negative data, no lower sketch L), Alg. 6's anytime budget
 (the break after a term once the time budget, counted in postings, is
-spent)."""
+spent) and bfloat16 sketch bins (Sec. 4.1 notes; upper bins rounded up,
+lower bins down)."""
 import numpy as np
 import pytest
 
@@ -119,3 +120,54 @@ def test_budget_change_records_a_plan_again():
         for i, s_ in zip(ids[r], sc[r]):
             assert parity.score_close(s_, e[i], m[i])
         assert np.mean(ids[r] == ref["ids"][r]) >= 0.8
+
+
+# ------------------------------------------------------- bfloat16 sketch
+
+def _bf16_pair(w, docs, tile_docs=1024, flags=0):
+    gpu = sinnamon.Index(w.n, w.m, w.h, tile_docs=tile_docs,
+                         flags=flags | sinnamon.SINN_FLAG_BF16_SKETCH)
+    ora = oracle.OracleIndex(w.n, w.m, w.h, sketch_bf16=True)
+    g = gpu.insert(_ip(docs), _ix(docs), docs.values).cpu().numpy().astype(np.uint32)
+    assert np.array_equal(g, ora.insert(docs.indptr, docs.indices, docs.values))
+    return gpu, ora
+
+
+@pytest.mark.parametrize("name,n_docs,nq", [("mixed", 6000, 40), ("text", 9000, 48)])
+def test_bf16_sketch_matches_the_oracle(name, n_docs, nq):
+    """Bins bit for bit (the oracle's directed rounding), Alg. 6 scores within
+    the fp32 bar of the oracle's FP64 sums of the same rounded bins, and the
+    search within the tie band."""
+    w = synth.scaled(synth.WORKLOADS[name], n_docs, n=min(synth.WORKLOADS[name].n, 4000))
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=nq)
+    gpu, ora = _bf16_pair(w, docs)
+    full, _ = _pair(w, docs, tile_docs=1024)
+    assert gpu.stats()["bytes_sketch"] * 2 == full.stats()["bytes_sketch"]
+    ids = np.arange(0, n_docs, 53, dtype=np.int32)
+    u, l = gpu.sketch_columns(ids)
+    u, l = u.cpu().numpy(), l.cpu().numpy()
+    assert np.all(u.view(np.uint32) & 0xFFFF == 0) and np.all(l.view(np.uint32) & 0xFFFF == 0)
+    for r, i in enumerate(ids):
+        uo, lo = ora.sketch_column(int(i))
+        assert np.array_equal(u[r].astype(np.float64), uo)
+        assert np.array_equal(l[r].astype(np.float64), lo)
+    s = gpu.scores(_ip(qs), _ix(qs), qs.values).cpu().numpy()
+    live = ora.live_mask()
+    for r in range(qs.rows):
+        qi, qv = qs.row(r)
+        ref, mag = ora.scores(qi, qv, with_magnitude=True)
+        parity.check_dense_scores(s[r][: ref.size], ref, mag, live)
+    _check_search(gpu, ora, qs, 10, 300)
+
+
+def test_bf16_sketch_streams_and_combines_with_nonneg():
+    w = synth.scaled(synth.WORKLOADS["text"], 6000, n=3000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=36)
+    gpu, ora = _bf16_pair(w, docs.slice(0, 5000), flags=sinnamon.SINN_FLAG_NONNEG)
+    dele = np.arange(7, 5000, 13, dtype=np.uint32)
+    gpu.delete(dele.astype(np.int32))
+    ora.delete(dele)
+    rest = docs.slice(5000, 6000)
+    g = gpu.insert(_ip(rest), _ix(rest), rest.values).cpu().numpy().astype(np.uint32)
+    assert np.array_equal(g, ora.insert(rest.indptr, rest.indices, rest.values))
+    _check_search(gpu, ora, qs, 10, 200)
