@@ -2,17 +2,17 @@
 //
 // One search launch handles a batch of B queries:
 //   k_qprep      nz(q), sorted by |q_j| descending, ties by j (Alg. 6 lines 1-2)
-//   k_score_emit grid (query, tile), queries fastest so the blocks resident at
-//                any time share one tile's lists and sketch rows in L2: walks
-//                the query's lists inside one tile of T ids, decodes each
-//                posting from the sketch (least upper bound from U for
-//                q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6
-//                lines 5-12) and accumulates q_j * x~ in shared memory.  Each
-//                block adds its 4096-bin histogram of score keys (top 12
-//                bits) to the query's histogram, and every few tiles one block
-//                turns that histogram into a lower bound on the k'-th best
-//                score: at least k' scores already seen are at or above it.
-//                Only ids at or above the bound are emitted as candidates.
+//   k_score_emit grid (query, group of tiles), queries fastest so the blocks
+//                resident at any time share the tiles' lists and sketch rows
+//                in L2: walks the query's lists inside each tile of T ids,
+//                decodes each posting from the sketch (least upper bound from
+//                U for q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6
+//                lines 5-12) and accumulates q_j * x~ in shared memory.  Score
+//                keys at or above the query's running bound are counted in its
+//                4096-bin histogram (top 12 bits) and emitted as candidates;
+//                every few tiles a block turns the histogram into a new lower
+//                bound on the k'-th best score (at least k' scores already seen
+//                are at or above it).
 //   k_pick_list/k_compact_list/k_refine
 //                FindLargest(scores, k') of Alg. 7 line 1 as a radix select:
 //                the complete histogram gives the bin holding the k'-th best;
@@ -310,8 +310,8 @@ __device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool 
 //   The epilogue runs on those registers: ids whose score key reaches the
 //   query's running bound are counted in the histogram and emitted (EMIT), or
 //   every live id's key is written and counted (dense).
-// The histogram covers all the block's tiles: it is cleared, merged into the
-// query's global histogram and used to refresh the bound once per block.
+// Counted keys go straight to the query's global histogram; the bound is
+// refreshed from it once per block.
 template <bool EMIT, int H, typename S>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
@@ -320,8 +320,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT;
   float *acc = (float *)sm;                          // T: array terms (atomics)
   float *bacc = acc + T;                             // T: bitmap terms (owner only)
-  uint32_t *hist = sm + 2 * T;                       // 4096
-  uint32_t *t_start = hist + 4096;                   // kTermBatch
+  uint32_t *t_start = sm + 2 * T;                    // kTermBatch
   uint32_t *t_cnt = t_start + kTermBatch;            // kTermBatch
   uint32_t *t_cp = t_cnt + kTermBatch;               // kTermBatch+1: chunk prefix (arrays)
   float *t_v = (float *)(t_cp + kTermBatch + 1);     // kTermBatch
@@ -333,15 +332,17 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
   const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
+  // the query's histogram of key bins, counted in place with L2 atomics:
+  // past the first tiles only the keys at or above the running bound are
+  // counted, too few to need a per-block copy (whose shared memory is worth
+  // more as L1 for the sketch gathers)
   uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
   uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
 
   if (tid == 0) s_lb = EMIT ? __ldcg(&bt.bound[b]) : 0u;
   __syncthreads();
-  // keys below the bound are neither counted nor emitted: their bins stay
-  // untouched
-  const uint32_t lb = s_lb, h0 = lb & ~31u;
-  for (uint32_t i = h0 + tid; i < 4096; i += kScoreThreads) hist[i] = 0;
+  // keys below the bound are neither counted nor emitted
+  const uint32_t lb = s_lb;
   const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
   for (uint32_t t = t_beg; t < t_end; ++t) {
     const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
@@ -501,7 +502,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
         for (uint32_t q = 0; q < 4; ++q) {
           const uint32_t key = sinn_f2key(rv[q] + 0.0f);
           const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
-          if (em) atomicAdd(&hist[key >> 20], 1u);
+          if (em) atomicAdd(&gh[key >> 20], 1u);
           if (__any_sync(0xFFFFFFFFu, em)) {
             const uint32_t p = warp_append(em, &bt.ecnt[b]);
             if (em && p < kEmitCap)
@@ -518,26 +519,19 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           kv[q] = lv ? key : 0u;
           const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
           const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
-          if (lv && lane == __ffs(grp) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(grp));
+          if (lv && lane == __ffs(grp) - 1) atomicAdd(&gh[bin], (uint32_t)__popc(grp));
         }
         if (in)
           *(uint4 *)(bt.keys + (uint64_t)b * a.cap + id0 + d0) = make_uint4(kv[0], kv[1], kv[2], kv[3]);
       }
     }
   }
-  __syncthreads();
-  if (!EMIT) {
-    for (uint32_t k = tid; k < 4096; k += kScoreThreads)
-      if (hist[k]) atomicAdd(&gh[k], hist[k]);
-    return;
-  }
+  if (!EMIT) return;
   // EMIT: the final boundary bin is never below any bound used, so the
   // histogram stays exact from the boundary bin up and every candidate is
-  // emitted.  Merge the block's counts, then refresh the query's bound each
-  // time the tiles done cross a multiple of bound_every.
-  for (uint32_t k = h0 + tid; k < 4096; k += kScoreThreads)
-    if (k >= lb && hist[k]) atomicAdd(&gh[k], hist[k]);
-  __threadfence();
+  // emitted.  Refresh the query's bound each time the tiles done cross a
+  // multiple of bound_every.
+  __threadfence();  // every count is visible before the tiles are reported done
   __syncthreads();
   if (tid == 0) part[NW + 1] = atomicAdd(&bt.tdone[b], t_end - t_beg);
   __syncthreads();
@@ -1157,7 +1151,7 @@ struct SearchReq {
 };
 
 size_t score_smem(const sinn_index *ix) {
-  return (size_t)ix->T * 8 + 4096 * 4 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
+  return (size_t)ix->T * 8 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
 }
 
 // Scratch supplied by the caller instead of the index's own (grown) buffer.
