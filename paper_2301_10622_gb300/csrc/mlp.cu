@@ -3,9 +3,10 @@
 // a 2-hidden-layer MLP with BF16 tensor-core GEMMs (FP32 accumulation), its
 // training step (pinball loss, Adam) and a search that uses its prediction.
 //
-// GEMMs use mma.sync.m16n8k16 (bf16 inputs, fp32 accumulators) on 64x64
-// tiles staged through shared memory; operands are read through arbitrary
-// (row, column) strides, so the same kernel computes X W^T, dY W and dY^T X.
+// GEMMs run on the 5th-generation tensor cores (tcgen05.mma, bf16 inputs,
+// fp32 accumulators in tensor memory) on 128x128 tiles staged through shared
+// memory; operands are read through arbitrary (row, column) strides, so the
+// same kernel computes X W^T, dY W and dY^T X.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -24,7 +25,6 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
 
 struct GemmArgs {
   // C[m][n] = alpha * sum_k A(m,k) B(n,k) (+ bias[n]) (ReLU) ; A, B bf16
@@ -44,83 +44,176 @@ struct GemmArgs {
   int64_t ldm;
 };
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// ---------------------------------------------------------------- GEMM
+// C = alpha * A B^T on the 5th-generation tensor cores: one 128x128 output
+// tile per CTA of 128 threads.  For each 64-wide slice of K the threads stage
+// A (128 x 64) and B (128 x 64) in shared memory in the canonical K-major
+// layout without swizzle -- core matrices of 8 rows x 16 bytes, 128 bytes
+// apart along K and 1024 bytes apart along M (N) -- and one thread issues four
+// tcgen05.mma (M = 128, N = 128, K = 16, bf16 in, fp32 accumulate) into a
+// 128-column tensor-memory accumulator, committing to an mbarrier that the
+// CTA waits on before it overwrites the operands.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes = rows 32w..32w+31).
+// Every wait is bounded: on a timeout the CTA raises g_tc_timeouts, still
+// waits (bounded) for its MMAs and frees its tensor memory.
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr uint32_t kTcSpin = 1u << 24;  // try_wait rounds before giving up
+
+__device__ unsigned int g_tc_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// 4 warps; warp w computes rows [32*(w/2), +32) x cols [32*(w%2), +32) of the tile
-__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
-  __shared__ __nv_bfloat16 As[BM][BK + 8];
-  __shared__ __nv_bfloat16 Bs[BN][BK + 8];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int wm = (w >> 1) * 32, wn = (w & 1) * 32;
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 128) {
-      const int r = e / BK, c = e % BK;
-      const int m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
-      const int n = n0 + r;
-      Bs[r][c] = (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
-    }
-    __syncthreads();
-    uint32_t af[2][4], bf[4][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int r = wm + i * 16 + gid;
-      af[i][0] = pack_bf16(As[r][tig * 2], As[r][tig * 2 + 1]);
-      af[i][1] = pack_bf16(As[r + 8][tig * 2], As[r + 8][tig * 2 + 1]);
-      af[i][2] = pack_bf16(As[r][tig * 2 + 8], As[r][tig * 2 + 9]);
-      af[i][3] = pack_bf16(As[r + 8][tig * 2 + 8], As[r + 8][tig * 2 + 9]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = wn + j * 8 + gid;
-      bf[j][0] = pack_bf16(Bs[n][tig * 2], Bs[n][tig * 2 + 1]);
-      bf[j][1] = pack_bf16(Bs[n][tig * 2 + 8], Bs[n][tig * 2 + 9]);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-            : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]),
-              "r"(bf[j][1]));
-    __syncthreads();
+// Byte offset of element (r, k) of a rows x 64 K-major tile.
+__device__ __forceinline__ uint32_t tc_off(uint32_t r, uint32_t k) {
+  return ((r >> 3) * (TC_K / 8) + (k >> 3)) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// Shared-memory matrix descriptor (no swizzle): start, leading byte offset
+// (between core matrices along K), stride byte offset (along M / N), the
+// descriptor version 1 in bits 46-47.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = (TC_K / 8) * 128;
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((lbo >> 4) & 0x3FFFu) << 16 |
+         ((sbo >> 4) & 0x3FFFu) << 32 | (uint64_t)1 << 46;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulator (bits 4-5 = 1), A and
+// B bf16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kTcSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
+  return false;
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
+  __shared__ __align__(1024) uint8_t As[TC_M * TC_K * 2];
+  __shared__ __align__(1024) uint8_t Bs[TC_N * TC_K * 2];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem, s_fail;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const uint32_t mb = smem_u32(&mbar);
+  if (warp == 0) {  // tensor memory: 128 fp32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"((uint32_t)TC_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  uint32_t phase = 0, issued = 0;
+  for (int k0 = 0; k0 < g.K; k0 += TC_K) {
+    // stage the slice (zeros beyond M, N, K)
+    for (int e = tid; e < TC_M * TC_K; e += 128) {
+      const int r = e / TC_K, c = e % TC_K;
+      const int m = m0 + r, n = n0 + r, k = k0 + c;
+      *(__nv_bfloat16 *)(As + tc_off(r, c)) =
+          (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+      *(__nv_bfloat16 *)(Bs + tc_off(r, c)) =
+          (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
+    }
+    // generic-proxy writes become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + tig * 2 + (r & 1);
-        if (m >= g.M || n >= g.N) continue;
-        float v = g.alpha * acc[i][j][r];
-        if (g.bias) v += g.bias[n];
-        if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) v = 0.0f;
-        if (g.relu) v = fmaxf(v, 0.0f);
-        if (g.C) g.C[m * g.ldc + n] = v;
-        if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(v);
+      for (int s = 0; s < TC_K / 16; ++s) {
+        const uint64_t da = tc_desc(smem_u32(As) + s * 256);  // 2 core matrices along K
+        const uint64_t db = tc_desc(smem_u32(Bs) + s * 256);
+        const uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc)
+            : "memory");
       }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              mb)
+          : "memory");
+    }
+    issued++;
+    // the MMAs have read the operands before they are overwritten
+    if (!mbar_wait(mb, phase)) {
+      if (tid == 0) atomicAdd(&g_tc_timeouts, 1u);
+      s_fail = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (s_fail) break;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (!s_fail && issued > 0) {
+    // warp w reads rows 32w + lane, 32 columns at a time
+    const uint32_t row = warp * 32 + (tid & 31);
+    const int m = m0 + (int)row;
+    for (int c0 = 0; c0 < TC_N; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (m < g.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= g.N) continue;
+          float x = g.alpha * __uint_as_float(v[j]);
+          if (g.bias) x += g.bias[n];
+          if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) x = 0.0f;
+          if (g.relu) x = fmaxf(x, 0.0f);
+          if (g.C) g.C[m * g.ldc + n] = x;
+          if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(x);
+        }
+      }
+    }
+  } else if (s_fail && tid == 0) {
+    // wait (bounded) for the MMAs still in flight before the memory goes
+    (void)mbar_wait(mb, phase ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)TC_N)
+                 : "memory");
 }
 
 void gemm(const GemmArgs &g, cudaStream_t s) {
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+  dim3 grid((g.N + TC_N - 1) / TC_N, (g.M + TC_M - 1) / TC_M);
+  k_gemm_tc<<<grid, 128, 0, s>>>(g);
 }
 
 // Features -> normalised bf16 inputs (padded to K columns with zeros).
