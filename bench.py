@@ -87,7 +87,7 @@ def make_inputs(args, rank):
 
 
 def algorithmic_bytes(w, docs, qs, cap, tiles):
-    """Bytes the scoring kernel must move per query: each
+    """Bytes the scoring kernel must move per query when it runs alone: each
     posting of the query's lists (2-byte id + h 4-byte sketch reads), one 4-byte
     score key per id slot written, the tile offsets read and the live bitmap."""
     nz = docs.values != 0
@@ -284,11 +284,20 @@ def measured_traffic(launches, queries, docs):
     return per_launch * (queries / launches) / q_launch
 
 
+WORKLOAD_TEXT = {
+    "text": ("text-like streaming: n={n}, {docs} docs with Zipf(1) coordinates, nnz/doc "
+             "lognormal(mean 120, sigma 0.5), values lognormal(0,0.7); {nq} queries/step nnz "
+             "lognormal(mean 45)"),
+    "mixed": ("mixed-sign streaming: n={n}, {docs} docs with uniform coordinates, nnz/doc "
+              "uniform 80-160, values N(0,1); {nq} queries/step of 40 nnz, values N(0,1)"),
+    "tiny": ("tiny: n={n}, {docs} docs of 32 uniform coordinates, values N(0,1); {nq} "
+             "queries/step of 16 nnz"),
+}
+
+
 def config_dict(args, w, docs, qs, tile_docs):
-    return {"workload": (f"text-like streaming: n={w.n}, {docs.rows} docs with Zipf(1) "
-                         f"coordinates, nnz/doc lognormal(mean 120, sigma 0.5), values "
-                         f"lognormal(0,0.7); {qs.rows} queries/step nnz lognormal(mean 45); "
-                         f"m={w.m}, h={w.h}, k={w.k}, k'={w.k_prime}; churn "
+    desc = WORKLOAD_TEXT[w.name].format(n=w.n, docs=docs.rows, nq=qs.rows)
+    return {"workload": (f"{desc}; m={w.m}, h={w.h}, k={w.k}, k'={w.k_prime}; churn "
                          f"{args.churn} deletes + {args.churn} inserts per step"),
             "docs": docs.rows, "queries_per_step": qs.rows, "churn_per_step": args.churn,
             "n": w.n, "m": w.m, "h": w.h, "k": w.k, "k_prime": w.k_prime,

@@ -289,7 +289,7 @@ def test_error_probability_closed_form_tiny_workload():
     with continuous values a coordinate's upper decode is exact iff it is the
     largest of its bin-mates, so P[err] = 1 - E[1/(1+T)] with T hypergeometric
     given the bin sizes; with equal bins this is 1 - (m/psi)(1-(1-1/m)^psi) =
-    0.2083 (SURVEY's finite-sample form of Thm. 2)."""
+    0.2083 (the finite-sample form of Thm. 2's error probability)."""
     from scipy import stats
     n, m, psi = 1000, 64, 32
     w = synth.WORKLOADS["tiny"]
