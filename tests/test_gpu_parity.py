@@ -397,3 +397,45 @@ def test_select_levels(case, nq):
             assert int(cnt[r]) == kp
             assert set(ci[r]) == set(ref["cand_ids"][0])
             assert list(gi[r]) == list(ref["ids"][0])
+
+
+def test_parameters_at_their_maxima():
+    """m = 4096 bins, h = 8 mappings, tiles of 16384 ids, a query with exactly
+    the default limit of 1024 non-zeros, k = 1024: the search matches the
+    oracle; one non-zero more is a malformed query."""
+    n = 6000
+    w = synth.scaled(synth.WORKLOADS["mixed"], 3000, n=n, m=4096, h=8)
+    docs = synth.make_docs(w)
+    gpu, ora = _pair(w, docs, tile_docs=16384)
+    rng = np.random.default_rng(17)
+    rows = []
+    for nnz in (1024, 700, 1):
+        idx = np.sort(rng.choice(n, nnz, replace=False)).astype(np.uint32)
+        rows.append((idx, rng.normal(0, 1, nnz).astype(np.float32)))
+    qs = synth.CSR(np.concatenate([[0], np.cumsum([r[0].size for r in rows])]).astype(np.uint64),
+                   np.concatenate([r[0] for r in rows]), np.concatenate([r[1] for r in rows]))
+    _check_search(gpu, ora, qs, 1024, 2048)
+    idx = np.sort(rng.choice(n, 1025, replace=False)).astype(np.int32)
+    gi, gs = gpu.search(np.array([0, 1025], np.int64), idx, np.ones(1025, np.float32),
+                        k=10, k_prime=20)
+    with pytest.raises(sinnamon.SinnError) as e:
+        gpu.sync()
+    assert e.value.code == sinnamon.SINN_EINVAL
+    assert np.all(gi.cpu().numpy() == -1)
+
+
+def test_empty_batches_are_no_ops():
+    """Zero documents to insert, zero ids to delete and zero queries to search
+    are accepted and change nothing."""
+    w = synth.scaled(synth.WORKLOADS["tiny"], 500)
+    docs = synth.make_docs(w)
+    gpu, ora = _pair(w, docs)
+    before = gpu.stats()
+    ids = gpu.insert(np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    assert ids.numel() == 0
+    gpu.delete(np.zeros(0, np.int32))
+    gi, gs = gpu.search(np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32),
+                        k=10, k_prime=20)
+    gpu.sync()
+    assert gi.shape == (0, 10) and gs.shape == (0, 10)
+    assert gpu.stats() == before
