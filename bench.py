@@ -295,15 +295,16 @@ WORKLOAD_TEXT = {
 }
 
 
-def config_dict(args, w, docs, qs, tile_docs):
+def config_dict(args, w, docs, qs, tile_docs, index_gb=0.0):
     desc = WORKLOAD_TEXT[w.name].format(n=w.n, docs=docs.rows, nq=qs.rows)
     return {"workload": (f"{desc}; m={w.m}, h={w.h}, k={w.k}, k'={w.k_prime}; churn "
                          f"{args.churn} deletes + {args.churn} inserts per step"),
             "docs": docs.rows, "queries_per_step": qs.rows, "churn_per_step": args.churn,
             "n": w.n, "m": w.m, "h": w.h, "k": w.k, "k_prime": w.k_prime,
             "tile_docs": tile_docs,
-            "l2": "inputs larger than L2: the index (~0.8 GB) and per-query score keys "
-                  "(4 MB each) are streamed every step"}
+            "l2": (f"inputs larger than L2: the index's lists and sketch "
+                   f"({index_gb:.2f} GB) are read by every step" if index_gb else
+                   "inputs larger than L2: the whole index is read by every step")}
 
 
 # ------------------------------------------------------------------- ours
@@ -327,6 +328,17 @@ def run_ours(args):
     w, docs, pool, qs = make_inputs(args, rank)
     k, kp = w.k, w.k_prime
     T = args.tile_docs
+    tile_choice = None
+    if T == 0:
+        # the tile size chosen by measurement (untimed): indexes of the
+        # collection at each candidate, launch-autotuned, timed on a sample
+        from paper_2301_10622_gb300 import autotune
+        t0 = time.time()
+        sq = qs.slice(0, min(qs.rows, 2000))
+        T, res = autotune.choose_tile_docs(w.n, w.m, w.h, docs, sq, k, kp, device=dev,
+                                           scratch_bytes=args.scratch_gb << 30, log=log)
+        tile_choice = {str(t): round(r["ms"], 3) for t, r in res.items()}
+        log(f"tile size {T} chosen in {time.time() - t0:.1f}s: {tile_choice}")
     ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
                         scratch_bytes=args.scratch_gb << 30)
     t0 = time.time()
@@ -574,7 +586,8 @@ def run_ours(args):
             extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
         if not args.skip_variants:
             extras.update(run_variants(args, w, docs, ix, (g_qip, g_qix, g_qv), qs, k, kp,
-                                       float(P.mean()), ora if not args.skip_oracle else None))
+                                       float(P.mean()), ora if not args.skip_oracle else None,
+                                       T))
         if args.serve_seconds > 0:
             extras["serving"] = run_serving(args, w, ix, qs, docs.rows, mlp, k, kp)
     if world > 1:
@@ -586,7 +599,10 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(config_dict(args, w, docs, qs, T), tuning=tuning,
+        "config": dict(config_dict(args, w, docs, qs, T,
+                                   (st["bytes_lists"] + st["bytes_sketch"]) / 1e9),
+                       tuning=tuning,
+                       tile_choice_ms=tile_choice,
                        search_launch=("one recorded CUDA graph per step (sinn_plan)"
                                       if plan is not None else "direct launches")),
         "roofline": roof,
@@ -613,7 +629,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora):
+def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs):
     """The paper's variants, untimed extras: Alg. 6 with an anytime budget
     (half and a quarter of the mean postings per query) on the bench's
     index, and a SINNAMON+ index (U only) of the original collection; each
@@ -645,7 +661,7 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora):
                      "qps": qps, "k_prime": kp, "recall_at_10": rec})
     ix.set_budget(0)
     out["anytime"] = runs
-    plus = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=args.tile_docs,
+    plus = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=tile_docs,
                           capacity_hint=docs.rows, scratch_bytes=args.scratch_gb << 30,
                           flags=sinnamon.SINN_FLAG_NONNEG)
     for a in range(0, docs.rows, 200_000):
@@ -657,7 +673,7 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora):
                             "bytes_sketch_full": ix.stats()["bytes_sketch"]}
     plus.close()
     # bfloat16 bins (upper rounded up, lower down) on the original collection
-    bf = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=args.tile_docs,
+    bf = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=tile_docs,
                         capacity_hint=docs.rows, scratch_bytes=args.scratch_gb << 30,
                         flags=sinnamon.SINN_FLAG_BF16_SKETCH)
     for a in range(0, docs.rows, 200_000):
@@ -747,7 +763,8 @@ def main():
     ap.add_argument("--docs", type=int, default=0)
     ap.add_argument("--queries", type=int, default=0)
     ap.add_argument("--churn", type=int, default=1000)
-    ap.add_argument("--tile-docs", type=int, default=4096)
+    ap.add_argument("--tile-docs", type=int, default=0,
+                    help="ids per tile; 0 = chosen by measurement")
     ap.add_argument("--scratch-gb", type=int, default=8)
     ap.add_argument("--plain-queries", type=int, default=300)
     ap.add_argument("--recall-queries", type=int, default=200)
