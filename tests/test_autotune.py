@@ -89,3 +89,15 @@ def test_autotune_picks_a_valid_tuning(setup):
     assert 1 <= t["dense_blocks_per_sm"] <= 32 and 1 <= t["emit_min_batch"] <= 65535
     assert 1 <= t["tiles_per_block"] <= 64
     _same(want, _run(ix, q))
+
+
+def test_tile_size_is_chosen_by_measurement():
+    from paper_2301_10622_gb300 import autotune
+    w = synth.scaled(synth.WORKLOADS["text"], 12000, n=6000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=120)
+    best, res = autotune.choose_tile_docs(w.n, w.m, w.h, docs, qs, k=10, k_prime=200,
+                                          candidates=(1024, 2048), reps=2,
+                                          scratch_bytes=256 << 20)
+    assert set(res) == {1024, 2048} and best in res
+    assert all(r["ms"] > 0 for r in res.values())
+    assert res[best]["ms"] == min(r["ms"] for r in res.values())
