@@ -7,9 +7,9 @@
  * real vectors that changes online (Sec. 1: insertions and deletions arrive
  * while queries run).  The index keeps, on one GPU:
  *   - an inverted index I: coordinate -> ids of the vectors non-zero there
- *     (Alg. 5 line 2), stored per tile of T consecutive ids as a container
+ *     (Alg. 5), stored per tile of T consecutive ids as a container
  *     of 16-bit local ids: a sorted array, or a T-bit bitmap when at least
- *     a quarter of the tile holds the coordinate; a deleted posting is
+ *     an eighth of the tile holds the coordinate; a deleted posting is
  *     tombstoned in place (Sec. 4.3);
  *   - the sketch matrix [U; L] (Alg. 5): 2m rows of fp32 over all id slots,
  *     row-major, so one query coordinate reads a fixed set of h rows;
@@ -29,7 +29,7 @@
  *   - A handle is not thread-safe: calls on one handle must be serialised.
  *   - Sparse inputs are CSR: indptr[rows+1] (uint64), indices (uint32, each
  *     < n, strictly increasing within a row), values (float32, finite).
- *     Entries equal to zero are not non-zeros (Alg. 5 line 1, Alg. 6 line 1):
+ *     Entries equal to zero are not non-zeros (Alg. 5, Alg. 6):
  *     they are neither indexed nor sketched nor scored.
  *   - Ties: every ranking puts the larger score first and, among equal
  *     scores, the smaller id first.
@@ -248,8 +248,8 @@ int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_in
                   uint32_t reps, sinn_tuning *out, void *stream);
 
 /* Per-phase device timing, for benchmarks.  Phases: 0 query preparation,
- * 1 scoring (Alg. 6), 2 top-k' selection (Alg. 7 line 1), 3 re-rank and
- * top-k (Alg. 7 lines 2-4), 4 insert (Alg. 5), 5 delete (Sec. 4.3). */
+ * 1 scoring (Alg. 6), 2 top-k' selection (Alg. 7), 3 re-rank and
+ * top-k (Alg. 7), 4 insert (Alg. 5), 5 delete (Sec. 4.3). */
 #define SINN_PHASES 6
 typedef struct sinn_timing {
   double ms[SINN_PHASES];        /* summed CUDA-event durations per phase */
@@ -289,7 +289,7 @@ int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out, uint64_t c
 int sinn_scores(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
                 const float *q_values, uint32_t n_q, float *out, void *stream);
 
-/* Alg. 7 line 1 only: the min(k', live) candidates of each query with their
+/* Alg. 7's candidate step only: the min(k', live) candidates of each query with their
  * approximate scores, in no particular order.  out_ids device uint32[n_q*k'],
  * out_scores device float[n_q*k'], out_count device uint32[n_q]. */
 int sinn_candidates(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,

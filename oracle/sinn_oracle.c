@@ -328,7 +328,7 @@ int orc_insert(orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
     }
     if (out_ids) out_ids[r] = id;
 
-    /* nz(x_i) = { j : x_i[j] != 0 } (Alg. 5 line 1); the vector is kept in
+    /* nz(x_i) = { j : x_i[j] != 0 } (Alg. 5); the vector is kept in
      * the store S for re-ranking. */
     uint32_t cnt = 0;
     for (uint64_t p = indptr[r]; p < indptr[r + 1]; ++p)
@@ -346,10 +346,10 @@ int orc_insert(orc_index *ix, const uint64_t *indptr, const uint32_t *indices,
       c++;
     }
 
-    /* I[j].Insert(i) for all j in nz(x_i) (Alg. 5 line 2). */
+    /* I[j].Insert(i) for all j in nz(x_i) (Alg. 5). */
     for (uint32_t t = 0; t < cnt; ++t) list_insert(&ix->lists[ix->doc_idx[id][t]], id);
 
-    /* Alg. 5 lines 3-7: u[k] is the max and l[k] the min of x_i[j] over the
+    /* Alg. 5, sketch: u[k] is the max and l[k] the min of x_i[j] over the
      * non-zeros j that some mapping sends to k.  Visiting each (j, o) pair
      * once and folding x_i[j] into bin pi_o(j) forms exactly these set
      * maxima / minima.  A bin no non-zero reaches keeps -inf / +inf. */
@@ -430,7 +430,7 @@ typedef struct {
   double v;
 } orc_qterm;
 
-/* Alg. 6 line 2: descending |q_j|; equal magnitudes by ascending j. */
+/* Alg. 6: query terms by descending |q_j|; equal magnitudes by ascending j. */
 static int qterm_cmp(const void *a, const void *b) {
   const orc_qterm *x = (const orc_qterm *)a, *y = (const orc_qterm *)b;
   double ax = fabs(x->v), ay = fabs(y->v);
@@ -468,18 +468,18 @@ static void alg6_scores(const orc_index *ix, const orc_qterm *terms, uint32_t nt
   for (uint32_t t = 0; t < nt; ++t) {
     uint32_t j = terms[t].j;
     double qj = terms[t].v;
-    const uint32_t *K = ix->pi + (size_t)j * ix->h; /* K = {pi_o(j)} (line 5) */
+    const uint32_t *K = ix->pi + (size_t)j * ix->h; /* K = {pi_o(j)} */
     const orc_plist *li = &ix->lists[j];
     for (uint32_t p = 0; p < li->len; ++p) {
       uint32_t i = li->ids[p];
       double xt;
-      if (qj > 0) { /* least upper bound (line 8) */
+      if (qj > 0) { /* least upper bound */
         xt = INFINITY;
         for (uint32_t o = 0; o < ix->h; ++o) {
           double c = ix->U[(size_t)i * ix->m + K[o]];
           if (c < xt) xt = c;
         }
-      } else { /* greatest lower bound (line 10) */
+      } else { /* greatest lower bound */
         xt = -INFINITY;
         for (uint32_t o = 0; o < ix->h; ++o) {
           double c = ix->L[(size_t)i * ix->m + K[o]];
@@ -650,7 +650,7 @@ static void ws_free(orc_ws *w) {
 /* Alg. 6 then Alg. 7 for one query.  Returns the number of results r =
  * min(k, live).  out_ids/out_scores get the top-k by exact score (padding
  * beyond r: id 0xFFFFFFFF, score -inf).  If cand_ids is given it receives the
- * min(k', live) candidates V of Alg. 7 line 1 in rank order, with their
+ * min(k', live) candidates V of Alg. 7 in rank order, with their
  * approximate scores and magnitudes. */
 static uint32_t search_one(const orc_index *ix, orc_ws *w, const uint32_t *qi, const float *qv,
                            uint32_t qnnz, uint32_t k, uint32_t kp, uint64_t budget,
@@ -663,7 +663,7 @@ static uint32_t search_one(const orc_index *ix, orc_ws *w, const uint32_t *qi, c
   uint32_t nt = query_terms(qi, qv, qnnz, w->terms);
   alg6_scores(ix, w->terms, anytime_terms(ix, w->terms, nt, budget), w->scores, w->mag);
 
-  /* Alg. 7 line 1: V = FindLargest(scores, k') over the live ids. */
+  /* Alg. 7, candidates: V = FindLargest(scores, k') over the live ids. */
   uint32_t cnt = 0;
   for (uint32_t i = 0; i < ix->n_slots; ++i) {
     if (!ix->live[i]) continue;
@@ -680,12 +680,12 @@ static uint32_t search_one(const orc_index *ix, orc_ws *w, const uint32_t *qi, c
     }
   }
 
-  /* Alg. 7 lines 2-3: s_v = <q, S.Fetch(v)> exactly. */
+  /* Alg. 7, re-rank: s_v = <q, S.Fetch(v)> exactly. */
   for (uint32_t t = 0; t < nt; ++t) w->qdense[w->terms[t].j] = w->terms[t].v;
   for (uint32_t t = 0; t < nv; ++t) w->cand[t].value = exact_dot(ix, w->qdense, w->cand[t].key, NULL);
   for (uint32_t t = 0; t < nt; ++t) w->qdense[w->terms[t].j] = 0.0;
 
-  /* Alg. 7 line 4: FindLargest({s_v}, k). */
+  /* Alg. 7, result: FindLargest({s_v}, k). */
   uint32_t r = find_largest(w->cand, nv, k, w->top);
   for (uint32_t t = 0; t < k; ++t) {
     out_ids[t] = t < r ? w->top[t].key : 0xFFFFFFFFu;
@@ -954,7 +954,7 @@ static void *run_lsjob(void *arg) {
   orc_item *items = (orc_item *)malloc(ns * sizeof(orc_item));
   orc_item *top = (orc_item *)malloc(((size_t)jb->k + 1) * sizeof(orc_item));
   for (uint32_t q = jb->q0; q < jb->q1; ++q) {
-    memset(scores, 0, ns * sizeof(double)); /* Alg. 2 line 2 */
+    memset(scores, 0, ns * sizeof(double)); /* Alg. 2: scores start at zero */
     for (uint64_t p = jb->indptr[q]; p < jb->indptr[q + 1]; ++p) {
       uint32_t j = jb->indices[p];
       double qj = (double)jb->values[p];

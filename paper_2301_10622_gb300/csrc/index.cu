@@ -10,7 +10,7 @@
 //   d_tile_dir  tiles x n uint2 per tile t and coordinate j, the container of
 //                               the postings of I[j] with ids in
 //                               [t*T, (t+1)*T): {start, count} in 16-bit words
-//                               of the tile's storage post_t.  count >= T/4:
+//                               of the tile's storage post_t.  count >= T/8:
 //                               a bitmap of T bits (bit d = local id d; a
 //                               deleted posting's bit is cleared); otherwise a
 //                               sorted array of count 16-bit local ids (bit 15
@@ -93,7 +93,7 @@ __global__ void k_fwd_write(const uint64_t *__restrict__ indptr,
   }
 }
 
-// Alg. 5 lines 3-9: u[k] = max and l[k] = min of x_i[j] over the non-zeros j
+// Alg. 5, sketch: u[k] = max and l[k] = min of x_i[j] over the non-zeros j
 // with pi_o(j) = k for some o; empty bins -inf / +inf.  Max and min are taken
 // on order-preserving integer keys, so the stored bins are the input floats
 // bit for bit.  A block sketches G rows in shared memory, then writes the

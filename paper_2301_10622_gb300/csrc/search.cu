@@ -1,20 +1,19 @@
 // Retrieval on the GPU: Alg. 6 (scoring) and Alg. 7 (ranking) of SINNAMON.
 //
 // One search launch handles a batch of B queries:
-//   k_qprep      nz(q), sorted by |q_j| descending, ties by j (Alg. 6 lines 1-2)
+//   k_qprep      nz(q), sorted by |q_j| descending, ties by j (Alg. 6)
 //   k_score_emit grid (query, group of tiles), queries fastest so the blocks
 //                resident at any time share the tiles' lists and sketch rows
 //                in L2: walks the query's lists inside each tile of T ids,
 //                decodes each posting from the sketch (least upper bound from
-//                U for q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6
-//                lines 5-12) and accumulates q_j * x~ in shared memory.  Score
+//                U for q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6) and accumulates q_j * x~ in shared memory.  Score
 //                keys at or above the query's running bound are counted in its
 //                4096-bin histogram (top 12 bits) and emitted as candidates;
 //                every few tiles a block turns the histogram into a new lower
 //                bound on the k'-th best score (at least k' scores already seen
 //                are at or above it).
 //   k_pick_list/k_compact_list/k_refine
-//                FindLargest(scores, k') of Alg. 7 line 1 as a radix select:
+//                FindLargest(scores, k') of Alg. 7 as a radix select:
 //                the complete histogram gives the bin holding the k'-th best;
 //                emitted keys above it are in, the rest of that bin is picked
 //                by (score, -id).
@@ -22,8 +21,8 @@
 //                is huge (massive ties), is rescored densely (one key per id)
 //                and selected with finer histogram levels (k_hist_level) or,
 //                for exact ties beyond the buffer, by id order.
-//   k_rerank     s_v = <q, S.Fetch(v)> for every candidate (Alg. 7 lines 2-3)
-//   k_final      FindLargest({s_v}, k) (Alg. 7 line 4), sorted best first
+//   k_rerank     s_v = <q, S.Fetch(v)> for every candidate (Alg. 7)
+//   k_final      FindLargest({s_v}, k) (Alg. 7), sorted best first
 // Ties rank the smaller id first: keys carry ~id in their low 32 bits.
 #include <algorithm>
 #include <cstring>
@@ -135,7 +134,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
   __syncthreads();
   const uint32_t cnt = s_bad ? 0u : s_cnt;
   QTerm *out = bt.terms + (uint64_t)b * qmax;
-  // Alg. 6 line 2: rank by |q_j| descending, ties by j ascending
+  // Alg. 6: terms ranked by |q_j| descending, ties by j ascending
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const float ai = fabsf(sv[i]);
     const uint32_t ji = sj[i];
@@ -250,7 +249,7 @@ __device__ uint32_t bound_from_hist(const uint32_t *gh, uint32_t kq, uint32_t lb
   return r;
 }
 
-// Decoded value x~ of one posting (Alg. 6 lines 7-11): the least upper bound
+// Decoded value x~ of one posting (Alg. 6): the least upper bound
 // over the term's h rows of U (q_j > 0) or the greatest lower bound over its
 // rows of L (q_j < 0).  row[o] already points at the tile's slice of the row.
 __device__ __forceinline__ float sk_load(const float *p) { return __ldg(p); }
@@ -277,7 +276,7 @@ __device__ __forceinline__ float decode(const S *const *row, uint32_t h, bool po
 
 // Sketch values of 4 consecutive ids (16-byte aligned: rows start on tile
 // boundaries): least upper bound over the rows for q_j > 0, greatest lower
-// bound for q_j < 0 (Alg. 6 lines 7-11).
+// bound for q_j < 0 (Alg. 6).
 template <int H, typename S>
 __device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool pos,
                                           uint32_t d0) {
@@ -296,22 +295,40 @@ __device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool 
   return y;
 }
 
+// One warp: start the copies of the directory entries {start, count} of the
+// first nt query terms in tile t into dst (8 bytes each, cp.async).
+__device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const QTerm *terms, uint32_t nt,
+                                          uint32_t t, uint2 *dst, uint32_t lane) {
+  const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
+  for (uint32_t k = lane; k < nt; k += 32) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + k);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(dir + terms[k].j)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // Alg. 6 for query slot b over tiles [t_beg, t_end).  A query term's postings
-// inside a tile sit in one container: a bitmap of T bits when at least a
-// quarter of the tile's ids hold the coordinate, else a sorted array of 16-bit
-// local ids.  Per tile:
-//   Array terms first: their postings are cut into chunks of 32 (one per
-//   lane), numbered in term order; each warp takes a contiguous range of
-//   chunks (so it finds a chunk's term by advancing one pointer) and adds
-//   q_j * x~ into shared memory with atomics (two terms may share an id).
-//   Bitmap terms next: thread t owns the 4 consecutive ids 4t..4t+3 of each
+// inside a tile sit in one container: a bitmap of T bits when at least an
+// eighth of the tile's ids hold the coordinate, else a sorted array of 16-bit
+// local ids.  Per tile, for each batch of up to kTermBatch terms:
+//   Staging (warp 0): the terms' directory entries (fetched a tile ahead with
+//   cp.async when the query has a single batch), sketch bins and weights,
+//   the prefix of the array terms' chunk counts and the list of bitmap terms.
+//   Bitmap terms: thread t owns the 4 consecutive ids 4t..4t+3 of each
 //   2048-id slice, holds their partial scores in registers and, per term,
 //   reads one bitmap word and one 16-byte group of sketch values; no atomics.
-//   The epilogue runs on those registers: ids whose score key reaches the
-//   query's running bound are counted in the histogram and emitted (EMIT), or
-//   every live id's key is written and counted (dense).
-// Counted keys go straight to the query's global histogram; the bound is
-// refreshed from it once per block.
+//   The sums go to a second accumulator only the owner touches, so no
+//   barrier separates them from the array terms.
+//   Array terms: their postings are cut into chunks of 32 (one per lane),
+//   numbered in term order; each warp takes a contiguous range of chunks (so
+//   it finds a chunk's term by advancing one pointer) and adds q_j * x~ into
+//   shared memory with atomics (two terms may share an id).
+// The epilogue adds the two accumulators: ids whose score key reaches the
+// query's running bound are counted in the histogram and emitted (EMIT), or
+// every live id's key is written and counted (dense).  Counted keys go
+// straight to the query's global histogram; the bound is refreshed from it
+// once per block.
 template <bool EMIT, int H, typename S>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
@@ -328,6 +345,9 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   __shared__ uint32_t part[NW + 2];
   __shared__ uint32_t s_nbm, s_lb;
   __shared__ uint8_t t_bl[kTermBatch];  // bitmap terms of the batch, in order
+  // directory entries of the query's terms for this tile and the next one
+  // (queries of at most kTermBatch terms: fetched a tile ahead by cp.async)
+  __shared__ uint2 s_dir[2][kTermBatch];
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
@@ -344,6 +364,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   // keys below the bound are neither counted nor emitted
   const uint32_t lb = s_lb;
   const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
+  if (wid == 0 && nbatch == 1 && t_beg < t_end) dir_fetch(a, terms, nt, t_beg, s_dir[0], lane);
   for (uint32_t t = t_beg; t < t_end; ++t) {
     const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
     const uint16_t *post = a.tile_post[t];
@@ -360,15 +381,22 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       if (wid == 0) {
         // stage the batch's terms, then the exclusive prefix of the array
         // chunk counts and the list of bitmap terms
+        const uint32_t pb = (t - t_beg) & 1u;
+        if (nbatch == 1) {
+          asm volatile("cp.async.wait_all;\n" ::: "memory");  // this tile's entries
+          __syncwarp();
+        }
         for (uint32_t k = lane; k < nb; k += 32) {
           const uint32_t j = terms[i0 + k].j;
-          const uint2 de = dir[j];
+          const uint2 de = nbatch == 1 ? s_dir[pb][k] : dir[j];
           t_start[k] = de.x;
           t_cnt[k] = de.y;
           t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
           t_v[k] = terms[i0 + k].v;
           for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
         }
+        // the next tile's entries arrive while this tile is scored
+        if (nbatch == 1 && t + 1 < t_end) dir_fetch(a, terms, nb, t + 1, s_dir[pb ^ 1u], lane);
         __syncwarp();
         uint32_t run = 0, nbm = 0;
         for (uint32_t base = 0; base < nb; base += 32) {
@@ -932,7 +960,7 @@ __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
   return (c * 0x9E3779B1u) >> 7 & mask;
 }
 
-// Alg. 7 lines 2-3: exact <q, x_v> from the vector store for each candidate v.
+// Alg. 7, re-rank: exact <q, x_v> from the vector store for each candidate v.
 // The query lives in a shared-memory hash table; one warp per candidate, lanes
 // over the vector's entries, fixed-order reduction.
 __global__ void k_rerank(RerankArgs a, Batch bt) {
@@ -1003,7 +1031,7 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
   }
 }
 
-// Alg. 7 line 4: best k of the re-ranked candidates, sorted best first.
+// Alg. 7, result: best k of the re-ranked candidates, sorted best first.
 __global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32_t k, uint32_t q0,
                                                 uint32_t *out_ids, float *out_scores) {
   __shared__ uint64_t sk[SINN_MAX_K];

@@ -18,9 +18,13 @@
 #define SINN_HIST1_BITS 12  // second level: key bits [19:8]
 #define SINN_HIST2_BITS 8   // third level: key bits [7:0]
 // A tile's container of one coordinate is a bitmap of T bits once it holds
-// at least T >> SINN_BITMAP_SHIFT postings (a quarter of the tile), else a
-// sorted array of 16-bit local ids.
-#define SINN_BITMAP_SHIFT 2
+// at least T >> SINN_BITMAP_SHIFT postings (an eighth of the tile), else a
+// sorted array of 16-bit local ids.  Scoring a bitmap reads the term's
+// sketch row for every id of the tile: up to 8x its postings, but coalesced
+// and without atomics or index loads; at T/8 and above that is the cheaper
+// of the two (measured against T/4 and T/16), and the bitmap (T/16 words)
+// is never larger than the array.
+#define SINN_BITMAP_SHIFT 3
 
 // device error bits (sticky flag)
 #define SINN_DERR_QUERY 1u     // malformed query
@@ -56,7 +60,7 @@ struct sinn_index {
   uint2 *d_fwd = nullptr;          // vector store pool: (coordinate, value bits)
   uint64_t fwd_cap = 0, fwd_used = 0;
   uint2 *d_tile_dir = nullptr;     // tiles_cap x n containers {start, count} per tile
-                                   // (count >= T/4: bitmap of T bits, else sorted array)
+                                   // (count >= T/8: bitmap of T bits, else sorted array)
   uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
   uint32_t *d_err = nullptr;       // sticky device error bits
   uint64_t *d_live_count = nullptr;  // live_count, kept on the device for the searches

@@ -29,7 +29,7 @@ def check_dense_scores(gpu, ref, mag, live):
 
 
 def check_candidate_set(gpu_ids, ora_ids, ref_scores, mag, kq):
-    """Candidate sets (Alg. 7 line 1) equal except inside the tie band around
+    """Candidate sets (Alg. 7) equal except inside the tie band around
     the k'-th approximate score."""
     g = set(int(x) for x in np.asarray(gpu_ids)[:kq])
     o = set(int(x) for x in np.asarray(ora_ids)[:kq])

@@ -13,9 +13,9 @@ the documents checked are its candidates, the 500 documents just below the
 k'-th by the GPU's dense scores, and random documents; on them:
   * the GPU's fp32 scores are within 1e-5 of the score magnitude of FP64;
   * every candidate scores at least the k'-th best FP64 score, and every
-    checked non-candidate at most it, up to that tolerance (Alg. 7 line 1);
+    checked non-candidate at most it, up to that tolerance (Alg. 7);
   * the returned top-k are the best of the candidates by FP64 exact score,
-    ids equal except inside the tie band (Alg. 7 lines 2-4).
+    ids equal except inside the tie band (Alg. 7).
 """
 import numpy as np
 import pytest

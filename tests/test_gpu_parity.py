@@ -261,6 +261,63 @@ def test_delete_leaves_stale_column_and_reuse_overwrites():
         assert np.array_equal(gpu.inverted_list(j), ora.inverted_list(j))
 
 
+@pytest.mark.parametrize("h", [1, 2])
+def test_containers_around_the_bitmap_threshold(h):
+    """Per-tile posting counts of a coordinate on both sides of every plausible
+    array/bitmap switch (T/16, T/8, T/4 of a T-id tile, and T itself), with
+    mixed signs, tombstones in both kinds of container and a rebuild: lists
+    stay bit-exact and the Alg. 6 scores and searches match the oracle."""
+    T, n = 1024, 64
+    w = synth.scaled(synth.WORKLOADS["tiny"], 0, n=n, m=16, h=h)
+    targets = [T // 16 - 1, T // 16, T // 8 - 1, T // 8, T // 4 - 1, T // 4, T // 2, T, 1, 3]
+    n_docs = 2 * T + 300
+    rng = np.random.default_rng(40 + h)
+    dense = np.zeros((n_docs, n), bool)
+    for t0 in range(0, n_docs, T):
+        rows = min(T, n_docs - t0)
+        for c, cnt in enumerate(targets):
+            dense[t0 + rng.choice(rows, size=min(cnt, rows), replace=False), c] = True
+    dense[:, n - 1] = True                                   # no empty vector
+    extra = rng.random((n_docs, n)) < 0.02                   # sparse background
+    extra[:, : len(targets)] = False                         # exact counts there
+    dense |= extra
+    idx = [np.flatnonzero(r).astype(np.uint32) for r in dense]
+    indptr = np.concatenate([[0], np.cumsum([a.size for a in idx])]).astype(np.uint64)
+    indices = np.concatenate(idx)
+    values = rng.standard_normal(indices.size).astype(np.float32)
+    values[values == 0] = 0.5
+    docs = synth.CSR(indptr, indices, values)
+    gpu, ora = _pair(w, docs, tile_docs=T)
+    qrows = []
+    for _ in range(16):
+        c = np.sort(rng.choice(len(targets), size=6, replace=False)).astype(np.uint32)
+        c = np.concatenate([c, np.sort(rng.choice(np.arange(len(targets), n), 3, replace=False)).astype(np.uint32)])
+        qrows.append(np.sort(c))
+    qip = np.concatenate([[0], np.cumsum([r.size for r in qrows])]).astype(np.uint64)
+    qs = synth.CSR(qip, np.concatenate(qrows), rng.standard_normal(int(qip[-1])).astype(np.float32))
+
+    def check():
+        for j in range(n):
+            assert np.array_equal(gpu.inverted_list(j), ora.inverted_list(j)), j
+        s = gpu.scores(_ip(qs), _ix(qs), qs.values).cpu().numpy()
+        live = ora.live_mask()
+        for r in range(qs.rows):
+            qi, qv = qs.row(r)
+            ref, mag = ora.scores(qi, qv, with_magnitude=True)
+            parity.check_dense_scores(s[r][: ref.size], ref, mag, live)
+        _check_search(gpu, ora, qs, 10, 200)
+
+    check()
+    dele = rng.choice(n_docs, size=n_docs // 7, replace=False)
+    gpu.delete(dele.astype(np.int32))
+    ora.delete(dele.astype(np.uint32))
+    check()
+    new = synth.CSR(indptr[:401] - indptr[0], indices[: int(indptr[400])], -values[: int(indptr[400])])
+    g = gpu.insert(_ip(new), _ix(new), new.values).cpu().numpy().astype(np.uint32)
+    assert np.array_equal(g, ora.insert(new.indptr, new.indices, new.values))
+    check()
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_empty_and_degenerate_queries():

@@ -383,7 +383,7 @@ def test_fewer_live_docs_than_k_pads():
 
 
 def test_zero_entries_are_not_indexed():
-    """nz(x) holds the coordinates with x[j] != 0 (Alg. 5 line 1)."""
+    """nz(x) holds the coordinates with x[j] != 0 (Alg. 5)."""
     ix = oracle.OracleIndex(10, 4, 1, table=np.arange(10) % 4)
     ix.insert(*_csr([([1, 2, 5], [1.0, 0.0, -0.0])]))
     assert list(ix.inverted_list(1)) == [0]
