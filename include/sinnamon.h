@@ -114,8 +114,10 @@ int sinn_destroy(sinn_index *ix);
  * vectors also enter the store S).  indptr/indices/values: device CSR.
  * out_ids: device uint32[n_docs] receiving each vector's id: free ids in
  * ascending order first (Sec. 4.3 reuse), then fresh ids, in row order.
- * The whole batch is validated before anything changes (EINVAL).  Waits for
- * the stream before returning. */
+ * The whole batch is validated before anything changes (EINVAL), and every
+ * allocation the insert needs is made before anything changes: on ENOMEM the
+ * index holds the same vectors as before (its capacity may have grown).
+ * Waits for the stream before returning. */
 int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
                 const float *values, uint32_t n_docs, uint32_t *out_ids, void *stream);
 
@@ -192,7 +194,7 @@ int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint32_t *q_ind
 
 /* Wait for the stream, then return and clear the sticky device error
  * (SINN_OK if none; SINN_EINVAL for a malformed query; SINN_EDEVICE for an
- * internal kernel error). */
+ * internal kernel error or a bounded wait inside a kernel that ran out). */
 int sinn_sync(sinn_index *ix, void *stream);
 
 /* Fill *out with the counters above (host). */
@@ -207,6 +209,20 @@ int sinn_set_budget(sinn_index *ix, uint64_t postings);
 
 /* The current budget (0 = none); 0 for a NULL index. */
 uint64_t sinn_get_budget(sinn_index *ix);
+
+/* ---- Test hooks: failures made on the host, none of them faults a GPU. */
+
+/* Allocation fault injection (process-wide): after `after` more successful
+ * device or pinned-host allocations by the library, the next one fails as
+ * if memory were exhausted (the call making it returns SINN_ENOMEM); then
+ * injection is off again.  after < 0 turns it off.  Always SINN_OK. */
+int sinn_debug_fail_alloc(int64_t after);
+
+/* One block waits on an mbarrier with the bounded wait the tensor-core
+ * kernels use, for at most `spins` polls: nothing completes the barrier
+ * (arrive = 0) or the block completes it first (arrive = 1).  Waits for the
+ * stream; SINN_EDEVICE if the wait ran out, SINN_OK if it completed. */
+int sinn_debug_wait_probe(uint32_t spins, int arrive, void *stream);
 
 /* ---- Launch tuning (the paper has no counterpart: these are GPU launch
  * parameters; results do not depend on them beyond fp32 summation order) -- */
@@ -249,7 +265,9 @@ int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_in
 
 /* Per-phase device timing, for benchmarks.  Phases: 0 query preparation,
  * 1 scoring (Alg. 6), 2 top-k' selection (Alg. 7), 3 re-rank and
- * top-k (Alg. 7), 4 insert (Alg. 5), 5 delete (Sec. 4.3). */
+ * top-k (Alg. 7), 4 insert (Alg. 5), 5 delete (Sec. 4.3).  Each phase is
+ * also an NVTX range on the calling thread ("sinn score", ...), timing on
+ * or off, for profilers' timelines. */
 #define SINN_PHASES 6
 typedef struct sinn_timing {
   double ms[SINN_PHASES];        /* summed CUDA-event durations per phase */

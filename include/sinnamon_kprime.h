@@ -69,6 +69,12 @@ int sinn_mlp_grad(sinn_mlp *m, const float *X, const float *t, uint32_t B, float
 int sinn_mlp_train_step(sinn_mlp *m, const float *X, const float *t, uint32_t B, float tau,
                         float lr, float *loss_out, void *stream);
 
+/* Wait for the stream, then return and clear the network's device error:
+ * SINN_EDEVICE if a bounded wait in one of its tensor-core GEMMs (forward,
+ * gradient or training step) ran out since the last call, else SINN_OK.  In
+ * sinn_search_learned the same errors go to the index (sinn_sync). */
+int sinn_mlp_sync(sinn_mlp *m, void *stream);
+
 /* sinn_search with k'[q] = clamp(ceil(2^network(features(q))), k_prime_min,
  * k_prime_max); the network must have n_in = SINN_KP_FEATURES.  out_kprime
  * (device uint32[n_q], nullable) receives the k' used per query. */

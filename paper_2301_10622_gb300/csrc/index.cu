@@ -24,9 +24,12 @@
 //                               costs no more per posting than walking an
 //                               array.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "sinn_internal.cuh"
 
@@ -40,6 +43,47 @@ int sinn_check_cuda(cudaError_t e) {
   if (e == cudaSuccess) return SINN_OK;
   (void)cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? SINN_ENOMEM : SINN_ECUDA;
+}
+
+// Allocation fault injection: >= 0 counts down the allocations still to
+// succeed before one fails (then it is off again); -1 is off.
+static std::atomic<int64_t> g_fail_alloc{-1};
+
+static bool alloc_should_fail() {
+  int64_t v = g_fail_alloc.load();
+  while (v >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
+cudaError_t sinn_dev_malloc(void **p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t sinn_dev_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
+cudaError_t sinn_host_malloc(void **p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+extern "C" int sinn_debug_fail_alloc(int64_t after) {
+  g_fail_alloc.store(after < 0 ? -1 : after);
+  return SINN_OK;
 }
 
 // SplitMix64's output function (Steele, Lea, Flood, OOPSLA 2014).
@@ -445,7 +489,13 @@ static void tm_record(cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
+// Phases as NVTX ranges, so that a profiler's timeline shows them by name.
+static const char *const kPhaseNames[SINN_PHASES] = {"sinn query prep", "sinn score",
+                                                     "sinn select", "sinn rerank",
+                                                     "sinn insert", "sinn delete"};
+
 SinnPhase::SinnPhase(sinn_index *ix_, cudaStream_t s_, int ph) : ix(ix_), s(s_), phase(ph) {
+  nvtxRangePushA(ph >= 0 && ph < SINN_PHASES ? kPhaseNames[ph] : "sinn");
   if (ix->tm_on) {
     a = tm_event(ix);
     tm_record(a, s);
@@ -458,6 +508,7 @@ SinnPhase::~SinnPhase() {
     tm_record(b, s);
     ix->tm_spans.push_back({phase, a, b});
   }
+  nvtxRangePop();
 }
 
 extern "C" int sinn_timing_start(sinn_index *ix) {
@@ -540,7 +591,7 @@ int sinn_ensure_scratch(sinn_index *ix, size_t bytes) {
     ix->scratch = nullptr;
     ix->scratch_size = 0;
   }
-  CK(cudaMalloc(&ix->scratch, bytes));
+  CK(sinn_dev_malloc((void **)&ix->scratch, bytes));
   ix->scratch_size = bytes;
   return SINN_OK;
 }
@@ -554,7 +605,7 @@ static int ensure_iscratch(sinn_index *ix, size_t bytes) {
     ix->iscratch_size = 0;
   }
   size_t b = std::max(bytes, ix->iscratch_size * 3 / 2);
-  CK(cudaMalloc(&ix->iscratch, b));
+  CK(sinn_dev_malloc((void **)&ix->iscratch, b));
   ix->iscratch_size = b;
   return SINN_OK;
 }
@@ -568,7 +619,7 @@ int sinn_ensure_pinned(sinn_index *ix, size_t bytes) {
     ix->pinned_size = 0;
   }
   size_t b = std::max(bytes, ix->pinned_size * 3 / 2);
-  CK(cudaMallocHost(&ix->pinned, b));
+  CK(sinn_host_malloc((void **)&ix->pinned, b));
   ix->pinned_size = b;
   return SINN_OK;
 }
@@ -576,7 +627,7 @@ int sinn_ensure_pinned(sinn_index *ix, size_t bytes) {
 template <typename T>
 static int realloc_copy(T **p, uint64_t old_elems, uint64_t new_elems, bool zero_rest) {
   T *q = nullptr;
-  CK(cudaMalloc(&q, new_elems * sizeof(T)));
+  CK(sinn_dev_malloc((void **)&q, new_elems * sizeof(T)));
   if (zero_rest) CK(cudaMemset(q, 0, new_elems * sizeof(T)));
   if (*p && old_elems) CK(cudaMemcpy(q, *p, old_elems * sizeof(T), cudaMemcpyDeviceToDevice));
   if (*p) CK(cudaFree(*p));
@@ -584,7 +635,9 @@ static int realloc_copy(T **p, uint64_t old_elems, uint64_t new_elems, bool zero
   return SINN_OK;
 }
 
-// Grow id capacity to hold ids < need (rounded up to whole tiles).
+// Grow id capacity to hold ids < need (rounded up to whole tiles).  Every new
+// array is allocated before any is filled: if one allocation fails, the
+// others are freed and the index is left as it was (SINN_ENOMEM).
 static int grow_capacity(sinn_index *ix, uint64_t need) {
   if (need <= ix->cap) return SINN_OK;
   uint64_t nc = std::max<uint64_t>(ix->cap * 2, need);
@@ -593,25 +646,49 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   if (need > max_cap) return SINN_ENOMEM;
   nc = std::min(nc, max_cap);
   const uint64_t ot = ix->cap / ix->T, nt = nc / ix->T;
-  CK(cudaDeviceSynchronize());
-  // sketch planes: copy the m rows into the wider layout
+  const size_t e = ix->sk_elem;
   const int planes = (ix->flags & SINN_FLAG_NONNEG) ? 1 : 2;  // SINNAMON+: U only
-  for (int plane = 0; plane < planes; ++plane) {
-    void **pp = plane ? &ix->d_L : &ix->d_U;
-    void *q = nullptr;
-    const size_t e = ix->sk_elem;
-    CK(cudaMalloc(&q, (uint64_t)ix->m * nc * e));
-    if (*pp && ix->cap)
-      CK(cudaMemcpy2D(q, nc * e, *pp, ix->cap * e, ix->cap * e, ix->m, cudaMemcpyDeviceToDevice));
-    if (*pp) CK(cudaFree(*pp));
-    *pp = q;
+  struct Grow {
+    void **dst;       // the index's pointer
+    size_t elem;      // bytes per element
+    uint64_t o, n;    // old and new elements (rows of the sketch planes: per row)
+    bool plane;       // a sketch plane: m rows, re-strided
+    void *q;
+  };
+  Grow g[7] = {
+      {&ix->d_U, e, ix->cap, nc, true, nullptr},
+      {&ix->d_L, e, ix->cap, nc, true, nullptr},
+      {(void **)&ix->d_live, 4, ix->cap / 32, nc / 32, false, nullptr},
+      {(void **)&ix->d_fwd_off, 8, ix->cap, nc, false, nullptr},
+      {(void **)&ix->d_fwd_nnz, 4, ix->cap, nc, false, nullptr},
+      {(void **)&ix->d_tile_dir, sizeof(uint2), ot * ix->n, nt * ix->n, false, nullptr},
+      {(void **)&ix->d_tile_post, sizeof(uint16_t *), ot, nt, false, nullptr},
+  };
+  CK(cudaDeviceSynchronize());
+  for (int i = 0; i < 7; ++i) {
+    if (i == 1 && planes == 1) continue;
+    const size_t bytes = g[i].elem * g[i].n * (g[i].plane ? ix->m : 1);
+    const cudaError_t err = sinn_dev_malloc(&g[i].q, bytes);
+    if (err != cudaSuccess) {
+      for (int k = 0; k < i; ++k)
+        if (g[k].q) cudaFree(g[k].q);
+      return sinn_check_cuda(err);
+    }
   }
-  int st;
-  if ((st = realloc_copy(&ix->d_live, ix->cap / 32, nc / 32, true))) return st;
-  if ((st = realloc_copy(&ix->d_fwd_off, ix->cap, nc, true))) return st;
-  if ((st = realloc_copy(&ix->d_fwd_nnz, ix->cap, nc, true))) return st;
-  if ((st = realloc_copy(&ix->d_tile_dir, ot * ix->n, nt * ix->n, true))) return st;
-  if ((st = realloc_copy(&ix->d_tile_post, ot, nt, true))) return st;
+  for (int i = 0; i < 7; ++i) {
+    if (!g[i].q) continue;
+    void *old = *g[i].dst;
+    if (g[i].plane) {  // copy the m rows into the wider layout
+      if (old && g[i].o)
+        CK(cudaMemcpy2D(g[i].q, g[i].n * e, old, g[i].o * e, g[i].o * e, ix->m,
+                        cudaMemcpyDeviceToDevice));
+    } else {
+      CK(cudaMemset(g[i].q, 0, g[i].elem * g[i].n));
+      if (old && g[i].o) CK(cudaMemcpy(g[i].q, old, g[i].elem * g[i].o, cudaMemcpyDeviceToDevice));
+    }
+    if (old) CK(cudaFree(old));
+    *g[i].dst = g[i].q;
+  }
   ix->cap = nc;
   ix->shape_version++;
   ix->live.resize(nc, 0);
@@ -677,15 +754,15 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
     release(ix);
     return s;
   };
-  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_pi, tab.size() * sizeof(uint32_t))))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_pi, tab.size() * sizeof(uint32_t))))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemcpy(ix->d_pi, tab.data(), tab.size() * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice))))
     return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_err, sizeof(uint32_t) * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_err, sizeof(uint32_t) * 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_err, 0, sizeof(uint32_t) * 4)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_live_count, sizeof(uint64_t))))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_live_count, sizeof(uint64_t))))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_live_count, 0, sizeof(uint64_t))))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&ix->d_coord_len, (size_t)n * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_coord_len, (size_t)n * 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_coord_len, 0, (size_t)n * 4)))) return fail(st);
   uint64_t hint = std::max<uint64_t>(cfg->capacity_hint, T);
   if ((st = grow_capacity(ix, hint))) return fail(st);
@@ -740,35 +817,80 @@ extern "C" int sinn_sync(sinn_index *ix, void *stream) {
   return SINN_OK;
 }
 
-// Rebuild the postings of a group of tiles (sorted, unique) from the store.
-static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cudaStream_t s) {
+// Storage a tile's rebuild writes into: a new buffer of `cap` 16-bit words,
+// or (p == nullptr) the tile's own buffer, rebuilt in place.
+struct TileAlloc {
+  uint16_t *p;
+  uint64_t cap;
+};
+
+// Words a tile of `nnz` stored entries needs: containers never need more words
+// than postings; bitmaps sit on T/16-word boundaries counted from the end.
+static uint64_t tile_words(const sinn_index *ix, uint64_t nnz) {
   const uint64_t W16 = ix->T / 16;
-  std::vector<uint64_t> pcap(nb);
-  for (uint32_t i = 0; i < nb; ++i)
-    // containers never need more words than postings; bitmaps sit on T/16-word
-    // boundaries counted from the end
-    pcap[i] = std::max<uint64_t>((ix->tile_nnz[tiles[i]] + W16 - 1) / W16 * W16, W16);
-  // scratch: counts, tiles, storage pointers, storage sizes, lengths
-  const size_t o_cn = 0;
-  const size_t o_tl = o_cn + (size_t)nb * ix->n * 4;
-  const size_t o_pt = (o_tl + (size_t)nb * 4 + 15) / 16 * 16;
-  const size_t o_pc = o_pt + (size_t)nb * 8;
-  const size_t o_ln = o_pc + (size_t)nb * 8;
-  const size_t bytes = o_ln + (size_t)nb * 4;
-  int st = ensure_iscratch(ix, bytes);
+  return std::max<uint64_t>((nnz + W16 - 1) / W16 * W16, W16);
+}
+
+// Storage for the rebuild of tile t once it holds `nnz` entries: its own
+// buffer if that is large enough and not over twice too large, else a new one
+// with a quarter of room to grow.  Allocation failures return SINN_ENOMEM.
+static int tile_alloc(sinn_index *ix, uint32_t t, uint64_t nnz, cudaStream_t s, TileAlloc *out) {
+  const uint64_t W16 = ix->T / 16, need = tile_words(ix, nnz);
+  if (ix->tile_post[t] && ix->tile_post_cap[t] >= need && ix->tile_post_cap[t] <= 2 * need) {
+    *out = {nullptr, ix->tile_post_cap[t]};  // the rebuild reads only the store
+    return SINN_OK;
+  }
+  const uint64_t cap = need + need / 4 / W16 * W16;
+  out->cap = cap;
+  out->p = nullptr;
+  CK(sinn_dev_malloc_async((void **)&out->p, cap * sizeof(uint16_t), s));
+  return SINN_OK;
+}
+
+// Device scratch of a rebuild of nb tiles: counts, tiles, storage pointers,
+// storage sizes, lengths.
+struct RebuildLayout {
+  size_t o_cn, o_tl, o_pt, o_pc, o_ln, bytes;
+};
+static RebuildLayout rebuild_layout(const sinn_index *ix, uint32_t nb) {
+  RebuildLayout L;
+  L.o_cn = 0;
+  L.o_tl = L.o_cn + (size_t)nb * ix->n * 4;
+  L.o_pt = (L.o_tl + (size_t)nb * 4 + 15) / 16 * 16;
+  L.o_pc = L.o_pt + (size_t)nb * 8;
+  L.o_ln = L.o_pc + (size_t)nb * 8;
+  L.bytes = L.o_ln + (size_t)nb * 4;
+  return L;
+}
+
+// Tiles rebuilt per group: their per-coordinate counts fit 1 GiB of scratch.
+static uint32_t rebuild_group_tiles(const sinn_index *ix, size_t tiles) {
+  const uint64_t per = (uint64_t)ix->n * 4;
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (1ull << 30) / per));
+}
+
+// Rebuild the postings of a group of tiles (sorted, unique) from the store,
+// into the storage `pre` gives per tile (allocated here if pre is null).
+static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cudaStream_t s,
+                         const TileAlloc *pre) {
+  const RebuildLayout RL = rebuild_layout(ix, nb);
+  const size_t o_cn = RL.o_cn, o_tl = RL.o_tl, o_pt = RL.o_pt, o_pc = RL.o_pc, o_ln = RL.o_ln;
+  int st = ensure_iscratch(ix, RL.bytes);
   if (st) return st;
   std::vector<uint16_t *> newp(nb);
+  std::vector<uint64_t> pcap(nb);
   for (uint32_t i = 0; i < nb; ++i) {
     const uint32_t t = tiles[i];
-    if (ix->tile_post[t] && ix->tile_post_cap[t] >= pcap[i] &&
-        ix->tile_post_cap[t] <= 2 * pcap[i]) {
-      newp[i] = ix->tile_post[t];  // rebuilt in place: the rebuild reads only the store
-      pcap[i] = ix->tile_post_cap[t];
-    } else {
-      const uint64_t alloc = pcap[i] + pcap[i] / 4 / W16 * W16;  // room to grow
-      CK(cudaMallocAsync((void **)&newp[i], alloc * sizeof(uint16_t), s));
-      pcap[i] = alloc;
+    TileAlloc ta;
+    if (pre) {
+      ta = pre[i];
+    } else if ((st = tile_alloc(ix, t, ix->tile_nnz[t], s, &ta))) {
+      for (uint32_t k = 0; k < i; ++k)
+        if (newp[k] != ix->tile_post[tiles[k]]) cudaFreeAsync(newp[k], s);
+      return st;
     }
+    newp[i] = ta.p ? ta.p : ix->tile_post[t];
+    pcap[i] = ta.cap;
   }
   const size_t hb = (size_t)nb * (4 + 8 + 8 + 4);
   CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
@@ -825,15 +947,15 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
 }
 
 // Rebuild the postings of the given tiles (sorted, unique), in groups whose
-// per-coordinate counts fit 1 GiB of scratch.
-static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s) {
+// per-coordinate counts fit 1 GiB of scratch, into the storage `pre` gives
+// per tile (or allocated as they go if pre is null).
+static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s,
+                         const std::vector<TileAlloc> *pre) {
   if (tiles.empty()) return SINN_OK;
-  const uint64_t per = (uint64_t)ix->n * 4;
-  const uint32_t g = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>(tiles.size(), (1ull << 30) / per));
+  const uint32_t g = rebuild_group_tiles(ix, tiles.size());
   for (size_t g0 = 0; g0 < tiles.size(); g0 += g) {
     const uint32_t nb = (uint32_t)std::min<size_t>(g, tiles.size() - g0);
-    int st = rebuild_group(ix, tiles.data() + g0, nb, s);
+    int st = rebuild_group(ix, tiles.data() + g0, nb, s, pre ? pre->data() + g0 : nullptr);
     if (st) return st;
   }
   return SINN_OK;
@@ -875,6 +997,9 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   }
   // ids: smallest free first, then fresh
   std::vector<uint32_t> ids(n_docs);
+  std::vector<uint32_t> tiles;      // tiles the batch lands in (sorted)
+  std::vector<uint64_t> tile_add;   // entries the batch adds to each
+  std::vector<TileAlloc> pre;       // their rebuilds' storage
   const uint64_t n_free = ix->free_ids.size();
   if (ix->next_id + (n_docs > n_free ? n_docs - n_free : 0) > 0xFFFFFFFEull) return SINN_ENOMEM;
   uint64_t max_id = 0;
@@ -892,6 +1017,36 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
     }
     if ((st = grow_capacity(ix, max_id + 1))) return st;
     if ((st = grow_store(ix, ix->fwd_used + total))) return st;
+    // the rest of the insert's allocations, made before anything changes: on
+    // SINN_ENOMEM the index is as it was
+    std::vector<std::pair<uint32_t, uint64_t>> te(n_docs);  // (tile, entries)
+    for (uint32_t r = 0; r < n_docs; ++r) te[r] = {ids[r] >> ix->log2T, ip[r + 1] - ip[r]};
+    std::sort(te.begin(), te.end());
+    for (const auto &x : te) {
+      if (tiles.empty() || tiles.back() != x.first) {
+        tiles.push_back(x.first);
+        tile_add.push_back(0);
+      }
+      tile_add.back() += x.second;
+    }
+    const uint32_t gmax = std::min<uint32_t>(rebuild_group_tiles(ix, tiles.size()),
+                                             (uint32_t)tiles.size());
+    const size_t o_off0 = ((size_t)n_docs * 4 + 15) / 16 * 16;
+    if ((st = ensure_iscratch(ix, std::max(o_off0 + (size_t)n_docs * 8,
+                                           rebuild_layout(ix, gmax).bytes))))
+      return st;
+    if ((st = sinn_ensure_pinned(ix, std::max(ipb + (size_t)n_docs * 12 + 64,
+                                              (size_t)gmax * 24))))
+      return st;
+    pre.resize(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) {
+      if ((st = tile_alloc(ix, tiles[i], ix->tile_nnz[tiles[i]] + tile_add[i], s, &pre[i]))) {
+        for (size_t k = 0; k < i; ++k)
+          if (pre[k].p) cudaFreeAsync(pre[k].p, s);
+        cudaStreamSynchronize(s);
+        return st;
+      }
+    }
     ix->free_ids = fq;
     if ((nid + ix->T - 1) / ix->T != (ix->next_id + ix->T - 1) / ix->T) ix->shape_version++;
     ix->next_id = nid;
@@ -923,22 +1078,17 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   CK(cudaGetLastError());
   k_set_live<<<(n_docs + 255) / 256, 256, 0, s>>>(d_ids, n_docs, ix->d_live, 1);
   CK(cudaGetLastError());
-  std::vector<uint32_t> tiles;
-  tiles.reserve(n_docs);
   for (uint32_t r = 0; r < n_docs; ++r) {
     uint32_t id = ids[r];
     ix->live[id] = 1;
     ix->nnz[id] = (uint32_t)(ip[r + 1] - ip[r]);
     ix->tile_nnz[id >> ix->log2T] += ix->nnz[id];
     ix->live_count++;
-    tiles.push_back(id >> ix->log2T);
   }
   ix->launches++;
   k_store_u64<<<1, 1, 0, s>>>(ix->d_live_count, ix->live_count);
   CK(cudaGetLastError());
-  std::sort(tiles.begin(), tiles.end());
-  tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
-  if ((st = rebuild_tiles(ix, tiles, s))) return st;
+  if ((st = rebuild_tiles(ix, tiles, s, &pre))) return st;
   uint32_t bits = 0;
   if ((st = read_and_clear_err(ix, s, &bits))) return st;
   return bits ? SINN_EDEVICE : SINN_OK;

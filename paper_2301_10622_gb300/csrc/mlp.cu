@@ -42,6 +42,7 @@ struct GemmArgs {
   int64_t ldcb;
   const float *mask;        // nullable: multiply by (mask[m*ldm+n] > 0)
   int64_t ldm;
+  uint32_t *err;            // device error word: SINN_DERR_TIMEOUT if a wait ran out
 };
 
 // ---------------------------------------------------------------- GEMM
@@ -54,12 +55,11 @@ struct GemmArgs {
 // 128-column tensor-memory accumulator, committing to an mbarrier that the
 // CTA waits on before it overwrites the operands.  The epilogue reads the
 // accumulator with tcgen05.ld (warp w owns TMEM lanes = rows 32w..32w+31).
-// Every wait is bounded: on a timeout the CTA raises g_tc_timeouts, still
-// waits (bounded) for its MMAs and frees its tensor memory.
+// Every wait is bounded: on a timeout the CTA sets SINN_DERR_TIMEOUT in the
+// caller's error word, still waits (bounded) for its MMAs and frees its
+// tensor memory.
 constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
 constexpr uint32_t kTcSpin = 1u << 24;  // try_wait rounds before giving up
-
-__device__ unsigned int g_tc_timeouts;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -85,8 +85,9 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                               ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kTcSpin; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          uint32_t spins = kTcSpin) {
+  for (uint32_t it = 0; it < spins; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
     issued++;
     // the MMAs have read the operands before they are overwritten
     if (!mbar_wait(mb, phase)) {
-      if (tid == 0) atomicAdd(&g_tc_timeouts, 1u);
+      if (tid == 0) atomicOr(g.err, SINN_DERR_TIMEOUT);
       s_fail = 1;
     }
     phase ^= 1u;
@@ -209,6 +210,21 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"((uint32_t)TC_N)
                  : "memory");
+}
+
+// A bounded wait on an mbarrier that nothing completes (arrive = 0) or that
+// the block completes itself first (arrive = 1): the GEMM's timeout path,
+// run alone.  A wait that runs out sets SINN_DERR_TIMEOUT in *err.
+__global__ void k_wait_probe(uint32_t spins, int arrive, uint32_t *err) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t mb = smem_u32(&bar);
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mb)
+                 : "memory");
+  __syncthreads();
+  if (!mbar_wait(mb, 0u, spins) && threadIdx.x == 0) atomicOr(err, SINN_DERR_TIMEOUT);
 }
 
 void gemm(const GemmArgs &g, cudaStream_t s) {
@@ -418,6 +434,7 @@ struct sinn_mlp {
   float *d_m1 = nullptr, *d_m2 = nullptr;
   float *d_mean = nullptr, *d_istd = nullptr;
   __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2tb = nullptr;
+  uint32_t *d_err = nullptr;  // device error bits of sinn_mlp_forward / _grad / _train_step
   uint64_t steps = 0;
   // activations (grow-only)
   uint32_t cap = 0;
@@ -482,7 +499,7 @@ int ensure_acts(sinn_mlp *m, uint32_t B, Acts *a) {
       m->act = nullptr;
     }
     const uint32_t c = std::max<uint32_t>(B, 1024);
-    CK(cudaMalloc(&m->act, acts_bytes(m, c)));
+    CK(sinn_dev_malloc((void **)&m->act, acts_bytes(m, c)));
     m->cap = c;
   }
   carve_acts(m, m->act, m->cap, a);
@@ -502,7 +519,7 @@ int refresh_bf16(sinn_mlp *m, cudaStream_t s) {
 
 // Forward through the network for B rows of raw features X; leaves the
 // activations in a (needed by the backward pass).
-int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s) {
+int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s, uint32_t *err) {
   int st = refresh_bf16(m, s);
   if (st) return st;
   Views v = views(m, m->d_p);
@@ -514,7 +531,7 @@ int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s) {
   g.A = a.Xb; g.sam = m->kpad; g.sak = 1;
   g.B = m->W1b; g.sbn = m->kpad; g.sbk = 1;
   g.M = (int)B; g.N = (int)m->hid; g.K = (int)m->kpad; g.alpha = 1.0f;
-  g.bias = v.b1; g.relu = 0; g.C = a.Z1; g.ldc = m->hid; g.Cb = nullptr;
+  g.bias = v.b1; g.relu = 0; g.C = a.Z1; g.ldc = m->hid; g.Cb = nullptr; g.err = err;
   gemm(g, s);
   GemmArgs r = g;  // H1 (bf16) = relu(Z1)
   r.relu = 1; r.C = nullptr; r.Cb = a.H1b; r.ldcb = m->hid;
@@ -524,7 +541,7 @@ int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s) {
   g2.A = a.H1b; g2.sam = m->hid; g2.sak = 1;
   g2.B = m->W2b; g2.sbn = m->hid; g2.sbk = 1;
   g2.M = (int)B; g2.N = (int)m->hid; g2.K = (int)m->hid; g2.alpha = 1.0f;
-  g2.bias = v.b2; g2.relu = 1; g2.C = a.H2; g2.ldc = m->hid;
+  g2.bias = v.b2; g2.relu = 1; g2.C = a.H2; g2.ldc = m->hid; g2.err = err;
   gemm(g2, s);
   k_head<<<(B + 7) / 8, 256, 0, s>>>(a.H2, B, m->hid, v.w3, v.b3, a.y);
   CK(cudaGetLastError());
@@ -532,7 +549,8 @@ int forward(sinn_mlp *m, const float *X, uint32_t B, Acts &a, cudaStream_t s) {
 }
 
 // Gradients of the mean pinball loss into m->d_g.
-int backward(sinn_mlp *m, const float *t, uint32_t B, float tau, Acts &a, cudaStream_t s) {
+int backward(sinn_mlp *m, const float *t, uint32_t B, float tau, Acts &a, cudaStream_t s,
+             uint32_t *err) {
   Views v = views(m, m->d_p);
   Views gv = views(m, m->d_g);
   k_pinball<<<1, 1024, 0, s>>>(a.y, t, B, tau, a.dy, a.loss);
@@ -547,7 +565,7 @@ int backward(sinn_mlp *m, const float *t, uint32_t B, float tau, Acts &a, cudaSt
   g.A = a.dZ2b; g.sam = 1; g.sak = m->hid;       // A(n_out, r) = dZ2[r][n_out]
   g.B = a.H1b; g.sbn = 1; g.sbk = m->hid;        // B(n_in, r) = H1[r][n_in]
   g.M = (int)m->hid; g.N = (int)m->hid; g.K = (int)B; g.alpha = 1.0f;
-  g.C = gv.W2; g.ldc = m->hid;
+  g.C = gv.W2; g.ldc = m->hid; g.err = err;
   gemm(g, s);
   k_colsum<<<(m->hid + 7) / 8, dim3(32, 8), 0, s>>>(a.dZ2, nullptr, B, m->hid, gv.b2);
   // dH1 = dZ2 W2 (B x hid) masked by Z1 > 0 -> dZ1 ; B(n, k) = W2[k][n] = W2t[n][k]
@@ -556,14 +574,14 @@ int backward(sinn_mlp *m, const float *t, uint32_t B, float tau, Acts &a, cudaSt
   h.B = m->W2tb; h.sbn = m->hid; h.sbk = 1;
   h.M = (int)B; h.N = (int)m->hid; h.K = (int)m->hid; h.alpha = 1.0f;
   h.mask = a.Z1; h.ldm = m->hid;
-  h.C = a.dH1; h.ldc = m->hid; h.Cb = a.dZ1b; h.ldcb = m->hid;
+  h.C = a.dH1; h.ldc = m->hid; h.Cb = a.dZ1b; h.ldcb = m->hid; h.err = err;
   gemm(h, s);
   // dW1 = dZ1^T X (hid x nin) ; db1 = colsum dZ1
   GemmArgs w{};
   w.A = a.dZ1b; w.sam = 1; w.sak = m->hid;
   w.B = a.Xb; w.sbn = 1; w.sbk = m->kpad;
   w.M = (int)m->hid; w.N = (int)m->nin; w.K = (int)B; w.alpha = 1.0f;
-  w.C = gv.W1; w.ldc = m->nin;
+  w.C = gv.W1; w.ldc = m->nin; w.err = err;
   gemm(w, s);
   k_colsum<<<(m->hid + 7) / 8, dim3(32, 8), 0, s>>>(a.dH1, nullptr, B, m->hid, gv.b1);
   CK(cudaGetLastError());
@@ -609,15 +627,17 @@ extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, si
     return e;
   };
   const size_t pb = m->nparams * 4;
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_p, pb)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_g, pb)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_m1, pb)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_m2, pb)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_mean, n_in * 4)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->d_istd, n_in * 4)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->W1b, (size_t)hidden * m->kpad * 2)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->W2b, (size_t)hidden * hidden * 2)))) return fail(st);
-  if ((st = sinn_check_cuda(cudaMalloc(&m->W2tb, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_p, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_g, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_m1, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_m2, pb)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_mean, n_in * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_istd, n_in * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W1b, (size_t)hidden * m->kpad * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2b, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2tb, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_err, 4)))) return fail(st);
+  if ((st = sinn_check_cuda(cudaMemset(m->d_err, 0, 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemcpy(m->d_p, p.data(), pb, cudaMemcpyHostToDevice))))
     return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(m->d_g, 0, pb)))) return fail(st);
@@ -645,11 +665,39 @@ extern "C" int sinn_mlp_destroy(sinn_mlp *m) {
   cudaFree(m->W2b);
   cudaFree(m->W2tb);
   cudaFree(m->act);
+  cudaFree(m->d_err);
   delete m;
   return SINN_OK;
 }
 
 extern "C" uint64_t sinn_mlp_num_params(sinn_mlp *m) { return m ? m->nparams : 0; }
+
+extern "C" int sinn_mlp_sync(sinn_mlp *m, void *stream) {
+  if (!m) return SINN_EINVAL;
+  cudaSetDevice(m->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t bits = 0;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(&bits, m->d_err, 4, cudaMemcpyDeviceToHost));
+  if (bits) CK(cudaMemset(m->d_err, 0, 4));
+  return bits ? SINN_EDEVICE : SINN_OK;
+}
+
+extern "C" int sinn_debug_wait_probe(uint32_t spins, int arrive, void *stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *d = nullptr, bits = 0;
+  CK(sinn_dev_malloc((void **)&d, 4));
+  int st = sinn_check_cuda(cudaMemsetAsync(d, 0, 4, s));
+  if (!st) {
+    k_wait_probe<<<1, 32, 0, s>>>(spins, arrive ? 1 : 0, d);
+    st = sinn_check_cuda(cudaGetLastError());
+  }
+  if (!st) st = sinn_check_cuda(cudaMemcpyAsync(&bits, d, 4, cudaMemcpyDeviceToHost, s));
+  if (!st) st = sinn_check_cuda(cudaStreamSynchronize(s));
+  cudaFree(d);
+  if (st) return st;
+  return (bits & SINN_DERR_TIMEOUT) ? SINN_EDEVICE : SINN_OK;
+}
 
 extern "C" int sinn_mlp_params(sinn_mlp *m, float *host_out, int which) {
   if (!m || !host_out) return SINN_EINVAL;
@@ -687,7 +735,7 @@ extern "C" int sinn_mlp_forward(sinn_mlp *m, const float *X, uint32_t B, float *
   Acts a;
   int st = ensure_acts(m, B, &a);
   if (st) return st;
-  if ((st = forward(m, X, B, a, s))) return st;
+  if ((st = forward(m, X, B, a, s, m->d_err))) return st;
   CK(cudaMemcpyAsync(y, a.y, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
   return SINN_OK;
 }
@@ -700,8 +748,8 @@ extern "C" int sinn_mlp_grad(sinn_mlp *m, const float *X, const float *t, uint32
   Acts a;
   int st = ensure_acts(m, B, &a);
   if (st) return st;
-  if ((st = forward(m, X, B, a, s))) return st;
-  if ((st = backward(m, t, B, tau, a, s))) return st;
+  if ((st = forward(m, X, B, a, s, m->d_err))) return st;
+  if ((st = backward(m, t, B, tau, a, s, m->d_err))) return st;
   if (grad_out) CK(cudaMemcpyAsync(grad_out, m->d_g, m->nparams * 4, cudaMemcpyDeviceToDevice, s));
   if (loss_out) CK(cudaMemcpyAsync(loss_out, a.loss, 4, cudaMemcpyDeviceToDevice, s));
   return SINN_OK;
@@ -752,7 +800,7 @@ extern "C" int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *
   uint32_t *kp = (uint32_t *)a.dZ2;        // n_q
   if (m->hid < SINN_KP_FEATURES) return SINN_EINVAL;
   if ((st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream))) return st;
-  if ((st = forward(m, feat, n_q, a, s))) return st;
+  if ((st = forward(m, feat, n_q, a, s, ix->d_err))) return st;
   k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
   CK(cudaGetLastError());
   ix->launches += 8;
@@ -793,7 +841,7 @@ extern "C" int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m,
   int st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream);
   if (st) return st;
   if ((st = refresh_bf16(m, s))) return st;
-  if ((st = forward(m, feat, n_q, a, s))) return st;
+  if ((st = forward(m, feat, n_q, a, s, ix->d_err))) return st;
   k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
   CK(cudaGetLastError());
   if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));

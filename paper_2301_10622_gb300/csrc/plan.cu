@@ -143,7 +143,7 @@ extern "C" int sinn_plan_create(sinn_index *ix, sinn_mlp *mlp, const uint64_t *q
   int st = sinn_ctx_create(ix, scratch_bytes, &p->ctx);
   if (!st && mlp) {
     p->act_bytes = sinn_mlp_act_bytes(mlp, n_q);
-    if (cudaMalloc(&p->act, p->act_bytes) != cudaSuccess) {
+    if (sinn_dev_malloc((void **)&p->act, p->act_bytes) != cudaSuccess) {
       (void)cudaGetLastError();
       st = SINN_ENOMEM;
     }

@@ -1461,7 +1461,7 @@ extern "C" int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr,
       ix->hstage = nullptr;
       ix->hstage_size = 0;
     }
-    CK(cudaMalloc(&ix->hstage, need));
+    CK(sinn_dev_malloc((void **)&ix->hstage, need));
     ix->hstage_size = need;
   }
   char *p = (char *)ix->hstage;
@@ -1571,7 +1571,7 @@ extern "C" int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx 
   sinn_ctx *c = new (std::nothrow) sinn_ctx();
   if (!c) return SINN_ENOMEM;
   cudaSetDevice(ix->device);
-  if (cudaMalloc(&c->scratch, scratch_bytes) != cudaSuccess) {
+  if (sinn_dev_malloc((void **)&c->scratch, scratch_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete c;
     return SINN_ENOMEM;
@@ -1664,8 +1664,8 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   uint32_t *ids = nullptr;
   float *sc = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CK(cudaMalloc(&ids, (size_t)n_q * k * 4));
-  CK(cudaMalloc(&sc, (size_t)n_q * k * 4));
+  CK(sinn_dev_malloc((void **)&ids, (size_t)n_q * k * 4));
+  CK(sinn_dev_malloc((void **)&sc, (size_t)n_q * k * 4));
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   auto run = [&](float *ms) -> int {

@@ -30,6 +30,7 @@
 #define SINN_DERR_QUERY 1u     // malformed query
 #define SINN_DERR_INTERNAL 2u  // an internal capacity check failed
 #define SINN_DERR_INSERT 4u    // malformed insert batch (validation kernel)
+#define SINN_DERR_TIMEOUT 8u   // a bounded wait in a kernel ran out
 
 // ------------------------------------------------------------ index object
 struct sinn_index {
@@ -118,6 +119,11 @@ struct SinnPhase {
 };
 
 // host helpers shared across translation units
+// Every device and pinned-host allocation of the library goes through these,
+// so that a test can make the n-th next one fail (sinn_debug_fail_alloc).
+cudaError_t sinn_dev_malloc(void **p, size_t bytes);
+cudaError_t sinn_dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
+cudaError_t sinn_host_malloc(void **p, size_t bytes);
 int sinn_ensure_scratch(sinn_index *ix, size_t bytes);
 int sinn_ensure_pinned(sinn_index *ix, size_t bytes);
 int sinn_check_cuda(cudaError_t e);

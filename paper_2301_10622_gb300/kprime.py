@@ -111,6 +111,7 @@ def train(ix, queries, kp_labels, k: int = 10, tau: float = 0.9, epochs: int = 3
             tot += float(loss.item()) * idx.numel()
         if log:
             log(f"epoch {ep}: pinball loss {tot / n:.4f}")
+    mlp.sync()  # raises if a tensor-core GEMM's bounded wait ran out
     return mlp
 
 

@@ -34,12 +34,12 @@ EXPORTS = [
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
     "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
     "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
-    "sinn_set_budget", "sinn_get_budget",
+    "sinn_set_budget", "sinn_get_budget", "sinn_debug_fail_alloc", "sinn_debug_wait_probe",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
     "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned", "sinn_mlp_act_bytes",
-    "sinn_search_learned_ctx",
+    "sinn_search_learned_ctx", "sinn_mlp_sync",
     # sinnamon_plan.h
     "sinn_plan_create", "sinn_plan_run", "sinn_plan_recordings", "sinn_plan_destroy",
 ]
@@ -164,6 +164,9 @@ def load(build_if_missing: bool = False):
         "sinn_get_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_set_budget": ([vp, u64], C.c_int),
         "sinn_get_budget": ([vp], u64),
+        "sinn_debug_fail_alloc": ([C.c_int64], C.c_int),
+        "sinn_debug_wait_probe": ([u32, C.c_int, vp], C.c_int),
+        "sinn_mlp_sync": ([vp, vp], C.c_int),
         "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
                           C.c_int),
@@ -542,6 +545,22 @@ class MLP:
                                           _s(stream)), "sinn_mlp_train_step")
         return loss
 
+    def sync(self, stream=None):
+        """Waits for the stream; raises if a GEMM's bounded wait ran out."""
+        _check(load().sinn_mlp_sync(self._h, _s(stream)), "sinn_mlp_sync")
+
+
+def sinn_debug_fail_alloc(after: int):
+    """The library's allocation after `after` more successful ones fails
+    (SINN_ENOMEM from the call making it); after < 0 turns this off."""
+    _check(load().sinn_debug_fail_alloc(int(after)), "sinn_debug_fail_alloc")
+
+
+def sinn_debug_wait_probe(spins: int, arrive: bool, stream=None) -> int:
+    """Status of one bounded mbarrier wait of at most `spins` polls that
+    nothing completes (arrive False) or that completes (arrive True)."""
+    return int(load().sinn_debug_wait_probe(int(spins), 1 if arrive else 0, _s(stream)))
+
 
 # ------------------------------------------------------------- convenience
 
@@ -553,7 +572,8 @@ class Index:
         with torch.cuda.device(self.device):
             self._h = sinn_create_ex(n, m, h, **cfg)
         self.n, self.m, self.h = n, m, h
-        self.nonneg = bool(cfg.get("flags", 0) & SINN_FLAG_NONNEG)
+        self.flags = int(cfg.get("flags", 0))
+        self.nonneg = bool(self.flags & SINN_FLAG_NONNEG)
 
     def close(self):
         if getattr(self, "_h", None):

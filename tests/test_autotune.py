@@ -101,3 +101,23 @@ def test_tile_size_is_chosen_by_measurement():
     assert set(res) == {1024, 2048} and best in res
     assert all(r["ms"] > 0 for r in res.values())
     assert res[best]["ms"] == min(r["ms"] for r in res.values())
+
+
+
+def test_cached_autotune_measures_once_then_reuses(tmp_path):
+    """autotune_cached on a new key measures and stores the tuning; on the
+    same key it sets the stored tuning without measuring."""
+    from paper_2301_10622_gb300 import autotune
+    w = synth.scaled(synth.WORKLOADS["text"], 9000, n=6000)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=200)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=1024)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    path = str(tmp_path / "tunings.json")
+    msgs = []
+    t1 = autotune.autotune_cached(ix, qs, 10, 300, path, reps=1, log=msgs.append)
+    assert "measured" in msgs[-1]
+    ix.set_tuning(tiles_per_block=1, bound_every=1)
+    t2 = autotune.autotune_cached(ix, qs, 10, 300, path, reps=1, log=msgs.append)
+    assert "from cache" in msgs[-1] and t2 == t1
+    assert {f: ix.tuning()[f] for f in t1} == t1
+    ix.close()
