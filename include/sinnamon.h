@@ -51,6 +51,7 @@ extern "C" {
 #define SINN_ECUDA 4     /* a CUDA runtime call failed */
 #define SINN_EDEVICE 5   /* a kernel reported an error (see sinn_sync) */
 #define SINN_ESCRATCH 6  /* sinn_search_noalloc: one query needs more than its fixed scratch */
+#define SINN_EIO 7       /* sinn_save / sinn_load: file error, or not a saved index */
 
 typedef struct sinn_index sinn_index; /* opaque; owned by the library */
 
@@ -97,6 +98,8 @@ typedef struct sinn_stats {
   uint64_t bytes_store;    /* device bytes of the vector store */
   uint64_t bytes_scratch;  /* device bytes of search scratch currently held */
   uint32_t n, m, h, tile_docs;
+  uint32_t flags;          /* the index's SINN_FLAG_* bits */
+  uint32_t reserved;
 } sinn_stats_t;
 
 /* Create an empty index on the current CUDA device with default settings.
@@ -209,6 +212,19 @@ int sinn_set_budget(sinn_index *ix, uint64_t postings);
 
 /* The current budget (0 = none); 0 for a NULL index. */
 uint64_t sinn_get_budget(sinn_index *ix);
+
+/* Checkpoint: write the whole index (parameters, mapping table, sketch,
+ * lists, vector store, free ids, counters, tuning and budget) to the file at
+ * `path`, replacing it.  Waits for the device.  SINN_EIO if the file cannot
+ * be written.  The format is the library's own (little-endian, versioned). */
+int sinn_save(sinn_index *ix, const char *path);
+
+/* Resume: a new index on the current CUDA device holding exactly what
+ * sinn_save wrote: the same live vectors under the same ids, free ids,
+ * sketch, lists and store, so searches, inserts (ids included) and deletes
+ * behave as they would have on the saved index.  SINN_EIO for a missing,
+ * truncated or foreign file; *out is NULL on any error. */
+int sinn_load(const char *path, sinn_index **out);
 
 /* ---- Test hooks: failures made on the host, none of them faults a GPU. */
 

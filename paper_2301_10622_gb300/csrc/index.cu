@@ -121,11 +121,13 @@ __global__ void k_fwd_write(const uint64_t *__restrict__ indptr,
                             const float *__restrict__ values, uint32_t rows,
                             const uint32_t *__restrict__ ids, const uint64_t *__restrict__ offs,
                             uint2 *__restrict__ fwd, uint64_t *__restrict__ fwd_off,
-                            uint32_t *__restrict__ fwd_nnz, uint32_t *__restrict__ coord_len) {
+                            uint32_t *__restrict__ fwd_nnz, uint32_t *__restrict__ coord_len,
+                            uint64_t fwd_cap, uint64_t cap, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (w >= rows) return;
   const uint64_t s = indptr[w], e = indptr[w + 1], o = offs[w];
+  if (!SINN_IN_BOUNDS(o + (e - s) <= fwd_cap && ids[w] < cap, err)) return;
   for (uint64_t p = s + lane; p < e; p += 32) {
     const float v = values[p];
     fwd[o + (p - s)] = make_uint2(indices[p], __float_as_uint(v));
@@ -146,7 +148,7 @@ __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__
                          const float *__restrict__ values, uint32_t rows,
                          const uint32_t *__restrict__ ids, const uint32_t *__restrict__ pi,
                          uint32_t m, uint32_t h, uint64_t cap, uint32_t G, void *__restrict__ U,
-                         void *__restrict__ L, int bf16) {
+                         void *__restrict__ L, int bf16, uint32_t *err) {
   extern __shared__ uint32_t sk[];
   uint32_t *uk = sk;          // G*m
   uint32_t *lk = sk + G * m;  // G*m
@@ -168,6 +170,7 @@ __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__
       uint32_t c = indices[p];
       for (uint32_t o = 0; o < h; ++o) {
         uint32_t k = pi[(uint64_t)c * h + o];
+        if (!SINN_IN_BOUNDS(k < m, err)) continue;
         atomicMax(&uk[g * m + k], key);
         atomicMin(&lk[g * m + k], key);
       }
@@ -177,6 +180,7 @@ __global__ void k_sketch(const uint64_t *__restrict__ indptr, const uint32_t *__
   for (uint32_t t = threadIdx.x; t < g_cnt * m; t += blockDim.x) {
     uint32_t k = t / g_cnt, g = t % g_cnt;
     uint64_t id = ids[r0 + g];
+    if (!SINN_IN_BOUNDS(id < cap, err)) continue;
     const uint64_t at = (uint64_t)k * cap + id;
     const float u = sinn_key2f(uk[g * m + k]), l = sinn_key2f(lk[g * m + k]);
     if (bf16) {  // bounds stay bounds: U rounds up, L rounds down
@@ -246,6 +250,7 @@ struct RebuildArgs {
   uint32_t *cnt;              // n per entry: counts, then array cursors
   uint32_t *out_len;          // postings per entry
   uint32_t nb, n, T, log2T;
+  uint32_t *err;              // device error word (bounds-check builds)
 };
 
 __global__ void __launch_bounds__(256)
@@ -341,9 +346,11 @@ __global__ void __launch_bounds__(256)
       if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
       const uint2 de = dir[pr.x];
       if (de.y >= BMIN) {
-        atomicOr((uint32_t *)(post + de.x) + (d >> 5), 1u << (d & 31));
+        if (SINN_IN_BOUNDS((uint64_t)de.x + a.T / 16 <= a.post_cap[i], a.err))
+          atomicOr((uint32_t *)(post + de.x) + (d >> 5), 1u << (d & 31));
       } else {
-        post[atomicAdd(&cur[pr.x], 1u)] = (uint16_t)d;
+        const uint32_t at = atomicAdd(&cur[pr.x], 1u);
+        if (SINN_IN_BOUNDS(at < de.x + de.y && at < a.post_cap[i], a.err)) post[at] = (uint16_t)d;
       }
     }
   }
@@ -793,6 +800,7 @@ extern "C" const char *sinn_strerror(int code) {
     case SINN_ECUDA: return "CUDA runtime error";
     case SINN_EDEVICE: return "device-side error";
     case SINN_ESCRATCH: return "request needs more than the fixed no-allocation scratch";
+    case SINN_EIO: return "file could not be read or written, or is not a saved index";
     default: return "unknown error";
   }
 }
@@ -812,7 +820,7 @@ extern "C" int sinn_sync(sinn_index *ix, void *stream) {
   int st = read_and_clear_err(ix, s, &bits);
   if (st) return st;
   CK(cudaStreamSynchronize(s));
-  if (bits & SINN_DERR_INTERNAL) return SINN_EDEVICE;
+  if (bits & SINN_DERR_DEVICE) return SINN_EDEVICE;
   if (bits) return SINN_EINVAL;
   return SINN_OK;
 }
@@ -914,6 +922,7 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   a.n = ix->n;
   a.T = ix->T;
   a.log2T = ix->log2T;
+  a.err = ix->d_err;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   const uint64_t cap_blocks = (uint64_t)std::max(1, sms) * 32;
@@ -1069,12 +1078,12 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   ix->launches += 3;  // store, sketch, live bits (the tile rebuild counts itself)
   k_fwd_write<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, d_ids, d_off,
                                               ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz,
-                                              ix->d_coord_len);
+                                              ix->d_coord_len, ix->fwd_cap, ix->cap, ix->d_err);
   CK(cudaGetLastError());
   uint32_t G = std::max<uint32_t>(1, std::min<uint32_t>(32, 6144 / ix->m));
   k_sketch<<<(n_docs + G - 1) / G, 256, (size_t)2 * G * ix->m * 4, s>>>(
       indptr, indices, values, n_docs, d_ids, ix->d_pi, ix->m, ix->h, ix->cap, G, ix->d_U,
-      ix->d_L, ix->sk_elem == 2 ? 1 : 0);
+      ix->d_L, ix->sk_elem == 2 ? 1 : 0, ix->d_err);
   CK(cudaGetLastError());
   k_set_live<<<(n_docs + 255) / 256, 256, 0, s>>>(d_ids, n_docs, ix->d_live, 1);
   CK(cudaGetLastError());
@@ -1169,6 +1178,7 @@ extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   out->m = ix->m;
   out->h = ix->h;
   out->tile_docs = ix->T;
+  out->flags = ix->flags;
   return SINN_OK;
 }
 
@@ -1225,5 +1235,216 @@ extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out,
     }
   }
   *len = cnt;
+  return SINN_OK;
+}
+
+// ------------------------------------------------------------ save / load
+// A saved index is the index's whole state, device arrays copied through a
+// host buffer: a header (magic, version, parameters, counters, tuning), then
+// the mapping table, the sketch planes, the live bits, the store offsets,
+// counts and entries, the tile directory, the per-coordinate live counts, the
+// host mirror (live flags, counts, free ids, per-tile sizes) and each tile's
+// container storage.  Every array is preceded by its byte count, checked on
+// load.  Little-endian hosts only (x86-64 and aarch64 both are).
+namespace {
+
+constexpr char kMagic[8] = {'S', 'I', 'N', 'N', 'I', 'D', 'X', '1'};
+constexpr uint32_t kVersion = 1;
+
+struct SaveHeader {
+  char magic[8];
+  uint32_t version, n, m, h, T, flags, max_qnnz, sk_elem;
+  uint64_t seed, cap, next_id, live_count, fwd_used, fwd_cap, budget, scratch_budget, tombstones;
+  sinn_tuning tune;
+};
+
+constexpr size_t kChunk = 64ull << 20;  // host staging per copy
+
+struct File {
+  FILE *f = nullptr;
+  std::vector<char> buf;
+  ~File() {
+    if (f) fclose(f);
+  }
+  bool put(const void *p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
+  bool get(void *p, size_t n) { return n == 0 || fread(p, 1, n, f) == n; }
+};
+
+// One array: its byte count, then the bytes (from the device if dev).
+int put_array(File &F, const void *src, uint64_t bytes, bool dev) {
+  if (!F.put(&bytes, 8)) return SINN_EIO;
+  if (!dev) return F.put(src, bytes) ? SINN_OK : SINN_EIO;
+  for (uint64_t o = 0; o < bytes; o += kChunk) {
+    const size_t n = (size_t)std::min<uint64_t>(kChunk, bytes - o);
+    CK(cudaMemcpy(F.buf.data(), (const char *)src + o, n, cudaMemcpyDeviceToHost));
+    if (!F.put(F.buf.data(), n)) return SINN_EIO;
+  }
+  return SINN_OK;
+}
+
+// One array of exactly `bytes` bytes into dst (on the device if dev).
+int get_array(File &F, void *dst, uint64_t bytes, bool dev) {
+  uint64_t have = 0;
+  if (!F.get(&have, 8) || have != bytes) return SINN_EIO;
+  if (!dev) return F.get(dst, bytes) ? SINN_OK : SINN_EIO;
+  for (uint64_t o = 0; o < bytes; o += kChunk) {
+    const size_t n = (size_t)std::min<uint64_t>(kChunk, bytes - o);
+    if (!F.get(F.buf.data(), n)) return SINN_EIO;
+    CK(cudaMemcpy((char *)dst + o, F.buf.data(), n, cudaMemcpyHostToDevice));
+  }
+  return SINN_OK;
+}
+
+}  // namespace
+
+extern "C" int sinn_save(sinn_index *ix, const char *path) {
+  if (!ix || !path) return SINN_EINVAL;
+  cudaSetDevice(ix->device);
+  CK(cudaDeviceSynchronize());
+  File F;
+  F.f = fopen(path, "wb");
+  if (!F.f) return SINN_EIO;
+  F.buf.resize(kChunk);
+  SaveHeader hd{};
+  memcpy(hd.magic, kMagic, 8);
+  hd.version = kVersion;
+  hd.n = ix->n;
+  hd.m = ix->m;
+  hd.h = ix->h;
+  hd.T = ix->T;
+  hd.flags = ix->flags;
+  hd.max_qnnz = ix->max_qnnz;
+  hd.sk_elem = ix->sk_elem;
+  hd.seed = ix->seed;
+  hd.cap = ix->cap;
+  hd.next_id = ix->next_id;
+  hd.live_count = ix->live_count;
+  hd.fwd_used = ix->fwd_used;
+  hd.fwd_cap = ix->fwd_cap;
+  hd.budget = ix->budget;
+  hd.scratch_budget = ix->scratch_budget;
+  hd.tombstones = ix->tombstones;
+  hd.tune = ix->tune;
+  if (!F.put(&hd, sizeof hd)) return SINN_EIO;
+  const uint64_t cap = ix->cap, tiles = cap / ix->T, plane = (uint64_t)ix->m * cap * ix->sk_elem;
+  int st;
+  if ((st = put_array(F, ix->d_pi, (uint64_t)ix->n * ix->h * 4, true))) return st;
+  if ((st = put_array(F, ix->d_U, plane, true))) return st;
+  if ((st = put_array(F, ix->d_L, ix->d_L ? plane : 0, true))) return st;
+  if ((st = put_array(F, ix->d_live, cap / 32 * 4, true))) return st;
+  if ((st = put_array(F, ix->d_fwd_off, cap * 8, true))) return st;
+  if ((st = put_array(F, ix->d_fwd_nnz, cap * 4, true))) return st;
+  if ((st = put_array(F, ix->d_fwd, ix->fwd_used * 8, true))) return st;
+  if ((st = put_array(F, ix->d_tile_dir, tiles * ix->n * 8, true))) return st;
+  if ((st = put_array(F, ix->d_coord_len, (uint64_t)ix->n * 4, true))) return st;
+  if ((st = put_array(F, ix->live.data(), cap, false))) return st;
+  if ((st = put_array(F, ix->nnz.data(), cap * 4, false))) return st;
+  std::vector<uint32_t> free_ids;
+  for (auto q = ix->free_ids; !q.empty(); q.pop()) free_ids.push_back(q.top());
+  if ((st = put_array(F, free_ids.data(), free_ids.size() * 4, false))) return st;
+  if ((st = put_array(F, ix->tile_post_len.data(), tiles * 8, false))) return st;
+  if ((st = put_array(F, ix->tile_post_cap.data(), tiles * 8, false))) return st;
+  if ((st = put_array(F, ix->tile_nnz.data(), tiles * 8, false))) return st;
+  if ((st = put_array(F, ix->tile_tombs.data(), tiles * 8, false))) return st;
+  for (uint64_t t = 0; t < tiles; ++t)
+    if ((st = put_array(F, ix->tile_post[t], ix->tile_post[t] ? ix->tile_post_cap[t] * 2 : 0,
+                        true)))
+      return st;
+  if (fflush(F.f) != 0) return SINN_EIO;
+  return SINN_OK;
+}
+
+extern "C" int sinn_load(const char *path, sinn_index **out) {
+  if (!path || !out) return SINN_EINVAL;
+  *out = nullptr;
+  File F;
+  F.f = fopen(path, "rb");
+  if (!F.f) return SINN_EIO;
+  SaveHeader hd{};
+  if (!F.get(&hd, sizeof hd) || memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kVersion)
+    return SINN_EIO;
+  // parameters as sinn_create_ex accepts them, and counters that fit them
+  if (hd.n == 0 || hd.m == 0 || hd.h == 0 || hd.h > hd.m || hd.h > SINN_MAX_H || hd.m > 4096 ||
+      hd.T < 1024 || hd.T > 16384 || (hd.T & (hd.T - 1)) || hd.cap % hd.T || hd.cap == 0 ||
+      hd.cap > 65535ull * hd.T || hd.next_id > hd.cap || hd.live_count > hd.next_id ||
+      hd.fwd_used > hd.fwd_cap || hd.sk_elem != ((hd.flags & SINN_FLAG_BF16_SKETCH) ? 2u : 4u) ||
+      (hd.flags & ~(SINN_FLAG_NONNEG | SINN_FLAG_BF16_SKETCH)))
+    return SINN_EIO;
+  F.buf.resize(kChunk);
+  std::vector<uint32_t> table((uint64_t)hd.n * hd.h);
+  int st = get_array(F, table.data(), table.size() * 4, false);
+  if (st) return st;
+  for (uint32_t b : table)
+    if (b >= hd.m) return SINN_EIO;
+  sinn_config cfg{};
+  cfg.n = hd.n;
+  cfg.m = hd.m;
+  cfg.h = hd.h;
+  cfg.tile_docs = hd.T;
+  cfg.seed = hd.seed;
+  cfg.capacity_hint = hd.cap;
+  cfg.table = table.data();
+  cfg.max_query_nnz = hd.max_qnnz;
+  cfg.flags = hd.flags;
+  cfg.scratch_bytes = hd.scratch_budget;
+  sinn_index *ix = nullptr;
+  if ((st = sinn_create_ex(&cfg, &ix))) return st;
+  auto fail = [&](int e) {
+    release(ix);
+    return e;
+  };
+  if (ix->cap != hd.cap) return fail(SINN_EIO);
+  if ((st = grow_store(ix, std::max<uint64_t>(hd.fwd_cap, 1)))) return fail(st);
+  const uint64_t cap = hd.cap, tiles = cap / hd.T, plane = (uint64_t)hd.m * cap * hd.sk_elem;
+  if ((st = get_array(F, ix->d_U, plane, true))) return fail(st);
+  if ((st = get_array(F, ix->d_L, ix->d_L ? plane : 0, true))) return fail(st);
+  if ((st = get_array(F, ix->d_live, cap / 32 * 4, true))) return fail(st);
+  if ((st = get_array(F, ix->d_fwd_off, cap * 8, true))) return fail(st);
+  if ((st = get_array(F, ix->d_fwd_nnz, cap * 4, true))) return fail(st);
+  if ((st = get_array(F, ix->d_fwd, hd.fwd_used * 8, true))) return fail(st);
+  if ((st = get_array(F, ix->d_tile_dir, tiles * hd.n * 8, true))) return fail(st);
+  if ((st = get_array(F, ix->d_coord_len, (uint64_t)hd.n * 4, true))) return fail(st);
+  if ((st = get_array(F, ix->live.data(), cap, false))) return fail(st);
+  if ((st = get_array(F, ix->nnz.data(), cap * 4, false))) return fail(st);
+  uint64_t nfree = 0;
+  if (!F.get(&nfree, 8) || nfree % 4 || nfree / 4 > hd.next_id) return fail(SINN_EIO);
+  std::vector<uint32_t> free_ids(nfree / 4);
+  if (!F.get(free_ids.data(), nfree)) return fail(SINN_EIO);
+  for (uint32_t id : free_ids) {
+    if (id >= hd.next_id || ix->live[id]) return fail(SINN_EIO);
+    ix->free_ids.push(id);
+  }
+  if ((st = get_array(F, ix->tile_post_len.data(), tiles * 8, false))) return fail(st);
+  if ((st = get_array(F, ix->tile_post_cap.data(), tiles * 8, false))) return fail(st);
+  if ((st = get_array(F, ix->tile_nnz.data(), tiles * 8, false))) return fail(st);
+  if ((st = get_array(F, ix->tile_tombs.data(), tiles * 8, false))) return fail(st);
+  for (uint64_t t = 0; t < tiles; ++t) {
+    uint64_t bytes = 0;
+    if (!F.get(&bytes, 8)) return fail(SINN_EIO);
+    if (bytes == 0) {  // a tile without storage
+      ix->tile_post_cap[t] = 0;
+      continue;
+    }
+    if (bytes != ix->tile_post_cap[t] * 2) return fail(SINN_EIO);
+    uint16_t *p = nullptr;
+    if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&p, bytes)))) return fail(st);
+    ix->tile_post[t] = p;
+    for (uint64_t o = 0; o < bytes; o += kChunk) {
+      const size_t n = (size_t)std::min<uint64_t>(kChunk, bytes - o);
+      if (!F.get(F.buf.data(), n)) return fail(SINN_EIO);
+      CK(cudaMemcpy((char *)p + o, F.buf.data(), n, cudaMemcpyHostToDevice));
+    }
+  }
+  CK(cudaMemcpy(ix->d_tile_post, ix->tile_post.data(), tiles * sizeof(uint16_t *),
+                cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ix->d_live_count, &hd.live_count, 8, cudaMemcpyHostToDevice));
+  ix->next_id = hd.next_id;
+  ix->live_count = hd.live_count;
+  ix->fwd_used = hd.fwd_used;
+  ix->budget = hd.budget;
+  ix->tombstones = hd.tombstones;
+  if (sinn_set_tuning(ix, &hd.tune) != SINN_OK) return fail(SINN_EIO);
+  ix->shape_version++;
+  *out = ix;
   return SINN_OK;
 }

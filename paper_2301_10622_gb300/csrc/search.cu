@@ -195,6 +195,8 @@ struct ScoreArgs {
   uint32_t n, h, T, log2T, qmax, tiles;
   uint32_t bound_every;  // tiles between refreshes of the running bound
   uint32_t tpb;          // tiles per block of the batched kernel
+  uint32_t *err;         // sticky device error bits (bounds-check builds)
+  uint32_t m;            // sketch rows per plane (bounds-check builds)
 };
 
 // Lower-bound bin of the kq-th largest key from a (partial) histogram: the
@@ -393,7 +395,10 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           t_cnt[k] = de.y;
           t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
           t_v[k] = terms[i0 + k].v;
-          for (uint32_t o = 0; o < a.h; ++o) t_bin[k * a.h + o] = a.pi[(uint64_t)j * a.h + o];
+          for (uint32_t o = 0; o < a.h; ++o) {
+            const uint32_t bin = a.pi[(uint64_t)j * a.h + o];
+            t_bin[k * a.h + o] = SINN_IN_BOUNDS(bin < a.m, a.err) ? bin : 0u;
+          }
         }
         // the next tile's entries arrive while this tile is scored
         if (nbatch == 1 && t + 1 < t_end) dir_fetch(a, terms, nb, t + 1, s_dir[pb ^ 1u], lane);
@@ -500,6 +505,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           for (uint32_t u = 0; u < 4; ++u) {
             const uint32_t p = p0 + u * 32;
             d[u] = (u < nck && p < len) ? (uint32_t)__ldg(post + lo + p) : SINN_TOMB;
+            if (!(d[u] & SINN_TOMB) && !SINN_IN_BOUNDS(d[u] < T, a.err)) d[u] = SINN_TOMB;
           }
           float x[4];
 #pragma unroll
@@ -944,6 +950,7 @@ struct RerankArgs {
   const uint32_t *fwd_nnz;
   const uint2 *fwd;
   uint64_t cap;
+  uint64_t fwd_cap;  // entries of the vector store (bounds-check builds)
   uint32_t *err;
   uint32_t qmax, kpmax;
 };
@@ -998,7 +1005,8 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
       continue;
     }
     const uint64_t fo = a.fwd_off[id];
-    const uint32_t nz = a.fwd_nnz[id];
+    uint32_t nz = a.fwd_nnz[id];
+    if (!SINN_IN_BOUNDS(fo + nz <= a.fwd_cap, a.err)) nz = 0;
     float s = 0.0f;
     // four entries per lane in flight, then their look-ups; the sum keeps
     // the entries' order within each lane
@@ -1230,6 +1238,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   sa.tiles = (uint32_t)(span / ix->T);
   sa.bound_every = ix->tune.bound_every;
   sa.tpb = ix->tune.tiles_per_block;
+  sa.err = ix->d_err;
+  sa.m = ix->m;
   RerankArgs ra;
   ra.fwd_off = ix->d_fwd_off;
   ra.fwd_nnz = ix->d_fwd_nnz;
@@ -1237,6 +1247,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   ra.qmax = ix->max_qnnz;
   ra.kpmax = kpmax;
   ra.cap = ix->cap;
+  ra.fwd_cap = ix->fwd_cap;
   ra.err = ix->d_err;
   uint32_t tsz = 64;
   while (tsz < 2 * ix->max_qnnz) tsz <<= 1;

@@ -31,6 +31,19 @@
 #define SINN_DERR_INTERNAL 2u  // an internal capacity check failed
 #define SINN_DERR_INSERT 4u    // malformed insert batch (validation kernel)
 #define SINN_DERR_TIMEOUT 8u   // a bounded wait in a kernel ran out
+#define SINN_DERR_BOUNDS 16u   // a checked index was out of range (bounds-check builds)
+// bits that mean a kernel went wrong (SINN_EDEVICE), not a malformed input
+#define SINN_DERR_DEVICE (SINN_DERR_INTERNAL | SINN_DERR_TIMEOUT | SINN_DERR_BOUNDS)
+
+// Index checks compiled in with -DSINN_BOUNDS_CHECK (the library's stand-in
+// for a memory checker): a failed check sets SINN_DERR_BOUNDS in the error
+// word `err` and the caller skips the access.  Compiled out, the condition is
+// not evaluated and the check is true.
+#ifdef SINN_BOUNDS_CHECK
+#define SINN_IN_BOUNDS(cond, err) ((cond) ? true : (atomicOr((err), SINN_DERR_BOUNDS), false))
+#else
+#define SINN_IN_BOUNDS(cond, err) true
+#endif
 
 // ------------------------------------------------------------ index object
 struct sinn_index {

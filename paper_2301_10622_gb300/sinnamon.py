@@ -22,7 +22,8 @@ from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
-SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH = range(7)
+(SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH,
+ SINN_EIO) = range(8)
 SINN_FLAG_NONNEG = 1
 SINN_FLAG_BF16_SKETCH = 2
 
@@ -34,7 +35,8 @@ EXPORTS = [
     "sinn_scores", "sinn_candidates", "sinn_timing_start", "sinn_timing_stop",
     "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
     "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
-    "sinn_set_budget", "sinn_get_budget", "sinn_debug_fail_alloc", "sinn_debug_wait_probe",
+    "sinn_set_budget", "sinn_get_budget", "sinn_save", "sinn_load", "sinn_debug_fail_alloc",
+    "sinn_debug_wait_probe",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
@@ -62,7 +64,7 @@ class SinnStats(C.Structure):
                 ("bytes_lists", C.c_uint64), ("bytes_sketch", C.c_uint64),
                 ("bytes_store", C.c_uint64), ("bytes_scratch", C.c_uint64),
                 ("n", C.c_uint32), ("m", C.c_uint32), ("h", C.c_uint32),
-                ("tile_docs", C.c_uint32)]
+                ("tile_docs", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -165,6 +167,8 @@ def load(build_if_missing: bool = False):
         "sinn_set_budget": ([vp, u64], C.c_int),
         "sinn_get_budget": ([vp], u64),
         "sinn_debug_fail_alloc": ([C.c_int64], C.c_int),
+        "sinn_save": ([vp, C.c_char_p], C.c_int),
+        "sinn_load": ([C.c_char_p, C.POINTER(vp)], C.c_int),
         "sinn_debug_wait_probe": ([u32, C.c_int, vp], C.c_int),
         "sinn_mlp_sync": ([vp, vp], C.c_int),
         "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
@@ -690,6 +694,25 @@ class Index:
 
     def sync(self, stream=None):
         sinn_sync(self._h, stream)
+
+    def save(self, path: str):
+        """Checkpoint the whole index to `path` (sinn_save)."""
+        _check(load().sinn_save(self._h, os.fsencode(path)), "sinn_save")
+
+    @classmethod
+    def load(cls, path: str, device=None) -> "Index":
+        """An index resumed from a sinn_save file on `device` (sinn_load)."""
+        obj = cls.__new__(cls)
+        obj.device = torch.device(device or "cuda")
+        out = C.c_void_p()
+        with torch.cuda.device(obj.device):
+            _check(load().sinn_load(os.fsencode(path), C.byref(out)), "sinn_load")
+        obj._h = out
+        st = obj.stats()
+        obj.n, obj.m, obj.h = st["n"], st["m"], st["h"]
+        obj.flags = st["flags"]
+        obj.nonneg = bool(obj.flags & SINN_FLAG_NONNEG)
+        return obj
 
     def stats(self) -> dict:
         return sinn_stats(self._h)
