@@ -261,7 +261,10 @@ typedef struct sinn_tuning {
   uint32_t persistent_blocks_per_sm; /* 0 (default): one block per (query, tile group);
                                         1..4: that many resident blocks per SM take
                                         (query, tile group) items from a counter */
-  uint32_t reserved[1];      /* zero */
+  uint32_t array_walk;       /* how a tile's array-container postings are shared out:
+                                0 (default): each warp takes whole 32-posting chunks of
+                                one term; 1: the block's threads take consecutive
+                                postings across all terms (for thin lists) */
 } sinn_tuning;
 
 /* Current tuning of the index into *out (host). */

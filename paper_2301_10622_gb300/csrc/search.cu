@@ -331,7 +331,7 @@ __device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const QTerm *terms
 // every live id's key is written and counted (dense).  Counted keys go
 // straight to the query's global histogram; the bound is refreshed from it
 // once per block.
-template <bool EMIT, int H, typename S>
+template <bool EMIT, int H, typename S, bool WALK>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
@@ -393,7 +393,8 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           const uint2 de = nbatch == 1 ? s_dir[pb][k] : dir[j];
           t_start[k] = de.x;
           t_cnt[k] = de.y;
-          t_cp[k] = de.y >= BMIN ? 0u : (de.y + 31) >> 5;
+          // array terms' chunks of 32 postings (walk 0) or postings (walk 1)
+          t_cp[k] = de.y >= BMIN ? 0u : (WALK ? de.y : (de.y + 31) >> 5);
           t_v[k] = terms[i0 + k].v;
           for (uint32_t o = 0; o < a.h; ++o) {
             const uint32_t bin = a.pi[(uint64_t)j * a.h + o];
@@ -467,8 +468,51 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       }
       // array terms
       const uint32_t C = part[0];
-      const uint32_t c_beg = (uint32_t)((uint64_t)C * wid / NW);
-      const uint32_t c_end = (uint32_t)((uint64_t)C * (wid + 1) / NW);
+      if (WALK) {
+        // walk 1: the batch's array postings as one sequence, thread tid taking
+        // postings tid, tid + kScoreThreads, ... (4 per pass, loads in flight
+        // together); a posting's term is the last i with t_cp[i] <= p
+        for (uint32_t q0 = tid; q0 < C; q0 += 4 * kScoreThreads) {
+          uint32_t d[4], ti[4];
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t p = q0 + u * kScoreThreads;
+            d[u] = SINN_TOMB;
+            ti[u] = 0;
+            if (p < C) {
+              uint32_t i = 0, hi = nb;
+              while (hi - i > 1) {
+                const uint32_t mid = (i + hi) >> 1;
+                if (t_cp[mid] <= p) i = mid;
+                else hi = mid;
+              }
+              ti[u] = i;
+              d[u] = (uint32_t)__ldg(post + t_start[i] + (p - t_cp[i]));
+              if (!(d[u] & SINN_TOMB) && !SINN_IN_BOUNDS(d[u] < T, a.err)) d[u] = SINN_TOMB;
+            }
+          }
+          float x[4];
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u) {
+            x[u] = 0.0f;
+            if (d[u] & SINN_TOMB) continue;
+            const uint32_t k = ti[u];
+            const float v = t_v[k];
+            const bool pos = v > 0.0f;
+            const S *plane = (const S *)(pos ? a.U : a.L);
+            const S *row[HS];
+#pragma unroll
+            for (uint32_t o = 0; o < HS; ++o)
+              if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+            x[u] = v * decode<H, S>(row, a.h, pos, d[u]);
+          }
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u)
+            if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], x[u]);
+        }
+      }
+      const uint32_t c_beg = WALK ? 0u : (uint32_t)((uint64_t)C * wid / NW);
+      const uint32_t c_end = WALK ? 0u : (uint32_t)((uint64_t)C * (wid + 1) / NW);
       if (c_beg < c_end) {
         uint32_t i = 0, hi = nb;  // term of c_beg: last i with t_cp[i] <= c_beg
         while (hi - i > 1) {
@@ -578,17 +622,17 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
 }
 
 // Grid (query, group of tiles_per_block tiles), queries fastest.
-template <int H, typename S>
+template <int H, typename S, bool WALK>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Batch bt) {
   extern __shared__ uint32_t sm[];
   const uint32_t t0 = blockIdx.y * a.tpb;
-  score_tiles<true, H, S>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
+  score_tiles<true, H, S, WALK>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
 }
 
 // The same work as k_score_emit from a fixed grid of blocks: each block takes
 // (query, group) items from a counter in the same query-fastest order until
 // none is left.
-template <int H, typename S>
+template <int H, typename S, bool WALK>
 __global__ void __launch_bounds__(kScoreThreads, 4)
     k_score_emit_persistent(ScoreArgs a, Batch bt, uint32_t nb, unsigned long long *next) {
   extern __shared__ uint32_t sm[];
@@ -601,7 +645,7 @@ __global__ void __launch_bounds__(kScoreThreads, 4)
     __syncthreads();  // every thread has read the item before the next draw
     if (item >= total) break;
     const uint32_t b = (uint32_t)(item % nb), t0 = (uint32_t)(item / nb) * a.tpb;
-    score_tiles<true, H, S>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
+    score_tiles<true, H, S, WALK>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
   }
 }
 
@@ -612,7 +656,7 @@ __global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, B
   const uint32_t nf = *bt.nflag;
   for (uint64_t w = blockIdx.x; w < (uint64_t)nf * a.tiles; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / a.tiles], t = (uint32_t)(w % a.tiles);
-    score_tiles<false, H, S>(a, bt, b, t, t + 1, sm);
+    score_tiles<false, H, S, false>(a, bt, b, t, t + 1, sm);
     __syncthreads();
   }
 }
@@ -625,16 +669,20 @@ struct ScoreKernels {
   void (*persistent)(ScoreArgs, Batch, uint32_t, unsigned long long *);
 };
 
-template <typename S>
+template <typename S, bool WALK>
 ScoreKernels score_kernels_for(uint32_t h) {
-  if (h == 1) return {k_score_emit<1, S>, k_score_dense<1, S>, k_score_emit_persistent<1, S>};
-  if (h == 2) return {k_score_emit<2, S>, k_score_dense<2, S>, k_score_emit_persistent<2, S>};
-  return {k_score_emit<0, S>, k_score_dense<0, S>, k_score_emit_persistent<0, S>};
+  if (h == 1)
+    return {k_score_emit<1, S, WALK>, k_score_dense<1, S>, k_score_emit_persistent<1, S, WALK>};
+  if (h == 2)
+    return {k_score_emit<2, S, WALK>, k_score_dense<2, S>, k_score_emit_persistent<2, S, WALK>};
+  return {k_score_emit<0, S, WALK>, k_score_dense<0, S>, k_score_emit_persistent<0, S, WALK>};
 }
 
-// Sketch bins as fp32 or as bfloat16 bits.
-ScoreKernels score_kernels(uint32_t h, bool bf16) {
-  return bf16 ? score_kernels_for<uint16_t>(h) : score_kernels_for<float>(h);
+// Sketch bins as fp32 or as bfloat16 bits; array postings walked in per-term
+// chunks or spread over the block (the dense fallback always takes chunks).
+ScoreKernels score_kernels(uint32_t h, bool bf16, bool walk) {
+  if (bf16) return walk ? score_kernels_for<uint16_t, true>(h) : score_kernels_for<uint16_t, false>(h);
+  return walk ? score_kernels_for<float, true>(h) : score_kernels_for<float, false>(h);
 }
 
 // ------------------------------------------------------------------ select
@@ -1213,7 +1261,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   }
   Batch bt = views(fixed ? fixed->base : ix->scratch, L, (uint32_t)B);
   const size_t ssm = score_smem(ix);
-  const ScoreKernels sk = score_kernels(ix->h, ix->sk_elem == 2);
+  const ScoreKernels sk = score_kernels(ix->h, ix->sk_elem == 2, ix->tune.array_walk != 0);
   CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
   CK(cudaFuncSetAttribute(sk.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
@@ -1644,7 +1692,7 @@ static bool tuning_ok(const sinn_tuning &t) {
   return t.bound_every >= 1 && t.bound_every <= 64 && t.emit_min_batch >= 1 &&
          t.emit_min_batch <= 65535 && t.rerank_blocks <= 1024 &&
          t.dense_blocks_per_sm >= 1 && t.dense_blocks_per_sm <= 32 && t.tiles_per_block >= 1 &&
-         t.tiles_per_block <= 64 && t.persistent_blocks_per_sm <= 4;
+         t.tiles_per_block <= 64 && t.persistent_blocks_per_sm <= 4 && t.array_walk <= 1;
 }
 
 extern "C" int sinn_get_tuning(sinn_index *ix, sinn_tuning *out) {
@@ -1656,7 +1704,6 @@ extern "C" int sinn_get_tuning(sinn_index *ix, sinn_tuning *out) {
 extern "C" int sinn_set_tuning(sinn_index *ix, const sinn_tuning *t) {
   if (!ix || !t || !tuning_ok(*t)) return SINN_EINVAL;
   ix->tune = *t;
-  memset(ix->tune.reserved, 0, sizeof(ix->tune.reserved));
   ix->shape_version++;
   return SINN_OK;
 }
@@ -1705,6 +1752,7 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   };
   const Field fields[] = {
       {&sinn_tuning::max_batch, 6, {0, 256, 512, 1024, 2048, 4096}},
+      {&sinn_tuning::array_walk, 2, {0, 1}},
       {&sinn_tuning::tiles_per_block, 6, {1, 2, 4, 8, 16, 32}},
       {&sinn_tuning::persistent_blocks_per_sm, 3, {0, 2, 4}},
       {&sinn_tuning::bound_every, 6, {1, 2, 4, 8, 16, 32}},

@@ -60,8 +60,9 @@ struct sinn_index {
   // at about the same time, so the bound could not prune); batches as large
   // as the scratch allows; re-rank blocks per query sized to k' (about 64
   // candidates each); 4 dense blocks per SM; 4 tiles per block of the
-  // batched scoring kernel, one block per item.
-  sinn_tuning tune{4, 32, 0, 0, 4, 4, 0, {0}};
+  // batched scoring kernel, one block per item; array postings in per-term
+  // chunks.
+  sinn_tuning tune{4, 32, 0, 0, 4, 4, 0, 0};
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings

@@ -83,9 +83,10 @@ class SinnTuning(C.Structure):
     _fields_ = [("bound_every", C.c_uint32), ("emit_min_batch", C.c_uint32),
                 ("max_batch", C.c_uint32), ("rerank_blocks", C.c_uint32),
                 ("dense_blocks_per_sm", C.c_uint32), ("tiles_per_block", C.c_uint32),
-                ("persistent_blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32 * 1)]
+                ("persistent_blocks_per_sm", C.c_uint32), ("array_walk", C.c_uint32)]
     FIELDS = ["bound_every", "emit_min_batch", "max_batch", "rerank_blocks",
-              "dense_blocks_per_sm", "tiles_per_block", "persistent_blocks_per_sm"]
+              "dense_blocks_per_sm", "tiles_per_block", "persistent_blocks_per_sm",
+              "array_walk"]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f in self.FIELDS}

@@ -53,7 +53,9 @@ def _run(ix, q, kp=300):
     dict(dense_blocks_per_sm=32, emit_min_batch=500), dict(tiles_per_block=1),
     dict(tiles_per_block=3, bound_every=5), dict(tiles_per_block=64, bound_every=1),
     dict(persistent_blocks_per_sm=4), dict(persistent_blocks_per_sm=1, tiles_per_block=2,
-                                           max_batch=50)])
+                                           max_batch=50),
+    dict(array_walk=1), dict(array_walk=1, persistent_blocks_per_sm=2, tiles_per_block=3),
+    dict(array_walk=1, max_batch=20, emit_min_batch=64)])
 def test_every_tuning_gives_the_same_results(setup, fields):
     ix, q = setup
     base = ix.tuning()
@@ -71,7 +73,7 @@ def test_every_tuning_gives_the_same_results(setup, fields):
                                           ("dense_blocks_per_sm", 0),
                                           ("dense_blocks_per_sm", 33), ("tiles_per_block", 0),
                                           ("tiles_per_block", 65),
-                                          ("persistent_blocks_per_sm", 5)])
+                                          ("persistent_blocks_per_sm", 5), ("array_walk", 2)])
 def test_invalid_tuning_is_rejected(setup, field, value):
     ix, _ = setup
     before = ix.tuning()
@@ -121,3 +123,18 @@ def test_cached_autotune_measures_once_then_reuses(tmp_path):
     assert "from cache" in msgs[-1] and t2 == t1
     assert {f: ix.tuning()[f] for f in t1} == t1
     ix.close()
+
+
+@pytest.mark.parametrize("h,tile", [(2, 1024), (1, 2048), (3, 1024)])
+def test_spread_array_walk_matches_the_oracle(h, tile):
+    """array_walk = 1 (array postings spread over the block) on thin,
+    mixed-sign lists with h sketch rows: the search equals the oracle's, as
+    with per-term chunks."""
+    from tests.test_gpu_parity import _check_search, _pair
+    w = synth.scaled(synth.WORKLOADS["mixed"], 9000, n=20000, h=h)
+    docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=48)
+    gpu, ora = _pair(w, docs, tile_docs=tile)
+    gpu.set_tuning(array_walk=1)
+    _check_search(gpu, ora, qs, 10, 300)
+    gpu.set_tuning(array_walk=0)
+    _check_search(gpu, ora, qs, 10, 300)
