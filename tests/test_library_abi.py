@@ -53,3 +53,28 @@ def test_binding_loads_and_names_match(lib_path):
 def test_library_targets_sm103a(lib_path):
     from paper_2301_10622_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_bounds_checked_build_exports_the_same_boundary(lib_path):
+    """The -DSINN_BOUNDS_CHECK build (libsinnamon_bc.so) is the same library
+    with index checks compiled in: it builds for sm_103a and exports the same
+    declared symbols."""
+    from paper_2301_10622_gb300 import build
+    bc = build.build(bounds_check=True)
+    assert bc != lib_path and os.path.basename(bc) == "libsinnamon_bc.so"
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                             text=True, check=True).stdout
+        return {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert _declared() <= exported(bc)
+    assert {s for s in exported(bc) if s.startswith("sinn_")} == \
+        {s for s in exported(lib_path) if s.startswith("sinn_")}
+
+
+def test_status_codes_have_names():
+    from paper_2301_10622_gb300 import sinnamon
+    sinnamon.load()
+    names = [sinnamon.sinn_strerror(c) for c in range(sinnamon.SINN_EIO + 1)]
+    assert len(set(names)) == len(names) and "unknown error" not in names
+    assert sinnamon.sinn_strerror(99) == "unknown error"
