@@ -415,6 +415,9 @@ def run_ours(args):
         tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
                              k, kp, reps=2)
         log(f"autotuned in {time.time() - t0:.1f}s: {tuning}")
+    if args.tuning:  # fields set by hand, after (or instead of) the autotuner
+        ix.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1])
+                         for kv in args.tuning.split(",")})
     tuning = ix.tuning()
     # the step's search as one recorded CUDA graph, replayed every step
     plan = None
@@ -793,6 +796,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--no-graph", action="store_true", help="launch the search directly")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="launch tuning fields to set, e.g. array_walk=1,tiles_per_block=2")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rates", default="20000,2000,5000",
