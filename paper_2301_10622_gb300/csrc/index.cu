@@ -761,15 +761,19 @@ extern "C" int sinn_create_ex(const sinn_config *cfg, sinn_index **out) {
     release(ix);
     return s;
   };
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_pi, tab.size() * sizeof(uint32_t))))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_pi, tab.size() * sizeof(uint32_t)))))
+    return fail(st);
   if ((st = sinn_check_cuda(cudaMemcpy(ix->d_pi, tab.data(), tab.size() * sizeof(uint32_t),
                                        cudaMemcpyHostToDevice))))
     return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_err, sizeof(uint32_t) * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_err, sizeof(uint32_t) * 4))))
+    return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_err, 0, sizeof(uint32_t) * 4)))) return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_live_count, sizeof(uint64_t))))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_live_count, sizeof(uint64_t)))))
+    return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_live_count, 0, sizeof(uint64_t))))) return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_coord_len, (size_t)n * 4)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&ix->d_coord_len, (size_t)n * 4))))
+    return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(ix->d_coord_len, 0, (size_t)n * 4)))) return fail(st);
   uint64_t hint = std::max<uint64_t>(cfg->capacity_hint, T);
   if ((st = grow_capacity(ix, hint))) return fail(st);

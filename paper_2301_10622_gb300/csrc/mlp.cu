@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
 __global__ void k_wait_probe(uint32_t spins, int arrive, uint32_t *err) {
   __shared__ __align__(8) uint64_t bar;
   const uint32_t mb = smem_u32(&bar);
-  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
   __syncthreads();
   if (arrive && threadIdx.x == 0)
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mb)
@@ -633,9 +634,12 @@ extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, si
   if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_m2, pb)))) return fail(st);
   if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_mean, n_in * 4)))) return fail(st);
   if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_istd, n_in * 4)))) return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W1b, (size_t)hidden * m->kpad * 2)))) return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2b, (size_t)hidden * hidden * 2)))) return fail(st);
-  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2tb, (size_t)hidden * hidden * 2)))) return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W1b, (size_t)hidden * m->kpad * 2))))
+    return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2b, (size_t)hidden * hidden * 2))))
+    return fail(st);
+  if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->W2tb, (size_t)hidden * hidden * 2))))
+    return fail(st);
   if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&m->d_err, 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemset(m->d_err, 0, 4)))) return fail(st);
   if ((st = sinn_check_cuda(cudaMemcpy(m->d_p, p.data(), pb, cudaMemcpyHostToDevice))))

@@ -6,7 +6,8 @@
 //                resident at any time share the tiles' lists and sketch rows
 //                in L2: walks the query's lists inside each tile of T ids,
 //                decodes each posting from the sketch (least upper bound from
-//                U for q_j > 0, greatest lower bound from L for q_j < 0, Alg. 6) and accumulates q_j * x~ in shared memory.  Score
+//                U for q_j > 0, greatest lower bound from L for q_j < 0,
+//                Alg. 6) and accumulates q_j * x~ in shared memory.  Score
 //                keys at or above the query's running bound are counted in its
 //                4096-bin histogram (top 12 bits) and emitted as candidates;
 //                every few tiles a block turns the histogram into a new lower
