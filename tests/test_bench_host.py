@@ -1,0 +1,106 @@
+"""Host logic of bench.py (no GPU): the algorithmic byte count behind the
+roofline, the oracle's reconstruction of the streamed collection, the
+comment-insensitive source hash that ties a profile to the kernel it
+measured, the traffic scaling read from that profile, and the clock
+sampler's parsing."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bench  # noqa: E402
+from paper_2301_10622_gb300 import synth  # noqa: E402
+
+
+def _csr(rows):
+    ip = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.uint64)
+    idx = np.array([c for r in rows for c, _ in r], np.uint32)
+    val = np.array([v for r in rows for _, v in r], np.float32)
+    return synth.CSR(ip, idx, val)
+
+
+def test_algorithmic_bytes_by_hand():
+    w = synth.scaled(synth.WORKLOADS["tiny"], 3, n=5, m=4, h=2)
+    # |I[0]| = 2, |I[1]| = 1 (an explicit zero is not a posting), |I[3]| = 3
+    docs = _csr([[(0, 1.0), (3, 2.0)], [(0, -1.0), (1, 0.0), (3, 1.0)], [(1, 5.0), (3, 4.0)]])
+    qs = _csr([[(0, 1.0), (3, -2.0)], [(1, 0.0), (2, 1.0)], []])
+    cap, tiles = 4096, 1
+    per_q, P = bench.algorithmic_bytes(w, docs, qs, cap, tiles)
+    assert list(P) == [5, 0, 0]  # the zero-valued query term reads no list
+    fixed = 4 * cap + cap / 8
+    assert per_q[0] == 5 * (2 + 4 * 2) + fixed + 8 * tiles * 2
+    assert per_q[1] == 0 + fixed + 8 * tiles * 1
+    assert per_q[2] == fixed
+
+
+def test_reconstruct_matches_the_id_reuse_rule():
+    """Each step deletes ids and re-inserts as many vectors, which take the
+    freed ids in ascending order; the reconstruction equals doing that by
+    hand."""
+    w = synth.scaled(synth.WORKLOADS["tiny"], 40, n=50)
+    docs = synth.make_docs(w)
+    rng = np.random.default_rng(0)
+    dels, parts, rows = [], [], [list(zip(*docs.row(i))) for i in range(docs.rows)]
+    for s in range(3):
+        d = rng.choice(40, size=7, replace=False)
+        ins = synth.make_docs(w, n_docs=7, seed=100 + s)
+        dels.append(torch.from_numpy(d.astype(np.int32)))
+        parts.append((None, None, None, ins))
+        for slot, i in enumerate(np.sort(d)):
+            rows[i] = list(zip(*ins.row(slot)))
+    got = bench.reconstruct(docs, parts, dels, [0, 1, 2])
+    want = _csr(rows)
+    assert np.array_equal(got.indptr.astype(np.int64), want.indptr.astype(np.int64))
+    assert np.array_equal(got.indices, want.indices)
+    assert np.array_equal(got.values, want.values)
+    # only the executed steps count
+    first = bench.reconstruct(docs, parts, dels, [0])
+    assert not np.array_equal(first.indptr.astype(np.int64), got.indptr.astype(np.int64)) or \
+        not np.array_equal(first.values, got.values)
+
+
+def test_source_hash_ignores_comments_only(tmp_path):
+    a = tmp_path / "a.cu"
+    a.write_text("int f(int x) {\n  return x + 1;  // one more\n}\n/* block\n comment */\n")
+    h = bench.source_code_hash(str(a))
+    a.write_text("// header\nint f(int x) {\n\n  return x + 1;   \n}\n")
+    assert bench.source_code_hash(str(a)) == h
+    a.write_text("int f(int x) {\n  return x + 2;\n}\n")
+    assert bench.source_code_hash(str(a)) != h
+
+
+def test_measured_traffic_scales_and_checks_its_source(tmp_path, monkeypatch):
+    src = tmp_path / "paper_2301_10622_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "search.cu").write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    h = bench.source_code_hash(str(src / "search.cu"))
+    prof = tmp_path / "profiles" / "k_score_emit_text.md"
+    prof.write_text(f"source_code_sha256_16: {h}\ntraffic_bytes_per_launch: 1000000\n"
+                    "queries_per_launch: 100\ndocs_in_index: 5000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # 4 launches of 50 queries: half the queries per launch, half the bytes
+    assert bench.measured_traffic(4, 200, 5000) == pytest.approx(500000.0)
+    assert bench.measured_traffic(0, 200, 5000) is None
+    assert bench.measured_traffic(4, 200, 6000) is None          # another index size
+    (src / "search.cu").write_text("__global__ void k() { int x; }\n")
+    assert bench.measured_traffic(4, 200, 5000) is None          # the kernel changed
+    os.remove(prof)
+    assert bench.measured_traffic(4, 200, 5000) is None
+
+
+def test_clock_summary_reads_throttle_reasons():
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1399.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["0, 1400, 2070, 500, 0x0, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
