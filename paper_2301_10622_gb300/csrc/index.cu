@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Dynamic shared memory: T/32 words per warp.
+// Sorts each array container of the rebuilt tiles: up to 32 postings in
+// registers (a bitonic network), more through a T-bit bitmap in shared
+// memory.  Dynamic shared memory: T/32 words per warp.
 __global__ void __launch_bounds__(256)
     k_rb_sort(RebuildArgs a, const uint2 *__restrict__ tile_dir) {
   extern __shared__ uint32_t sm[];
@@ -370,6 +372,20 @@ __global__ void __launch_bounds__(256)
     const uint2 de = tile_dir[(uint64_t)a.tiles[i] * a.n + c];
     if (de.y < 2 || de.y >= BMIN) continue;  // warp-uniform
     uint16_t *seg = a.new_post[i] + de.x;
+    if (de.y <= 32) {
+      // one posting per lane, sorted by a bitonic network over the warp
+      // (empty lanes hold 0xFFFF, above every local id)
+      uint32_t d = lane < de.y ? (seg[lane] & 0x7FFFu) : 0xFFFFu;
+      for (uint32_t k = 2; k <= 32; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, d, j);
+          const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+          d = (lower == up) ? min(d, o) : max(d, o);
+        }
+      }
+      if (lane < de.y) seg[lane] = (uint16_t)d;
+      continue;
+    }
     for (uint32_t j = lane; j < words; j += 32) bm[j] = 0u;
     __syncwarp();
     for (uint32_t e = lane; e < de.y; e += 32) {
