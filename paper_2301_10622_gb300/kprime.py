@@ -49,35 +49,44 @@ def labels(ix: "sinnamon.Index", queries, k: int = 10, cap: int = 20000, keep: i
                                      qs.values, cap)
         ix.sync()
         nq = qs.rows
-        # candidates in approximate-rank order: score desc, id asc
-        cid64 = cid.to(torch.int64)
-        valid = torch.arange(cap, device=cid.device)[None, :] < cnt[:, None].to(torch.int64)
-        cs = torch.where(valid, cs, torch.full_like(cs, -float("inf")))
-        cid64 = torch.where(valid, cid64, torch.full_like(cid64, 1 << 40))
-        o1 = torch.argsort(cid64, dim=1, stable=True)
-        s1 = torch.gather(cs, 1, o1)
-        o2 = torch.argsort(-s1, dim=1, stable=True)
-        order = torch.gather(o1, 1, o2)
-        ranked_ids = torch.gather(cid64, 1, order)               # rank r -> id
-        tau = torch.where(cnt > 0, torch.gather(s1, 1, o2)[torch.arange(nq, device=cs.device), (cnt - 1).clamp(min=0)
-                                                             .to(torch.int64)],
-                          torch.zeros(nq, device=cs.device))
-        # rank of each exact top-k id among the candidates (1-based)
-        ids64 = ids.to(torch.int64)
-        match = ranked_ids[:, None, :] == ids64[:, :, None]      # nq x k x cap
-        has = match.any(dim=2)
-        rank = match.to(torch.int8).argmax(dim=2).to(torch.int64) + 1
-        rank = torch.where(has & (ids64 >= 0), rank, torch.full_like(rank, cap + 1))
-        kth = torch.sort(rank, dim=1).values[:, keep - 1]
-        tenth = sc[:, k - 1]
-        full = cnt.to(torch.int64) < cap                         # every live id is a candidate
-        cert = full | (tenth >= tau)
-        kp = torch.where(cert, kth.clamp(max=cap), torch.full_like(kth, cap))
+        kp, cert = labels_from(cid, cs, cnt, ids, sc, cap, k, keep)
         out_kp[a:a + nq] = kp.cpu().numpy()
         out_ok[a:a + nq] = cert.cpu().numpy()
-        out_ids[a:a + nq] = ids64.cpu().numpy()
-        del match
+        out_ids[a:a + nq] = ids.to(torch.int64).cpu().numpy()
     return out_kp, out_ok, out_ids
+
+
+def labels_from(cid, cs, cnt, ids, sc, cap: int, k: int = 10, keep: int = 9):
+    """Steps 2-3 above for a batch: from each query's cnt candidates (ids cid,
+    approximate scores cs, rows of length cap) and its exact top-k (ids, sc,
+    best first), the least k' with recall >= keep/k and whether the top-k is
+    certified exact.  Returns (k' int64[nq], certified bool[nq])."""
+    nq = cid.shape[0]
+    # candidates in approximate-rank order: score desc, id asc
+    cid64 = cid.to(torch.int64)
+    valid = torch.arange(cap, device=cid.device)[None, :] < cnt[:, None].to(torch.int64)
+    cs = torch.where(valid, cs, torch.full_like(cs, -float("inf")))
+    cid64 = torch.where(valid, cid64, torch.full_like(cid64, 1 << 40))
+    o1 = torch.argsort(cid64, dim=1, stable=True)
+    s1 = torch.gather(cs, 1, o1)
+    o2 = torch.argsort(-s1, dim=1, stable=True)
+    order = torch.gather(o1, 1, o2)
+    ranked_ids = torch.gather(cid64, 1, order)               # rank r -> id
+    tau = torch.where(cnt > 0, torch.gather(s1, 1, o2)[torch.arange(nq, device=cs.device),
+                                                       (cnt - 1).clamp(min=0).to(torch.int64)],
+                      torch.zeros(nq, device=cs.device))
+    # rank of each exact top-k id among the candidates (1-based)
+    ids64 = ids.to(torch.int64)
+    match = ranked_ids[:, None, :] == ids64[:, :, None]      # nq x k x cap
+    has = match.any(dim=2)
+    rank = match.to(torch.int8).argmax(dim=2).to(torch.int64) + 1
+    rank = torch.where(has & (ids64 >= 0), rank, torch.full_like(rank, cap + 1))
+    kth = torch.sort(rank, dim=1).values[:, keep - 1]
+    tenth = sc[:, k - 1]
+    full = cnt.to(torch.int64) < cap                         # every live id is a candidate
+    cert = full | (tenth >= tau)
+    kp = torch.where(cert, kth.clamp(max=cap), torch.full_like(kth, cap))
+    return kp, cert
 
 
 def features(ix, queries, batch: int = 8192) -> torch.Tensor:
