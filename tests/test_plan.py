@@ -90,7 +90,7 @@ def test_replay_follows_inserts_deletes_and_growth():
     ix = _index(w, docs, 20000)
     q = _dev(qs)
     rng = np.random.default_rng(4)
-    # one round of churn first: the append-only vector store doubles once
+    # one churn step first: the append-only vector store doubles once
     first = rng.choice(20000, 300, replace=False).astype(np.int32)
     ix.delete(first)
     part = docs.slice(20000, 20300)
