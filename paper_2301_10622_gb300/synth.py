@@ -7,10 +7,11 @@ Every collection is returned as CSR: ``indptr`` (uint64, rows+1), ``indices``
 (uint32, strictly increasing within a row) and ``values`` (float32).
 
 Distribution readings (the workload descriptions give only the family names):
-  * "lognormal (mean mu, sigma)" for a count: the distribution's mean is mu, so
-    the log-space location is ln(mu) - sigma^2/2; draws are rounded to the
-    nearest integer and clamped to [1, n].  When sigma is not given it is 0.5.
-  * "lognormal(0, s)" for values: log-space location 0, scale s.
+  * a lognormal count with mean mu and spread sigma: the distribution's mean
+    is mu, so the log-space location is ln(mu) - sigma^2/2; draws are rounded
+    to the nearest integer and clamped to [1, n].  When sigma is not given it
+    is 0.5.
+  * lognormal values with parameters (0, s): log-space location 0, scale s.
   * Zipf(s) coordinates: coordinate c (0-based) has weight 1/(c+1)^s; a vector's
     coordinates are drawn one after another without replacement (each draw is
     proportional to the weights of the coordinates not yet taken).
