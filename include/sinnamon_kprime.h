@@ -36,7 +36,8 @@ int sinn_kp_features(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q
 /* A network n_in -> hidden -> hidden -> 1 with ReLU, fp32 master weights
  * initialised from seed (uniform, fan-in scaled), bf16 tensor-core GEMMs with
  * fp32 accumulation.  Inputs are standardised with the normaliser (mean 0,
- * stdev 1 until set).  EINVAL for n_in = 0 or > 1024, hidden = 0 or > 4096. */
+ * stdev 1 until set).  EINVAL for n_in = 0 or > 1024, hidden = 0 or > 4096.
+ * *out is NULL after any error. */
 int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, sinn_mlp **out);
 int sinn_mlp_destroy(sinn_mlp *m);
 

@@ -603,8 +603,9 @@ uint64_t splitmix_next(uint64_t &s) {
 int sinn_mlp_refresh(sinn_mlp *m, cudaStream_t s) { return refresh_bf16(m, s); }
 
 extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, sinn_mlp **out) {
-  if (!out || n_in == 0 || hidden == 0 || hidden > 4096 || n_in > 1024) return SINN_EINVAL;
+  if (!out) return SINN_EINVAL;
   *out = nullptr;
+  if (n_in == 0 || hidden == 0 || hidden > 4096 || n_in > 1024) return SINN_EINVAL;
   sinn_mlp *m = new (std::nothrow) sinn_mlp();
   if (!m) return SINN_ENOMEM;
   cudaGetDevice(&m->device);
