@@ -166,9 +166,11 @@ int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q
  * fixed 64 MiB device array inside the library, present on every device that
  * loads it until the library is unloaded.  Queries are processed in groups
  * that fit it; SINN_ESCRATCH if even one query does not fit (one query needs
- * about 4 bytes per id slot of the index plus 1.6 MB).  The first call on a
- * device looks the array's address up, so make that first call before any
- * stream capture.  Every call on a device shares the array and overwrites
+ * about 4 bytes per id slot of the index plus 1.6 MB).  Each call looks the
+ * array's device address up in the current context (no allocation), except
+ * on a stream being captured, where it uses the address an earlier call on
+ * that device found: make the first call on a device before any stream
+ * capture (SINN_ECUDA otherwise).  Every call on a device shares the array and overwrites
  * what the last call left there: calls that overlap on the GPU (on different
  * streams, or for different indexes of the same device) race, so order them.
  * The call itself allocates nothing and records no timing events. */

@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -536,7 +537,7 @@ SinnPhase::~SinnPhase() {
 
 extern "C" int sinn_timing_start(sinn_index *ix) {
   if (!ix) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   for (auto &sp : ix->tm_spans) {
     ix->tm_pool.push_back(sp.a);
     ix->tm_pool.push_back(sp.b);
@@ -553,7 +554,7 @@ extern "C" int sinn_timing_start(sinn_index *ix) {
 
 extern "C" int sinn_timing_stop(sinn_index *ix, sinn_timing_t *out) {
   if (!ix || !out) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   memset(out, 0, sizeof(*out));
   ix->tm_on = false;
   for (auto &sp : ix->tm_spans) {
@@ -578,7 +579,7 @@ extern "C" int sinn_timing_stop(sinn_index *ix, sinn_timing_t *out) {
 
 static void release(sinn_index *ix) {
   if (!ix) return;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaDeviceSynchronize();
   for (uint16_t *p : ix->tile_post)
     if (p) cudaFree(p);
@@ -834,7 +835,7 @@ static int read_and_clear_err(sinn_index *ix, cudaStream_t s, uint32_t *bits) {
 
 extern "C" int sinn_sync(sinn_index *ix, void *stream) {
   if (!ix) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t bits = 0;
   int st = read_and_clear_err(ix, s, &bits);
@@ -996,7 +997,7 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   if (!ix) return SINN_EINVAL;
   if (n_docs == 0) return SINN_OK;
   if (!indptr || !out_ids) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   // host copy of the row pointers (sizes drive allocation)
@@ -1127,7 +1128,7 @@ extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, 
   if (!ix) return SINN_EINVAL;
   if (n_ids == 0) return SINN_OK;
   if (!ids) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
@@ -1204,7 +1205,7 @@ extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
 
 extern "C" int sinn_hash_table(sinn_index *ix, uint32_t *table) {
   if (!ix || !table) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   CK(cudaMemcpy(table, ix->d_pi, (size_t)ix->n * ix->h * 4, cudaMemcpyDeviceToHost));
   return SINN_OK;
 }
@@ -1213,7 +1214,7 @@ extern "C" int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t
                                    float *u_out, float *l_out, void *stream) {
   if (!ix || (n_ids && (!ids || !u_out)) || (l_out && !ix->d_L)) return SINN_EINVAL;
   if (n_ids == 0) return SINN_OK;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   uint64_t tot = (uint64_t)n_ids * ix->m;
   k_gather_columns<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ids, n_ids, ix->d_U, ix->d_L,
@@ -1227,7 +1228,7 @@ extern "C" int sinn_sketch_columns(sinn_index *ix, const uint32_t *ids, uint32_t
 extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out, uint64_t cap,
                                   uint64_t *len) {
   if (!ix || coord >= ix->n || !len || (cap && !out)) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   CK(cudaDeviceSynchronize());
   const uint64_t nt = ix->cap / ix->T;
   const uint32_t W16 = ix->T / 16;
@@ -1315,15 +1316,8 @@ int get_array(File &F, void *dst, uint64_t bytes, bool dev) {
   return SINN_OK;
 }
 
-}  // namespace
-
-extern "C" int sinn_save(sinn_index *ix, const char *path) {
-  if (!ix || !path) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
-  CK(cudaDeviceSynchronize());
-  File F;
-  F.f = fopen(path, "wb");
-  if (!F.f) return SINN_EIO;
+// Everything sinn_save writes after opening the file.
+int save_body(sinn_index *ix, File &F) {
   F.buf.resize(kChunk);
   SaveHeader hd{};
   memcpy(hd.magic, kMagic, 8);
@@ -1370,17 +1364,65 @@ extern "C" int sinn_save(sinn_index *ix, const char *path) {
     if ((st = put_array(F, ix->tile_post[t], ix->tile_post[t] ? ix->tile_post_cap[t] * 2 : 0,
                         true)))
       return st;
-  if (fflush(F.f) != 0) return SINN_EIO;
   return SINN_OK;
 }
 
-extern "C" int sinn_load(const char *path, sinn_index **out) {
-  if (!path || !out) return SINN_EINVAL;
-  *out = nullptr;
+}  // namespace
+
+extern "C" int sinn_save(sinn_index *ix, const char *path) {
+  if (!ix || !path) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  CK(cudaDeviceSynchronize());
+  // written to a temporary file beside the target and renamed over it only
+  // when every byte is on disk: an error part-way leaves the previous
+  // checkpoint as it was
+  const std::string tmp = std::string(path) + ".tmp";
   File F;
-  F.f = fopen(path, "rb");
+  F.f = fopen(tmp.c_str(), "wb");
   if (!F.f) return SINN_EIO;
+  const int st = save_body(ix, F);
+  const bool flushed = st == SINN_OK && fflush(F.f) == 0;
+  const bool closed = fclose(F.f) == 0;
+  F.f = nullptr;
+  if (st != SINN_OK || !flushed || !closed || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return st != SINN_OK ? st : SINN_EIO;
+  }
+  return SINN_OK;
+}
+
+namespace {
+
+// What sinn_load's first pass keeps: the header, every array the kernels
+// index through (checked), and where the value-only arrays sit in the file.
+struct LoadPlan {
   SaveHeader hd{};
+  std::vector<uint32_t> table, live_bits, fwd_nnz, coord_len, nnz, free_ids;
+  std::vector<uint64_t> fwd_off, post_len, post_cap, tile_nnz, tile_tombs;
+  std::vector<uint8_t> live;
+  std::vector<uint2> dir;
+  off_t at_U = 0, at_L = 0, at_fwd = 0;  // file offsets of those arrays' bytes
+  std::vector<off_t> at_post;            // per tile (0: no storage)
+};
+
+// The byte count of the next array, which must be `bytes`; then skip it and
+// note where its bytes begin.
+bool skip_array(File &F, uint64_t bytes, off_t *at) {
+  uint64_t have = 0;
+  if (!F.get(&have, 8) || have != bytes) return false;
+  *at = ftello(F.f);
+  return *at >= 0 && fseeko(F.f, (off_t)bytes, SEEK_CUR) == 0;
+}
+
+// First pass, on the host only: read the file and check it against the
+// invariants every saved index satisfies.  The sketch planes hold values
+// (never used as indices) and are only located.  Everything the kernels
+// index through -- live bits, store offsets, counts and coordinates, the tile
+// directory and the tile containers -- is checked here, so that a damaged or
+// foreign file is SINN_EIO before the device is touched rather than an
+// out-of-range access on the GPU.
+int load_check(File &F, LoadPlan &L) {
+  SaveHeader &hd = L.hd;
   if (!F.get(&hd, sizeof hd) || memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kVersion)
     return SINN_EIO;
   // parameters as sinn_create_ex accepts them, and counters that fit them
@@ -1391,11 +1433,148 @@ extern "C" int sinn_load(const char *path, sinn_index **out) {
       (hd.flags & ~(SINN_FLAG_NONNEG | SINN_FLAG_BF16_SKETCH)))
     return SINN_EIO;
   F.buf.resize(kChunk);
-  std::vector<uint32_t> table((uint64_t)hd.n * hd.h);
-  int st = get_array(F, table.data(), table.size() * 4, false);
+  const uint64_t cap = hd.cap, tiles = cap / hd.T, n = hd.n;
+  const uint64_t plane = (uint64_t)hd.m * cap * hd.sk_elem;
+  const bool has_L = !(hd.flags & SINN_FLAG_NONNEG);
+  L.table.resize(n * hd.h);
+  int st = get_array(F, L.table.data(), L.table.size() * 4, false);
   if (st) return st;
-  for (uint32_t b : table)
+  for (uint32_t b : L.table)
     if (b >= hd.m) return SINN_EIO;
+  if (!skip_array(F, plane, &L.at_U) || !skip_array(F, has_L ? plane : 0, &L.at_L))
+    return SINN_EIO;
+  L.live_bits.resize(cap / 32);
+  L.fwd_off.resize(cap);
+  L.fwd_nnz.resize(cap);
+  if ((st = get_array(F, L.live_bits.data(), cap / 32 * 4, false))) return st;
+  if ((st = get_array(F, L.fwd_off.data(), cap * 8, false))) return st;
+  if ((st = get_array(F, L.fwd_nnz.data(), cap * 4, false))) return st;
+  {  // the store's entries: every coordinate < n (each came from a validated insert)
+    uint64_t have = 0;
+    const uint64_t bytes = hd.fwd_used * 8;
+    if (!F.get(&have, 8) || have != bytes) return SINN_EIO;
+    L.at_fwd = ftello(F.f);
+    for (uint64_t o = 0; o < bytes; o += kChunk) {
+      const size_t nb = (size_t)std::min<uint64_t>(kChunk, bytes - o);
+      if (!F.get(F.buf.data(), nb)) return SINN_EIO;
+      const uint2 *e = (const uint2 *)F.buf.data();
+      for (size_t i = 0; i < nb / 8; ++i)
+        if (e[i].x >= n) return SINN_EIO;
+    }
+  }
+  L.dir.resize(tiles * n);
+  L.coord_len.resize(n);
+  L.live.resize(cap);
+  L.nnz.resize(cap);
+  if ((st = get_array(F, L.dir.data(), tiles * n * 8, false))) return st;
+  if ((st = get_array(F, L.coord_len.data(), n * 4, false))) return st;
+  if ((st = get_array(F, L.live.data(), cap, false))) return st;
+  if ((st = get_array(F, L.nnz.data(), cap * 4, false))) return st;
+  uint64_t nfree = 0;
+  if (!F.get(&nfree, 8) || nfree % 4 || nfree / 4 > hd.next_id) return SINN_EIO;
+  L.free_ids.resize(nfree / 4);
+  if (!F.get(L.free_ids.data(), nfree)) return SINN_EIO;
+  L.post_len.resize(tiles);
+  L.post_cap.resize(tiles);
+  L.tile_nnz.resize(tiles);
+  L.tile_tombs.resize(tiles);
+  if ((st = get_array(F, L.post_len.data(), tiles * 8, false))) return st;
+  if ((st = get_array(F, L.post_cap.data(), tiles * 8, false))) return st;
+  if ((st = get_array(F, L.tile_nnz.data(), tiles * 8, false))) return st;
+  if ((st = get_array(F, L.tile_tombs.data(), tiles * 8, false))) return st;
+  // live ids: host flags equal the device bits, only below next_id, as many
+  // as the header says; each live vector's entries lie inside the used store
+  // and its count is the host's; per tile, the entries of its live vectors
+  // are the host's running sum (it sizes the tile's storage on a rebuild)
+  uint64_t nlive = 0;
+  std::vector<uint64_t> tile_sum(tiles, 0);
+  for (uint64_t i = 0; i < cap; ++i) {
+    const uint8_t l = L.live[i];
+    const bool bit = (L.live_bits[i >> 5] >> (i & 31)) & 1u;
+    if (l > 1 || bit != (l == 1)) return SINN_EIO;
+    if (!l) continue;
+    if (i >= hd.next_id || L.fwd_nnz[i] != L.nnz[i] || L.fwd_off[i] > hd.fwd_used ||
+        L.fwd_nnz[i] > hd.fwd_used - L.fwd_off[i])
+      return SINN_EIO;
+    ++nlive;
+    tile_sum[i / hd.T] += L.fwd_nnz[i];
+  }
+  if (nlive != hd.live_count) return SINN_EIO;
+  for (uint64_t t = 0; t < tiles; ++t)
+    if (tile_sum[t] != L.tile_nnz[t]) return SINN_EIO;
+  // free ids: distinct, below next_id, not live; with the live ids they are
+  // every id handed out
+  {
+    std::vector<uint8_t> seen(hd.next_id, 0);
+    for (uint32_t id : L.free_ids) {
+      if (id >= hd.next_id || L.live[id] || seen[id]) return SINN_EIO;
+      seen[id] = 1;
+    }
+    if (L.free_ids.size() + hd.live_count != hd.next_id) return SINN_EIO;
+  }
+  // containers inside their tile's storage (arrays from the front, bitmaps
+  // on T/16-word boundaries from the back, read as 32-bit words); array
+  // entries are local ids < T
+  const uint32_t BMIN = hd.T >> SINN_BITMAP_SHIFT, W16 = hd.T / 16;
+  std::vector<uint16_t> words;
+  L.at_post.assign(tiles, 0);
+  for (uint64_t t = 0; t < tiles; ++t) {
+    uint64_t bytes = 0;
+    if (!F.get(&bytes, 8)) return SINN_EIO;
+    const uint2 *de = L.dir.data() + t * n;
+    if (bytes == 0) {  // a tile without storage holds no container
+      for (uint64_t j = 0; j < n; ++j)
+        if (de[j].y) return SINN_EIO;
+      if (L.post_len[t]) return SINN_EIO;
+      L.post_cap[t] = 0;
+      continue;
+    }
+    if (bytes != L.post_cap[t] * 2) return SINN_EIO;
+    L.at_post[t] = ftello(F.f);
+    words.resize(bytes / 2);
+    if (!F.get(words.data(), bytes)) return SINN_EIO;
+    const uint64_t wcap = L.post_cap[t];
+    for (uint64_t j = 0; j < n; ++j) {
+      const uint64_t start = de[j].x, cnt = de[j].y;
+      if (cnt == 0) continue;
+      if (cnt > hd.T) return SINN_EIO;
+      const uint64_t w = cnt >= BMIN ? W16 : cnt;
+      if (start > wcap || w > wcap - start) return SINN_EIO;
+      if (cnt >= BMIN && start % W16) return SINN_EIO;
+      if (cnt < BMIN)
+        for (uint64_t q = start; q < start + cnt; ++q)
+          if ((words[q] & 0x7FFFu) >= hd.T) return SINN_EIO;
+    }
+  }
+  return SINN_OK;
+}
+
+// One value-only array of `bytes` bytes at file offset `at`, to the device.
+int upload_from(File &F, off_t at, void *dst, uint64_t bytes) {
+  if (!bytes) return SINN_OK;
+  if (fseeko(F.f, at, SEEK_SET) != 0) return SINN_EIO;
+  for (uint64_t o = 0; o < bytes; o += kChunk) {
+    const size_t nb = (size_t)std::min<uint64_t>(kChunk, bytes - o);
+    if (!F.get(F.buf.data(), nb)) return SINN_EIO;
+    CK(cudaMemcpy((char *)dst + o, F.buf.data(), nb, cudaMemcpyHostToDevice));
+  }
+  return SINN_OK;
+}
+
+}  // namespace
+
+extern "C" int sinn_load(const char *path, sinn_index **out) {
+  if (!path || !out) return SINN_EINVAL;
+  *out = nullptr;
+  File F;
+  F.f = fopen(path, "rb");
+  if (!F.f) return SINN_EIO;
+  LoadPlan L;
+  int st = load_check(F, L);
+  if (st) return st;
+  const SaveHeader &hd = L.hd;
+  // second pass: an index of the same parameters, filled from the checked
+  // arrays and the value-only ones re-read from the file
   sinn_config cfg{};
   cfg.n = hd.n;
   cfg.m = hd.m;
@@ -1403,61 +1582,47 @@ extern "C" int sinn_load(const char *path, sinn_index **out) {
   cfg.tile_docs = hd.T;
   cfg.seed = hd.seed;
   cfg.capacity_hint = hd.cap;
-  cfg.table = table.data();
+  cfg.table = L.table.data();
   cfg.max_query_nnz = hd.max_qnnz;
   cfg.flags = hd.flags;
   cfg.scratch_bytes = hd.scratch_budget;
   sinn_index *ix = nullptr;
   if ((st = sinn_create_ex(&cfg, &ix))) return st;
+  SinnDevice dev_guard_(ix->device);
   auto fail = [&](int e) {
     release(ix);
     return e;
   };
+  auto up = [&](void *dst, const void *src, uint64_t bytes) {
+    return bytes ? sinn_check_cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice)) : SINN_OK;
+  };
   if (ix->cap != hd.cap) return fail(SINN_EIO);
   if ((st = grow_store(ix, std::max<uint64_t>(hd.fwd_cap, 1)))) return fail(st);
   const uint64_t cap = hd.cap, tiles = cap / hd.T, plane = (uint64_t)hd.m * cap * hd.sk_elem;
-  if ((st = get_array(F, ix->d_U, plane, true))) return fail(st);
-  if ((st = get_array(F, ix->d_L, ix->d_L ? plane : 0, true))) return fail(st);
-  if ((st = get_array(F, ix->d_live, cap / 32 * 4, true))) return fail(st);
-  if ((st = get_array(F, ix->d_fwd_off, cap * 8, true))) return fail(st);
-  if ((st = get_array(F, ix->d_fwd_nnz, cap * 4, true))) return fail(st);
-  if ((st = get_array(F, ix->d_fwd, hd.fwd_used * 8, true))) return fail(st);
-  if ((st = get_array(F, ix->d_tile_dir, tiles * hd.n * 8, true))) return fail(st);
-  if ((st = get_array(F, ix->d_coord_len, (uint64_t)hd.n * 4, true))) return fail(st);
-  if ((st = get_array(F, ix->live.data(), cap, false))) return fail(st);
-  if ((st = get_array(F, ix->nnz.data(), cap * 4, false))) return fail(st);
-  uint64_t nfree = 0;
-  if (!F.get(&nfree, 8) || nfree % 4 || nfree / 4 > hd.next_id) return fail(SINN_EIO);
-  std::vector<uint32_t> free_ids(nfree / 4);
-  if (!F.get(free_ids.data(), nfree)) return fail(SINN_EIO);
-  for (uint32_t id : free_ids) {
-    if (id >= hd.next_id || ix->live[id]) return fail(SINN_EIO);
-    ix->free_ids.push(id);
-  }
-  if ((st = get_array(F, ix->tile_post_len.data(), tiles * 8, false))) return fail(st);
-  if ((st = get_array(F, ix->tile_post_cap.data(), tiles * 8, false))) return fail(st);
-  if ((st = get_array(F, ix->tile_nnz.data(), tiles * 8, false))) return fail(st);
-  if ((st = get_array(F, ix->tile_tombs.data(), tiles * 8, false))) return fail(st);
+  if ((st = upload_from(F, L.at_U, ix->d_U, plane))) return fail(st);
+  if ((st = upload_from(F, L.at_L, ix->d_L, ix->d_L ? plane : 0))) return fail(st);
+  if ((st = upload_from(F, L.at_fwd, ix->d_fwd, hd.fwd_used * 8))) return fail(st);
   for (uint64_t t = 0; t < tiles; ++t) {
-    uint64_t bytes = 0;
-    if (!F.get(&bytes, 8)) return fail(SINN_EIO);
-    if (bytes == 0) {  // a tile without storage
-      ix->tile_post_cap[t] = 0;
-      continue;
-    }
-    if (bytes != ix->tile_post_cap[t] * 2) return fail(SINN_EIO);
+    if (!L.post_cap[t]) continue;
     uint16_t *p = nullptr;
-    if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&p, bytes)))) return fail(st);
+    if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&p, L.post_cap[t] * 2)))) return fail(st);
     ix->tile_post[t] = p;
-    for (uint64_t o = 0; o < bytes; o += kChunk) {
-      const size_t n = (size_t)std::min<uint64_t>(kChunk, bytes - o);
-      if (!F.get(F.buf.data(), n)) return fail(SINN_EIO);
-      CK(cudaMemcpy((char *)p + o, F.buf.data(), n, cudaMemcpyHostToDevice));
-    }
+    if ((st = upload_from(F, L.at_post[t], p, L.post_cap[t] * 2))) return fail(st);
   }
-  CK(cudaMemcpy(ix->d_tile_post, ix->tile_post.data(), tiles * sizeof(uint16_t *),
-                cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ix->d_live_count, &hd.live_count, 8, cudaMemcpyHostToDevice));
+  if ((st = up(ix->d_live, L.live_bits.data(), cap / 32 * 4))) return fail(st);
+  if ((st = up(ix->d_fwd_off, L.fwd_off.data(), cap * 8))) return fail(st);
+  if ((st = up(ix->d_fwd_nnz, L.fwd_nnz.data(), cap * 4))) return fail(st);
+  if ((st = up(ix->d_tile_dir, L.dir.data(), tiles * hd.n * 8))) return fail(st);
+  if ((st = up(ix->d_coord_len, L.coord_len.data(), (uint64_t)hd.n * 4))) return fail(st);
+  if ((st = up(ix->d_tile_post, ix->tile_post.data(), tiles * sizeof(uint16_t *)))) return fail(st);
+  if ((st = up(ix->d_live_count, &hd.live_count, 8))) return fail(st);
+  ix->live = L.live;
+  ix->nnz = L.nnz;
+  for (uint32_t id : L.free_ids) ix->free_ids.push(id);
+  ix->tile_post_len = L.post_len;
+  ix->tile_post_cap = L.post_cap;
+  ix->tile_nnz = L.tile_nnz;
+  ix->tile_tombs = L.tile_tombs;
   ix->next_id = hd.next_id;
   ix->live_count = hd.live_count;
   ix->fwd_used = hd.fwd_used;

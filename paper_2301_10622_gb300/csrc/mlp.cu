@@ -658,7 +658,7 @@ extern "C" int sinn_mlp_create(uint32_t n_in, uint32_t hidden, uint64_t seed, si
 
 extern "C" int sinn_mlp_destroy(sinn_mlp *m) {
   if (!m) return SINN_OK;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   cudaDeviceSynchronize();
   cudaFree(m->d_p);
   cudaFree(m->d_g);
@@ -679,7 +679,7 @@ extern "C" uint64_t sinn_mlp_num_params(sinn_mlp *m) { return m ? m->nparams : 0
 
 extern "C" int sinn_mlp_sync(sinn_mlp *m, void *stream) {
   if (!m) return SINN_EINVAL;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t bits = 0;
   CK(cudaStreamSynchronize(s));
@@ -706,7 +706,7 @@ extern "C" int sinn_debug_wait_probe(uint32_t spins, int arrive, void *stream) {
 
 extern "C" int sinn_mlp_params(sinn_mlp *m, float *host_out, int which) {
   if (!m || !host_out) return SINN_EINVAL;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   const float *src = which == 0 ? m->d_p : m->d_g;
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(host_out, src, m->nparams * 4, cudaMemcpyDeviceToHost));
@@ -715,7 +715,7 @@ extern "C" int sinn_mlp_params(sinn_mlp *m, float *host_out, int which) {
 
 extern "C" int sinn_mlp_set_params(sinn_mlp *m, const float *host_in) {
   if (!m || !host_in) return SINN_EINVAL;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(m->d_p, host_in, m->nparams * 4, cudaMemcpyHostToDevice));
   m->bf16_fresh = false;
@@ -726,7 +726,7 @@ extern "C" int sinn_mlp_set_normalizer(sinn_mlp *m, const float *mean, const flo
   if (!m || !mean || !stdev) return SINN_EINVAL;
   std::vector<float> is(m->nin);
   for (uint32_t i = 0; i < m->nin; ++i) is[i] = stdev[i] > 0.0f ? 1.0f / stdev[i] : 1.0f;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   CK(cudaMemcpy(m->d_mean, mean, m->nin * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->d_istd, is.data(), m->nin * 4, cudaMemcpyHostToDevice));
   return SINN_OK;
@@ -735,7 +735,7 @@ extern "C" int sinn_mlp_set_normalizer(sinn_mlp *m, const float *mean, const flo
 extern "C" int sinn_mlp_forward(sinn_mlp *m, const float *X, uint32_t B, float *y, void *stream) {
   if (!m || (B && (!X || !y))) return SINN_EINVAL;
   if (B == 0) return SINN_OK;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   Acts a;
   int st = ensure_acts(m, B, &a);
@@ -748,7 +748,7 @@ extern "C" int sinn_mlp_forward(sinn_mlp *m, const float *X, uint32_t B, float *
 extern "C" int sinn_mlp_grad(sinn_mlp *m, const float *X, const float *t, uint32_t B, float tau,
                              float *grad_out, float *loss_out, void *stream) {
   if (!m || B == 0 || !X || !t || tau <= 0.0f || tau >= 1.0f) return SINN_EINVAL;
-  cudaSetDevice(m->device);
+  SinnDevice dev_guard_(m->device);
   cudaStream_t s = (cudaStream_t)stream;
   Acts a;
   int st = ensure_acts(m, B, &a);
@@ -779,7 +779,7 @@ extern "C" int sinn_kp_features(sinn_index *ix, const uint64_t *q_indptr, const 
                                 const float *q_values, uint32_t n_q, float *out, void *stream) {
   if (!ix || (n_q && (!q_indptr || !out))) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   k_features<<<n_q, 256, 0, (cudaStream_t)stream>>>(q_indptr, q_indices, q_values, ix->n,
                                                     ix->d_tile_dir, (uint32_t)(ix->cap / ix->T),
                                                     out);
@@ -795,7 +795,7 @@ extern "C" int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *
   if (!ix || !m || m->nin != SINN_KP_FEATURES) return SINN_EINVAL;
   if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   // features, prediction and k' live in the model's activation buffer tail
   Acts a;
@@ -836,7 +836,7 @@ extern "C" int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m,
   if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (act_bytes < sinn_mlp_act_bytes(m, n_q)) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   Acts a;
   carve_acts(m, act, n_q, &a);

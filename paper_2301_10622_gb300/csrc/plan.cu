@@ -124,7 +124,7 @@ extern "C" int sinn_plan_create(sinn_index *ix, sinn_mlp *mlp, const uint64_t *q
   if (k == 0 || k > SINN_MAX_K || k_prime_max < k) return SINN_EINVAL;
   if (mlp && (k_prime_min < k || k_prime_max < k_prime_min)) return SINN_EINVAL;
   *out = nullptr;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   sinn_plan *p = new (std::nothrow) sinn_plan();
   if (!p) return SINN_ENOMEM;
   p->ix = ix;
@@ -163,7 +163,7 @@ extern "C" int sinn_plan_create(sinn_index *ix, sinn_mlp *mlp, const uint64_t *q
 extern "C" int sinn_plan_run(sinn_plan *p, void *stream) {
   if (!p) return SINN_EINVAL;
   sinn_index *ix = p->ix;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   if (!p->exec || p->version != ix->shape_version) {
@@ -196,7 +196,7 @@ extern "C" uint64_t sinn_plan_recordings(sinn_plan *p) { return p ? p->recording
 
 extern "C" int sinn_plan_destroy(sinn_plan *p) {
   if (!p) return SINN_OK;
-  cudaSetDevice(p->ix->device);
+  SinnDevice dev_guard_(p->ix->device);
   cudaDeviceSynchronize();
   drop_recording(p);
   if (p->cs) cudaStreamDestroy(p->cs);

@@ -26,6 +26,7 @@
 //   k_final      FindLargest({s_v}, k) (Alg. 7), sorted best first
 // Ties rank the smaller id first: keys carry ~id in their low 32 bits.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "sinn_internal.cuh"
@@ -1409,7 +1410,7 @@ extern "C" int sinn_search(sinn_index *ix, const uint64_t *q_indptr, const uint3
   if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!out_ids || !out_scores) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   SearchReq r{};
   r.q_indptr = q_indptr;
   r.q_idx = q_indices;
@@ -1434,7 +1435,7 @@ extern "C" int sinn_search_kp(sinn_index *ix, const uint64_t *q_indptr, const ui
   if (k == 0 || k > SINN_MAX_K || k_prime_max < k || !k_prime) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!out_ids || !out_scores) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   SearchReq r{};
   r.q_indptr = q_indptr;
   r.q_idx = q_indices;
@@ -1457,7 +1458,7 @@ extern "C" int sinn_scores(sinn_index *ix, const uint64_t *q_indptr, const uint3
   if (st) return st;
   if (n_q == 0) return SINN_OK;
   if (!out) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   SearchReq r{};
   r.q_indptr = q_indptr;
   r.q_idx = q_indices;
@@ -1481,7 +1482,7 @@ extern "C" int sinn_candidates(sinn_index *ix, const uint64_t *q_indptr,
   if (k_prime == 0) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!out_ids || !out_scores || !out_count) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   SearchReq r{};
   r.q_indptr = q_indptr;
   r.q_idx = q_indices;
@@ -1506,7 +1507,7 @@ extern "C" int sinn_search_host(sinn_index *ix, const uint64_t *q_indptr,
   if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!q_indptr || !out_ids || !out_scores) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   const uint64_t nnz = q_indptr[n_q] - q_indptr[0];
   if (nnz && (!q_indices || !q_values)) return SINN_EINVAL;
@@ -1562,22 +1563,39 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices] = {};
+// Last address found per device, read only while a stream is being captured.
+std::atomic<void *> g_noalloc_ptr[kMaxDevices];
 
-// The array's device address, looked up once per device (with that device
-// current).  In host code the array's name is only a host-side stand-in.
-int noalloc_scratch(int dev, void **out) {
+// The array's device address in the current context.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// the device current -- on every call, which keeps it right after a context
+// is torn down and made again (cudaDeviceReset) in the same process; the
+// lookup allocates nothing.  While the stream is being captured no lookup is
+// made (it could load the module) and the address an earlier call found on
+// this device is used: the first call on a device must come before any
+// capture.  Concurrent first calls from several host threads each look the
+// address up and store the same value.
+int noalloc_scratch(int dev, cudaStream_t s, void **out) {
   if (dev < 0 || dev >= kMaxDevices) return SINN_ECUDA;
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      (void)cudaGetLastError();
-      return SINN_ECUDA;
-    }
-    g_noalloc_ptr[dev] = p;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SINN_ECUDA;
   }
-  *out = g_noalloc_ptr[dev];
+  if (cs != cudaStreamCaptureStatusNone) {
+    void *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) return SINN_ECUDA;
+    *out = p;
+    return SINN_OK;
+  }
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    (void)cudaGetLastError();
+    return SINN_ECUDA;
+  }
+  g_noalloc_ptr[dev].store(p, std::memory_order_release);
+  *out = p;
   return SINN_OK;
 }
 }  // namespace
@@ -1591,9 +1609,9 @@ extern "C" int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr,
   if (k == 0 || k > SINN_MAX_K || k_prime < k) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!out_ids || !out_scores) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   FixedScratch fx;
-  if ((st = noalloc_scratch(ix->device, &fx.base))) return st;
+  if ((st = noalloc_scratch(ix->device, (cudaStream_t)stream, &fx.base))) return st;
   fx.bytes = kNoAllocBytes;
   SearchReq r{};
   r.q_indptr = q_indptr;
@@ -1630,7 +1648,7 @@ extern "C" int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx 
   *out = nullptr;
   sinn_ctx *c = new (std::nothrow) sinn_ctx();
   if (!c) return SINN_ENOMEM;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   if (sinn_dev_malloc((void **)&c->scratch, scratch_bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     delete c;
@@ -1644,7 +1662,7 @@ extern "C" int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx 
 
 extern "C" int sinn_ctx_destroy(sinn_ctx *c) {
   if (!c) return SINN_OK;
-  cudaSetDevice(c->ix->device);
+  SinnDevice dev_guard_(c->ix->device);
   cudaDeviceSynchronize();
   cudaFree(c->scratch);
   delete c;
@@ -1669,7 +1687,7 @@ extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint
   if (k == 0 || k > SINN_MAX_K || k_prime_max < k) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
   if (!out_ids || !out_scores) return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   FixedScratch fx{c->scratch, c->bytes};
   SearchReq r{};
   r.q_indptr = q_indptr;
@@ -1718,7 +1736,7 @@ extern "C" int sinn_autotune(sinn_index *ix, const uint64_t *q_indptr, const uin
   if (st) return st;
   if (n_q == 0 || reps == 0 || reps > 8 || k == 0 || k > SINN_MAX_K || k_prime < k)
     return SINN_EINVAL;
-  cudaSetDevice(ix->device);
+  SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t *ids = nullptr;
   float *sc = nullptr;

@@ -132,6 +132,23 @@ struct SinnPhase {
   ~SinnPhase();
 };
 
+// Makes `dev` the calling thread's current device for the scope of an ABI
+// call and restores the caller's device on the way out (every return path),
+// so a host thread that drives several GPUs keeps its own current device.
+struct SinnDevice {
+  int prev = -1;
+  explicit SinnDevice(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~SinnDevice() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  SinnDevice(const SinnDevice &) = delete;
+  SinnDevice &operator=(const SinnDevice &) = delete;
+};
+
 // host helpers shared across translation units
 // Every device and pinned-host allocation of the library goes through these,
 // so that a test can make the n-th next one fail (sinn_debug_fail_alloc).

@@ -164,13 +164,9 @@ def test_search_matches_oracle(name, n_docs, tile, nq, k, kp):
     w = synth.scaled(synth.WORKLOADS[name], n_docs, n=min(synth.WORKLOADS[name].n, 5000))
     docs, qs = synth.make_docs(w), synth.make_queries(w, n_q=nq)
     gpu, ora = _pair(w, docs, tile_docs=tile)
+    # at k' >= |X| every live id is a candidate, so the tie-band check of the
+    # top k against the candidates is the check against the exact top k
     _check_search(gpu, ora, qs, k, kp)
-    if kp >= n_docs:
-        gi, gs = gpu.search(_ip(qs), _ix(qs), qs.values, k=k, k_prime=kp)
-        ex = ora.exact_topk(qs.indptr, qs.indices, qs.values, k=k)
-        gi = gi.cpu().numpy().astype(np.uint32)
-        agree = (gi == ex["ids"]).mean()
-        assert agree > 0.99
 
 
 def test_per_query_kprime():

@@ -80,3 +80,122 @@ def test_missing_file(tmp_path):
     lib = sinnamon.load()
     assert lib.sinn_save(None, b"x") == sinnamon.SINN_EINVAL
     assert lib.sinn_load(None, C.byref(C.c_void_p())) == sinnamon.SINN_EINVAL
+
+
+# ---- payload checks: a whole small index written in the file format, then
+# one entry of what the kernels index through damaged at a time
+
+def _index_file(corrupt=None):
+    """A saved index of n=100, m=16, h=1, T=1024 (one tile): ids 0..9 handed
+    out, 3 and 7 deleted (free), the others live with 10 entries each; one
+    array container per coordinate.  `corrupt` names one damage to apply."""
+    import numpy as np
+    n, m, T, cap = 100, 16, 1024, 1024
+    rng = np.random.default_rng(5)
+    ids = np.arange(10)
+    free = [3, 7]
+    live = np.zeros(cap, np.uint8)
+    live[[i for i in ids if i not in free]] = 1
+    vecs = [np.sort(rng.choice(n, 10, replace=False)).astype(np.uint32) for _ in ids]
+    fwd = np.zeros((100, 2), np.uint32)
+    fwd_off = np.zeros(cap, np.uint64)
+    fwd_nnz = np.zeros(cap, np.uint32)
+    nnz = np.zeros(cap, np.uint32)
+    for i in ids:
+        fwd[10 * i:10 * i + 10, 0] = vecs[i]
+        fwd[10 * i:10 * i + 10, 1] = np.float32(1.5).view(np.uint32)
+        fwd_off[i], fwd_nnz[i] = 10 * i, 10
+        if live[i]:
+            nnz[i] = 10
+    # the tile's containers: per coordinate, the sorted live ids holding it
+    posts = {j: [i for i in ids if live[i] and j in vecs[i]] for j in range(n)}
+    dirs = np.zeros((n, 2), np.uint32)
+    words, run = [], 0
+    for j in range(n):
+        if posts[j]:
+            dirs[j] = (run, len(posts[j]))
+            words += posts[j]
+            run += len(posts[j])
+    post_cap = 128
+    words = np.array(words + [0] * (post_cap - len(words)), np.uint16)
+    coord_len = np.array([len(posts[j]) for j in range(n)], np.uint32)
+    live_bits = np.zeros(cap // 32, np.uint32)
+    for i in np.nonzero(live)[0]:
+        live_bits[i >> 5] |= np.uint32(1 << (i & 31))
+    tile_nnz = np.array([int(nnz.sum())], np.uint64)
+    post_len = np.array([run], np.uint64)
+    free_arr = np.array(free, np.uint32)
+    hdr = dict(n=n, m=m, h=1, T=T, cap=cap, next_id=10, live_count=int(live.sum()),
+               fwd_used=100, fwd_cap=65536)
+    if corrupt == "live bit":
+        live_bits[0] ^= np.uint32(1 << 3)           # a free id's device bit set
+    elif corrupt == "store offset":
+        fwd_off[0] = 95                              # 95 + 10 > 100 entries used
+    elif corrupt == "store count":
+        fwd_nnz[1] = 9                               # differs from the host count
+    elif corrupt == "store coordinate":
+        fwd[12, 0] = n                               # a coordinate outside [0, n)
+    elif corrupt == "container past storage":
+        j = int(np.nonzero(dirs[:, 1])[0][0])
+        dirs[j, 0] = post_cap - int(dirs[j, 1]) + 1  # its last entry is past the words
+    elif corrupt == "local id":
+        words[0] = T + 1                             # an array entry outside the tile
+    elif corrupt == "bitmap alignment":
+        j = int(np.nonzero(dirs[:, 1] == 0)[0][0])
+        dirs[j] = (1, T // 8)                        # a bitmap at an odd word
+    elif corrupt == "tile entries":
+        tile_nnz[0] += 1
+    elif corrupt == "free id live":
+        free_arr[0] = 4
+    elif corrupt == "free id repeated":
+        free_arr[1] = 3
+    elif corrupt == "storage without containers":
+        post_cap = 0
+    table = [(j * 7) % m for j in range(n)]
+
+    def arr(a):
+        b = np.ascontiguousarray(a).tobytes()
+        return struct.pack("<Q", len(b)) + b
+
+    plane = np.zeros(m * cap, np.float32)
+    out = _header(**hdr) + struct.pack("<Q", 4 * n) + struct.pack(f"<{n}I", *table)
+    out += arr(plane) + arr(plane) + arr(live_bits) + arr(fwd_off) + arr(fwd_nnz) + arr(fwd)
+    out += arr(dirs) + arr(coord_len) + arr(live) + arr(nnz) + arr(free_arr)
+    out += arr(post_len) + arr(np.array([post_cap], np.uint64)) + arr(tile_nnz)
+    out += arr(np.zeros(1, np.uint64))
+    out += arr(words[:post_cap])
+    return out
+
+
+def test_a_sound_index_file_passes_the_checks(tmp_path):
+    """The undamaged file gets past every check: without a GPU the load then
+    fails creating the index on the device (never SINN_EIO)."""
+    p = tmp_path / "ok.sinn"
+    p.write_bytes(_index_file())
+    rc, out = _load(p)
+    if rc == sinnamon.SINN_OK:      # run where a GPU is present
+        assert sinnamon.load().sinn_destroy(C.c_void_p(out)) == sinnamon.SINN_OK
+        return
+    assert rc in (sinnamon.SINN_ECUDA, sinnamon.SINN_ENOMEM), rc
+    assert out is None
+
+
+@pytest.mark.parametrize("damage", [
+    "live bit", "store offset", "store count", "store coordinate", "container past storage",
+    "local id", "bitmap alignment", "tile entries", "free id live", "free id repeated",
+    "storage without containers"])
+def test_damaged_payload_is_refused_before_the_device(tmp_path, damage):
+    p = tmp_path / "bad.sinn"
+    p.write_bytes(_index_file(damage))
+    rc, out = _load(p)
+    assert rc == sinnamon.SINN_EIO, damage
+    assert out is None
+
+
+def test_truncated_payload_is_refused(tmp_path):
+    full = _index_file()
+    for cut in (len(full) - 1, len(full) - 300, len(full) // 2):
+        p = tmp_path / f"cut{cut}.sinn"
+        p.write_bytes(full[:cut])
+        rc, out = _load(p)
+        assert rc == sinnamon.SINN_EIO and out is None

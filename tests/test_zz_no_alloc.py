@@ -76,3 +76,36 @@ def test_noalloc_rejects_requests_beyond_its_scratch(built):
     with pytest.raises(sinnamon.SinnError) as e:
         sinnamon.sinn_search_noalloc(ix.handle, ip, ii, vv, 1, 1, ids, sc)
     assert e.value.code == sinnamon.SINN_ESCRATCH
+
+
+def test_noalloc_first_search_on_a_fresh_index_allocates_nothing(built):
+    """What the entry point is for: on an index that has never searched (so
+    its own scratch was never grown), the call still succeeds with every
+    library allocation made to fail, and the index holds no more scratch
+    afterwards.  Results equal sinn_search's."""
+    sinnamon, synth = built
+    w = synth.scaled(synth.WORKLOADS["tiny"], 3000)
+    docs = synth.make_docs(w)
+    ix = sinnamon.Index(w.n, w.m, w.h, tile_docs=1024)
+    ix.insert(docs.indptr.astype(np.int64), docs.indices.astype(np.int32), docs.values)
+    dev = ix.device
+    qs = synth.make_queries(w, n_q=50, seed=9)
+    ip = torch.from_numpy(qs.indptr.astype(np.int64)).to(dev)
+    ii = torch.from_numpy(qs.indices.astype(np.int32)).to(dev)
+    vv = torch.from_numpy(qs.values).to(dev)
+    k, kp = 10, 100
+    ids_b = torch.full((qs.rows, k), 7, dtype=torch.int32, device=dev)
+    sc_b = torch.zeros((qs.rows, k), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    before = ix.stats()["bytes_scratch"]
+    sinnamon.sinn_debug_fail_alloc(0)   # the next library allocation fails
+    try:
+        sinnamon.sinn_search_noalloc(ix.handle, ip, ii, vv, k, kp, ids_b, sc_b)
+        ix.sync()
+    finally:
+        sinnamon.sinn_debug_fail_alloc(-1)
+    assert ix.stats()["bytes_scratch"] == before
+    ids_a, sc_a = ix.search(ip, ii, vv, k=k, k_prime=kp)
+    ix.sync()
+    _same_results(ids_a.cpu().numpy(), sc_a.cpu().numpy(), ids_b.cpu().numpy(),
+                  sc_b.cpu().numpy(), k)
