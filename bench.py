@@ -3,12 +3,13 @@
 
 One step = one pass of the whole path over one batch of synthetic input:
 delete D live vectors (Sec. 4.3), insert D new ones (Alg. 5; they reuse the
-freed ids), then search a batch of Q queries (Alg. 6 + Alg. 7) with k' chosen
-per query by the learned network (trained before timing on the method's own
-labels; --fixed-kprime uses k' = 1000 instead).  The metric is queries/s (Q
-per step); recall@10 against the FP64 exact top-10 is measured on the same
-index and reported beside it, as are the plain baseline (one query per call,
-fixed k') and the batched fixed-k' search.
+freed ids), then search a batch of Q queries (Alg. 6 + Alg. 7) with each
+query's Alg. 6 budget and k' chosen by the learned network (trained before
+timing on the method's own labels; --fixed-kprime uses the whole query and
+k' = 1000 instead).  The metric is queries/s (Q per step); recall@10 against
+the FP64 exact top-10 is measured on the same index and reported beside it,
+as are the plain baseline (one query per call, fixed k'), the batched
+fixed-k' search and the mixed-sign workload's line.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -31,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "queries/s at recall@10>=0.9 (batched search with learned per-query k')"
+METRIC = "queries/s at recall@10>=0.9 (batched search with learned per-query k' and Alg. 6 budget)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -56,9 +57,18 @@ def job_throughput(elapsed_s: float, units: float, device=None):
 
 # ----------------------------------------------------------------- inputs
 
+def _synth_key():
+    """First 12 hex digits of synth.py's sha256: a change to the generator
+    (or its seeds) makes new cache files instead of reusing stale inputs."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2301_10622_gb300", "synth.py")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+
+
 def cached(name, fn):
-    """Generated inputs are cached in /tmp (regenerated when absent)."""
-    path = f"/tmp/sinn_bench_{name}.npz"
+    """Generated inputs are cached in /tmp under their name (which carries
+    the size and seed) and the generator's hash; regenerated when absent."""
+    path = f"/tmp/sinn_bench_{name}_{_synth_key()}.npz"
     if os.path.exists(path):
         z = np.load(path)
         from paper_2301_10622_gb300.synth import CSR
@@ -70,34 +80,55 @@ def cached(name, fn):
     return c
 
 
-def make_inputs(args, rank):
+def make_inputs(args, rank, workload=None, n_docs=0):
     from paper_2301_10622_gb300 import synth
-    w = synth.WORKLOADS[args.workload]
-    nd = args.docs or w.n_docs
+    w = synth.WORKLOADS[workload or args.workload]
+    nd = n_docs or args.docs or w.n_docs
     t0 = time.time()
-    docs = cached(f"{w.name}_docs_{nd}", lambda: synth.make_docs(w, n_docs=nd))
-    pool_n = args.churn * (args.steps + args.warmup + 1)
-    pool = cached(f"{w.name}_pool_{pool_n}", lambda: synth.make_docs(w, n_docs=pool_n, seed=5000))
+    docs = cached(f"{w.name}_docs_{nd}_s{synth._seed(w, 1000)}",
+                  lambda: synth.make_docs(w, n_docs=nd))
+    pool_n = args.churn * (args.steps + args.warmup + 8)
+    pool = cached(f"{w.name}_pool_{pool_n}_s5000",
+                  lambda: synth.make_docs(w, n_docs=pool_n, seed=5000))
     nq = args.queries or w.n_queries
-    qs = cached(f"{w.name}_q_{nq}_{rank}", lambda: synth.make_queries(
-        w, n_q=nq, seed=2000 + 2 + 100 * rank))
+    qseed = synth._seed(w, 2000) + 100 * rank
+    qs = cached(f"{w.name}_q_{nq}_s{qseed}", lambda: synth.make_queries(w, n_q=nq, seed=qseed))
     log(f"inputs ready in {time.time() - t0:.1f}s: docs={docs.rows} nnz={docs.nnz} "
         f"queries={qs.rows} pool={pool.rows}")
     return w, docs, pool, qs
 
 
-def algorithmic_bytes(w, docs, qs, cap, tiles):
-    """Bytes the scoring kernel must move per query when it runs alone: each
-    posting of the query's lists (2-byte id + h 4-byte sketch reads), one 4-byte
-    score key per id slot written, the tile offsets read and the live bitmap."""
+def list_lengths(w, docs):
     nz = docs.values != 0
-    lens = np.bincount(docs.indices[nz], minlength=w.n).astype(np.int64)
-    rows = np.repeat(np.arange(qs.rows), np.diff(qs.indptr.astype(np.int64)))
-    qnz = qs.values != 0
-    P = np.bincount(rows[qnz], weights=lens[qs.indices[qnz]], minlength=qs.rows)
-    psi = np.bincount(rows[qnz], minlength=qs.rows)
-    per_q = P * (2 + 4 * w.h) + 4 * cap + 8 * tiles * psi + cap / 8
-    return per_q, P
+    return np.bincount(docs.indices[nz], minlength=w.n).astype(np.int64)
+
+
+def scored_postings(qs, lens, budgets=None):
+    """Postings Alg. 6 visits per query: every term's list, or with budgets[q]
+    > 0 the terms in Alg. 6 order (|q_j| descending, ties j ascending) up to
+    the first at which the running sum reaches the budget."""
+    out = np.zeros(qs.rows, np.int64)
+    for r in range(qs.rows):
+        qi, qv = qs.row(r)
+        keep = qv != 0
+        qi, qv = qi[keep], qv[keep]
+        ln = lens[qi]
+        b = 0 if budgets is None else int(budgets[r])
+        if b == 0:
+            out[r] = int(ln.sum())
+            continue
+        order = np.lexsort((qi, -np.abs(qv)))
+        cum = np.cumsum(ln[order])
+        t = int(np.searchsorted(cum, b))          # first term with cum >= b
+        out[r] = int(cum[min(t, cum.size - 1)]) if cum.size else 0
+    return out
+
+
+def algorithmic_bytes(w, postings):
+    """Bytes the scoring kernel must move per query (the unshared
+    algorithmic count): for each posting of the lists it scores, a 4-byte id
+    and h 4-byte sketch reads (only the sign's plane is read)."""
+    return postings.astype(np.float64) * (4 + 4 * w.h)
 
 
 # ----------------------------------------------------------------- clocks
@@ -169,8 +200,8 @@ def oracle_index(w, docs):
 
 
 def cpu_baseline(ora, w, qs, target_s, k, kp):
-    """The oracle (Alg. 6 + Alg. 7, FP64) on a bounded sample of the queries,
-    all host cores."""
+    """The oracle (Alg. 6 + Alg. 7, FP64) on bounded samples of the queries:
+    all host cores (the reported value) and one thread beside it."""
     cores = os.cpu_count() or 1
     one = qs.slice(0, 1)
     t0 = time.time()
@@ -181,9 +212,15 @@ def cpu_baseline(ora, w, qs, target_s, k, kp):
     t0 = time.time()
     ora.search(sample.indptr, sample.indices, sample.values, k=k, k_prime=kp, threads=cores)
     dt = time.time() - t0
+    s1 = int(min(qs.rows, max(1, 0.5 * target_s / t1)))
+    t0 = time.time()
+    ora.search(qs.indptr[:s1 + 1], qs.indices, qs.values, k=k, k_prime=kp, threads=1)
+    dt1 = time.time() - t0
     return {"value": s / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"first {s} of {qs.rows} queries over the full index "
-                      f"(k={k}, k'={kp}), FP64 Alg. 6+7, {dt:.1f}s"}
+                      f"(k={k}, k'={kp}), FP64 Alg. 6+7, {dt:.1f}s on {cores} threads",
+            "single_thread": {"value": s1 / dt1, "unit": "queries/s", "cores": 1,
+                              "sample": f"first {s1} queries, {dt1:.1f}s on 1 thread"}}
 
 
 def recall_at_10(ora, qs_sample, gpu_ids, threads):
@@ -274,25 +311,47 @@ def source_code_hash(path):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-def measured_traffic(launches, queries, docs):
-    """DRAM bytes per scoring launch from the committed ncu summary, scaled to
-    this run's queries per launch; None if the kernel source changed since the
-    counters were taken or the index is not the size they were taken on."""
-    prof = os.path.join(ROOT, "profiles", "k_score_emit_text.md")
-    src = os.path.join(ROOT, "paper_2301_10622_gb300", "csrc", "search.cu")
+def profile_figures(name, src_file="search.cu"):
+    """Figures of a committed ncu summary (profiles/<name>.md) as a dict of
+    its `key: value` lines, or None when the summary is missing or the
+    kernel source changed since its counters were taken."""
+    prof = os.path.join(ROOT, "profiles", name + ".md")
+    src = os.path.join(ROOT, "paper_2301_10622_gb300", "csrc", src_file)
     try:
         text = open(prof).read()
-        want = text.split("source_code_sha256_16:")[1].split()[0]
-        per_launch = float(text.split("traffic_bytes_per_launch:")[1].split()[0])
-        q_launch = float(text.split("queries_per_launch:")[1].split()[0])
-        p_docs = int(text.split("docs_in_index:")[1].split()[0])
-    except (OSError, IndexError, ValueError):
+    except OSError:
         return None
-    if source_code_hash(src) != want or launches == 0:
+    fig = {}
+    for ln in text.splitlines():
+        ln = ln.strip()
+        if ":" in ln and " " not in ln.split(":")[0]:
+            key, val = ln.split(":", 1)
+            try:
+                fig[key] = float(val.split()[0])
+            except (ValueError, IndexError):
+                fig[key] = val.strip()
+    want = fig.get("source_code_sha256_16")
+    if want is None or source_code_hash(src) != str(want).split()[0]:
         return None
-    if p_docs != docs:
-        return None
-    return per_launch * (queries / launches) / q_launch
+    return fig
+
+
+def dram_figures(fig, launch_ms, peak, units_per_launch, docs):
+    """DRAM bytes per launch from a profile's counters, scaled to this run's
+    units per launch; the DRAM fraction of peak over the live launch time;
+    and the L1 / L2 throughput fractions the profile read.  None entries
+    when the profile does not match this kernel or this index size."""
+    out = {"traffic": None, "dram_frac": None, "l1_frac": None, "l2_frac": None}
+    if not fig or fig.get("docs_in_index") != docs:
+        return out
+    per, q = fig.get("traffic_bytes_per_launch"), fig.get("queries_per_launch")
+    if per and q and launch_ms:
+        t = per * units_per_launch / q
+        out["traffic"] = t
+        out["dram_frac"] = t / (launch_ms / 1000.0) / 1e9 / peak
+    out["l1_frac"] = fig.get("l1_throughput_frac")
+    out["l2_frac"] = fig.get("l2_throughput_frac")
+    return out
 
 
 WORKLOAD_TEXT = {
@@ -319,6 +378,98 @@ def config_dict(args, w, docs, qs, tile_docs, index_gb=0.0):
 
 
 # ------------------------------------------------------------------- ours
+
+def build_index(sinnamon, w, docs, dev, T, scratch_gb, flags=0):
+    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
+                        scratch_bytes=scratch_gb << 30, flags=flags)
+    for a in range(0, docs.rows, 200_000):
+        part = docs.slice(a, min(docs.rows, a + 200_000))
+        ix.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+    return ix
+
+
+def train_policy(args, w, ix, k, kp):
+    """The learned Alg. 6 budget with k' (trained before timing, on labels
+    the method generates): per budget level P_q / 2^s the least k' keeping 9
+    of the exact top 10; a network over (features, -s); the per-posting cost
+    measured; the margin calibrated on held-out queries for recall >= 0.92."""
+    from paper_2301_10622_gb300 import kprime, synth
+    t0 = time.time()
+    tq = cached(f"{w.name}_train_{args.train_queries}_s3000",
+                lambda: synth.make_queries(w, n_q=args.train_queries, seed=3000))
+    cq = cached(f"{w.name}_cal_{args.cal_queries}_s3002",
+                lambda: synth.make_queries(w, n_q=args.cal_queries, seed=3002))
+    shifts = tuple(int(x) for x in args.shifts.split(","))
+    _, cert, ex = kprime.labels(ix, tq, k=k, cap=args.kp_cap)
+    lv = kprime.level_labels(ix, tq, ex, cert, shifts, k=k, cap=args.kp_cap)
+    t_lab = time.time() - t0
+    mlp = kprime.train_levels(ix, tq, lv, shifts, k=k, epochs=args.epochs)
+    t_fit = time.time() - t0 - t_lab
+    pc = kprime.measure_costs(ix, cq, k=k, k_prime=kp)
+    mlp.set_policy(shifts, pc, 0.0)
+    _, _, ex_c = kprime.labels(ix, cq, k=k, cap=args.kp_cap)
+    margin, cal_rec = kprime.calibrate_margin(ix, mlp, cq, ex_c, k=k, kp_min=k,
+                                              kp_max=args.kp_max, target=args.cal_recall)
+    info = {"train_queries": tq.rows, "label_cap": args.kp_cap, "search_cap": args.kp_max,
+            "certified_labels": float(np.mean(cert)), "levels_shifts": list(shifts),
+            "label_median_per_level": [float(np.median(lv[:, i])) for i in range(len(shifts))],
+            "label_feasible_per_level": [float(np.mean(lv[:, i] <= args.kp_max))
+                                         for i in range(len(shifts))],
+            "posting_cost": pc, "margin": margin, "calibration_queries": cq.rows,
+            "calibration_recall": cal_rec, "label_seconds": t_lab, "fit_seconds": t_fit,
+            "train_seconds": time.time() - t0}
+    log(f"budget + k' network trained: {info}")
+    return mlp, info
+
+
+def timed_best(fn, reps=3):
+    """Best CUDA-event time (ms) of fn() on the current stream, after one warm-up."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def plain_search(sinnamon, h, qs, g_qix, g_qv, k, kp, dev, npl, alg_full):
+    """One query per call (the plain per-query arm): queries/s, latency
+    percentiles and the scorer-bytes rate of a lone query."""
+    import torch
+    npl = min(npl, qs.rows)
+    one_ids = torch.empty((1, k), dtype=torch.int32, device=dev)
+    one_sc = torch.empty((1, k), dtype=torch.float32, device=dev)
+    offs = qs.indptr.astype(np.int64)
+    qip1 = [torch.tensor([0, offs[r + 1] - offs[r]], dtype=torch.int64, device=dev)
+            for r in range(npl)]
+    for r in range(min(3, npl)):
+        a = int(offs[r])
+        sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(npl)]
+    t0 = time.perf_counter()
+    for r in range(npl):
+        a = int(offs[r])
+        evs[r][0].record()
+        sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
+        evs[r][1].record()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    bytes_q = float(np.mean(alg_full[:npl]))
+    return {"qps": npl / plain_s, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "queries": npl, "k_prime": kp,
+            "alg_bytes_per_query": bytes_q,
+            "effective_gbs_at_mean_latency": bytes_q / (float(lat.mean()) / 1000.0) / 1e9}
+
 
 def run_ours(args):
     import torch
@@ -350,33 +501,29 @@ def run_ours(args):
                                            scratch_bytes=args.scratch_gb << 30, log=log)
         tile_choice = {str(t): round(r["ms"], 3) for t, r in res.items()}
         log(f"tile size {T} chosen in {time.time() - t0:.1f}s: {tile_choice}")
-    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
-                        scratch_bytes=args.scratch_gb << 30)
     t0 = time.time()
-    step_docs = 200_000
-    for a in range(0, docs.rows, step_docs):
-        part = docs.slice(a, min(docs.rows, a + step_docs))
-        ix.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+    ix = build_index(sinnamon, w, docs, dev, T, args.scratch_gb)
     torch.cuda.synchronize()
     st = ix.stats()
     log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
-    cap, tiles = st["capacity"], st["capacity"] // st["tile_docs"]
+    lens = list_lengths(w, docs)
 
-    # the learned k' (trained before timing, on labels the method generates)
+    # launch tuning chosen by the autotuner on a sample of the step's queries
+    tuning = None
+    if not args.no_autotune:
+        t0 = time.time()
+        sq = qs.slice(0, min(qs.rows, 2000))
+        tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
+                             k, kp, reps=2)
+        log(f"autotuned in {time.time() - t0:.1f}s: {tuning}")
+    if args.tuning:  # fields set by hand, after (or instead of) the autotuner
+        ix.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1])
+                         for kv in args.tuning.split(",")})
+    tuning = ix.tuning()
+
     mlp, kp_info = None, None
     if not args.fixed_kprime:
-        from paper_2301_10622_gb300 import kprime, synth
-        t0 = time.time()
-        tq = cached(f"{w.name}_train_{args.train_queries}", lambda: synth.make_queries(
-            w, n_q=args.train_queries, seed=3000))
-        kp_train, cert, _ = kprime.labels(ix, tq, k=k, cap=args.kp_cap)
-        mlp = kprime.train(ix, tq, kp_train, k=k, epochs=args.epochs)
-        kp_info = {"train_queries": tq.rows, "label_cap": args.kp_cap, "search_cap": args.kp_max,
-                   "certified_labels": float(cert.mean()),
-                   "label_median": float(np.median(kp_train)),
-                   "label_p90": float(np.percentile(kp_train, 90)),
-                   "train_seconds": time.time() - t0}
-        log(f"k' network trained: {kp_info}")
+        mlp, kp_info = train_policy(args, w, ix, k, kp)
 
     # device-resident step inputs
     g_qip = torch.from_numpy(qs.indptr.astype(np.int64)).to(dev)
@@ -385,11 +532,13 @@ def run_ours(args):
     out_ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
     out_sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
     nsteps = args.warmup + args.steps
+    n_e2e = args.e2e_steps
     rng = np.random.default_rng(7 + rank)
+    nparts = nsteps + n_e2e + 2
     dels = [torch.from_numpy(rng.choice(docs.rows, size=args.churn, replace=False)
-                             .astype(np.int32)).to(dev) for _ in range(2 * nsteps + 2)]
+                             .astype(np.int32)).to(dev) for _ in range(nparts)]
     parts = []
-    for s_ in range(2 * nsteps + 2):
+    for s_ in range(nparts):
         p = pool.slice((s_ * args.churn) % max(1, pool.rows - args.churn),
                        (s_ * args.churn) % max(1, pool.rows - args.churn) + args.churn)
         parts.append((torch.from_numpy(p.indptr.astype(np.int64)).to(dev),
@@ -407,18 +556,6 @@ def run_ours(args):
             sinnamon.sinn_search_learned(h, mlp.handle, qip, qix, qv, k, k, args.kp_max, oids,
                                          osc, out_kp)
 
-    # launch tuning chosen by the autotuner on a sample of the step's queries
-    tuning = None
-    if not args.no_autotune:
-        t0 = time.time()
-        sq = qs.slice(0, min(qs.rows, 2000))
-        tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
-                             k, kp, reps=2)
-        log(f"autotuned in {time.time() - t0:.1f}s: {tuning}")
-    if args.tuning:  # fields set by hand, after (or instead of) the autotuner
-        ix.set_tuning(**{kv.split("=")[0]: int(kv.split("=")[1])
-                         for kv in args.tuning.split(",")})
-    tuning = ix.tuning()
     # the step's search as one recorded CUDA graph, replayed every step
     plan = None
     if not args.no_graph:
@@ -461,129 +598,112 @@ def run_ours(args):
     value, elapsed = job_throughput(elapsed, qs.rows * args.steps, dev)
     ms_step = 1000 * elapsed / args.steps
 
-    # roofline of the scoring kernel (live CUDA-event durations from the library)
-    per_q, P = algorithmic_bytes(w, docs, qs, cap, tiles)
+    # roofline of the scoring kernel (live CUDA-event durations from the
+    # library): the bytes Alg. 6 must move for the postings each query
+    # actually scored (its learned budget), 4-byte ids + h 4-byte bins each
+    budgets = None
+    if mlp is not None:
+        _, bud = ix.kp_choose(mlp, g_qip, g_qix, g_qv, k, args.kp_max)
+        budgets = bud.cpu().numpy()
+    P_full = scored_postings(qs, lens)
+    P_scored = scored_postings(qs, lens, budgets)
+    alg_q = algorithmic_bytes(w, P_scored)
     score_ms = tm["ms"]["score"]
-    alg_bytes = float(per_q.sum()) * args.steps
-    achieved = alg_bytes / (score_ms / 1000.0) / 1e9 if score_ms > 0 else None
+    launches = max(1, tm["spans"]["score"])
+    achieved = float(alg_q.sum()) * args.steps / (score_ms / 1000.0) / 1e9 if score_ms else None
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = measured_traffic(tm["spans"]["score"], qs.rows * args.steps, docs.rows)
+    dr = dram_figures(profile_figures(f"k_score_emit_{w.name}"), score_ms / launches, peak,
+                      qs.rows * args.steps / launches, docs.rows)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "effective": True,
-            "kernel": "k_score", "launches": tm["spans"]["score"],
-            "avg_launch_ms": score_ms / max(1, tm["spans"]["score"]),
+            "frac": (achieved / peak) if achieved else None,
+            "frac_kind": ("effective: algorithmic bytes (4 + 4h per scored posting) over the "
+                          "scoring time; queries resident together share each tile's lists and "
+                          "sketch rows through L2, so it can exceed 1"),
+            "traffic": dr["traffic"], "dram_frac": dr["dram_frac"], "l1_frac": dr["l1_frac"],
+            "l2_frac": dr["l2_frac"], "kernel": "k_score_emit", "launches": launches,
+            "avg_launch_ms": score_ms / launches,
             "peak_source": "measured" if peaks else "fallback",
-            "alg_bytes_per_query": float(per_q.mean()), "postings_per_query": float(P.mean())}
+            "alg_bytes_per_query": float(alg_q.mean()),
+            "postings_scored_per_query": float(P_scored.mean()),
+            "postings_per_query_unbudgeted": float(P_full.mean())}
 
     # ---- untimed extras on rank 0: e2e, plain per-query, recall, CPU baseline
     extras = {}
     if rank == 0:
-        # e2e through the host-buffer C ABI call (copies inside the timed region)
-        h_qip = qs.indptr.astype(np.uint64)
-        h_ids = np.zeros((qs.rows, k), np.uint32)
-        h_sc = np.zeros((qs.rows, k), np.float32)
-        pin = {}
-        for si in range(2):
-            ip, ii, vv, p = parts[si + nsteps]
-            pin[si] = (torch.from_numpy(p.indptr.astype(np.int64)).pin_memory(),
-                       torch.from_numpy(p.indices.astype(np.int32)).pin_memory(),
-                       torch.from_numpy(p.values).pin_memory(),
-                       torch.from_numpy(dels[si + nsteps].cpu().numpy()).pin_memory())
-        qidx_pin = torch.from_numpy(qs.indices.view(np.int32)).pin_memory()
-        qval_pin = torch.from_numpy(qs.values).pin_memory()
-        qip_pin = torch.from_numpy(qs.indptr.astype(np.int64)).pin_memory()
-        e_ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
-        e_sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
+        # e2e: the same step through the host-buffer C ABI search, copies of
+        # the step's inputs and results inside the timed region
+        pin_q = (torch.from_numpy(qs.indptr.astype(np.int64)).pin_memory(),
+                 torch.from_numpy(qs.indices.view(np.int32)).pin_memory(),
+                 torch.from_numpy(qs.values).pin_memory())
         ids_pin = torch.empty((qs.rows, k), dtype=torch.int32).pin_memory()
         sc_pin = torch.empty((qs.rows, k), dtype=torch.float32).pin_memory()
+        kp_pin = torch.empty(qs.rows, dtype=torch.int32).pin_memory()
         hid_pin = torch.empty(args.churn, dtype=torch.int32).pin_memory()
+        pin_m = []
+        for si in range(n_e2e):
+            _, _, _, p = parts[si + nsteps]
+            pin_m.append((torch.from_numpy(p.indptr.astype(np.int64)).pin_memory(),
+                          torch.from_numpy(p.indices.astype(np.int32)).pin_memory(),
+                          torch.from_numpy(p.values).pin_memory(),
+                          torch.from_numpy(dels[si + nsteps].cpu().numpy()).pin_memory()))
         torch.cuda.synchronize()
-        e_times = []
-        for si in range(2):
-            t0 = time.perf_counter()
-            pip, pii, pvv, pdl = pin[si]
+        t0 = time.perf_counter()
+        for si in range(n_e2e):
+            pip, pii, pvv, pdl = pin_m[si]
             executed.append(si + nsteps)
-            d_dl = pdl.to(dev, non_blocking=True)
-            sinnamon.sinn_delete(h, d_dl)
-            d_ip, d_ii, d_vv = (pip.to(dev, non_blocking=True), pii.to(dev, non_blocking=True),
-                                pvv.to(dev, non_blocking=True))
-            sinnamon.sinn_insert(h, d_ip, d_ii, d_vv, new_ids)
+            sinnamon.sinn_delete(h, pdl.to(dev, non_blocking=True))
+            sinnamon.sinn_insert(h, pip.to(dev, non_blocking=True),
+                                 pii.to(dev, non_blocking=True), pvv.to(dev, non_blocking=True),
+                                 new_ids)
             hid_pin.copy_(new_ids, non_blocking=True)
             if mlp is None:
-                sinnamon.sinn_search_host(h, h_qip, qidx_pin.numpy(), qval_pin.numpy(), k, kp,
-                                          h_ids, h_sc)
+                sinnamon.sinn_search_host(h, *pin_q, k, kp, ids_pin, sc_pin)
             else:
-                e_ip = qip_pin.to(dev, non_blocking=True)
-                e_ix = qidx_pin.to(dev, non_blocking=True)
-                e_v = qval_pin.to(dev, non_blocking=True)
-                search(e_ip, e_ix.view(torch.int32), e_v, e_ids, e_sc)
-                ids_pin.copy_(e_ids, non_blocking=True)
-                sc_pin.copy_(e_sc, non_blocking=True)
+                sinnamon.sinn_search_learned_host(h, mlp.handle, *pin_q, k, k, args.kp_max,
+                                                  ids_pin, sc_pin, kp_pin)
             torch.cuda.synchronize()
-            e_times.append(time.perf_counter() - t0)
-        e2e_s = float(np.median(e_times))
-        h2d = int(qs.indptr.nbytes + qs.indices.nbytes + qs.values.nbytes
-                  + parts[0][3].indptr.nbytes + parts[0][3].indices.nbytes
-                  + parts[0][3].values.nbytes + args.churn * 4)
-        d2h = int(qs.rows * k * 8 + args.churn * 4)
-        extras["e2e"] = {"value": qs.rows / e2e_s, "unit": "queries/s",
-                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e_s = (time.perf_counter() - t0) / max(1, n_e2e)
+        p0 = parts[nsteps][3]
+        h2d = int(qs.indptr.nbytes + qs.indices.nbytes + qs.values.nbytes + p0.indptr.nbytes
+                  + p0.indices.nbytes + p0.values.nbytes + args.churn * 4)
+        d2h = int(qs.rows * k * 8 + args.churn * 4 + (qs.rows * 4 if mlp is not None else 0))
+        extras["e2e"] = {"value": qs.rows / e2e_s, "unit": "queries/s", "steps": n_e2e,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                         "call": "sinn_search_learned_host" if mlp is not None
+                         else "sinn_search_host"}
 
-        # plain per-query search: one query per call
-        npl = min(args.plain_queries, qs.rows)
-        lat = []
-        one_ids = torch.empty((1, k), dtype=torch.int32, device=dev)
-        one_sc = torch.empty((1, k), dtype=torch.float32, device=dev)
-        offs = qs.indptr.astype(np.int64)
-        qip1 = [torch.tensor([0, offs[r + 1] - offs[r]], dtype=torch.int64, device=dev)
-                for r in range(npl)]
-        for r in range(min(3, npl)):
-            a = int(offs[r])
-            sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(npl)]
-        t0 = time.perf_counter()
-        for r in range(npl):
-            a = int(offs[r])
-            evs[r][0].record()
-            sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
-            evs[r][1].record()
-        torch.cuda.synchronize()
-        plain_s = time.perf_counter() - t0
-        lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
-        extras["plain"] = {"qps": npl / plain_s, "p50_ms": float(np.percentile(lat, 50)),
-                           "p99_ms": float(np.percentile(lat, 99)), "queries": npl}
+        # plain per-query search: one query per call, fixed k'
+        alg_full = algorithmic_bytes(w, P_full)
+        extras["plain"] = plain_search(sinnamon, h, qs, g_qix, g_qv, k, kp, dev,
+                                       args.plain_queries, alg_full)
+        extras["plain"]["frac_of_peak_effective"] = (
+            extras["plain"]["effective_gbs_at_mean_latency"] / peak)
 
         # batched latency (learned, as timed) and the batched fixed-k' search
-        ev0.record()
-        if plan is not None:
-            plan.run()
-        else:
-            search(g_qip, g_qix, g_qv, out_ids, out_sc)
-        ev1.record()
-        torch.cuda.synchronize()
-        extras["batched"] = {"qps": value / world, "batch_ms": ev0.elapsed_time(ev1),
-                             "p50_ms": ev0.elapsed_time(ev1), "p99_ms": ev0.elapsed_time(ev1),
+        ms_b = timed_best(lambda: plan.run() if plan is not None
+                          else search(g_qip, g_qix, g_qv, out_ids, out_sc))
+        extras["batched"] = {"qps": value / world, "batch_ms": ms_b,
                              "plan_recordings": plan.recordings if plan is not None else None}
-        fx_ids = torch.empty_like(out_ids)
-        fx_sc = torch.empty_like(out_sc)
-        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids, fx_sc)
-        torch.cuda.synchronize()
-        ev0.record()
-        sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids, fx_sc)
-        ev1.record()
-        torch.cuda.synchronize()
-        extras["batched_fixed_kprime"] = {"qps": qs.rows / (ev0.elapsed_time(ev1) / 1000.0),
+        fx_ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
+        fx_sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
+        ms_f = timed_best(lambda: sinnamon.sinn_search(h, g_qip, g_qix, g_qv, k, kp, fx_ids,
+                                                       fx_sc))
+        extras["batched_fixed_kprime"] = {"qps": qs.rows / (ms_f / 1000.0), "batch_ms": ms_f,
                                           "k_prime": kp}
+        if plan is not None:
+            plan.run()   # the learned results on the index as it stands now
+        torch.cuda.synchronize()
         if mlp is not None:
             kps = out_kp.float()
-            extras["learned_kprime"] = dict(kp_info, mean=float(kps.mean().item()),
-                                            p50=float(kps.median().item()),
-                                            p90=float(kps.quantile(0.9).item()),
-                                            max=float(kps.max().item()))
+            bfrac = np.where(budgets > 0, P_scored / np.maximum(P_full, 1), 1.0)
+            extras["learned_kprime"] = dict(
+                kp_info, mean=float(kps.mean().item()), p50=float(kps.median().item()),
+                p90=float(kps.quantile(0.9).item()), max=float(kps.max().item()),
+                mean_scored_fraction=float(bfrac.mean()),
+                queries_with_budget=float(np.mean(budgets > 0)),
+                speedup_vs_fixed_kprime=extras["batched_fixed_kprime"]["batch_ms"] / ms_b)
+        ora = None
         if not args.skip_oracle:
             import oracle
             oracle.build()
@@ -592,18 +712,21 @@ def run_ours(args):
             ora = oracle_index(w, live_docs)
             nr = min(args.recall_queries, qs.rows)
             samp = qs.slice(0, nr)
-            gids = out_ids.cpu().numpy()[:nr]
-            extras["recall_at_10"] = recall_at_10(ora, samp, gids, os.cpu_count() or 1)
+            extras["recall_at_10"] = recall_at_10(ora, samp, out_ids.cpu().numpy()[:nr],
+                                                  os.cpu_count() or 1)
             extras["recall_at_10_fixed_kprime"] = recall_at_10(
                 ora, samp, fx_ids.cpu().numpy()[:nr], os.cpu_count() or 1)
             extras["recall_queries"] = nr
             extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
         if not args.skip_variants:
             extras.update(run_variants(args, w, docs, ix, (g_qip, g_qix, g_qv), qs, k, kp,
-                                       float(P.mean()), ora if not args.skip_oracle else None,
-                                       T))
+                                       float(P_full.mean()), ora, T))
         if args.serve_seconds > 0:
             extras["serving"] = run_serving(args, w, ix, qs, docs.rows, mlp, k, kp)
+        if ora is not None:
+            ora.close()
+        if not args.skip_mixed:
+            extras["mixed"] = run_mixed(args, dev)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -617,6 +740,9 @@ def run_ours(args):
                                    (st["bytes_lists"] + st["bytes_sketch"]) / 1e9),
                        tuning=tuning,
                        tile_choice_ms=tile_choice,
+                       search=("learned per-query Alg. 6 budget and k' (sinn_search_learned "
+                               "with a budget-level policy)" if mlp is not None
+                               else f"fixed k'={kp}"),
                        search_launch=("one recorded CUDA graph per step (sinn_plan)"
                                       if plan is not None else "direct launches")),
         "roofline": roof,
@@ -637,10 +763,79 @@ def run_ours(args):
         "bf16_sketch": extras.get("bf16_sketch"),
         "phases_ms_per_step": {p: v / args.steps for p, v in tm["ms"].items()},
         "index": st,
+        "extra": {"mixed": extras.get("mixed"), "plain": extras.get("plain")},
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_mixed(args, dev):
+    """The mixed-sign workload (8.8M documents, uniform coordinates, N(0,1)
+    values, m = 64, h = 2: both sketch planes read) as an extra line: its
+    batched fixed-k' search of 10,000 queries, one-query searches, the
+    scorer's roofline, and recall@10 against the FP64 oracle on a sample."""
+    import torch
+    from paper_2301_10622_gb300 import sinnamon
+    w, docs, _, qs = make_inputs(args, 0, workload="mixed", n_docs=args.mixed_docs)
+    k, kp = w.k, w.k_prime
+    t0 = time.time()
+    ix = build_index(sinnamon, w, docs, dev, 4096, args.scratch_gb)
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    sq = qs.slice(0, min(qs.rows, 2000))
+    tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
+                         k, kp, reps=1)
+    g = (torch.from_numpy(qs.indptr.astype(np.int64)).to(dev),
+         torch.from_numpy(qs.indices.astype(np.int32)).to(dev), torch.from_numpy(qs.values).to(dev))
+    ids = torch.empty((qs.rows, k), dtype=torch.int32, device=dev)
+    sc = torch.empty((qs.rows, k), dtype=torch.float32, device=dev)
+    ms = timed_best(lambda: sinnamon.sinn_search(ix.handle, *g, k, kp, ids, sc))
+    sinnamon.sinn_timing_start(ix.handle)
+    sinnamon.sinn_search(ix.handle, *g, k, kp, ids, sc)
+    torch.cuda.synchronize()
+    tm = sinnamon.sinn_timing_stop(ix.handle)
+    lens = list_lengths(w, docs)
+    P = scored_postings(qs, lens)
+    alg = algorithmic_bytes(w, P)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    s_ms = tm["ms"]["score"]
+    launches = max(1, tm["spans"]["score"])
+    achieved = float(alg.sum()) / (s_ms / 1000.0) / 1e9
+    floor = P.astype(np.float64) * (4 + 32 * w.h)   # a 32-byte sector per bin gather
+    fl_gbs = float(floor.sum()) / (s_ms / 1000.0) / 1e9
+    dr = dram_figures(profile_figures("k_score_emit_mixed"), s_ms / launches, peak,
+                      qs.rows / launches, docs.rows)
+    out = {"workload": (f"mixed-sign: n={w.n}, {docs.rows} docs, uniform coordinates, nnz/doc "
+                        f"uniform 80-160, N(0,1) values; {qs.rows} queries of 40 nnz; "
+                        f"m={w.m}, h={w.h}, k={k}, k'={kp}"),
+           "qps": qs.rows / (ms / 1000.0), "batch_ms": ms,
+           "phases_ms": tm["ms"], "tuning": tuning, "index_build_s": t_build,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "frac_kind": "effective (4 + 4h bytes per "
+                        "scored posting over the scoring time)",
+                        "sector_floor_gbs": fl_gbs, "sector_floor_frac": fl_gbs / peak,
+                        "traffic": dr["traffic"], "dram_frac": dr["dram_frac"],
+                        "l1_frac": dr["l1_frac"], "l2_frac": dr["l2_frac"],
+                        "kernel": "k_score_emit", "launches": launches,
+                        "avg_launch_ms": s_ms / launches,
+                        "alg_bytes_per_query": float(alg.mean()),
+                        "postings_per_query": float(P.mean())}}
+    out["plain"] = plain_search(sinnamon, ix.handle, qs, g[1], g[2], k, kp, dev,
+                                min(100, args.plain_queries), alg)
+    if not args.skip_oracle:
+        import oracle
+        oracle.build()
+        ora = oracle_index(w, docs)
+        nr = min(args.mixed_recall_queries, qs.rows)
+        out["recall_at_10"] = recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr],
+                                           os.cpu_count() or 1)
+        out["recall_queries"] = nr
+        ora.close()
+    ix.close()
+    log(f"mixed: {out}")
+    return out
 
 
 def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs):
@@ -786,11 +981,19 @@ def main():
                     help="ids per tile; 0 = chosen by measurement")
     ap.add_argument("--scratch-gb", type=int, default=8)
     ap.add_argument("--plain-queries", type=int, default=300)
-    ap.add_argument("--recall-queries", type=int, default=200)
+    ap.add_argument("--recall-queries", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--fixed-kprime", action="store_true")
-    ap.add_argument("--train-queries", type=int, default=20000)
+    ap.add_argument("--train-queries", type=int, default=200000)
+    ap.add_argument("--cal-queries", type=int, default=2000)
+    ap.add_argument("--cal-recall", type=float, default=0.92)
+    ap.add_argument("--shifts", default="0,1,2,3,4,5",
+                    help="budget levels P_q / 2^s of the learned policy")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--skip-mixed", action="store_true")
+    ap.add_argument("--mixed-docs", type=int, default=0)
+    ap.add_argument("--mixed-recall-queries", type=int, default=500)
     ap.add_argument("--kp-cap", type=int, default=20000)
     ap.add_argument("--kp-max", type=int, default=4096)
     ap.add_argument("--epochs", type=int, default=30)

@@ -150,6 +150,23 @@ int sinn_search_kp(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_i
                    const float *q_values, uint32_t n_q, uint32_t k, const uint32_t *k_prime,
                    uint32_t k_prime_max, uint32_t *out_ids, float *out_scores, void *stream);
 
+/* As sinn_search_kp with, besides the per-query k' (k_prime: device
+ * uint32[n_q] clamped to [k, k_prime_max], or NULL for k_prime_max
+ * everywhere), a per-query anytime budget of Alg. 6: budget is device
+ * uint64[n_q], budget[q] the postings query q may visit (0 = T = infinity;
+ * the break follows sinn_set_budget's rule), or NULL for the index's budget.
+ * The re-rank of Alg. 7 always takes every query term. */
+int sinn_search_kpb(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                    const float *q_values, uint32_t n_q, uint32_t k, const uint32_t *k_prime,
+                    uint32_t k_prime_max, const uint64_t *budget, uint32_t *out_ids,
+                    float *out_scores, void *stream);
+
+/* Alg. 6's postings of each query with no budget: out[q] = the sum over the
+ * query's non-zeros j of |I[j]| (live postings), device uint64[n_q]; 0 for a
+ * malformed row. */
+int sinn_query_postings(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                        const float *q_values, uint32_t n_q, uint64_t *out, void *stream);
+
 /* As sinn_search with every buffer in host memory: the call copies the
  * queries to the device, searches, copies the results back and waits.
  * Device errors are returned directly. */
@@ -334,6 +351,13 @@ int sinn_scores(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indi
 int sinn_candidates(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
                     const float *q_values, uint32_t n_q, uint32_t k_prime, uint32_t *out_ids,
                     float *out_scores, uint32_t *out_count, void *stream);
+
+/* sinn_candidates with a per-query anytime budget (device uint64[n_q] as in
+ * sinn_search_kpb, or NULL for the index's budget). */
+int sinn_candidates_kpb(sinn_index *ix, const uint64_t *q_indptr, const uint32_t *q_indices,
+                        const float *q_values, uint32_t n_q, uint32_t k_prime,
+                        const uint64_t *budget, uint32_t *out_ids, float *out_scores,
+                        uint32_t *out_count, void *stream);
 
 #ifdef __cplusplus
 }

@@ -77,13 +77,74 @@ int sinn_mlp_train_step(sinn_mlp *m, const float *X, const float *t, uint32_t B,
 int sinn_mlp_sync(sinn_mlp *m, void *stream);
 
 /* sinn_search with k'[q] = clamp(ceil(2^network(features(q))), k_prime_min,
- * k_prime_max); the network must have n_in = SINN_KP_FEATURES.  out_kprime
- * (device uint32[n_q], nullable) receives the k' used per query. */
+ * k_prime_max); the network must have n_in = SINN_KP_FEATURES.  With a
+ * policy (below), the per-query k' and Alg. 6 budget the policy chooses
+ * instead.  out_kprime (device uint32[n_q], nullable) receives the k' used
+ * per query. */
 int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
                         const uint32_t *q_indices, const float *q_values, uint32_t n_q,
                         uint32_t k, uint32_t k_prime_min, uint32_t k_prime_max,
                         uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
                         void *stream);
+
+/* ---- Learned Alg. 6 budget with k' --------------------------------------
+ * Alg. 6 may stop scoring once a time budget is spent (its anytime break,
+ * counted in postings here, as in sinn_set_budget), and Alg. 7 can recover
+ * what a short budget loses with a deeper re-rank.  A policy lets the network
+ * pick both per query: for each of a few budget levels it predicts the least
+ * k' that keeps 9 of the exact top 10 at that level, and the query takes the
+ * level of least predicted cost.
+ *   Level l scores the terms of Alg. 6, in its order, until the postings
+ *   visited reach ceil(P_q / 2^shift[l]), P_q being the query's postings
+ *   with no budget (sinn_query_postings); shift[0] must be 0 (the whole
+ *   query) and the shifts strictly increase (at most 31).
+ *   The network then has n_in = SINN_KP_FEATURES + 1 inputs: the query's
+ *   features followed by -shift[l], and its output for that row is log2 of
+ *   that level's k'.
+ *   k'_l = max(ceil(2^(output + margin)), k_prime_min); the level is
+ *   feasible when k'_l <= k_prime_max.  The feasible level of least
+ *   posting_cost * (its postings) + k'_l is chosen (ties: the earlier level,
+ *   the larger budget); when no level is feasible, level 0 at k_prime_max.
+ *   posting_cost is the time of scoring one posting in units of the time of
+ *   re-ranking one candidate (a measured ratio).
+ * With a policy set, sinn_search_learned, sinn_search_learned_ctx and
+ * learned plans search with the chosen per-query k' and budget (the re-rank
+ * always takes every term).  Set the policy before sizing activation
+ * buffers with sinn_mlp_act_bytes. */
+#define SINN_KP_MAX_LEVELS 8
+typedef struct sinn_kp_policy {
+  uint32_t n_levels;                   /* 1..SINN_KP_MAX_LEVELS */
+  uint32_t shift[SINN_KP_MAX_LEVELS];  /* budget P_q / 2^shift[l]; shift[0] = 0 */
+  float posting_cost;                  /* >= 0: one posting's cost in candidates */
+  float margin;                        /* added to every predicted log2 k' */
+} sinn_kp_policy;
+
+/* Set (p != NULL) or clear (p == NULL) the network's policy.  EINVAL for a
+ * malformed policy or a network without SINN_KP_FEATURES + 1 inputs. */
+int sinn_mlp_set_policy(sinn_mlp *m, const sinn_kp_policy *p);
+
+/* The current policy into *out (n_levels = 0: none). */
+int sinn_mlp_get_policy(sinn_mlp *m, sinn_kp_policy *out);
+
+/* The learned search's choice alone: features, network and (with a policy)
+ * the level choice for n_q queries (device CSR), into device
+ * out_kprime[n_q] and, nullable, device out_budget[n_q] (Alg. 6 budgets in
+ * postings, 0 = the whole query; all 0 without a policy).  Searching with
+ * sinn_search_kpb at these values gives sinn_search_learned's results. */
+int sinn_kp_choose(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
+                   const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                   uint32_t k_prime_min, uint32_t k_prime_max, uint32_t *out_kprime,
+                   uint64_t *out_budget, void *stream);
+
+/* sinn_search_learned with every buffer in host memory (queries as CSR, the
+ * results and, nullable, the k' per query): the call copies the queries to
+ * the device, searches, copies the results back and waits for them; device
+ * errors are returned directly. */
+int sinn_search_learned_host(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
+                             const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                             uint32_t k, uint32_t k_prime_min, uint32_t k_prime_max,
+                             uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
+                             void *stream);
 
 /* Device bytes of the activation buffer sinn_search_learned_ctx needs for
  * n_q queries. */

@@ -286,6 +286,40 @@ class OracleIndex:
             res.update(cand_ids=ci[:nq], cand_scores=cs[:nq], cand_mag=cm[:nq])
         return res
 
+    def search_per_query(self, indptr, indices, values, k: int, k_primes, budgets,
+                         candidates: bool = False):
+        """Alg. 6 + Alg. 7 with query r's own k' (k_primes[r]) and anytime
+        budget (budgets[r] postings, 0 = none): one oracle search per query
+        (small cases).  Candidate rows are padded to the largest k'."""
+        ip = np.asarray(indptr, np.uint64)
+        nq = ip.size - 1
+        kpm = int(max(k_primes)) if nq else k
+        ids = np.zeros((nq, k), np.uint32)
+        sc = np.zeros((nq, k), np.float64)
+        cnt = np.zeros(nq, np.uint32)
+        ci = np.full((nq, kpm), 0xFFFFFFFF, np.uint32)
+        cs = np.full((nq, kpm), -np.inf, np.float64)
+        cm = np.zeros((nq, kpm), np.float64)
+        for r in range(nq):
+            a, b = int(ip[r]), int(ip[r + 1])
+            one = self.search(np.array([0, b - a], np.uint64), indices[a:b], values[a:b], k=k,
+                              k_prime=int(k_primes[r]), candidates=candidates,
+                              budget=int(budgets[r]))
+            ids[r], sc[r], cnt[r] = one["ids"][0], one["scores"][0], one["count"][0]
+            if candidates:
+                kp = int(k_primes[r])
+                ci[r, :kp], cs[r, :kp], cm[r, :kp] = (one["cand_ids"][0], one["cand_scores"][0],
+                                                      one["cand_mag"][0])
+        res = {"ids": ids, "scores": sc, "count": cnt}
+        if candidates:
+            res.update(cand_ids=ci, cand_scores=cs, cand_mag=cm)
+        return res
+
+    def query_postings(self, qi, qv) -> int:
+        """Postings Alg. 6 visits with no budget: the sum of |I[j]| (live ids)
+        over the query's non-zeros."""
+        return int(sum(self.inverted_list(int(j)).size for j, v in zip(qi, qv) if v != 0))
+
     def exact_topk(self, indptr, indices, values, k: int, threads: int = 1):
         ip, ix, vv = _csr(indptr, indices, values)
         nq = ip.size - 1

@@ -63,3 +63,73 @@ def grad(p, X, t, tau, mean, std, n_in, hidden):
     db1 = dZ1.sum(axis=0)
     g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, db3])
     return g, pinball(y, t, tau)
+
+
+def _amb(Z, Zabs, eps):
+    """Pre-activations whose sign a perturbation of relative size eps (of the
+    magnitude Zabs of their terms) could flip."""
+    return np.abs(Z) <= eps * Zabs
+
+
+def error_bounds(p, X, t, tau, mean, std, n_in, hidden, eps):
+    """Per-element error budget of a reduced-precision evaluation of the
+    network, its loss gradient and its output, against this module's FP64
+    values, written out layer by layer as the FP64 forward and backward
+    passes are.  An evaluation whose operands and intermediate values carry
+    relative errors up to eps (of the magnitude of the terms summed into
+    them) is wrong by at most about a small multiple of eps times the
+    magnitude below, plus the flip allowance:
+
+      magnitude: the same passes over absolute values -- |standardised X|,
+        |W|, |b|, |dy| -- with every unit counted whose ReLU is active or
+        could be flipped by such errors (|Z| <= eps * its magnitude); it is
+        the sum of |terms| behind each output and gradient element;
+      flip allowance: a ReLU whose sign such errors could flip may pass or
+        block its whole gradient term, so the terms routed through those
+        units (and through rows whose pinball residual t - y could change
+        sign) enter at full magnitude.
+
+    Returns (y_mag [B], g_mag [P], g_flip [P]) in the flat parameter order."""
+    W1, b1, W2, b2, w3, b3 = unpack(p, n_in, hidden)
+    y, (Xn, Z1, H1, Z2, H2) = forward(p, X, mean, std, n_in, hidden)
+    B = y.size
+    aX = np.abs(Xn)
+    Z1a = aX @ np.abs(W1).T + np.abs(b1)
+    a1 = _amb(Z1, Z1a, eps)
+    on1 = (Z1 > 0) | a1                       # units that may carry a value
+    H1a = Z1a * on1
+    Z2a = H1a @ np.abs(W2).T + np.abs(b2)
+    a2 = _amb(Z2, Z2a, eps)
+    on2 = (Z2 > 0) | a2
+    H2a = Z2a * on2
+    ya = H2a @ np.abs(w3) + abs(b3[0])
+    u = np.asarray(t, np.float64) - y
+    ay = np.abs(u) <= eps * (ya + np.abs(np.asarray(t, np.float64)))
+    dya = np.full(B, max(tau, 1.0 - tau) / B)
+    dyf = np.where(ay, 1.0 / B, 0.0)          # a residual sign flip moves dy by 1/B
+
+    def pack(dW1, db1, dW2, db2, dw3, db3):
+        return np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, db3])
+
+    def back(dyv):
+        # the backward pass over absolute values, rows weighted by dyv
+        dZ2 = np.outer(dyv, np.abs(w3)) * on2
+        dH1 = dZ2 @ np.abs(W2)
+        dZ1 = dH1 * on1
+        return pack(dZ1.T @ aX, dZ1.sum(axis=0), dZ2.T @ H1a, dZ2.sum(axis=0), H2a.T @ dyv,
+                    np.array([dyv.sum()])), dH1
+
+    g_mag, dH1a = back(dya)
+    # flip allowance: (a) rows whose residual sign may flip, through every
+    # carried unit; (b) layer-2 units that may flip: their whole dZ2 term and
+    # what it feeds below; (c) layer-1 units that may flip: their whole dZ1
+    # term
+    fa, _ = back(dyf)
+    dZ2f = np.outer(dya, np.abs(w3)) * a2
+    dZ1b = (dZ2f @ np.abs(W2)) * on1
+    fb = pack(dZ1b.T @ aX, dZ1b.sum(axis=0), dZ2f.T @ H1a, dZ2f.sum(axis=0), np.zeros(hidden),
+              np.zeros(1))
+    dZ1c = dH1a * a1
+    fc = pack(dZ1c.T @ aX, dZ1c.sum(axis=0), np.zeros((hidden, hidden)), np.zeros(hidden),
+              np.zeros(hidden), np.zeros(1))
+    return ya, g_mag, fa + fb + fc

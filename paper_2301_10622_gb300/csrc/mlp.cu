@@ -423,6 +423,54 @@ __global__ void k_kprime(const float *y, uint32_t B, uint32_t lo, uint32_t hi, u
   kp[i] = min(max((uint32_t)ceilf(v), lo), hi);
 }
 
+// Network inputs of the budget levels: row q*L + l is query q's features
+// followed by the level's input, -shift[l] (log2 of its budget fraction).
+__global__ void k_level_rows(const float *F, uint32_t n_q, uint32_t L, sinn_kp_policy pol,
+                             float *X) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  constexpr uint32_t NI = SINN_KP_FEATURES + 1;
+  if (i >= (uint64_t)n_q * L * NI) return;
+  const uint64_t row = i / NI;
+  const uint32_t c = (uint32_t)(i % NI);
+  const uint64_t q = row / L;
+  const uint32_t l = (uint32_t)(row % L);
+  X[i] = c < SINN_KP_FEATURES ? F[q * SINN_KP_FEATURES + c] : -(float)pol.shift[l];
+}
+
+// The policy's choice per query (one thread each).  Level l scores the terms
+// of Alg. 6 until ceil(P_q / 2^shift[l]) postings are reached and needs
+// k'_l = ceil(2^(y[q*L+l] + margin)) (at least lo); it is feasible when
+// k'_l <= hi.  The feasible level of least cost posting_cost * postings +
+// k'_l wins (ties: the earlier level, the larger budget); with none
+// feasible, level 0 (the whole query) at k' = hi.  Budget 0 means the whole
+// query (no break).
+__global__ void k_policy(const float *y, const uint64_t *P, uint32_t n_q, sinn_kp_policy pol,
+                         uint32_t lo, uint32_t hi, uint32_t *kp, uint64_t *budget) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_q) return;
+  const uint64_t pq = P[q];
+  int best = -1;
+  float best_cost = 0.0f;
+  uint32_t best_kp = hi;
+  for (uint32_t l = 0; l < pol.n_levels; ++l) {
+    const float v = fminf(fmaxf(y[(uint64_t)q * pol.n_levels + l] + pol.margin, 0.0f), 31.0f);
+    const float need = ceilf(exp2f(v));
+    if (need > (float)hi) continue;
+    const uint32_t k_l = max((uint32_t)need, lo);
+    const uint32_t sh = pol.shift[l];
+    const uint64_t b = sh ? (pq + (1ull << sh) - 1) >> sh : pq;
+    const float cost = fmaf(pol.posting_cost, (float)b, (float)k_l);
+    if (best < 0 || cost < best_cost) {
+      best = (int)l;
+      best_cost = cost;
+      best_kp = k_l;
+    }
+  }
+  const uint32_t sh = best < 0 ? 0u : pol.shift[best];
+  kp[q] = best_kp;
+  budget[q] = sh ? (pq + (1ull << sh) - 1) >> sh : 0ull;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ model
@@ -441,6 +489,9 @@ struct sinn_mlp {
   uint32_t cap = 0;
   void *act = nullptr;
   bool bf16_fresh = false;
+  // budget levels (n_levels = 0: none; the network then predicts k' alone)
+  sinn_kp_policy policy{};
+  uint64_t version = 0;  // bumped when the policy changes (recorded searches)
 };
 
 namespace {
@@ -787,43 +838,222 @@ extern "C" int sinn_kp_features(sinn_index *ix, const uint64_t *q_indptr, const 
   return SINN_OK;
 }
 
+namespace {
+
+// Rows of the network per query: one per budget level, or one.
+uint32_t level_rows(const sinn_mlp *m) { return m->policy.n_levels ? m->policy.n_levels : 1u; }
+
+// Bytes of the activations of n_q queries (their level rows) plus the tail
+// the choice uses: features, postings, k' and budgets per query, and the
+// expanded network inputs.
+size_t learned_bytes(const sinn_mlp *m, uint32_t n_q) {
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t R = (size_t)n_q * level_rows(m);
+  return acts_bytes(m, R) + r((size_t)n_q * SINN_KP_FEATURES * 4) + r((size_t)n_q * 8) +
+         r((size_t)n_q * 4) + r((size_t)n_q * 8) + r(R * (SINN_KP_FEATURES + 1) * 4);
+}
+
+struct Choice {
+  uint32_t *kp;
+  uint64_t *budget;  // null without a policy
+};
+
+// Features, the network and the choice of k' (and with a policy the Alg. 6
+// budget) of n_q queries, on activations carved from `base` for their rows.
+int choose(sinn_index *ix, sinn_mlp *m, void *base, const uint64_t *q_indptr,
+           const uint32_t *q_indices, const float *q_values, uint32_t n_q, uint32_t kp_min,
+           uint32_t kp_max, cudaStream_t s, Choice *out) {
+  const uint32_t L = level_rows(m);
+  const size_t R = (size_t)n_q * L;
+  Acts a;
+  carve_acts(m, base, R, &a);
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  char *t = (char *)base + acts_bytes(m, R);
+  float *feat = (float *)t;
+  t += r((size_t)n_q * SINN_KP_FEATURES * 4);
+  uint64_t *P = (uint64_t *)t;
+  t += r((size_t)n_q * 8);
+  out->kp = (uint32_t *)t;
+  t += r((size_t)n_q * 4);
+  out->budget = m->policy.n_levels ? (uint64_t *)t : nullptr;
+  t += r((size_t)n_q * 8);
+  float *X = (float *)t;
+  int st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, s);
+  if (st) return st;
+  if ((st = refresh_bf16(m, s))) return st;
+  if (!m->policy.n_levels) {
+    if ((st = forward(m, feat, n_q, a, s, ix->d_err))) return st;
+    k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, kp_min, kp_max, out->kp);
+    CK(cudaGetLastError());
+    ix->launches += 8;
+    return SINN_OK;
+  }
+  if ((st = sinn_query_postings(ix, q_indptr, q_indices, q_values, n_q, P, s))) return st;
+  const uint64_t nx = R * (SINN_KP_FEATURES + 1);
+  k_level_rows<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(feat, n_q, L, m->policy, X);
+  if ((st = forward(m, X, (uint32_t)R, a, s, ix->d_err))) return st;
+  k_policy<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, P, n_q, m->policy, kp_min, kp_max, out->kp,
+                                             out->budget);
+  CK(cudaGetLastError());
+  ix->launches += 9;
+  return SINN_OK;
+}
+
+// The network's own activation buffer holds learned_bytes(n_q): rows enough
+// for the queries' level rows and, past them, the tail (under one row's bytes
+// per query).
+int ensure_learned(sinn_mlp *m, uint32_t n_q) {
+  const uint64_t need = learned_bytes(m, n_q);
+  if (m->act && acts_bytes(m, m->cap) >= need) return SINN_OK;
+  const uint64_t rows = (uint64_t)n_q * level_rows(m) + n_q + 64;
+  if (rows > 0xFFFFFFFFull) return SINN_EINVAL;
+  Acts a;
+  int st = ensure_acts(m, (uint32_t)rows, &a);
+  if (st) return st;
+  return acts_bytes(m, m->cap) >= need ? SINN_OK : SINN_ENOMEM;
+}
+
+bool learned_args_ok(sinn_index *ix, sinn_mlp *m, uint32_t k, uint32_t kp_min, uint32_t kp_max) {
+  if (!ix || !m) return false;
+  if (m->nin != SINN_KP_FEATURES + (m->policy.n_levels ? 1u : 0u)) return false;
+  if (m->hid < SINN_KP_FEATURES + 1) return false;
+  return k > 0 && kp_min >= k && kp_max >= kp_min;
+}
+
+}  // namespace
+
+extern "C" int sinn_mlp_set_policy(sinn_mlp *m, const sinn_kp_policy *p) {
+  if (!m) return SINN_EINVAL;
+  if (!p) {
+    m->policy = sinn_kp_policy{};
+    m->version++;
+    return SINN_OK;
+  }
+  if (p->n_levels == 0 || p->n_levels > SINN_KP_MAX_LEVELS || p->shift[0] != 0 ||
+      !(p->posting_cost >= 0.0f) || !std::isfinite(p->posting_cost) || !std::isfinite(p->margin))
+    return SINN_EINVAL;
+  for (uint32_t l = 1; l < p->n_levels; ++l)
+    if (p->shift[l] <= p->shift[l - 1] || p->shift[l] > 31) return SINN_EINVAL;
+  if (m->nin != SINN_KP_FEATURES + 1) return SINN_EINVAL;
+  m->policy = *p;
+  for (uint32_t l = p->n_levels; l < SINN_KP_MAX_LEVELS; ++l) m->policy.shift[l] = 0;
+  m->version++;
+  return SINN_OK;
+}
+
+extern "C" int sinn_mlp_get_policy(sinn_mlp *m, sinn_kp_policy *out) {
+  if (!m || !out) return SINN_EINVAL;
+  *out = m->policy;
+  return SINN_OK;
+}
+
+extern "C" int sinn_kp_choose(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
+                              const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                              uint32_t k_prime_min, uint32_t k_prime_max, uint32_t *out_kprime,
+                              uint64_t *out_budget, void *stream) {
+  if (!learned_args_ok(ix, m, 1, k_prime_min, k_prime_max) || k_prime_min == 0)
+    return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!q_indptr || !out_kprime) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_learned(m, n_q);
+  if (st) return st;
+  Choice c;
+  if ((st = choose(ix, m, m->act, q_indptr, q_indices, q_values, n_q, k_prime_min, k_prime_max,
+                   s, &c)))
+    return st;
+  CK(cudaMemcpyAsync(out_kprime, c.kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
+  if (out_budget) {
+    if (c.budget) CK(cudaMemcpyAsync(out_budget, c.budget, (size_t)n_q * 8, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemsetAsync(out_budget, 0, (size_t)n_q * 8, s));
+  }
+  return SINN_OK;
+}
+
 extern "C" int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
                                    const uint32_t *q_indices, const float *q_values, uint32_t n_q,
                                    uint32_t k, uint32_t k_prime_min, uint32_t k_prime_max,
                                    uint32_t *out_ids, float *out_scores, uint32_t *out_kprime,
                                    void *stream) {
-  if (!ix || !m || m->nin != SINN_KP_FEATURES) return SINN_EINVAL;
-  if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
+  if (!learned_args_ok(ix, m, k, k_prime_min, k_prime_max)) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
+  if (!q_indptr) return SINN_EINVAL;
   SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // features, prediction and k' live in the model's activation buffer tail
-  Acts a;
-  int st = ensure_acts(m, n_q, &a);
+  int st = ensure_learned(m, n_q);
   if (st) return st;
-  float *feat = a.dH1;                     // n_q x 19 <= n_q x hid floats
-  uint32_t *kp = (uint32_t *)a.dZ2;        // n_q
-  if (m->hid < SINN_KP_FEATURES) return SINN_EINVAL;
-  if ((st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream))) return st;
-  if ((st = forward(m, feat, n_q, a, s, ix->d_err))) return st;
-  k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
-  CK(cudaGetLastError());
-  ix->launches += 8;
-  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
-  return sinn_search_kp(ix, q_indptr, q_indices, q_values, n_q, k, kp, k_prime_max, out_ids,
-                        out_scores, stream);
+  Choice c;
+  if ((st = choose(ix, m, m->act, q_indptr, q_indices, q_values, n_q, k_prime_min, k_prime_max,
+                   s, &c)))
+    return st;
+  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, c.kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
+  return sinn_search_ext(ix, nullptr, q_indptr, q_indices, q_values, n_q, k, c.kp, k_prime_max,
+                         c.budget, out_ids, out_scores, s);
+}
+
+// sinn_search_learned over host buffers: queries copied to the index's
+// device staging buffer, searched, results copied back, then a wait.
+extern "C" int sinn_search_learned_host(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
+                                        const uint32_t *q_indices, const float *q_values,
+                                        uint32_t n_q, uint32_t k, uint32_t k_prime_min,
+                                        uint32_t k_prime_max, uint32_t *out_ids,
+                                        float *out_scores, uint32_t *out_kprime, void *stream) {
+  if (!learned_args_ok(ix, m, k, k_prime_min, k_prime_max) || k > SINN_MAX_K) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!q_indptr || !out_ids || !out_scores) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (q_indptr[n_q] < q_indptr[0]) return SINN_EINVAL;
+  const uint64_t nnz = q_indptr[n_q] - q_indptr[0];
+  if (nnz && (!q_indices || !q_values)) return SINN_EINVAL;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_ip = al(((size_t)n_q + 1) * 8), b_ix = al(nnz * 4), b_v = al(nnz * 4),
+               b_oi = al((size_t)n_q * k * 4), b_os = al((size_t)n_q * k * 4),
+               b_kp = al((size_t)n_q * 4);
+  const size_t need = b_ip + b_ix + b_v + b_oi + b_os + b_kp;
+  if (need > ix->hstage_size) {
+    if (ix->hstage) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaFree(ix->hstage));
+      ix->hstage = nullptr;
+      ix->hstage_size = 0;
+    }
+    CK(sinn_dev_malloc((void **)&ix->hstage, need));
+    ix->hstage_size = need;
+  }
+  char *p = (char *)ix->hstage;
+  uint64_t *d_ip = (uint64_t *)p;
+  uint32_t *d_ix = (uint32_t *)(p + b_ip);
+  float *d_v = (float *)(p + b_ip + b_ix);
+  uint32_t *d_oi = (uint32_t *)(p + b_ip + b_ix + b_v);
+  float *d_os = (float *)(p + b_ip + b_ix + b_v + b_oi);
+  uint32_t *d_kp = (uint32_t *)(p + b_ip + b_ix + b_v + b_oi + b_os);
+  // row pointers rebased to zero on the device side
+  std::vector<uint64_t> ip(q_indptr, q_indptr + n_q + 1);
+  const uint64_t base = ip[0];
+  for (auto &x : ip) x -= base;
+  CK(cudaMemcpyAsync(d_ip, ip.data(), ((size_t)n_q + 1) * 8, cudaMemcpyHostToDevice, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(d_ix, q_indices + base, nnz * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_v, q_values + base, nnz * 4, cudaMemcpyHostToDevice, s));
+  }
+  int st = sinn_search_learned(ix, m, d_ip, d_ix, d_v, n_q, k, k_prime_min, k_prime_max, d_oi,
+                               d_os, d_kp, stream);
+  if (st) {
+    cudaStreamSynchronize(s);  // the staged copies must not outlive the host vector
+    return st;
+  }
+  CK(cudaMemcpyAsync(out_ids, d_oi, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(out_scores, d_os, (size_t)n_q * k * 4, cudaMemcpyDeviceToHost, s));
+  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, d_kp, (size_t)n_q * 4, cudaMemcpyDeviceToHost, s));
+  return sinn_sync(ix, stream);
 }
 
 // sinn_search_learned on a context: the network's activations come from a
 // caller buffer (act, act_bytes) so concurrent contexts share one model.
-struct sinn_ctx;
-extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint32_t *q_indices,
-                               const float *q_values, uint32_t n_q, uint32_t k,
-                               const uint32_t *k_prime, uint32_t k_prime_max, uint32_t *out_ids,
-                               float *out_scores, void *stream);
-
 extern "C" uint64_t sinn_mlp_act_bytes(sinn_mlp *m, uint32_t rows) {
-  return m ? acts_bytes(m, rows) + (uint64_t)rows * (SINN_KP_FEATURES * 4 + 4) + 512 : 0;
+  return m ? learned_bytes(m, rows) + 512 : 0;
 }
 
 extern "C" int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m, void *act,
@@ -832,24 +1062,20 @@ extern "C" int sinn_search_learned_ctx(sinn_ctx *c, sinn_index *ix, sinn_mlp *m,
                                        uint32_t n_q, uint32_t k, uint32_t k_prime_min,
                                        uint32_t k_prime_max, uint32_t *out_ids, float *out_scores,
                                        uint32_t *out_kprime, void *stream) {
-  if (!c || !ix || !m || !act || m->nin != SINN_KP_FEATURES) return SINN_EINVAL;
-  if (k == 0 || k_prime_min < k || k_prime_max < k_prime_min) return SINN_EINVAL;
+  if (!c || !act || !learned_args_ok(ix, m, k, k_prime_min, k_prime_max)) return SINN_EINVAL;
   if (n_q == 0) return SINN_OK;
+  if (!q_indptr) return SINN_EINVAL;
   if (act_bytes < sinn_mlp_act_bytes(m, n_q)) return SINN_EINVAL;
   SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
-  Acts a;
-  carve_acts(m, act, n_q, &a);
-  char *tail = (char *)act + acts_bytes(m, n_q);
-  float *feat = (float *)tail;
-  uint32_t *kp = (uint32_t *)(tail + ((size_t)n_q * SINN_KP_FEATURES * 4 + 255) / 256 * 256);
-  int st = sinn_kp_features(ix, q_indptr, q_indices, q_values, n_q, feat, stream);
+  Choice ch;
+  int st = choose(ix, m, act, q_indptr, q_indices, q_values, n_q, k_prime_min, k_prime_max, s,
+                  &ch);
   if (st) return st;
-  if ((st = refresh_bf16(m, s))) return st;
-  if ((st = forward(m, feat, n_q, a, s, ix->d_err))) return st;
-  k_kprime<<<(n_q + 255) / 256, 256, 0, s>>>(a.y, n_q, k_prime_min, k_prime_max, kp);
-  CK(cudaGetLastError());
-  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
-  return sinn_search_ctx(c, q_indptr, q_indices, q_values, n_q, k, kp, k_prime_max, out_ids,
-                         out_scores, stream);
+  if (out_kprime) CK(cudaMemcpyAsync(out_kprime, ch.kp, (size_t)n_q * 4, cudaMemcpyDeviceToDevice, s));
+  return sinn_search_ext(ix, c, q_indptr, q_indices, q_values, n_q, k, ch.kp, k_prime_max,
+                         ch.budget, out_ids, out_scores, s);
 }
+
+// The network's version (bumped by a policy change), for recorded searches.
+uint64_t sinn_mlp_version(sinn_mlp *m) { return m ? m->version : 0; }

@@ -11,6 +11,7 @@
 #include "sinn_internal.cuh"
 
 int sinn_mlp_refresh(sinn_mlp *m, cudaStream_t s);  // mlp.cu
+uint64_t sinn_mlp_version(sinn_mlp *m);              // mlp.cu
 
 #define CK(x)                                          \
   do {                                                 \
@@ -35,6 +36,7 @@ struct sinn_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t version = ~0ull;   // index shape the recording belongs to
+  uint64_t mlp_version = 0;   // network policy the recording belongs to
   uint64_t launches = 0;      // kernels one replay runs
   uint64_t recordings = 0;
   std::vector<sinn_index::Span> spans;  // phase events recorded inside the graph
@@ -108,6 +110,7 @@ int record(sinn_plan *p) {
   p->spans = std::move(spans);
   p->launches = nl;
   p->version = ix->shape_version;
+  p->mlp_version = sinn_mlp_version(p->m);
   p->recordings++;
   return SINN_OK;
 }
@@ -166,13 +169,23 @@ extern "C" int sinn_plan_run(sinn_plan *p, void *stream) {
   SinnDevice dev_guard_(ix->device);
   cudaStream_t s = (cudaStream_t)stream;
   int st;
-  if (!p->exec || p->version != ix->shape_version) {
+  if (!p->exec || p->version != ix->shape_version || p->mlp_version != sinn_mlp_version(p->m)) {
     // the capture stream must see the caller's earlier work (index updates)
     cudaEvent_t ready;
     CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     CK(cudaEventRecord(ready, s));
     CK(cudaStreamWaitEvent(p->cs, ready, 0));
     cudaEventDestroy(ready);
+    if (p->m && sinn_mlp_act_bytes(p->m, p->n_q) > p->act_bytes) {
+      // a policy set since creation may want more network rows
+      CK(cudaStreamSynchronize(p->cs));
+      CK(cudaFree(p->act));
+      p->act = nullptr;
+      p->act_bytes = 0;
+      const uint64_t need = sinn_mlp_act_bytes(p->m, p->n_q);
+      CK(sinn_dev_malloc((void **)&p->act, need));
+      p->act_bytes = need;
+    }
     if ((st = record(p))) return st;
   }
   if (p->m && (st = sinn_mlp_refresh(p->m, s))) return st;

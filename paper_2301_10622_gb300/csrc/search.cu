@@ -107,8 +107,8 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
                         const float *__restrict__ q_val, uint32_t q0, uint32_t n, uint32_t qmax,
                         uint32_t kp_scalar, const uint32_t *__restrict__ kp_arr, uint32_t kp_min,
                         uint32_t kp_max, const uint64_t *live_count, Batch bt,
-                        const uint32_t *__restrict__ coord_len, uint64_t budget, int nonneg,
-                        uint32_t *err) {
+                        const uint32_t *__restrict__ coord_len, uint64_t budget,
+                        const uint64_t *__restrict__ budget_arr, int nonneg, uint32_t *err) {
   extern __shared__ uint32_t sq[];
   uint32_t *sj = sq;                  // qmax
   float *sv = (float *)(sq + qmax);   // qmax
@@ -148,11 +148,13 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     out[r].j = ji;
     out[r].v = sv[i];
   }
-  if (budget) __syncthreads();  // thread 0 reads the sorted terms
+  if (budget || budget_arr) __syncthreads();  // thread 0 reads the sorted terms
   if (threadIdx.x == 0) {
-    // Alg. 6's anytime break, the budget counted in postings: score the terms
-    // up to the first one at which the postings visited reach the budget (the
+    // Alg. 6's anytime break, the budget counted in postings (the index's, or
+    // this query's own when per-query budgets are given): score the terms up
+    // to the first one at which the postings visited reach the budget (the
     // re-rank still takes every term: Alg. 7's exact inner product)
+    if (budget_arr) budget = budget_arr[q];
     uint32_t scored = cnt;
     if (budget) {
       uint64_t visited = 0;
@@ -1229,6 +1231,7 @@ struct SearchReq {
   const float *q_val;
   uint32_t n_q, k, kp, kp_min, kp_max;
   const uint32_t *kp_arr;
+  const uint64_t *budget_arr;  // per-query Alg. 6 budgets (0 = none), or null: the index's
   uint32_t *out_ids;
   float *out_scores;
   uint32_t *out_count;
@@ -1313,6 +1316,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
                                                          ix->n, ix->max_qnnz, r.kp, r.kp_arr,
                                                          r.kp_min, r.kp_max, ix->d_live_count, bt,
                                                          ix->d_coord_len, ix->budget,
+                                                         r.budget_arr,
                                                          (ix->flags & SINN_FLAG_NONNEG) ? 1 : 0,
                                                          ix->d_err);
       CK(cudaGetLastError());
@@ -1703,6 +1707,114 @@ extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint
   r.out_scores = out_scores;
   r.stage = Stage::kFull;
   return run_search(ix, r, (cudaStream_t)stream, &fx);
+}
+
+// ------------------------------------------- per-query k' and Alg. 6 budget
+// One search with a per-query k' (or k_prime_max for all) and a per-query
+// anytime budget (or the index's), on a context's scratch or the index's own.
+int sinn_search_ext(sinn_index *ix, sinn_ctx *c, const uint64_t *q_indptr,
+                    const uint32_t *q_indices, const float *q_values, uint32_t n_q, uint32_t k,
+                    const uint32_t *k_prime, uint32_t k_prime_max, const uint64_t *budget,
+                    uint32_t *out_ids, float *out_scores, cudaStream_t s) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k == 0 || k > SINN_MAX_K || k_prime_max < k) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = k;
+  r.kp = k_prime_max;
+  r.kp_arr = k_prime;
+  r.kp_min = k;
+  r.kp_max = k_prime_max;
+  r.budget_arr = budget;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.stage = Stage::kFull;
+  if (!c) return run_search(ix, r, s);
+  FixedScratch fx{c->scratch, c->bytes};
+  return run_search(ix, r, s, &fx);
+}
+
+extern "C" int sinn_search_kpb(sinn_index *ix, const uint64_t *q_indptr,
+                               const uint32_t *q_indices, const float *q_values, uint32_t n_q,
+                               uint32_t k, const uint32_t *k_prime, uint32_t k_prime_max,
+                               const uint64_t *budget, uint32_t *out_ids, float *out_scores,
+                               void *stream) {
+  return sinn_search_ext(ix, nullptr, q_indptr, q_indices, q_values, n_q, k, k_prime,
+                         k_prime_max, budget, out_ids, out_scores, (cudaStream_t)stream);
+}
+
+extern "C" int sinn_candidates_kpb(sinn_index *ix, const uint64_t *q_indptr,
+                                   const uint32_t *q_indices, const float *q_values,
+                                   uint32_t n_q, uint32_t k_prime, const uint64_t *budget,
+                                   uint32_t *out_ids, float *out_scores, uint32_t *out_count,
+                                   void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (k_prime == 0) return SINN_EINVAL;
+  if (n_q == 0) return SINN_OK;
+  if (!out_ids || !out_scores || !out_count) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  SearchReq r{};
+  r.q_indptr = q_indptr;
+  r.q_idx = q_indices;
+  r.q_val = q_values;
+  r.n_q = n_q;
+  r.k = 1;
+  r.kp = k_prime;
+  r.kp_min = 1;
+  r.kp_max = k_prime;
+  r.budget_arr = budget;
+  r.out_ids = out_ids;
+  r.out_scores = out_scores;
+  r.out_count = out_count;
+  r.stage = Stage::kCandidates;
+  return run_search(ix, r, (cudaStream_t)stream);
+}
+
+namespace {
+// P_q = sum over the query's non-zeros of |I[j]| (live postings): what Alg. 6
+// visits with no budget.  One warp per query; a malformed row gives 0.
+__global__ void k_query_postings(const uint64_t *__restrict__ ip, const uint32_t *__restrict__ idx,
+                                 const float *__restrict__ val, uint32_t n_q, uint32_t n,
+                                 const uint32_t *__restrict__ coord_len, uint64_t *out) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= n_q) return;
+  const uint64_t s = ip[q], e = ip[q + 1];
+  uint64_t sum = 0;
+  bool bad = e < s;
+  for (uint64_t p = s + lane; !bad && p < e; p += 32) {
+    const uint32_t j = idx[p];
+    const float v = val[p];
+    if (j >= n || !isfinite(v) || (p > s && idx[p - 1] >= j)) bad = true;
+    else if (v != 0.0f) sum += coord_len[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+  bad = __any_sync(0xFFFFFFFFu, bad);
+  if (lane == 0) out[q] = bad ? 0ull : sum;
+}
+}  // namespace
+
+extern "C" int sinn_query_postings(sinn_index *ix, const uint64_t *q_indptr,
+                                   const uint32_t *q_indices, const float *q_values,
+                                   uint32_t n_q, uint64_t *out, void *stream) {
+  int st = check_query_args(ix, q_indptr, n_q);
+  if (st) return st;
+  if (n_q == 0) return SINN_OK;
+  if (!out) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  ix->launches++;
+  k_query_postings<<<(unsigned)(((uint64_t)n_q * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      q_indptr, q_indices, q_values, n_q, ix->n, ix->d_coord_len, out);
+  CK(cudaGetLastError());
+  return SINN_OK;
 }
 
 // ------------------------------------------------------------------ tuning

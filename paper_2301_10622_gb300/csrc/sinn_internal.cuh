@@ -159,6 +159,15 @@ int sinn_ensure_scratch(sinn_index *ix, size_t bytes);
 int sinn_ensure_pinned(sinn_index *ix, size_t bytes);
 int sinn_check_cuda(cudaError_t e);
 
+struct sinn_ctx;
+// sinn_search with a per-query k' (k_prime null: k_prime_max for every query)
+// and a per-query Alg. 6 budget in postings (budget null: the index's), on a
+// context's scratch (c) or, c null, the index's own (search.cu).
+int sinn_search_ext(sinn_index *ix, sinn_ctx *c, const uint64_t *q_indptr,
+                    const uint32_t *q_indices, const float *q_values, uint32_t n_q, uint32_t k,
+                    const uint32_t *k_prime, uint32_t k_prime_max, const uint64_t *budget,
+                    uint32_t *out_ids, float *out_scores, cudaStream_t s);
+
 // ---------------------------------------------------------- device helpers
 // Order-preserving map from float to uint32 (for all non-NaN values: a < b as
 // floats iff key(a) < key(b) as unsigned integers).

@@ -36,17 +36,28 @@ EXPORTS = [
     "sinn_search_noalloc", "sinn_ctx_create", "sinn_ctx_destroy", "sinn_ctx_query_bytes",
     "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
     "sinn_set_budget", "sinn_get_budget", "sinn_save", "sinn_load", "sinn_debug_fail_alloc",
-    "sinn_debug_wait_probe",
+    "sinn_debug_wait_probe", "sinn_search_kpb", "sinn_candidates_kpb", "sinn_query_postings",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
     "sinn_mlp_grad", "sinn_mlp_train_step", "sinn_search_learned", "sinn_mlp_act_bytes",
-    "sinn_search_learned_ctx", "sinn_mlp_sync",
+    "sinn_search_learned_ctx", "sinn_mlp_sync", "sinn_mlp_set_policy", "sinn_mlp_get_policy",
+    "sinn_kp_choose", "sinn_search_learned_host",
     # sinnamon_plan.h
     "sinn_plan_create", "sinn_plan_run", "sinn_plan_recordings", "sinn_plan_destroy",
 ]
 
 KP_FEATURES = 19
+KP_MAX_LEVELS = 8
+
+
+class SinnKpPolicy(C.Structure):
+    _fields_ = [("n_levels", C.c_uint32), ("shift", C.c_uint32 * KP_MAX_LEVELS),
+                ("posting_cost", C.c_float), ("margin", C.c_float)]
+
+    def as_dict(self):
+        return {"shifts": [int(self.shift[i]) for i in range(self.n_levels)],
+                "posting_cost": float(self.posting_cost), "margin": float(self.margin)}
 
 PHASES = ["prep", "score", "select", "rerank", "insert", "delete"]
 
@@ -175,6 +186,14 @@ def load(build_if_missing: bool = False):
         "sinn_set_tuning": ([vp, C.POINTER(SinnTuning)], C.c_int),
         "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
                           C.c_int),
+        "sinn_search_kpb": ([vp, vp, vp, vp, u32, u32, vp, u32, vp, vp, vp, vp], C.c_int),
+        "sinn_candidates_kpb": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp, vp], C.c_int),
+        "sinn_query_postings": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
+        "sinn_mlp_set_policy": ([vp, C.POINTER(SinnKpPolicy)], C.c_int),
+        "sinn_mlp_get_policy": ([vp, C.POINTER(SinnKpPolicy)], C.c_int),
+        "sinn_kp_choose": ([vp, vp, vp, vp, vp, u32, u32, u32, vp, vp, vp], C.c_int),
+        "sinn_search_learned_host": ([vp, vp, vp, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp],
+                                     C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +286,65 @@ def sinn_search_kp(ix, q_indptr, q_indices, q_values, k, k_prime, k_prime_max, o
     _check(load().sinn_search_kp(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
                                  _p(k_prime), k_prime_max, _p(out_ids), _p(out_scores),
                                  _s(stream)), "sinn_search_kp")
+
+
+def sinn_search_kpb(ix, q_indptr, q_indices, q_values, k, k_prime, k_prime_max, budget,
+                    out_ids, out_scores, stream=None):
+    """Per-query k' (int32 tensor or None) and per-query Alg. 6 budget in
+    postings (int64 tensor or None)."""
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_search_kpb(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q, k,
+                                  _p(k_prime), k_prime_max, _p(budget), _p(out_ids),
+                                  _p(out_scores), _s(stream)), "sinn_search_kpb")
+
+
+def sinn_candidates_kpb(ix, q_indptr, q_indices, q_values, k_prime, budget, out_ids, out_scores,
+                        out_count, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_candidates_kpb(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q,
+                                      k_prime, _p(budget), _p(out_ids), _p(out_scores),
+                                      _p(out_count), _s(stream)), "sinn_candidates_kpb")
+
+
+def sinn_query_postings(ix, q_indptr, q_indices, q_values, out, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_query_postings(ix, _p(q_indptr), _p(q_indices), _p(q_values), n_q,
+                                      _p(out), _s(stream)), "sinn_query_postings")
+
+
+def sinn_mlp_set_policy(mlp, shifts=None, posting_cost: float = 0.0, margin: float = 0.0):
+    """shifts None clears the policy."""
+    if shifts is None:
+        _check(load().sinn_mlp_set_policy(mlp, None), "sinn_mlp_set_policy")
+        return
+    pol = SinnKpPolicy(n_levels=len(shifts), posting_cost=posting_cost, margin=margin)
+    for i, v in enumerate(shifts):
+        pol.shift[i] = int(v)
+    _check(load().sinn_mlp_set_policy(mlp, C.byref(pol)), "sinn_mlp_set_policy")
+
+
+def sinn_mlp_get_policy(mlp) -> dict:
+    pol = SinnKpPolicy()
+    _check(load().sinn_mlp_get_policy(mlp, C.byref(pol)), "sinn_mlp_get_policy")
+    return pol.as_dict()
+
+
+def sinn_kp_choose(ix, mlp, q_indptr, q_indices, q_values, kp_min, kp_max, out_kprime,
+                   out_budget, stream=None):
+    n_q = q_indptr.numel() - 1
+    _check(load().sinn_kp_choose(ix, mlp, _p(q_indptr), _p(q_indices), _p(q_values), n_q,
+                                 kp_min, kp_max, _p(out_kprime), _p(out_budget), _s(stream)),
+           "sinn_kp_choose")
+
+
+def sinn_search_learned_host(ix, mlp, q_indptr, q_indices, q_values, k, kp_min, kp_max,
+                             out_ids, out_scores, out_kprime=None, stream=None):
+    """All buffers host (numpy arrays or CPU tensors); waits for completion."""
+    n_q = (q_indptr.numel() if isinstance(q_indptr, torch.Tensor) else q_indptr.size) - 1
+    _check(load().sinn_search_learned_host(ix, mlp, _p(q_indptr), _p(q_indices), _p(q_values),
+                                           n_q, k, kp_min, kp_max, _p(out_ids), _p(out_scores),
+                                           _p(out_kprime), _s(stream)),
+           "sinn_search_learned_host")
 
 
 def sinn_search_noalloc(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
@@ -554,6 +632,14 @@ class MLP:
         """Waits for the stream; raises if a GEMM's bounded wait ran out."""
         _check(load().sinn_mlp_sync(self._h, _s(stream)), "sinn_mlp_sync")
 
+    def set_policy(self, shifts=None, posting_cost: float = 0.0, margin: float = 0.0):
+        """Budget levels P_q / 2^shift (shifts[0] = 0) chosen per query by
+        least posting_cost * postings + k'; None clears the policy."""
+        sinn_mlp_set_policy(self._h, shifts, posting_cost, margin)
+
+    def policy(self) -> dict:
+        return sinn_mlp_get_policy(self._h)
+
 
 def sinn_debug_fail_alloc(after: int):
     """The library's allocation after `after` more successful ones fails
@@ -664,6 +750,44 @@ class Index:
 
     def hash_table(self) -> np.ndarray:
         return sinn_hash_table(self._h, self.n, self.h)
+
+    def search_kpb(self, indptr, indices, values, k: int, k_prime=None, k_prime_max: int = 0,
+                   budget=None, stream=None):
+        """Search with per-query k' (None: k_prime_max for all) and per-query
+        Alg. 6 budgets in postings (None: the index's budget)."""
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        ids = torch.empty((nq, k), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nq, k), dtype=torch.float32, device=self.device)
+        kp = None if k_prime is None else _dev(k_prime, torch.int32, self.device)
+        bd = None if budget is None else _dev(budget, torch.int64, self.device)
+        sinn_search_kpb(self._h, ip, ix, v, k, kp, int(k_prime_max), bd, ids, sc, stream)
+        return ids, sc
+
+    def candidates_kpb(self, indptr, indices, values, k_prime: int, budget=None, stream=None):
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        ids = torch.empty((nq, k_prime), dtype=torch.int32, device=self.device)
+        sc = torch.empty((nq, k_prime), dtype=torch.float32, device=self.device)
+        cnt = torch.empty(nq, dtype=torch.int32, device=self.device)
+        bd = None if budget is None else _dev(budget, torch.int64, self.device)
+        sinn_candidates_kpb(self._h, ip, ix, v, k_prime, bd, ids, sc, cnt, stream)
+        return ids, sc, cnt
+
+    def query_postings(self, indptr, indices, values, stream=None) -> torch.Tensor:
+        ip, ix, v = self._csr(indptr, indices, values)
+        out = torch.empty(ip.numel() - 1, dtype=torch.int64, device=self.device)
+        sinn_query_postings(self._h, ip, ix, v, out, stream)
+        return out
+
+    def kp_choose(self, mlp, indptr, indices, values, kp_min: int, kp_max: int, stream=None):
+        """The learned search's (k', budget) per query."""
+        ip, ix, v = self._csr(indptr, indices, values)
+        nq = ip.numel() - 1
+        kp = torch.empty(nq, dtype=torch.int32, device=self.device)
+        bd = torch.empty(nq, dtype=torch.int64, device=self.device)
+        sinn_kp_choose(self._h, mlp.handle, ip, ix, v, kp_min, kp_max, kp, bd, stream)
+        return kp, bd
 
     def kp_features(self, indptr, indices, values, stream=None) -> torch.Tensor:
         ip, ix, v = self._csr(indptr, indices, values)

@@ -1,8 +1,8 @@
 """Host logic of bench.py (no GPU): the algorithmic byte count behind the
-roofline, the oracle's reconstruction of the streamed collection, the
-comment-insensitive source hash that ties a profile to the kernel it
-measured, the traffic scaling read from that profile, and the clock
-sampler's parsing."""
+roofline (postings scored under the anytime break), the oracle's
+reconstruction of the streamed collection, the comment-insensitive source
+hash that ties a profile to the kernel it measured, the figures and traffic
+scaling read from that profile, and the clock sampler's parsing."""
 import os
 
 import numpy as np
@@ -26,13 +26,23 @@ def test_algorithmic_bytes_by_hand():
     # |I[0]| = 2, |I[1]| = 1 (an explicit zero is not a posting), |I[3]| = 3
     docs = _csr([[(0, 1.0), (3, 2.0)], [(0, -1.0), (1, 0.0), (3, 1.0)], [(1, 5.0), (3, 4.0)]])
     qs = _csr([[(0, 1.0), (3, -2.0)], [(1, 0.0), (2, 1.0)], []])
-    cap, tiles = 4096, 1
-    per_q, P = bench.algorithmic_bytes(w, docs, qs, cap, tiles)
+    lens = bench.list_lengths(w, docs)
+    assert list(lens) == [2, 1, 0, 3, 0]
+    P = bench.scored_postings(qs, lens)
     assert list(P) == [5, 0, 0]  # the zero-valued query term reads no list
-    fixed = 4 * cap + cap / 8
-    assert per_q[0] == 5 * (2 + 4 * 2) + fixed + 8 * tiles * 2
-    assert per_q[1] == 0 + fixed + 8 * tiles * 1
-    assert per_q[2] == fixed
+    # 4-byte id + h = 2 four-byte bins per posting
+    assert list(bench.algorithmic_bytes(w, P)) == [5 * 12, 0, 0]
+
+
+def test_scored_postings_follow_the_anytime_break():
+    """Terms in Alg. 6 order (|q_j| descending, ties j ascending); scoring
+    stops after the first term at which the postings reach the budget."""
+    lens = np.array([10, 20, 30, 40, 50], np.int64)
+    # |q|: coord 4 (3.0) > coord 1 (2.0) = coord 3 (-2.0) > coord 0 (0.5)
+    qs = _csr([[(0, 0.5), (1, 2.0), (3, -2.0), (4, 3.0)]] * 5)
+    got = bench.scored_postings(qs, lens, np.array([0, 1, 50, 51, 10 ** 6]))
+    # order 4 (50), 1 (20), 3 (40), 0 (10): running 50, 70, 110, 120
+    assert list(got) == [120, 50, 50, 70, 120]
 
 
 def test_reconstruct_matches_the_id_reuse_rule():
@@ -71,24 +81,29 @@ def test_source_hash_ignores_comments_only(tmp_path):
     assert bench.source_code_hash(str(a)) != h
 
 
-def test_measured_traffic_scales_and_checks_its_source(tmp_path, monkeypatch):
+def test_profile_figures_scale_and_check_their_source(tmp_path, monkeypatch):
     src = tmp_path / "paper_2301_10622_gb300" / "csrc"
     src.mkdir(parents=True)
     (src / "search.cu").write_text("__global__ void k() {}\n")
     (tmp_path / "profiles").mkdir()
     h = bench.source_code_hash(str(src / "search.cu"))
     prof = tmp_path / "profiles" / "k_score_emit_text.md"
-    prof.write_text(f"source_code_sha256_16: {h}\ntraffic_bytes_per_launch: 1000000\n"
-                    "queries_per_launch: 100\ndocs_in_index: 5000\n")
+    prof.write_text(f"# title: words\nsource_code_sha256_16: {h}\n"
+                    "traffic_bytes_per_launch: 1000000\nqueries_per_launch: 100\n"
+                    "docs_in_index: 5000\nl2_throughput_frac: 0.5\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    # 4 launches of 50 queries: half the queries per launch, half the bytes
-    assert bench.measured_traffic(4, 200, 5000) == pytest.approx(500000.0)
-    assert bench.measured_traffic(0, 200, 5000) is None
-    assert bench.measured_traffic(4, 200, 6000) is None          # another index size
+    fig = bench.profile_figures("k_score_emit_text")
+    assert fig["traffic_bytes_per_launch"] == 1e6 and fig["docs_in_index"] == 5000
+    # 50 queries per launch: half the bytes; 1 ms per launch at 1000 GB/s peak
+    d = bench.dram_figures(fig, 1.0, 1000.0, 50, 5000)
+    assert d["traffic"] == pytest.approx(500000.0)
+    assert d["dram_frac"] == pytest.approx(500000.0 / 1e-3 / 1e9 / 1000.0)
+    assert d["l2_frac"] == 0.5 and d["l1_frac"] is None
+    assert bench.dram_figures(fig, 1.0, 1000.0, 50, 6000)["traffic"] is None  # another size
     (src / "search.cu").write_text("__global__ void k() { int x; }\n")
-    assert bench.measured_traffic(4, 200, 5000) is None          # the kernel changed
+    assert bench.profile_figures("k_score_emit_text") is None                  # kernel changed
     os.remove(prof)
-    assert bench.measured_traffic(4, 200, 5000) is None
+    assert bench.profile_figures("k_score_emit_text") is None
 
 
 def test_clock_summary_reads_throttle_reasons():

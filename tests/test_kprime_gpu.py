@@ -20,44 +20,50 @@ def _lib():
     __graft_entry__.build()
 
 
-def _blocks(n_in, hid):
-    sizes = [hid * n_in, hid, hid * hid, hid, hid, 1]
-    return np.cumsum([0] + sizes)
+# bf16 keeps 8 significant bits: each operand the GEMMs read (inputs, weights,
+# hidden activations, back-propagated terms) carries a relative rounding
+# error of at most 2^-8; accumulation is fp32
+U_BF16 = 2.0 ** -8
 
 
-@pytest.mark.parametrize("B", [300, 64, 1])
-def test_network_forward_and_gradient_match_fp64(B):
-    """GEMMs run in bf16 with fp32 accumulation: outputs and each parameter
-    block's gradient agree with the FP64 reference to bf16 accuracy."""
-    n_in, hid = sinnamon.KP_FEATURES, 256
+@pytest.mark.parametrize("B,n_in", [(300, sinnamon.KP_FEATURES), (64, sinnamon.KP_FEATURES),
+                                    (1, sinnamon.KP_FEATURES), (200, sinnamon.KP_FEATURES + 1)])
+def test_network_forward_and_gradient_match_fp64(B, n_in):
+    """Element by element: each output and each parameter's gradient is
+    within 4 * 2^-8 of the magnitude of its terms (the sum of their absolute
+    values, from the FP64 reference over |W|, |X|, |dy|) of the FP64 value,
+    plus the full terms routed through ReLUs whose sign that error could flip
+    (oracle.mlp.error_bounds)."""
+    hid = 256
     net = sinnamon.MLP(n_in, hid, seed=3)
     rng = np.random.default_rng(B)
     X = rng.normal(2.0, 3.0, (B, n_in)).astype(np.float32)
-    t = rng.normal(0.5, 1.0, B).astype(np.float32)
     mean, std = X.mean(0), X.std(0) + 1e-3
     if B == 1:
         mean, std = np.zeros(n_in, np.float32), np.ones(n_in, np.float32)
     net.set_normalizer(mean, std)
     p = net.params()
-    y = net.forward(X).cpu().numpy()
-    y_ref, _ = omlp.forward(p, X, mean.astype(np.float64), std.astype(np.float64), n_in, hid)
-    scale = np.abs(y_ref).max() + 1e-3
-    assert np.max(np.abs(y - y_ref)) <= 2e-2 * scale
+    m64, s64 = mean.astype(np.float64), std.astype(np.float64)
+    y = net.forward(X).cpu().numpy().astype(np.float64)
+    y_ref, _ = omlp.forward(p, X, m64, s64, n_in, hid)
+    # targets away from the outputs: no residual changes sign under rounding
+    t = (y_ref + np.where(rng.random(B) < 0.5, -1.0, 1.0) * (0.5 + rng.random(B))).astype(np.float32)
+    eps = 4 * U_BF16
+    ya, gm, gf = omlp.error_bounds(p, X, t, 0.9, m64, s64, n_in, hid, eps)
+    bad = np.abs(y - y_ref) > eps * ya
+    assert not bad.any(), (np.nonzero(bad)[0][:5], y[bad][:5], y_ref[bad][:5])
     g, loss = net.grad(X, t, 0.9)
-    g = g.cpu().numpy()
-    g_ref, l_ref = omlp.grad(p, X, t, 0.9, mean.astype(np.float64), std.astype(np.float64),
-                             n_in, hid)
-    assert abs(float(loss.item()) - l_ref) <= 2e-2 * abs(l_ref) + 1e-4
-    cut = _blocks(n_in, hid)
-    for a, b in zip(cut[:-1], cut[1:]):
-        ga, gr = g[a:b], g_ref[a:b]
-        nr = np.linalg.norm(gr)
-        if nr < 1e-9:
-            assert np.linalg.norm(ga) < 1e-6
-            continue
-        cos = float(ga @ gr / (np.linalg.norm(ga) * nr))
-        assert cos > 0.995, (a, b, cos)
-        assert np.linalg.norm(ga - gr) <= 5e-2 * nr, (a, b)
+    g = g.cpu().numpy().astype(np.float64)
+    g_ref, l_ref = omlp.grad(p, X, t, 0.9, m64, s64, n_in, hid)
+    assert abs(float(loss.item()) - l_ref) <= eps * np.mean(np.abs(t - y_ref) + ya) + 1e-6
+    err = np.abs(g - g_ref)
+    lim = eps * gm + gf + 1e-12
+    bad = err > lim
+    assert not bad.any(), (np.nonzero(bad)[0][:5], err[bad][:5], lim[bad][:5])
+    # the limit stays a small fraction of the magnitude on average (ReLU
+    # flips are rare): the check is not vacuous
+    nz = gm > 0
+    assert np.mean(lim[nz] / gm[nz]) < 0.25
 
 
 def test_training_reduces_the_loss():
