@@ -455,6 +455,7 @@ def plain_search(sinnamon, h, qs, g_qix, g_qv, k, kp, dev, npl, alg_full):
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(npl)]
+    torch.cuda.nvtx.range_push("bench plain searches")
     t0 = time.perf_counter()
     for r in range(npl):
         a = int(offs[r])
@@ -462,6 +463,7 @@ def plain_search(sinnamon, h, qs, g_qix, g_qv, k, kp, dev, npl, alg_full):
         sinnamon.sinn_search(h, qip1[r], g_qix[a:], g_qv[a:], k, kp, one_ids, one_sc)
         evs[r][1].record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     plain_s = time.perf_counter() - t0
     lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
     bytes_q = float(np.mean(alg_full[:npl]))
@@ -587,10 +589,12 @@ def run_ours(args):
     clocks = ClockSampler(local)
     with clocks:
         sinnamon.sinn_timing_start(h)
+        torch.cuda.nvtx.range_push("bench timed steps")  # a profiler can select these launches
         ev0.record()
         for si in range(args.warmup, nsteps):
             step(si)
         ev1.record()
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         tm = sinnamon.sinn_timing_stop(h)
     ix.sync()

@@ -65,29 +65,30 @@ def grad(p, X, t, tau, mean, std, n_in, hidden):
     return g, pinball(y, t, tau)
 
 
-def _amb(Z, Zabs, eps):
-    """Pre-activations whose sign a perturbation of relative size eps (of the
-    magnitude Zabs of their terms) could flip."""
-    return np.abs(Z) <= eps * Zabs
+def _amb(Z, Zabs, tol):
+    """Values whose sign an error of at most tol * Zabs (Zabs the magnitude
+    of the terms summed into them) could flip."""
+    return np.abs(Z) <= tol * Zabs
 
 
 def error_bounds(p, X, t, tau, mean, std, n_in, hidden, eps):
     """Per-element error budget of a reduced-precision evaluation of the
     network, its loss gradient and its output, against this module's FP64
     values, written out layer by layer as the FP64 forward and backward
-    passes are.  An evaluation whose operands and intermediate values carry
-    relative errors up to eps (of the magnitude of the terms summed into
-    them) is wrong by at most about a small multiple of eps times the
-    magnitude below, plus the flip allowance:
+    passes are.  eps is the relative error of each stored operand (inputs,
+    weights, hidden activations, back-propagated terms; 2^-8 for bfloat16).
 
       magnitude: the same passes over absolute values -- |standardised X|,
         |W|, |b|, |dy| -- with every unit counted whose ReLU is active or
-        could be flipped by such errors (|Z| <= eps * its magnitude); it is
-        the sum of |terms| behind each output and gradient element;
-      flip allowance: a ReLU whose sign such errors could flip may pass or
-        block its whole gradient term, so the terms routed through those
-        units (and through rows whose pinball residual t - y could change
-        sign) enter at full magnitude.
+        could be flipped; it is the sum of |terms| behind each output and
+        gradient element, and a reduced-precision value is within a small
+        multiple of eps times it;
+      flips: a first-layer pre-activation carries at most 2 eps of its
+        magnitude (rounded inputs and weights), a second-layer one 5 eps
+        (its rounded inputs and weights, and the first layer's error through
+        |W2|), the output 6 eps; a ReLU (or a pinball residual t - y) that
+        close to zero may pass or block its whole gradient term, so the terms
+        routed through it enter the allowance at full magnitude.
 
     Returns (y_mag [B], g_mag [P], g_flip [P]) in the flat parameter order."""
     W1, b1, W2, b2, w3, b3 = unpack(p, n_in, hidden)
@@ -95,16 +96,15 @@ def error_bounds(p, X, t, tau, mean, std, n_in, hidden, eps):
     B = y.size
     aX = np.abs(Xn)
     Z1a = aX @ np.abs(W1).T + np.abs(b1)
-    a1 = _amb(Z1, Z1a, eps)
+    a1 = _amb(Z1, Z1a, 2 * eps)
     on1 = (Z1 > 0) | a1                       # units that may carry a value
     H1a = Z1a * on1
     Z2a = H1a @ np.abs(W2).T + np.abs(b2)
-    a2 = _amb(Z2, Z2a, eps)
+    a2 = _amb(Z2, Z2a, 5 * eps)
     on2 = (Z2 > 0) | a2
     H2a = Z2a * on2
     ya = H2a @ np.abs(w3) + abs(b3[0])
-    u = np.asarray(t, np.float64) - y
-    ay = np.abs(u) <= eps * (ya + np.abs(np.asarray(t, np.float64)))
+    ay = _amb(np.asarray(t, np.float64) - y, ya, 6 * eps)
     dya = np.full(B, max(tau, 1.0 - tau) / B)
     dyf = np.where(ay, 1.0 / B, 0.0)          # a residual sign flip moves dy by 1/B
 

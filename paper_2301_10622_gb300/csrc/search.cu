@@ -46,6 +46,8 @@ constexpr uint32_t kChunk = 8192;       // keys per block in the dense select pa
 constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
 constexpr uint32_t kBmGroups = 2;       // 4-id groups per thread a bitmap term pass holds
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
+constexpr uint32_t kTouchCap = 2048;    // ids a touched-list tile may list
+constexpr uint32_t kZeroBin = 0x800u;   // key bin (top 12 bits) of a zero score
 
 enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
 
@@ -302,13 +304,14 @@ __device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool 
 }
 
 // One warp: start the copies of the directory entries {start, count} of the
-// first nt query terms in tile t into dst (8 bytes each, cp.async).
-__device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const QTerm *terms, uint32_t nt,
+// first nt query terms (coordinates tj, in shared memory) in tile t into dst
+// (8 bytes each, cp.async).
+__device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const uint32_t *tj, uint32_t nt,
                                           uint32_t t, uint2 *dst, uint32_t lane) {
   const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
   for (uint32_t k = lane; k < nt; k += 32) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + k);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(dir + terms[k].j)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(dir + tj[k])
                  : "memory");
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -317,10 +320,12 @@ __device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const QTerm *terms
 // Alg. 6 for query slot b over tiles [t_beg, t_end).  A query term's postings
 // inside a tile sit in one container: a bitmap of T bits when at least an
 // eighth of the tile's ids hold the coordinate, else a sorted array of 16-bit
-// local ids.  Per tile, for each batch of up to kTermBatch terms:
+// local ids.  The query's coordinates, weights and sketch bins are staged
+// once for all the block's tiles (queries of at most kTermBatch terms; longer
+// ones restage each batch of terms per tile).  Per tile, for each batch:
 //   Staging (warp 0): the terms' directory entries (fetched a tile ahead with
-//   cp.async when the query has a single batch), sketch bins and weights,
-//   the prefix of the array terms' chunk counts and the list of bitmap terms.
+//   cp.async when the query has a single batch), the prefix of the array
+//   terms' chunk counts and the list of bitmap terms.
 //   Bitmap terms: thread t owns the 4 consecutive ids 4t..4t+3 of each
 //   2048-id slice, holds their partial scores in registers and, per term,
 //   reads one bitmap word and one 16-byte group of sketch values; no atomics.
@@ -330,11 +335,16 @@ __device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const QTerm *terms
 //   numbered in term order; each warp takes a contiguous range of chunks (so
 //   it finds a chunk's term by advancing one pointer) and adds q_j * x~ into
 //   shared memory with atomics (two terms may share an id).
-// The epilogue adds the two accumulators: ids whose score key reaches the
-// query's running bound are counted in the histogram and emitted (EMIT), or
-// every live id's key is written and counted (dense).  Counted keys go
-// straight to the query's global histogram; the bound is refreshed from it
-// once per block.
+// The epilogue adds the two accumulators and leaves them zero for the next
+// tile: ids whose score key reaches the query's running bound are counted in
+// the histogram and emitted (EMIT), or every live id's key is written and
+// counted (dense).  Counted keys go straight to the query's global
+// histogram; the bound is refreshed from it once per block.
+// Touched-list tiles: when a tile holds only array containers of the query
+// and the running bound is above the bin of a zero score, an id no posting
+// reached scores 0 and cannot be a candidate.  Each array posting then also
+// marks its id in a T-bit bitmap, the first mark appending the id to a list,
+// and the epilogue visits the listed ids only (instead of all T).
 template <bool EMIT, int H, typename S, bool WALK>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
@@ -343,13 +353,16 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT;
   float *acc = (float *)sm;                          // T: array terms (atomics)
   float *bacc = acc + T;                             // T: bitmap terms (owner only)
-  uint32_t *t_start = sm + 2 * T;                    // kTermBatch
+  uint32_t *touched = sm + 2 * T;                    // T/32: ids an array posting reached
+  uint16_t *tlist = (uint16_t *)(touched + T / 32);  // kTouchCap: those ids, first touch order
+  uint32_t *t_start = (uint32_t *)(tlist + kTouchCap);  // kTermBatch
   uint32_t *t_cnt = t_start + kTermBatch;            // kTermBatch
   uint32_t *t_cp = t_cnt + kTermBatch;               // kTermBatch+1: chunk prefix (arrays)
   float *t_v = (float *)(t_cp + kTermBatch + 1);     // kTermBatch
-  uint32_t *t_bin = (uint32_t *)(t_v + kTermBatch);  // kTermBatch * h
+  uint32_t *t_j = (uint32_t *)(t_v + kTermBatch);    // kTermBatch: coordinates
+  uint32_t *t_bin = t_j + kTermBatch;                // kTermBatch * h
   __shared__ uint32_t part[NW + 2];
-  __shared__ uint32_t s_nbm, s_lb;
+  __shared__ uint32_t s_nbm, s_lb, s_ntl, s_apost, s_dirty;
   __shared__ uint8_t t_bl[kTermBatch];  // bitmap terms of the batch, in order
   // directory entries of the query's terms for this tile and the next one
   // (queries of at most kTermBatch terms: fetched a tile ahead by cp.async)
@@ -364,57 +377,83 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   // more as L1 for the sketch gathers)
   uint32_t *gh = bt.hist0 + (uint64_t)b * 4096;
   uint64_t *el = bt.elist + (uint64_t)b * kEmitCap;
+  const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
 
+  // the block starts with zero accumulators and no marks; every epilogue
+  // leaves them so
+  for (uint32_t d = 4 * tid; d < T; d += 4 * kScoreThreads) {
+    *(float4 *)(acc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *(float4 *)(bacc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (uint32_t w = tid; w < T / 32; w += kScoreThreads) touched[w] = 0u;
   if (tid == 0) s_lb = EMIT ? __ldcg(&bt.bound[b]) : 0u;
+  if (nbatch == 1 && wid == 0) {
+    // the query's coordinates, weights and bins, the same for every tile
+    for (uint32_t k = lane; k < nt; k += 32) {
+      const uint32_t j = terms[k].j;
+      t_j[k] = j;
+      t_v[k] = terms[k].v;
+      for (uint32_t o = 0; o < a.h; ++o) {
+        const uint32_t bin = a.pi[(uint64_t)j * a.h + o];
+        t_bin[k * a.h + o] = SINN_IN_BOUNDS(bin < a.m, a.err) ? bin : 0u;
+      }
+    }
+    __syncwarp();
+    if (t_beg < t_end) dir_fetch(a, t_j, nt, t_beg, s_dir[0], lane);
+  }
   __syncthreads();
   // keys below the bound are neither counted nor emitted
   const uint32_t lb = s_lb;
-  const uint32_t nbatch = nt == 0 ? 1 : (nt + kTermBatch - 1) / kTermBatch;
-  if (wid == 0 && nbatch == 1 && t_beg < t_end) dir_fetch(a, terms, nt, t_beg, s_dir[0], lane);
   for (uint32_t t = t_beg; t < t_end; ++t) {
     const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
     const uint16_t *post = a.tile_post[t];
     const uint64_t id0 = (uint64_t)t << a.log2T;
-    __syncthreads();  // the previous tile's epilogue is done with acc and bacc
-    for (uint32_t d = 4 * tid; d < T; d += 4 * kScoreThreads) {
-      *(float4 *)(acc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
-      *(float4 *)(bacc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    __syncthreads();  // the previous tile's epilogue is done with acc, bacc and the list
+    bool touch = false;
     for (uint32_t bi = 0; bi < nbatch; ++bi) {
       const uint32_t i0 = bi * kTermBatch;
       const uint32_t nb = nt > i0 ? min(kTermBatch, nt - i0) : 0u;
       if (bi > 0) __syncthreads();  // the previous batch is consumed
       if (wid == 0) {
-        // stage the batch's terms, then the exclusive prefix of the array
-        // chunk counts and the list of bitmap terms
+        // the batch's directory entries, then the exclusive prefix of the
+        // array chunk counts and the list of bitmap terms
         const uint32_t pb = (t - t_beg) & 1u;
         if (nbatch == 1) {
           asm volatile("cp.async.wait_all;\n" ::: "memory");  // this tile's entries
           __syncwarp();
         }
         for (uint32_t k = lane; k < nb; k += 32) {
-          const uint32_t j = terms[i0 + k].j;
-          const uint2 de = nbatch == 1 ? s_dir[pb][k] : dir[j];
+          uint2 de;
+          if (nbatch == 1) {
+            de = s_dir[pb][k];
+          } else {
+            const uint32_t j = terms[i0 + k].j;
+            de = dir[j];
+            t_v[k] = terms[i0 + k].v;
+            for (uint32_t o = 0; o < a.h; ++o) {
+              const uint32_t bin = a.pi[(uint64_t)j * a.h + o];
+              t_bin[k * a.h + o] = SINN_IN_BOUNDS(bin < a.m, a.err) ? bin : 0u;
+            }
+          }
           t_start[k] = de.x;
           t_cnt[k] = de.y;
           // array terms' chunks of 32 postings (walk 0) or postings (walk 1)
           t_cp[k] = de.y >= BMIN ? 0u : (WALK ? de.y : (de.y + 31) >> 5);
-          t_v[k] = terms[i0 + k].v;
-          for (uint32_t o = 0; o < a.h; ++o) {
-            const uint32_t bin = a.pi[(uint64_t)j * a.h + o];
-            t_bin[k * a.h + o] = SINN_IN_BOUNDS(bin < a.m, a.err) ? bin : 0u;
-          }
         }
         // the next tile's entries arrive while this tile is scored
-        if (nbatch == 1 && t + 1 < t_end) dir_fetch(a, terms, nb, t + 1, s_dir[pb ^ 1u], lane);
+        if (nbatch == 1 && t + 1 < t_end) dir_fetch(a, t_j, nb, t + 1, s_dir[pb ^ 1u], lane);
         __syncwarp();
-        uint32_t run = 0, nbm = 0;
+        uint32_t run = 0, nbm = 0, apost = 0;
         for (uint32_t base = 0; base < nb; base += 32) {
           const uint32_t i = base + lane;
           const uint32_t v = i < nb ? t_cp[i] : 0;
-          const uint32_t isb = __ballot_sync(0xFFFFFFFFu, i < nb && t_cnt[i] >= BMIN);
-          if ((isb >> lane) & 1u) t_bl[nbm + __popc(isb & ((1u << lane) - 1u))] = (uint8_t)i;
+          const bool isbm = i < nb && t_cnt[i] >= BMIN;
+          const uint32_t isb = __ballot_sync(0xFFFFFFFFu, isbm);
+          if (isbm) t_bl[nbm + __popc(isb & ((1u << lane) - 1u))] = (uint8_t)i;
           nbm += __popc(isb);
+          uint32_t ap = (i < nb && !isbm) ? t_cnt[i] : 0u;
+          for (int dd = 16; dd > 0; dd >>= 1) ap += __shfl_xor_sync(0xFFFFFFFFu, ap, dd);
+          apost += ap;
           uint32_t x = v;
           for (int dd = 1; dd < 32; dd <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, dd);
@@ -427,9 +466,15 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           t_cp[nb] = run;
           part[0] = run;
           s_nbm = nbm;
+          s_apost = apost;
+          s_ntl = 0;
+          // accumulators the tile writes: 1 acc (array terms), 2 bacc (bitmaps)
+          s_dirty = (bi ? s_dirty : 0u) | (run ? 1u : 0u) | (nbm ? 2u : 0u);
         }
       }
       __syncthreads();
+      // a touched-list tile (block-uniform): arrays only, bound above zero
+      touch = EMIT && nbatch == 1 && s_nbm == 0 && lb > kZeroBin && s_apost <= kTouchCap;
       // bitmap terms: thread tid owns ids 4*tid + 4*kScoreThreads*g .. +3;
       // their partial sums go to bacc, which only the owner touches, so the
       // array terms need not wait for them
@@ -470,7 +515,14 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           if (d0 < T) *(float4 *)(bacc + d0) = r[g];
         }
       }
-      // array terms
+      // array terms; on a touched-list tile each first mark of an id lists it
+      auto add = [&](uint32_t d, float x) {
+        atomicAdd(&acc[d], x);
+        if (touch) {
+          const uint32_t bit = 1u << (d & 31);
+          if (!(atomicOr(&touched[d >> 5], bit) & bit)) tlist[atomicAdd(&s_ntl, 1u)] = (uint16_t)d;
+        }
+      };
       const uint32_t C = part[0];
       if (WALK) {
         // walk 1: the batch's array postings as one sequence, thread tid taking
@@ -512,7 +564,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           }
 #pragma unroll
           for (uint32_t u = 0; u < 4; ++u)
-            if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], x[u]);
+            if (!(d[u] & SINN_TOMB)) add(d[u], x[u]);
         }
       }
       const uint32_t c_beg = WALK ? 0u : (uint32_t)((uint64_t)C * wid / NW);
@@ -561,20 +613,53 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
             x[u] = (d[u] & SINN_TOMB) ? 0.0f : decode<H, S>(row, a.h, pos, d[u]);
 #pragma unroll
           for (uint32_t u = 0; u < 4; ++u)
-            if (!(d[u] & SINN_TOMB)) atomicAdd(&acc[d[u]], v * x[u]);
+            if (!(d[u] & SINN_TOMB)) add(d[u], v * x[u]);
           c += nck;
         }
       }
     }
     __syncthreads();  // the array terms' atomics are complete
+    if (EMIT && touch) {
+      // touched-list epilogue: the ids an array posting reached, each read,
+      // cleared and, at or above the bound, counted and emitted
+      const uint32_t ntl = s_ntl;
+      for (uint32_t base = 0; base < ntl; base += kScoreThreads) {
+        const uint32_t i = base + tid;
+        const bool in = i < ntl;
+        const uint32_t d = in ? tlist[i] : 0u;
+        float sc = 0.0f;
+        if (in) {
+          sc = acc[d];
+          acc[d] = 0.0f;
+          touched[d >> 5] = 0u;
+        }
+        const uint32_t key = sinn_f2key(sc + 0.0f);
+        const bool em = in && sinn_is_live(a.live, id0 + d) && (key >> 20) >= lb;
+        if (em) atomicAdd(&gh[key >> 20], 1u);
+        if (__any_sync(0xFFFFFFFFu, em)) {
+          const uint32_t p = warp_append(em, &bt.ecnt[b]);
+          if (em && p < kEmitCap) el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d);
+        }
+      }
+      continue;
+    }
     // epilogue, 4 consecutive ids per thread: score = array part + bitmap part
+    const uint32_t dirty = s_dirty;
     for (uint32_t g0 = 0; g0 < T; g0 += 4 * kScoreThreads) {
       const uint32_t d0 = g0 + 4 * tid;
       const bool in = d0 < T;
       float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
       if (in) {
-        const float4 x = *(const float4 *)(acc + d0), y = *(const float4 *)(bacc + d0);
-        sa = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (dirty & 1u) {
+          sa = *(const float4 *)(acc + d0);
+          *(float4 *)(acc + d0) = z;
+        }
+        if (dirty & 2u) {
+          const float4 y = *(const float4 *)(bacc + d0);
+          *(float4 *)(bacc + d0) = z;
+          sa = make_float4(sa.x + y.x, sa.y + y.y, sa.z + y.z, sa.w + y.w);
+        }
       }
       const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
       const float rv[4] = {sa.x, sa.y, sa.z, sa.w};
@@ -1240,7 +1325,10 @@ struct SearchReq {
 };
 
 size_t score_smem(const sinn_index *ix) {
-  return (size_t)ix->T * 8 + (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 * ix->h) + 4;
+  // two T-float accumulators, the T-bit touched marks and list, the staged
+  // terms (start, count, chunk prefix + 1, weight, coordinate, h bins)
+  return (size_t)ix->T * 8 + (size_t)ix->T / 8 + (size_t)kTouchCap * 2 +
+         (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 + 4 * ix->h) + 4;
 }
 
 // Scratch supplied by the caller instead of the index's own (grown) buffer.

@@ -317,8 +317,12 @@ def sinn_mlp_set_policy(mlp, shifts=None, posting_cost: float = 0.0, margin: flo
     if shifts is None:
         _check(load().sinn_mlp_set_policy(mlp, None), "sinn_mlp_set_policy")
         return
+    if not 0 < len(shifts) <= KP_MAX_LEVELS:
+        raise SinnError(SINN_EINVAL, "sinn_mlp_set_policy")
     pol = SinnKpPolicy(n_levels=len(shifts), posting_cost=posting_cost, margin=margin)
     for i, v in enumerate(shifts):
+        if not 0 <= int(v) < 2 ** 32:
+            raise SinnError(SINN_EINVAL, "sinn_mlp_set_policy")
         pol.shift[i] = int(v)
     _check(load().sinn_mlp_set_policy(mlp, C.byref(pol)), "sinn_mlp_set_policy")
 
