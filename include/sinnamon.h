@@ -273,8 +273,8 @@ typedef struct sinn_tuning {
                                 scratch holds (default 0) */
   uint32_t rerank_blocks;    /* re-rank blocks per query, 1..1024, or 0 (default) for
                                 one per 64 candidates of the largest k' */
-  uint32_t dense_blocks_per_sm; /* grid of the dense scoring kernel per SM, 1..32
-                                   (default 4) */
+  uint32_t dense_blocks_per_sm; /* grid of the dense scoring kernel (launches of few
+                                   queries) per SM, 1..32 (default 8) */
   uint32_t tiles_per_block;  /* tiles one block of the batched scoring kernel covers,
                                 1..64 (default 4) */
   uint32_t persistent_blocks_per_sm; /* 0 (default): one block per (query, tile group);

@@ -28,6 +28,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "sinn_internal.cuh"
 
@@ -42,7 +44,7 @@ namespace {
 constexpr uint32_t kBoundCap = 65536;   // boundary-bin entries kept per query
 constexpr uint32_t kEmitCap = 131072;   // emitted candidates kept per query
 constexpr uint32_t kScoreThreads = 512;
-constexpr uint32_t kChunk = 8192;       // keys per block in the dense select passes
+constexpr uint32_t kChunk = 2048;       // keys per block in the dense select passes
 constexpr uint32_t kTermBatch = 64;     // query terms staged in shared memory at a time
 constexpr uint32_t kBmGroups = 2;       // 4-id groups per thread a bitmap term pass holds
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
@@ -110,12 +112,32 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
                         uint32_t kp_scalar, const uint32_t *__restrict__ kp_arr, uint32_t kp_min,
                         uint32_t kp_max, const uint64_t *live_count, Batch bt,
                         const uint32_t *__restrict__ coord_len, uint64_t budget,
-                        const uint64_t *__restrict__ budget_arr, int nonneg, uint32_t *err) {
+                        const uint64_t *__restrict__ budget_arr, int nonneg, int dense_all,
+                        uint32_t *err) {
   extern __shared__ uint32_t sq[];
   uint32_t *sj = sq;                  // qmax
   float *sv = (float *)(sq + qmax);   // qmax
   __shared__ uint32_t s_cnt, s_bad;
   const uint32_t b = blockIdx.x, q = q0 + b;
+  // the slot's selection state starts empty: histograms, emitted count,
+  // running bound, tiles done; block 0 also resets the launch's counters
+  // (flagged queries, the persistent kernel's work counter)
+  for (uint32_t i = threadIdx.x; i < 4096 + 4096 + 256; i += blockDim.x) {
+    const uint32_t which = i < 4096 ? 0 : (i < 8192 ? 1 : 2);
+    uint32_t *h = which == 0 ? bt.hist0 + (uint64_t)b * 4096
+                             : which == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
+    h[i - (which == 0 ? 0u : which == 1 ? 4096u : 8192u)] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    bt.ecnt[b] = 0u;
+    bt.bound[b] = 0u;
+    bt.tdone[b] = 0u;
+    if (dense_all) bt.flagged[b] = b;  // every query of the launch scores densely
+    if (b == 0) {
+      *bt.nflag = dense_all ? gridDim.x : 0u;
+      *(unsigned long long *)(((uintptr_t)(bt.nflag + 1) + 7) & ~(uintptr_t)7) = 0ull;
+    }
+  }
   const uint64_t s = q_indptr[q], e = q_indptr[q + 1];
   if (threadIdx.x == 0) {
     s_cnt = 0;
@@ -181,7 +203,7 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     st.kq = s_bad ? 0u : (uint32_t)(lc < kp ? lc : (uint64_t)kp);
     st.ncand = 0;
     st.nbnd = 0;
-    st.dense = 0;
+    st.dense = dense_all ? 1u : 0u;
     bt.sel[b] = st;
   }
 }
@@ -337,15 +359,14 @@ __device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const uint32_t *tj
 //   shared memory with atomics (two terms may share an id).
 // The epilogue adds the two accumulators and leaves them zero for the next
 // tile: ids whose score key reaches the query's running bound are counted in
-// the histogram and emitted (EMIT), or every live id's key is written and
-// counted (dense).  Counted keys go straight to the query's global
-// histogram; the bound is refreshed from it once per block.
+// the histogram and emitted as candidates.  Counted keys go straight to the
+// query's global histogram; the bound is refreshed from it once per block.
 // Touched-list tiles: when a tile holds only array containers of the query
 // and the running bound is above the bin of a zero score, an id no posting
 // reached scores 0 and cannot be a candidate.  Each array posting then also
 // marks its id in a T-bit bitmap, the first mark appending the id to a list,
 // and the epilogue visits the listed ids only (instead of all T).
-template <bool EMIT, int H, typename S, bool WALK>
+template <int H, typename S, bool WALK>
 __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uint32_t t_beg,
                             uint32_t t_end, uint32_t *sm) {
   constexpr uint32_t NW = kScoreThreads / 32;
@@ -386,7 +407,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
     *(float4 *)(bacc + d) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   for (uint32_t w = tid; w < T / 32; w += kScoreThreads) touched[w] = 0u;
-  if (tid == 0) s_lb = EMIT ? __ldcg(&bt.bound[b]) : 0u;
+  if (tid == 0) s_lb = __ldcg(&bt.bound[b]);
   if (nbatch == 1 && wid == 0) {
     // the query's coordinates, weights and bins, the same for every tile
     for (uint32_t k = lane; k < nt; k += 32) {
@@ -474,7 +495,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       }
       __syncthreads();
       // a touched-list tile (block-uniform): arrays only, bound above zero
-      touch = EMIT && nbatch == 1 && s_nbm == 0 && lb > kZeroBin && s_apost <= kTouchCap;
+      touch = nbatch == 1 && s_nbm == 0 && lb > kZeroBin && s_apost <= kTouchCap;
       // bitmap terms: thread tid owns ids 4*tid + 4*kScoreThreads*g .. +3;
       // their partial sums go to bacc, which only the owner touches, so the
       // array terms need not wait for them
@@ -619,7 +640,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       }
     }
     __syncthreads();  // the array terms' atomics are complete
-    if (EMIT && touch) {
+    if (touch) {
       // touched-list epilogue: the ids an array posting reached, each read,
       // cleared and, at or above the bound, counted and emitted
       const uint32_t ntl = s_ntl;
@@ -663,38 +684,21 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       }
       const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
       const float rv[4] = {sa.x, sa.y, sa.z, sa.w};
-      if (EMIT) {
-        // ids at or above the running bound count and are emitted
+      // ids at or above the running bound count and are emitted
 #pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
-          const uint32_t key = sinn_f2key(rv[q] + 0.0f);
-          const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
-          if (em) atomicAdd(&gh[key >> 20], 1u);
-          if (__any_sync(0xFFFFFFFFu, em)) {
-            const uint32_t p = warp_append(em, &bt.ecnt[b]);
-            if (em && p < kEmitCap)
-              el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
-          }
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t key = sinn_f2key(rv[q] + 0.0f);
+        const bool em = ((lwv >> q) & 1u) && (key >> 20) >= lb;
+        if (em) atomicAdd(&gh[key >> 20], 1u);
+        if (__any_sync(0xFFFFFFFFu, em)) {
+          const uint32_t p = warp_append(em, &bt.ecnt[b]);
+          if (em && p < kEmitCap)
+            el[p] = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)(id0 + d0 + q);
         }
-      } else {
-        // dense: a key for every id slot (0 = not live), counted
-        uint32_t kv[4];
-#pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
-          const bool lv = (lwv >> q) & 1u;
-          const uint32_t key = sinn_f2key(rv[q] + 0.0f);
-          kv[q] = lv ? key : 0u;
-          const uint32_t bin = lv ? (key >> 20) : 0xFFFFFFFFu;
-          const uint32_t grp = __match_any_sync(0xFFFFFFFFu, bin);
-          if (lv && lane == __ffs(grp) - 1) atomicAdd(&gh[bin], (uint32_t)__popc(grp));
-        }
-        if (in)
-          *(uint4 *)(bt.keys + (uint64_t)b * a.cap + id0 + d0) = make_uint4(kv[0], kv[1], kv[2], kv[3]);
       }
     }
   }
-  if (!EMIT) return;
-  // EMIT: the final boundary bin is never below any bound used, so the
+  // The final boundary bin is never below any bound used, so the
   // histogram stays exact from the boundary bin up and every candidate is
   // emitted.  Refresh the query's bound each time the tiles done cross a
   // multiple of bound_every.
@@ -715,7 +719,7 @@ template <int H, typename S, bool WALK>
 __global__ void __launch_bounds__(kScoreThreads, 4) k_score_emit(ScoreArgs a, Batch bt) {
   extern __shared__ uint32_t sm[];
   const uint32_t t0 = blockIdx.y * a.tpb;
-  score_tiles<true, H, S, WALK>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
+  score_tiles<H, S, WALK>(a, bt, blockIdx.x, t0, min(a.tiles, t0 + a.tpb), sm);
 }
 
 // The same work as k_score_emit from a fixed grid of blocks: each block takes
@@ -734,20 +738,189 @@ __global__ void __launch_bounds__(kScoreThreads, 4)
     __syncthreads();  // every thread has read the item before the next draw
     if (item >= total) break;
     const uint32_t b = (uint32_t)(item % nb), t0 = (uint32_t)(item / nb) * a.tpb;
-    score_tiles<true, H, S, WALK>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
+    score_tiles<H, S, WALK>(a, bt, b, t0, min(a.tiles, t0 + a.tpb), sm);
   }
 }
 
-// Dense scoring of the flagged queries (grid-stride over (query, tile)).
+// Dense scoring of the flagged queries: launches of few queries, and the
+// fallback of batched ones.  Work items are (query, tile, slice of
+// kLoneSlice ids), queries fastest so the blocks resident together share a
+// tile's lists and sketch rows, and one query alone still fills the GPU
+// (T / kLoneSlice items per tile).  A block stages the query's terms for
+// the item's tile (directory entries, weights, bins), then:
+//   bitmap terms: thread t owns ids 4t..4t+3 of the slice and keeps their
+//   partial scores in registers; terms are taken two at a time so their
+//   bitmap words and sketch values are in flight together;
+//   array terms: warp w takes terms w, w + 8, ...; its lanes read the
+//   container's postings and add those inside the slice into shared memory
+//   with atomics.
+// Every live id's key is written (0 for a slot that is not live) and its bin
+// counted in a shared histogram, added to the query's global one when the
+// block moves to another query or ends (few global atomics per bin, where
+// one histogram for the whole grid would serialise on the popular bins).
+constexpr uint32_t kLoneThreads = 256;
+constexpr uint32_t kLoneSlice = 4 * kLoneThreads;
+
 template <int H, typename S>
-__global__ void __launch_bounds__(kScoreThreads, 4) k_score_dense(ScoreArgs a, Batch bt) {
-  extern __shared__ uint32_t sm[];
+__device__ __forceinline__ void lone_bitmap_term(const ScoreArgs &a, const uint16_t *post,
+                                                 const uint32_t *t_start, const float *t_v,
+                                                 const uint32_t *t_bin, uint32_t k, uint64_t id0,
+                                                 uint32_t d0, uint32_t *bits, float4 *x,
+                                                 float *v) {
+  constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
+  *v = t_v[k];
+  const bool pos = *v > 0.0f;
+  const S *plane = (const S *)(pos ? a.U : a.L);
+  const S *row[HS];
+#pragma unroll
+  for (uint32_t o = 0; o < HS; ++o)
+    if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+  *bits = __ldg((const uint32_t *)(post + t_start[k]) + (d0 >> 5)) >> (d0 & 31);
+  *x = decode4<H, S>(row, a.h, pos, d0);
+}
+
+__device__ __forceinline__ void lone_fma(float4 &r, uint32_t bits, float4 x, float v) {
+  if (bits & 1u) r.x = fmaf(v, x.x, r.x);
+  if (bits & 2u) r.y = fmaf(v, x.y, r.y);
+  if (bits & 4u) r.z = fmaf(v, x.z, r.z);
+  if (bits & 8u) r.w = fmaf(v, x.w, r.w);
+}
+
+template <int H, typename S>
+__global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Batch bt) {
+  constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
+  constexpr uint32_t NW = kLoneThreads / 32;
+  __shared__ float4 acc4[kLoneSlice / 4];  // array terms of the slice (atomics)
+  __shared__ uint32_t hist[4096];          // key bins of the block's current query
+  __shared__ uint32_t t_start[kTermBatch], t_cnt[kTermBatch];
+  __shared__ uint32_t t_bin[kTermBatch * SINN_MAX_H];
+  __shared__ float t_v[kTermBatch];
+  __shared__ uint8_t t_bl[kTermBatch], t_al[kTermBatch];  // bitmap / array terms
+  __shared__ uint32_t s_nbm, s_nal;
+  float *acc = (float *)acc4;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT, spt = T / kLoneSlice;
   const uint32_t nf = *bt.nflag;
-  for (uint64_t w = blockIdx.x; w < (uint64_t)nf * a.tiles; w += gridDim.x) {
-    const uint32_t b = bt.flagged[w / a.tiles], t = (uint32_t)(w % a.tiles);
-    score_tiles<false, H, S, false>(a, bt, b, t, t + 1, sm);
-    __syncthreads();
+  const uint64_t items = (uint64_t)nf * a.tiles * spt;
+  for (uint32_t i = tid; i < 4096; i += kLoneThreads) hist[i] = 0u;
+  uint32_t cur = 0xFFFFFFFFu;  // query whose counts the histogram holds
+  auto flush = [&]() {
+    uint32_t *gh = bt.hist0 + (uint64_t)cur * 4096;
+    for (uint32_t i = tid; i < 4096; i += kLoneThreads) {
+      const uint32_t c = hist[i];
+      if (c) {
+        atomicAdd(&gh[i], c);
+        hist[i] = 0u;
+      }
+    }
+  };
+  for (uint64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const uint32_t b = bt.flagged[w % nf];
+    const uint64_t r0 = w / nf;
+    const uint32_t t = (uint32_t)(r0 / spt), s0 = (uint32_t)(r0 % spt) * kLoneSlice;
+    __syncthreads();  // the previous item is done with the shared state
+    if (b != cur) {   // block-uniform
+      if (cur != 0xFFFFFFFFu) flush();
+      cur = b;
+      __syncthreads();
+    }
+    const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
+    const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
+    const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
+    const uint16_t *post = a.tile_post[t];
+    const uint64_t id0 = (uint64_t)t << a.log2T;
+    const uint32_t d0 = s0 + 4 * tid;  // this thread's 4 ids
+    acc4[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t i0 = 0; i0 < nt; i0 += kTermBatch) {
+      const uint32_t nb = min(kTermBatch, nt - i0);
+      if (i0) __syncthreads();  // the previous batch is consumed
+      if (wid == 0) {
+        for (uint32_t k = lane; k < nb; k += 32) {
+          const QTerm q = terms[i0 + k];
+          const uint2 de = dir[q.j];
+          t_start[k] = de.x;
+          t_cnt[k] = de.y;
+          t_v[k] = q.v;
+          for (uint32_t o = 0; o < a.h; ++o) {
+            const uint32_t bin = a.pi[(uint64_t)q.j * a.h + o];
+            t_bin[k * a.h + o] = SINN_IN_BOUNDS(bin < a.m, a.err) ? bin : 0u;
+          }
+        }
+        __syncwarp();
+        uint32_t nbm = 0, nal = 0;
+        for (uint32_t base = 0; base < nb; base += 32) {
+          const uint32_t i = base + lane;
+          const uint32_t c = i < nb ? t_cnt[i] : 0u;
+          const uint32_t mb = __ballot_sync(0xFFFFFFFFu, c >= BMIN);
+          const uint32_t ma = __ballot_sync(0xFFFFFFFFu, c > 0 && c < BMIN);
+          const uint32_t below = (1u << lane) - 1u;
+          if (c >= BMIN) t_bl[nbm + __popc(mb & below)] = (uint8_t)i;
+          if (c > 0 && c < BMIN) t_al[nal + __popc(ma & below)] = (uint8_t)i;
+          nbm += __popc(mb);
+          nal += __popc(ma);
+        }
+        if (lane == 0) {
+          s_nbm = nbm;
+          s_nal = nal;
+        }
+      }
+      __syncthreads();  // also orders the zeroed accumulator before the atomics
+      const uint32_t nbm = s_nbm;
+      uint32_t kk = 0;
+      for (; kk + 1 < nbm; kk += 2) {
+        uint32_t b0, b1;
+        float4 x0, x1;
+        float v0, v1;
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk], id0, d0, &b0, &x0, &v0);
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk + 1], id0, d0, &b1, &x1,
+                               &v1);
+        lone_fma(r, b0, x0, v0);
+        lone_fma(r, b1, x1, v1);
+      }
+      if (kk < nbm) {
+        uint32_t b0;
+        float4 x0;
+        float v0;
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk], id0, d0, &b0, &x0, &v0);
+        lone_fma(r, b0, x0, v0);
+      }
+      const uint32_t nal = s_nal;
+      for (uint32_t ai = wid; ai < nal; ai += NW) {
+        const uint32_t k = t_al[ai];
+        const uint32_t lo = t_start[k], cnt = t_cnt[k];
+        const float v = t_v[k];
+        const bool pos = v > 0.0f;
+        const S *plane = (const S *)(pos ? a.U : a.L);
+        const S *row[HS];
+#pragma unroll
+        for (uint32_t o = 0; o < HS; ++o)
+          if (o < a.h) row[o] = plane + (uint64_t)t_bin[k * a.h + o] * a.cap + id0;
+        for (uint32_t p = lane; p < cnt; p += 32) {
+          const uint32_t dd = __ldg(post + lo + p);
+          if (dd & SINN_TOMB) continue;
+          if (!SINN_IN_BOUNDS(dd < T, a.err)) continue;
+          if (dd - s0 >= kLoneSlice) continue;  // outside the slice
+          atomicAdd(&acc[dd - s0], v * decode<H, S>(row, a.h, pos, dd));
+        }
+      }
+    }
+    __syncthreads();  // the array terms' atomics are complete
+    const float4 x = acc4[tid];
+    const float rv[4] = {r.x + x.x, r.y + x.y, r.z + x.z, r.w + x.w};
+    const uint32_t lwv = __ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31);
+    uint32_t kv[4];
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+      const bool lv = (lwv >> q) & 1u;
+      const uint32_t key = sinn_f2key(rv[q] + 0.0f);
+      kv[q] = lv ? key : 0u;
+      if (lv) atomicAdd(&hist[key >> 20], 1u);
+    }
+    *(uint4 *)(bt.keys + (uint64_t)b * a.cap + id0 + d0) = make_uint4(kv[0], kv[1], kv[2], kv[3]);
   }
+  __syncthreads();
+  if (cur != 0xFFFFFFFFu) flush();
 }
 
 // Kernels specialised for h = 1 and h = 2 (the common sketch shapes); other h
@@ -761,14 +934,14 @@ struct ScoreKernels {
 template <typename S, bool WALK>
 ScoreKernels score_kernels_for(uint32_t h) {
   if (h == 1)
-    return {k_score_emit<1, S, WALK>, k_score_dense<1, S>, k_score_emit_persistent<1, S, WALK>};
+    return {k_score_emit<1, S, WALK>, k_score_lone<1, S>, k_score_emit_persistent<1, S, WALK>};
   if (h == 2)
-    return {k_score_emit<2, S, WALK>, k_score_dense<2, S>, k_score_emit_persistent<2, S, WALK>};
-  return {k_score_emit<0, S, WALK>, k_score_dense<0, S>, k_score_emit_persistent<0, S, WALK>};
+    return {k_score_emit<2, S, WALK>, k_score_lone<2, S>, k_score_emit_persistent<2, S, WALK>};
+  return {k_score_emit<0, S, WALK>, k_score_lone<0, S>, k_score_emit_persistent<0, S, WALK>};
 }
 
-// Sketch bins as fp32 or as bfloat16 bits; array postings walked in per-term
-// chunks or spread over the block (the dense fallback always takes chunks).
+// Sketch bins as fp32 or as bfloat16 bits; array postings of the batched
+// kernels walked in per-term chunks or spread over the block.
 ScoreKernels score_kernels(uint32_t h, bool bf16, bool walk) {
   if (bf16) return walk ? score_kernels_for<uint16_t, true>(h) : score_kernels_for<uint16_t, false>(h);
   return walk ? score_kernels_for<float, true>(h) : score_kernels_for<float, false>(h);
@@ -950,33 +1123,88 @@ __global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t lev
 }
 
 // Dense-path collection: keys above the boundary bin are candidates; in
-// COMPACT mode the boundary bin's keys are buffered too.
-__global__ void k_compact(Batch bt, uint64_t cap, uint64_t span, uint32_t kpmax) {
+// COMPACT mode the boundary bin's keys are buffered too.  A block takes a
+// chunk of kChunk keys, 8 per thread, counts its hits, reserves room for the
+// whole block with one atomic per list and writes them.
+__global__ void __launch_bounds__(256) k_compact(Batch bt, uint64_t cap, uint64_t span,
+                                                 uint32_t kpmax) {
+  constexpr uint32_t PER = kChunk / 256;
+  __shared__ uint32_t wsum[2][8], s_base[2];
   const uint32_t nf = *bt.nflag;
   const uint64_t chunks = (span + kChunk - 1) / kChunk;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
-    const uint32_t b = bt.flagged[w / chunks];
-    const SelState st = bt.sel[b];
+    const uint32_t b = bt.flagged[w % nf];
+    const SelState st = bt.sel[b];  // block-uniform
     if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) continue;
     const uint32_t shift = 32 - st.pbits;
     const uint32_t *keys = bt.keys + (uint64_t)b * cap;
     uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
     uint64_t *bnd = bt.bnd + (uint64_t)b * kBoundCap;
     uint32_t *ncand = &bt.sel[b].ncand, *nbnd = &bt.sel[b].nbnd;
-    const uint64_t beg = (w % chunks) * kChunk;
-    const uint64_t end = (beg + kChunk < span) ? beg + kChunk : span;
-    for (uint64_t i0 = beg; i0 < end; i0 += blockDim.x) {
-      const uint64_t i = i0 + threadIdx.x;
-      const uint32_t key = i < end ? keys[i] : 0u;
-      const uint32_t top = shift == 32 ? 0u : (key >> shift);
-      const bool up = key != 0u && top > st.prefix;
-      const bool eq = key != 0u && top == st.prefix && st.mode == SEL_COMPACT;
-      const uint64_t k64 = ((uint64_t)key << 32) | (uint32_t)~(uint32_t)i;
-      uint32_t p = warp_append(up, ncand);
-      if (up && p < kpmax) cand[p] = k64;
-      p = warp_append(eq, nbnd);
-      if (eq && p < kBoundCap) bnd[p] = k64;
+    const uint64_t beg = (w / nf) * kChunk + (uint64_t)tid * PER;
+    uint32_t key[PER];
+    uint32_t nu = 0, ne = 0, fu = 0, fe = 0;  // counts and flag bits (up, equal)
+#pragma unroll
+    for (uint32_t q = 0; q < PER; q += 4) {
+      const uint4 v = beg + q + 4 <= span ? *(const uint4 *)(keys + beg + q)
+                                          : make_uint4(0u, 0u, 0u, 0u);
+      key[q] = v.x;
+      key[q + 1] = v.y;
+      key[q + 2] = v.z;
+      key[q + 3] = v.w;
     }
+#pragma unroll
+    for (uint32_t q = 0; q < PER; ++q) {
+      const uint32_t top = shift == 32 ? 0u : (key[q] >> shift);
+      const bool up = key[q] != 0u && top > st.prefix;
+      const bool eq = key[q] != 0u && top == st.prefix && st.mode == SEL_COMPACT;
+      fu |= (up ? 1u : 0u) << q;
+      fe |= (eq ? 1u : 0u) << q;
+      nu += up;
+      ne += eq;
+    }
+    // block prefix of the counts: within warps, then over warps
+    uint32_t xu = nu, xe = ne;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t yu = __shfl_up_sync(0xFFFFFFFFu, xu, d);
+      const uint32_t ye = __shfl_up_sync(0xFFFFFFFFu, xe, d);
+      if (lane >= (uint32_t)d) {
+        xu += yu;
+        xe += ye;
+      }
+    }
+    if (lane == 31) {
+      wsum[0][wid] = xu;
+      wsum[1][wid] = xe;
+    }
+    __syncthreads();
+    if (tid < 2) {
+      uint32_t tot = 0;
+      for (uint32_t i = 0; i < 8; ++i) {
+        const uint32_t v = wsum[tid][i];
+        wsum[tid][i] = tot;
+        tot += v;
+      }
+      s_base[tid] = tot ? atomicAdd(tid == 0 ? ncand : nbnd, tot) : 0u;
+    }
+    __syncthreads();
+    uint32_t pu = s_base[0] + wsum[0][wid] + xu - nu;
+    uint32_t pe = s_base[1] + wsum[1][wid] + xe - ne;
+#pragma unroll
+    for (uint32_t q = 0; q < PER; ++q) {
+      const uint64_t i = beg + q;
+      const uint64_t k64 = ((uint64_t)key[q] << 32) | (uint32_t)~(uint32_t)i;
+      if ((fu >> q) & 1u) {
+        if (pu < kpmax) cand[pu] = k64;
+        ++pu;
+      }
+      if ((fe >> q) & 1u) {
+        if (pe < kBoundCap) bnd[pe] = k64;
+        ++pe;
+      }
+    }
+    __syncthreads();  // wsum and s_base are reused by the next chunk
   }
 }
 
@@ -1005,19 +1233,38 @@ __device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
       if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t run = 0, rem = s_rem, dsel = 0;
-      for (int d = 255; d >= 0; --d) {
-        if (run + hist[d] >= rem) {
-          dsel = (uint32_t)d;
-          break;
-        }
-        run += hist[d];
+    if (threadIdx.x < 32) {
+      // the digit where the count from the top reaches rem: lane l sums the
+      // 8 digits 255 - 8l ... 248 - 8l, a scan over lanes finds the lane
+      // holding it, that lane finds the digit
+      const uint32_t lane = threadIdx.x, top = 255 - 8 * lane, rem = s_rem;
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < 8; ++i) {
+        c[i] = hist[top - i];
+        sum += c[i];
       }
-      s_rem = rem - run;
-      s_prefix = pre | ((uint64_t)dsel << shift);
-      s_mask = msk | (0xFFull << shift);
-      if (hist[dsel] == s_rem) s_stop = 1u;  // the whole digit bucket is in
+      uint32_t x = sum;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+      }
+      const uint32_t before = x - sum;
+      if (before < rem && x >= rem) {
+        uint32_t run = before, dsel = top;
+#pragma unroll
+        for (uint32_t i = 0; i < 8; ++i) {
+          if (run + c[i] >= rem) {
+            dsel = top - i;
+            break;
+          }
+          run += c[i];
+        }
+        s_rem = rem - run;
+        s_prefix = pre | ((uint64_t)dsel << shift);
+        s_mask = msk | (0xFFull << shift);
+        if (hist[dsel] == rem - run) s_stop = 1u;  // the whole digit bucket is in
+      }
     }
     __syncthreads();
   }
@@ -1196,12 +1443,14 @@ __global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32
       if (p < SINN_MAX_K) sk[p] = key;
     }
   }
-  for (uint32_t i = r + threadIdx.x; i < SINN_MAX_K; i += blockDim.x) sk[i] = 0ull;
+  // bitonic sort, descending, of the r keys padded to the next power of two
+  uint32_t P = 1;
+  while (P < r) P <<= 1;
+  for (uint32_t i = r + threadIdx.x; i < P; i += blockDim.x) sk[i] = 0ull;
   __syncthreads();
-  // bitonic sort, descending
-  for (uint32_t size = 2; size <= SINN_MAX_K; size <<= 1) {
+  for (uint32_t size = 2; size <= P; size <<= 1) {
     for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (uint32_t i = threadIdx.x; i < SINN_MAX_K; i += blockDim.x) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         const uint32_t j = i ^ stride;
         if (j > i) {
           const bool desc = (i & size) == 0;
@@ -1300,14 +1549,6 @@ Batch views(void *base, const Layout &L, uint32_t B) {
   return bt;
 }
 
-__global__ void k_flag_all(Batch bt, uint32_t nb) {
-  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-    bt.flagged[i] = i;
-    bt.sel[i].dense = 1;
-  }
-  if (threadIdx.x == 0) *bt.nflag = nb;
-}
-
 enum class Stage { kScores, kCandidates, kFull };
 
 struct SearchReq {
@@ -1329,6 +1570,37 @@ size_t score_smem(const sinn_index *ix) {
   // terms (start, count, chunk prefix + 1, weight, coordinate, h bins)
   return (size_t)ix->T * 8 + (size_t)ix->T / 8 + (size_t)kTouchCap * 2 +
          (size_t)kTermBatch * (4 + 4 + 4 + 4 + 4 + 4 * ix->h) + 4;
+}
+
+// The dynamic shared memory a kernel may use, raised only when a launch
+// needs more than was set before (the attribute belongs to the function and
+// persists; setting it on every search costs a driver call per kernel).
+cudaError_t set_dyn_smem(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> done;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+  if (e == cudaSuccess) done[fn] = bytes;
+  return e;
+}
+
+// Multiprocessor count of a device, asked once.
+int sm_count(int dev) {
+  static std::mutex mu;
+  static std::unordered_map<int, int> sms;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = sms.find(dev);
+  if (it != sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 1;
+  }
+  sms[dev] = n;
+  return n;
 }
 
 // Scratch supplied by the caller instead of the index's own (grown) buffer.
@@ -1355,9 +1627,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   Batch bt = views(fixed ? fixed->base : ix->scratch, L, (uint32_t)B);
   const size_t ssm = score_smem(ix);
   const ScoreKernels sk = score_kernels(ix->h, ix->sk_elem == 2, ix->tune.array_walk != 0);
-  CK(cudaFuncSetAttribute(sk.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-  CK(cudaFuncSetAttribute(sk.dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-  CK(cudaFuncSetAttribute(sk.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+  CK(set_dyn_smem((const void *)sk.emit, ssm));
+  CK(set_dyn_smem((const void *)sk.persistent, ssm));
   ScoreArgs sa;
   sa.tile_dir = ix->d_tile_dir;
   sa.tile_post = ix->d_tile_post;
@@ -1392,29 +1663,28 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   ra.err = ix->d_err;
   uint32_t tsz = 64;
   while (tsz < 2 * ix->max_qnnz) tsz <<= 1;
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  const int sms = sm_count(ix->device);
   const uint32_t fb_score_blocks = (uint32_t)std::max(1, sms) * ix->tune.dense_blocks_per_sm;
   for (uint32_t q0 = 0; q0 < r.n_q; q0 += (uint32_t)B) {
     const uint32_t nb = (uint32_t)std::min<uint64_t>(B, r.n_q - q0);
     {
       SinnPhase ph(ix, s, 0);
       ix->launches++;
+      // launches of fewer than emit_min_batch queries (and the dense score
+      // output) score every query densely
+      const bool dense = r.stage == Stage::kScores || nb < ix->tune.emit_min_batch;
       k_qprep<<<nb, 128, (size_t)ix->max_qnnz * 8, s>>>(r.q_indptr, r.q_idx, r.q_val, q0,
                                                          ix->n, ix->max_qnnz, r.kp, r.kp_arr,
                                                          r.kp_min, r.kp_max, ix->d_live_count, bt,
                                                          ix->d_coord_len, ix->budget,
                                                          r.budget_arr,
                                                          (ix->flags & SINN_FLAG_NONNEG) ? 1 : 0,
-                                                         ix->d_err);
+                                                         dense ? 1 : 0, ix->d_err);
       CK(cudaGetLastError());
-      CK(cudaMemsetAsync(bt.hist0, 0, (size_t)B * (4096 + 4096 + 256) * 4, s));
-      CK(cudaMemsetAsync(bt.ecnt, 0, ((size_t)3 * B + 4) * 4, s));
     }
     if (r.stage == Stage::kScores) {  // dense keys for every query
-      ix->launches += 3;
-      k_flag_all<<<1, 1024, 0, s>>>(bt, nb);
-      sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
+      ix->launches += 1 + nb;
+      sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
       for (uint32_t b = 0; b < nb; ++b) {
         uint64_t cnt = ix->cap;
         k_keys_to_scores<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
@@ -1427,9 +1697,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     {
       SinnPhase ph(ix, s, 1);
       if (dense_all) {
-        ix->launches += 2;
-        k_flag_all<<<1, 1024, 0, s>>>(bt, nb);
-        sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
+        ix->launches++;
+        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
       } else {
         ix->launches++;
         if (ix->tune.persistent_blocks_per_sm) {
@@ -1452,16 +1721,20 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
         ix->launches += 4;
         k_pick_list<<<nb, 128, 0, s>>>(bt);
         k_compact_list<<<nb, 512, 0, s>>>(bt, kpmax);
-        k_fb_reset<<<kFbBlocks, 256, 0, s>>>(bt);
-        sk.dense<<<fb_score_blocks, kScoreThreads, ssm, s>>>(sa, bt);
+        k_fb_reset<<<std::min(nb, kFbBlocks), 256, 0, s>>>(bt);
+        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
       }
       ix->launches += 7;
-      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 0);
-      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, 1);
-      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 1);
-      k_hist_level<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, 2);
-      k_pick<<<kFbBlocks, 128, 0, s>>>(bt, 2);
-      k_compact<<<kFbBlocks, 256, 0, s>>>(bt, ix->cap, span, kpmax);
+      // grids no larger than the work (the flagged queries are at most nb)
+      const uint32_t gq = std::min(nb, kFbBlocks);
+      const uint32_t gc = (uint32_t)std::min<uint64_t>(
+          (uint64_t)nb * ((span + kChunk - 1) / kChunk), (uint64_t)fb_score_blocks * 2);
+      k_pick<<<gq, 128, 0, s>>>(bt, 0);
+      k_hist_level<<<gc, 256, 0, s>>>(bt, ix->cap, span, 1);
+      k_pick<<<gq, 128, 0, s>>>(bt, 1);
+      k_hist_level<<<gc, 256, 0, s>>>(bt, ix->cap, span, 2);
+      k_pick<<<gq, 128, 0, s>>>(bt, 2);
+      k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax);
       k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, span, kpmax);
       CK(cudaGetLastError());
     }
@@ -1475,7 +1748,11 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       SinnPhase ph(ix, s, 3);
       ix->launches += 2;
       // blocks per query: the tuning's count, or (0) about 64 candidates each
-      const uint32_t rb = ix->tune.rerank_blocks ? ix->tune.rerank_blocks : (kpmax + 63) / 64;
+      // (for a launch of few queries, enough blocks to fill the GPU, down to
+      // one warp per candidate)
+      uint32_t rb = ix->tune.rerank_blocks ? ix->tune.rerank_blocks : (kpmax + 63) / 64;
+      if (!ix->tune.rerank_blocks)
+        rb = std::max<uint32_t>(rb, ((uint32_t)sms * 8 + nb - 1) / nb);
       k_rerank<<<dim3(std::min<uint32_t>(rb, (kpmax + 7) / 8), nb), 256,
                  (size_t)tsz * 8, s>>>(ra, bt);
       k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);

@@ -59,10 +59,10 @@ struct sinn_index {
   // tiles; launches of fewer than 32 queries score densely (their tiles run
   // at about the same time, so the bound could not prune); batches as large
   // as the scratch allows; re-rank blocks per query sized to k' (about 64
-  // candidates each); 4 dense blocks per SM; 4 tiles per block of the
-  // batched scoring kernel, one block per item; array postings in per-term
-  // chunks.
-  sinn_tuning tune{4, 32, 0, 0, 4, 4, 0, 0};
+  // candidates each); 8 dense blocks (of 256 threads) per SM; 4 tiles per
+  // block of the batched scoring kernel, one block per item; array postings
+  // in per-term chunks.
+  sinn_tuning tune{4, 32, 0, 0, 8, 4, 0, 0};
 
   // ---- device state
   uint32_t *d_pi = nullptr;        // n*h mappings
