@@ -749,8 +749,9 @@ __global__ void __launch_bounds__(kScoreThreads, 4)
 // (T / kLoneSlice items per tile).  A block stages the query's terms for
 // the item's tile (directory entries, weights, bins), then:
 //   bitmap terms: thread t owns ids 4t..4t+3 of the slice and keeps their
-//   partial scores in registers; terms are taken two at a time so their
-//   bitmap words and sketch values are in flight together;
+//   partial scores in registers; terms are taken four at a time (h = 1) or
+//   two at a time so their bitmap words and sketch values are in flight
+//   together;
 //   array terms: warp w takes terms w, w + 8, ...; its lanes read the
 //   container's postings and add those inside the slice into shared memory
 //   with atomics.
@@ -868,6 +869,23 @@ __global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Bat
       __syncthreads();  // also orders the zeroed accumulator before the atomics
       const uint32_t nbm = s_nbm;
       uint32_t kk = 0;
+      // (four terms in flight fit the registers with one sketch row per term)
+      for (; H == 1 && kk + 3 < nbm; kk += 4) {
+        uint32_t b0, b1, b2, b3;
+        float4 x0, x1, x2, x3;
+        float v0, v1, v2, v3;
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk], id0, d0, &b0, &x0, &v0);
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk + 1], id0, d0, &b1, &x1,
+                               &v1);
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk + 2], id0, d0, &b2, &x2,
+                               &v2);
+        lone_bitmap_term<H, S>(a, post, t_start, t_v, t_bin, t_bl[kk + 3], id0, d0, &b3, &x3,
+                               &v3);
+        lone_fma(r, b0, x0, v0);
+        lone_fma(r, b1, x1, v1);
+        lone_fma(r, b2, x2, v2);
+        lone_fma(r, b3, x3, v3);
+      }
       for (; kk + 1 < nbm; kk += 2) {
         uint32_t b0, b1;
         float4 x0, x1;
@@ -1730,9 +1748,12 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       const uint32_t gc = (uint32_t)std::min<uint64_t>(
           (uint64_t)nb * ((span + kChunk - 1) / kChunk), (uint64_t)fb_score_blocks * 2);
       k_pick<<<gq, 128, 0, s>>>(bt, 0);
-      k_hist_level<<<gc, 256, 0, s>>>(bt, ix->cap, span, 1);
+      // the finer levels only run for a boundary bin too large to buffer
+      // (massive ties): a smaller grid keeps the common no-op launch cheap
+      const uint32_t gh = std::min<uint32_t>(gc, nb * 64);
+      k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1);
       k_pick<<<gq, 128, 0, s>>>(bt, 1);
-      k_hist_level<<<gc, 256, 0, s>>>(bt, ix->cap, span, 2);
+      k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 2);
       k_pick<<<gq, 128, 0, s>>>(bt, 2);
       k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax);
       k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, span, kpmax);
