@@ -52,6 +52,14 @@ extern "C" {
 #define SINN_EDEVICE 5   /* a kernel reported an error (see sinn_sync) */
 #define SINN_ESCRATCH 6  /* sinn_search_noalloc: one query needs more than its fixed scratch */
 #define SINN_EIO 7       /* sinn_save / sinn_load: file error, or not a saved index */
+#define SINN_EBUSY 8     /* sinn_insert_at: a search older than a tile's last rebuild may
+                            still read it (sinn_reclaim first); sinn_save: deletions
+                            not yet reclaimed */
+
+/* Sequence numbers of snapshot searches and sequence-numbered mutations run
+ * from 0 to SINN_SEQ_LATEST; a search at SINN_SEQ_LATEST (the default) sees
+ * every mutation made so far. */
+#define SINN_SEQ_LATEST 0xFFFFFFFEu
 
 typedef struct sinn_index sinn_index; /* opaque; owned by the library */
 
@@ -99,7 +107,8 @@ typedef struct sinn_stats {
   uint64_t bytes_scratch;  /* device bytes of search scratch currently held */
   uint32_t n, m, h, tile_docs;
   uint32_t flags;          /* the index's SINN_FLAG_* bits */
-  uint32_t reserved;
+  uint32_t pending_deletes; /* ids deleted at a sequence number, not yet reclaimed
+                               (not counted in live) */
 } sinn_stats_t;
 
 /* Create an empty index on the current CUDA device with default settings.
@@ -130,6 +139,50 @@ int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
  * ENOTFOUND if an id is not live, EINVAL if an id repeats; then nothing
  * changes.  Waits for the stream before returning. */
 int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, void *stream);
+
+/* ---- Mutations while searches run (snapshots) ----------------------------
+ * The paper's setting has insertions and deletions arrive while queries run
+ * (Sec. 1, Sec. 4.3).  These calls let them overlap on the GPU: every
+ * request gets a sequence number, and a search at sequence number s (its
+ * context's snapshot, sinn_ctx_set_snapshot) counts exactly the vectors
+ * inserted at numbers <= s and not deleted at numbers <= s -- the same
+ * results as if it ran alone after the mutations numbered below it.
+ *   - A search must be launched after the mutations numbered below its own
+ *     number are enqueued, on a stream ordered after them (for example by
+ *     an event); it may then run while later mutations run on other
+ *     streams.
+ *   - Each tile of ids has two copies of its containers; a search reads the
+ *     current one, and a rebuild writes the other and then makes it current.
+ *   - Deleted ids keep their postings (so older searches still score them)
+ *     until sinn_reclaim removes them; only then can an insert reuse them.
+ * sinn_insert and sinn_delete are the stream-ordered forms (no search may be
+ * in flight); the forms below may be mixed with them. */
+
+/* Insert as sinn_insert, the vectors born at sequence number seq (searches
+ * at numbers below seq do not count them).  A tile it lands in is rebuilt
+ * into the copy searches do not read; a search numbered below that tile's
+ * previous sequence-numbered rebuild may still read that copy, so unless
+ * every such search has been reclaimed (sinn_reclaim with a horizon at least
+ * that rebuild's number) the call returns SINN_EBUSY and changes nothing.
+ * seq <= SINN_SEQ_LATEST. */
+int sinn_insert_at(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                   const float *values, uint32_t n_docs, uint32_t *out_ids, uint32_t seq,
+                   void *stream);
+
+/* Delete at sequence number seq: searches at numbers >= seq stop counting
+ * the ids, older ones still do; the postings are removed and the ids freed
+ * by a later sinn_reclaim.  ids: device uint32[n_ids] of live ids (ENOTFOUND
+ * otherwise, EINVAL for a repeat; nothing changes then).  Waits for the
+ * stream. */
+int sinn_delete_at(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, uint32_t seq,
+                   void *stream);
+
+/* The caller states that every search numbered below `horizon` has finished
+ * (horizon <= SINN_SEQ_LATEST + 1).  Deletions numbered at or below it are
+ * then carried out (postings tombstoned, ids freed for reuse) and inserted
+ * vectors numbered at or below it stop needing a snapshot check.  Horizons
+ * never move back.  Waits for the stream. */
+int sinn_reclaim(sinn_index *ix, uint32_t horizon, void *stream);
 
 /* Approximate top-k search for n_q queries: Alg. 6 scoring (T = infinity),
  * then Alg. 7: the k' best approximate scores among live ids, re-ranked by
@@ -205,6 +258,10 @@ int sinn_search_noalloc(sinn_index *ix, const uint64_t *q_indptr, const uint32_t
  * (SINN_ESCRATCH if one does not). */
 typedef struct sinn_ctx sinn_ctx;
 int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx **out);
+
+/* The sequence number the context's searches see (SINN_SEQ_LATEST after
+ * creation): see "Mutations while searches run" above. */
+int sinn_ctx_set_snapshot(sinn_ctx *c, uint32_t seq);
 int sinn_ctx_destroy(sinn_ctx *c);
 uint64_t sinn_ctx_query_bytes(sinn_ctx *c, uint32_t k_prime_max);
 

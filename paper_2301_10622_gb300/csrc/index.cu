@@ -7,10 +7,13 @@
 //                               as the paper stores the sketch matrix)
 //   d_live      cap bits        live ids
 //   d_fwd*      vector store    (coordinate, value) pairs per id
-//   d_tile_dir  tiles x n uint2 per tile t and coordinate j, the container of
-//                               the postings of I[j] with ids in
+//   d_tile_dir  2 x tiles x n   per tile t, copy v and coordinate j (at
+//               uint2           (2t + v) n + j), the container of the
+//                               postings of I[j] with ids in
 //                               [t*T, (t+1)*T): {start, count} in 16-bit words
-//                               of the tile's storage post_t.  count >= T/8:
+//                               of that copy's storage.  Searches read the
+//                               copy d_tile_sel[t]; a rebuild writes the
+//                               other one and then selects it.  count >= T/8:
 //                               a bitmap of T bits (bit d = local id d; a
 //                               deleted posting's bit is cleared); otherwise a
 //                               sorted array of count 16-bit local ids (bit 15
@@ -246,6 +249,7 @@ __device__ uint32_t block_scan_value(uint32_t x, uint32_t *part, uint32_t *total
 //           order through a bitmap of the tile's local ids
 struct RebuildArgs {
   const uint32_t *tiles;      // tile per group entry
+  const uint32_t *ver;        // copy (0 or 1) of the tile the entry rebuilds into
   uint16_t *const *new_post;  // storage per group entry
   const uint64_t *post_cap;   // storage size per entry (16-bit words, multiple of T/16)
   uint32_t *cnt;              // n per entry: counts, then array cursors
@@ -278,12 +282,12 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(1024)
     k_rb_plan(RebuildArgs a, uint2 *__restrict__ tile_dir, uint16_t **tile_post, uint32_t *err) {
   __shared__ uint32_t part[33];
-  const uint32_t i = blockIdx.x, t = a.tiles[i], n = a.n;
+  const uint32_t i = blockIdx.x, t = a.tiles[i], n = a.n, v = a.ver[i];
   const uint32_t W16 = a.T >> 4, BMIN = a.T >> SINN_BITMAP_SHIFT;
   uint16_t *post = a.new_post[i];
   const uint64_t cap16 = a.post_cap[i];
   uint32_t *cnt = a.cnt + (uint64_t)i * n;
-  uint2 *dir = tile_dir + (uint64_t)t * n;
+  uint2 *dir = tile_dir + ((uint64_t)t * 2 + v) * n;
   // each thread owns a contiguous run of coordinates
   const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
   const uint32_t c0 = min(n, threadIdx.x * per), c1 = min(n, c0 + per);
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(1024)
   for (uint64_t k = threadIdx.x; k < words; k += blockDim.x) z[k] = 0u;
   if (threadIdx.x == 0) {
     a.out_len[i] = tot_t;
-    tile_post[t] = post;
+    tile_post[(uint64_t)t * 2 + v] = post;
   }
 }
 
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(256)
     const uint64_t fo = fwd_off[id];
     const uint32_t nz = fwd_nnz[id];
     uint32_t *cur = a.cnt + (uint64_t)i * a.n;
-    const uint2 *dir = tile_dir + (uint64_t)t * a.n;
+    const uint2 *dir = tile_dir + ((uint64_t)t * 2 + a.ver[i]) * a.n;
     uint16_t *post = a.new_post[i];
     for (uint32_t e = lane; e < nz; e += 32) {
       const uint2 pr = fwd[fo + e];
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(256)
   for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
        w < (uint64_t)a.nb * a.n; w += nwarps) {
     const uint32_t i = (uint32_t)(w / a.n), c = (uint32_t)(w % a.n);
-    const uint2 de = tile_dir[(uint64_t)a.tiles[i] * a.n + c];
+    const uint2 de = tile_dir[((uint64_t)a.tiles[i] * 2 + a.ver[i]) * a.n + c];
     if (de.y < 2 || de.y >= BMIN) continue;  // warp-uniform
     uint16_t *seg = a.new_post[i] + de.x;
     if (de.y <= 32) {
@@ -415,6 +419,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// After a group's rebuild kernels: searches from now on read the copies just
+// written (the copies they read before stay as they were).
+__global__ void k_rb_flip(RebuildArgs a, uint32_t *tile_sel) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nb) tile_sel[a.tiles[i]] = a.ver[i];
+}
+
 // Sec. 4.3 deletion: for each deleted id, remove it from every list it is in
 // -- clear its bit in a bitmap container, or set the tombstone bit of its
 // posting in an array container (binary search: arrays are sorted) -- then
@@ -423,7 +434,8 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
                             const uint64_t *__restrict__ fwd_off,
                             const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd,
                             const uint2 *__restrict__ tile_dir, uint16_t *const *tile_post,
-                            uint32_t *live, uint32_t n, uint32_t log2T, uint32_t *tomb_count,
+                            const uint32_t *__restrict__ tile_sel, uint32_t *live, uint32_t n,
+                            uint32_t log2T, uint32_t *tomb_count,
                             uint32_t *coord_len, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -432,8 +444,9 @@ __global__ void k_tombstone(const uint32_t *__restrict__ ids, uint32_t cnt,
   const uint32_t t = id >> log2T;
   const uint32_t BMIN = (1u << log2T) >> SINN_BITMAP_SHIFT;
   const uint32_t d = id & ((1u << log2T) - 1u);
-  const uint2 *dir = tile_dir + (uint64_t)t * n;
-  uint16_t *post = tile_post[t];
+  const uint32_t v = tile_sel[t];  // the copy searches read
+  const uint2 *dir = tile_dir + ((uint64_t)t * 2 + v) * n;
+  uint16_t *post = tile_post[(uint64_t)t * 2 + v];
   const uint64_t fo = fwd_off[id];
   const uint32_t nz = fwd_nnz[id];
   uint32_t marked = 0;
@@ -490,6 +503,13 @@ __global__ void k_gather_columns(const uint32_t *__restrict__ ids, uint32_t cnt,
 }
 
 __global__ void k_store_u64(uint64_t *dst, uint64_t v) { *dst = v; }
+
+// arr[ids[i]] = v for i < cnt (birth and death sequence numbers).
+__global__ void k_fill_ids(const uint32_t *__restrict__ ids, uint32_t cnt, uint32_t *arr,
+                           uint32_t v) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) arr[ids[i]] = v;
+}
 
 // ------------------------------------------------------------- host side
 
@@ -597,6 +617,10 @@ static void release(sinn_index *ix) {
   cudaFree(ix->d_fwd);
   cudaFree(ix->d_tile_dir);
   cudaFree(ix->d_tile_post);
+  cudaFree(ix->d_tile_sel);
+  cudaFree(ix->d_born);
+  cudaFree(ix->d_died);
+  cudaFree(ix->d_recent);
   cudaFree(ix->d_err);
   cudaFree(ix->d_live_count);
   cudaFree(ix->d_coord_len);
@@ -679,17 +703,22 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
     bool plane;       // a sketch plane: m rows, re-strided
     void *q;
   };
-  Grow g[7] = {
+  constexpr int NG = 11;
+  Grow g[NG] = {
       {&ix->d_U, e, ix->cap, nc, true, nullptr},
       {&ix->d_L, e, ix->cap, nc, true, nullptr},
       {(void **)&ix->d_live, 4, ix->cap / 32, nc / 32, false, nullptr},
       {(void **)&ix->d_fwd_off, 8, ix->cap, nc, false, nullptr},
       {(void **)&ix->d_fwd_nnz, 4, ix->cap, nc, false, nullptr},
-      {(void **)&ix->d_tile_dir, sizeof(uint2), ot * ix->n, nt * ix->n, false, nullptr},
-      {(void **)&ix->d_tile_post, sizeof(uint16_t *), ot, nt, false, nullptr},
+      {(void **)&ix->d_tile_dir, sizeof(uint2), 2 * ot * ix->n, 2 * nt * ix->n, false, nullptr},
+      {(void **)&ix->d_tile_post, sizeof(uint16_t *), 2 * ot, 2 * nt, false, nullptr},
+      {(void **)&ix->d_tile_sel, 4, ot, nt, false, nullptr},
+      {(void **)&ix->d_born, 4, ix->cap, nc, false, nullptr},
+      {(void **)&ix->d_died, 4, ix->cap, nc, false, nullptr},
+      {(void **)&ix->d_recent, 4, ix->cap / 32, nc / 32, false, nullptr},
   };
   CK(cudaDeviceSynchronize());
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < NG; ++i) {
     if (i == 1 && planes == 1) continue;
     const size_t bytes = g[i].elem * g[i].n * (g[i].plane ? ix->m : 1);
     const cudaError_t err = sinn_dev_malloc(&g[i].q, bytes);
@@ -699,7 +728,7 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
       return sinn_check_cuda(err);
     }
   }
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < NG; ++i) {
     if (!g[i].q) continue;
     void *old = *g[i].dst;
     if (g[i].plane) {  // copy the m rows into the wider layout
@@ -717,11 +746,14 @@ static int grow_capacity(sinn_index *ix, uint64_t need) {
   ix->shape_version++;
   ix->live.resize(nc, 0);
   ix->nnz.resize(nc, 0);
-  ix->tile_post.resize(nt, nullptr);
+  ix->recent.resize(nc, 0);
+  ix->tile_post.resize(2 * nt, nullptr);
+  ix->tile_post_cap.resize(2 * nt, 0);
+  ix->tile_sel.resize(nt, 0);
+  ix->tile_flip_seq.resize(nt, 0);
   ix->tile_post_len.resize(nt, 0);
   ix->tile_nnz.resize(nt, 0);
   ix->tile_tombs.resize(nt, 0);
-  ix->tile_post_cap.resize(nt, 0);
   return SINN_OK;
 }
 
@@ -860,13 +892,17 @@ static uint64_t tile_words(const sinn_index *ix, uint64_t nnz) {
   return std::max<uint64_t>((nnz + W16 - 1) / W16 * W16, W16);
 }
 
-// Storage for the rebuild of tile t once it holds `nnz` entries: its own
-// buffer if that is large enough and not over twice too large, else a new one
-// with a quarter of room to grow.  Allocation failures return SINN_ENOMEM.
+// Storage for the rebuild of tile t once it holds `nnz` entries.  A rebuild
+// writes the tile's other copy (the one searches do not read): into that
+// copy's storage if it is large enough and not over twice too large, else
+// into a new buffer with a quarter of room to grow.  Allocation failures
+// return SINN_ENOMEM.
 static int tile_alloc(sinn_index *ix, uint32_t t, uint64_t nnz, cudaStream_t s, TileAlloc *out) {
   const uint64_t W16 = ix->T / 16, need = tile_words(ix, nnz);
-  if (ix->tile_post[t] && ix->tile_post_cap[t] >= need && ix->tile_post_cap[t] <= 2 * need) {
-    *out = {nullptr, ix->tile_post_cap[t]};  // the rebuild reads only the store
+  const uint64_t slot = (uint64_t)t * 2 + (1u - ix->tile_sel[t]);
+  if (ix->tile_post[slot] && ix->tile_post_cap[slot] >= need &&
+      ix->tile_post_cap[slot] <= 2 * need) {
+    *out = {nullptr, ix->tile_post_cap[slot]};  // the rebuild reads only the store
     return SINN_OK;
   }
   const uint64_t cap = need + need / 4 / W16 * W16;
@@ -876,16 +912,17 @@ static int tile_alloc(sinn_index *ix, uint32_t t, uint64_t nnz, cudaStream_t s, 
   return SINN_OK;
 }
 
-// Device scratch of a rebuild of nb tiles: counts, tiles, storage pointers,
-// storage sizes, lengths.
+// Device scratch of a rebuild of nb tiles: counts, tiles, target copies,
+// storage pointers, storage sizes, lengths.
 struct RebuildLayout {
-  size_t o_cn, o_tl, o_pt, o_pc, o_ln, bytes;
+  size_t o_cn, o_tl, o_vr, o_pt, o_pc, o_ln, bytes;
 };
 static RebuildLayout rebuild_layout(const sinn_index *ix, uint32_t nb) {
   RebuildLayout L;
   L.o_cn = 0;
   L.o_tl = L.o_cn + (size_t)nb * ix->n * 4;
-  L.o_pt = (L.o_tl + (size_t)nb * 4 + 15) / 16 * 16;
+  L.o_vr = L.o_tl + (size_t)nb * 4;
+  L.o_pt = (L.o_vr + (size_t)nb * 4 + 15) / 16 * 16;
   L.o_pc = L.o_pt + (size_t)nb * 8;
   L.o_ln = L.o_pc + (size_t)nb * 8;
   L.bytes = L.o_ln + (size_t)nb * 4;
@@ -898,47 +935,56 @@ static uint32_t rebuild_group_tiles(const sinn_index *ix, size_t tiles) {
   return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (1ull << 30) / per));
 }
 
-// Rebuild the postings of a group of tiles (sorted, unique) from the store,
-// into the storage `pre` gives per tile (allocated here if pre is null).
+// Rebuild the postings of a group of tiles (sorted, unique) from the store
+// into each tile's other copy, with the storage `pre` gives per tile
+// (allocated here if pre is null), then make those copies the ones searches
+// read.  A search already reading a tile keeps its copy intact; flip_seq is
+// the sequence number recorded for the switch.
 static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cudaStream_t s,
-                         const TileAlloc *pre) {
+                         const TileAlloc *pre, uint32_t flip_seq) {
   const RebuildLayout RL = rebuild_layout(ix, nb);
-  const size_t o_cn = RL.o_cn, o_tl = RL.o_tl, o_pt = RL.o_pt, o_pc = RL.o_pc, o_ln = RL.o_ln;
   int st = ensure_iscratch(ix, RL.bytes);
   if (st) return st;
   std::vector<uint16_t *> newp(nb);
   std::vector<uint64_t> pcap(nb);
+  std::vector<uint32_t> ver(nb);
   for (uint32_t i = 0; i < nb; ++i) {
     const uint32_t t = tiles[i];
+    ver[i] = 1u - ix->tile_sel[t];
+    const uint64_t slot = (uint64_t)t * 2 + ver[i];
     TileAlloc ta;
     if (pre) {
       ta = pre[i];
     } else if ((st = tile_alloc(ix, t, ix->tile_nnz[t], s, &ta))) {
       for (uint32_t k = 0; k < i; ++k)
-        if (newp[k] != ix->tile_post[tiles[k]]) cudaFreeAsync(newp[k], s);
+        if (newp[k] != ix->tile_post[(uint64_t)tiles[k] * 2 + ver[k]]) cudaFreeAsync(newp[k], s);
       return st;
     }
-    newp[i] = ta.p ? ta.p : ix->tile_post[t];
+    newp[i] = ta.p ? ta.p : ix->tile_post[slot];
     pcap[i] = ta.cap;
   }
-  const size_t hb = (size_t)nb * (4 + 8 + 8 + 4);
+  const size_t hb = (size_t)nb * (4 + 4 + 8 + 8);
   CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
   if ((st = sinn_ensure_pinned(ix, hb))) return st;
   char *hp = (char *)ix->pinned;
   memcpy(hp, tiles, (size_t)nb * 4);
-  memcpy(hp + (size_t)nb * 4, newp.data(), (size_t)nb * 8);
-  memcpy(hp + (size_t)nb * 12, pcap.data(), (size_t)nb * 8);
+  memcpy(hp + (size_t)nb * 4, ver.data(), (size_t)nb * 4);
+  memcpy(hp + (size_t)nb * 8, newp.data(), (size_t)nb * 8);
+  memcpy(hp + (size_t)nb * 16, pcap.data(), (size_t)nb * 8);
   char *sp = (char *)ix->iscratch;
-  CK(cudaMemcpyAsync(sp + o_tl, hp, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_pt, hp + (size_t)nb * 4, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sp + o_pc, hp + (size_t)nb * 12, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(sp + o_cn, 0, (size_t)nb * ix->n * 4, s));
+  CK(cudaMemcpyAsync(sp + RL.o_tl, hp, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + RL.o_vr, hp + (size_t)nb * 4, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + RL.o_pt, hp + (size_t)nb * 8, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sp + RL.o_pc, hp + (size_t)nb * 16, (size_t)nb * 8, cudaMemcpyHostToDevice,
+                     s));
+  CK(cudaMemsetAsync(sp + RL.o_cn, 0, (size_t)nb * ix->n * 4, s));
   RebuildArgs a;
-  a.tiles = (const uint32_t *)(sp + o_tl);
-  a.new_post = (uint16_t *const *)(sp + o_pt);
-  a.post_cap = (const uint64_t *)(sp + o_pc);
-  a.cnt = (uint32_t *)(sp + o_cn);
-  a.out_len = (uint32_t *)(sp + o_ln);
+  a.tiles = (const uint32_t *)(sp + RL.o_tl);
+  a.ver = (const uint32_t *)(sp + RL.o_vr);
+  a.new_post = (uint16_t *const *)(sp + RL.o_pt);
+  a.post_cap = (const uint64_t *)(sp + RL.o_pc);
+  a.cnt = (uint32_t *)(sp + RL.o_cn);
+  a.out_len = (uint32_t *)(sp + RL.o_ln);
   a.nb = nb;
   a.n = ix->n;
   a.T = ix->T;
@@ -949,22 +995,29 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   const uint64_t cap_blocks = (uint64_t)std::max(1, sms) * 32;
   const uint64_t slot_blocks = std::min<uint64_t>(((uint64_t)nb * ix->T + 7) / 8, cap_blocks);
   const uint64_t pair_blocks = std::min<uint64_t>(((uint64_t)nb * ix->n + 7) / 8, cap_blocks);
-  ix->launches += 4;
+  ix->launches += 5;
   k_rb_count<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
                                                    ix->d_fwd);
   k_rb_plan<<<nb, 1024, 0, s>>>(a, ix->d_tile_dir, ix->d_tile_post, ix->d_err);
   k_rb_scatter<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
                                                      ix->d_fwd, ix->d_tile_dir);
   k_rb_sort<<<(unsigned)pair_blocks, 256, (size_t)8 * (ix->T / 32) * 4, s>>>(a, ix->d_tile_dir);
+  k_rb_flip<<<(nb + 255) / 256, 256, 0, s>>>(a, ix->d_tile_sel);
   CK(cudaGetLastError());
   for (uint32_t i = 0; i < nb; ++i) {
     const uint32_t t = tiles[i];
-    if (ix->tile_post[t] && ix->tile_post[t] != newp[i]) CK(cudaFreeAsync(ix->tile_post[t], s));
-    ix->tile_post[t] = newp[i];
-    ix->tile_post_cap[t] = pcap[i];
+    const uint64_t slot = (uint64_t)t * 2 + ver[i];
+    // the copy's previous storage (replaced by a larger or smaller buffer)
+    // is read by no search: searches read the other copy until the flip
+    if (ix->tile_post[slot] && ix->tile_post[slot] != newp[i])
+      CK(cudaFreeAsync(ix->tile_post[slot], s));
+    ix->tile_post[slot] = newp[i];
+    ix->tile_post_cap[slot] = pcap[i];
+    ix->tile_sel[t] = (uint8_t)ver[i];
+    ix->tile_flip_seq[t] = flip_seq;
   }
   std::vector<uint32_t> lens(nb);
-  CK(cudaMemcpyAsync(hp, sp + o_ln, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp, sp + RL.o_ln, (size_t)nb * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   memcpy(lens.data(), hp, (size_t)nb * 4);
   for (uint32_t i = 0; i < nb; ++i) {
@@ -980,20 +1033,33 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
 // per-coordinate counts fit 1 GiB of scratch, into the storage `pre` gives
 // per tile (or allocated as they go if pre is null).
 static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s,
-                         const std::vector<TileAlloc> *pre) {
+                         const std::vector<TileAlloc> *pre, uint32_t flip_seq) {
   if (tiles.empty()) return SINN_OK;
   const uint32_t g = rebuild_group_tiles(ix, tiles.size());
   for (size_t g0 = 0; g0 < tiles.size(); g0 += g) {
     const uint32_t nb = (uint32_t)std::min<size_t>(g, tiles.size() - g0);
-    int st = rebuild_group(ix, tiles.data() + g0, nb, s, pre ? pre->data() + g0 : nullptr);
+    int st = rebuild_group(ix, tiles.data() + g0, nb, s, pre ? pre->data() + g0 : nullptr,
+                           flip_seq);
     if (st) return st;
   }
   return SINN_OK;
 }
 
-extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
-                           const float *values, uint32_t n_docs, uint32_t *out_ids,
-                           void *stream) {
+// From the first sequence-numbered mutation on, searches check the snapshot
+// words (recorded searches are made again to pass them).
+static void mark_snapshots(sinn_index *ix) {
+  if (!ix->snapshots) {
+    ix->snapshots = true;
+    ix->shape_version++;
+  }
+}
+
+// Alg. 5 for a batch (sinn_insert; with `at`, sinn_insert_at: the new ids
+// are born at sequence number seq, and a tile may only be rebuilt once no
+// search older than its last rebuild can still read its other copy).
+static int insert_impl(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                       const float *values, uint32_t n_docs, uint32_t *out_ids, void *stream,
+                       bool at, uint32_t seq) {
   if (!ix) return SINN_EINVAL;
   if (n_docs == 0) return SINN_OK;
   if (!indptr || !out_ids) return SINN_EINVAL;
@@ -1033,6 +1099,7 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   const uint64_t n_free = ix->free_ids.size();
   if (ix->next_id + (n_docs > n_free ? n_docs - n_free : 0) > 0xFFFFFFFEull) return SINN_ENOMEM;
   uint64_t max_id = 0;
+  bool reuse_recent = false;  // a reused id still carries snapshot words
   {
     auto fq = ix->free_ids;  // commit only after allocations succeed
     uint64_t nid = ix->next_id;
@@ -1040,15 +1107,12 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
       if (!fq.empty()) {
         ids[r] = fq.top();
         fq.pop();
+        reuse_recent = reuse_recent || ix->recent[ids[r]];
       } else {
         ids[r] = (uint32_t)nid++;
       }
       max_id = std::max<uint64_t>(max_id, ids[r]);
     }
-    if ((st = grow_capacity(ix, max_id + 1))) return st;
-    if ((st = grow_store(ix, ix->fwd_used + total))) return st;
-    // the rest of the insert's allocations, made before anything changes: on
-    // SINN_ENOMEM the index is as it was
     std::vector<std::pair<uint32_t, uint64_t>> te(n_docs);  // (tile, entries)
     for (uint32_t r = 0; r < n_docs; ++r) te[r] = {ids[r] >> ix->log2T, ip[r + 1] - ip[r]};
     std::sort(te.begin(), te.end());
@@ -1059,6 +1123,17 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
       }
       tile_add.back() += x.second;
     }
+    // a sequence-numbered insert rebuilds a tile into the copy searches do
+    // not read; a search older than the tile's last rebuild may still read
+    // it, unless every such search has been reclaimed
+    if (at)
+      for (uint32_t t : tiles)
+        if (t < ix->tile_flip_seq.size() && ix->tile_flip_seq[t] > ix->reclaimed)
+          return SINN_EBUSY;
+    if ((st = grow_capacity(ix, max_id + 1))) return st;
+    if ((st = grow_store(ix, ix->fwd_used + total))) return st;
+    // the rest of the insert's allocations, made before anything changes: on
+    // SINN_ENOMEM the index is as it was
     const uint32_t gmax = std::min<uint32_t>(rebuild_group_tiles(ix, tiles.size()),
                                              (uint32_t)tiles.size());
     const size_t o_off0 = ((size_t)n_docs * 4 + 15) / 16 * 16;
@@ -1097,6 +1172,17 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
   CK(cudaMemcpyAsync(d_off, hoff, (size_t)n_docs * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(out_ids, d_ids, (size_t)n_docs * 4, cudaMemcpyDeviceToDevice, s));
   ix->launches += 3;  // store, sketch, live bits (the tile rebuild counts itself)
+  if (at || reuse_recent) {
+    // visibility before the live bits: a search older than seq that sees an
+    // id live also sees it was born after its snapshot (a plain insert is
+    // visible to every snapshot)
+    ix->launches += at ? 3 : 2;
+    const unsigned g = (n_docs + 255) / 256;
+    k_fill_ids<<<g, 256, 0, s>>>(d_ids, n_docs, ix->d_born, at ? seq : 0u);
+    k_fill_ids<<<g, 256, 0, s>>>(d_ids, n_docs, ix->d_died, SINN_SEQ_NEVER);
+    if (at) k_set_live<<<g, 256, 0, s>>>(d_ids, n_docs, ix->d_recent, 1);
+    CK(cudaGetLastError());
+  }
   k_fwd_write<<<(n_docs + 7) / 8, 256, 0, s>>>(indptr, indices, values, n_docs, d_ids, d_off,
                                               ix->d_fwd, ix->d_fwd_off, ix->d_fwd_nnz,
                                               ix->d_coord_len, ix->fwd_cap, ix->cap, ix->d_err);
@@ -1114,46 +1200,58 @@ extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_
     ix->nnz[id] = (uint32_t)(ip[r + 1] - ip[r]);
     ix->tile_nnz[id >> ix->log2T] += ix->nnz[id];
     ix->live_count++;
+    if (at) {
+      ix->recent[id] = 1;
+      ix->recent_ins.push_back({seq, id});
+    }
   }
   ix->launches++;
   k_store_u64<<<1, 1, 0, s>>>(ix->d_live_count, ix->live_count);
   CK(cudaGetLastError());
-  if ((st = rebuild_tiles(ix, tiles, s, &pre))) return st;
+  if ((st = rebuild_tiles(ix, tiles, s, &pre, at ? seq : 0u))) return st;
   uint32_t bits = 0;
   if ((st = read_and_clear_err(ix, s, &bits))) return st;
   return bits ? SINN_EDEVICE : SINN_OK;
 }
 
-extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, void *stream) {
-  if (!ix) return SINN_EINVAL;
-  if (n_ids == 0) return SINN_OK;
-  if (!ids) return SINN_EINVAL;
-  SinnDevice dev_guard_(ix->device);
-  cudaStream_t s = (cudaStream_t)stream;
+extern "C" int sinn_insert(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                           const float *values, uint32_t n_docs, uint32_t *out_ids,
+                           void *stream) {
+  return insert_impl(ix, indptr, indices, values, n_docs, out_ids, stream, false, 0);
+}
+
+extern "C" int sinn_insert_at(sinn_index *ix, const uint64_t *indptr, const uint32_t *indices,
+                              const float *values, uint32_t n_docs, uint32_t *out_ids,
+                              uint32_t seq, void *stream) {
+  if (!ix || seq > SINN_SEQ_LATEST) return SINN_EINVAL;
+  mark_snapshots(ix);
+  return insert_impl(ix, indptr, indices, values, n_docs, out_ids, stream, true, seq);
+}
+
+// Sec. 4.3 deletion of n_ids live ids (host list v, device copy d_src):
+// postings tombstoned in the copy searches read, live bits cleared, ids
+// freed for reuse.
+static int delete_physical(sinn_index *ix, const uint32_t *d_src, const std::vector<uint32_t> &v,
+                           cudaStream_t s) {
+  const uint32_t n_ids = (uint32_t)v.size();
   int st;
-  if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
-  uint32_t *h = (uint32_t *)ix->pinned;
-  CK(cudaMemcpyAsync(h, ids, (size_t)n_ids * 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  std::vector<uint32_t> v(h, h + n_ids);
-  for (uint32_t id : v)
-    if (id >= ix->next_id || !ix->live[id]) return SINN_ENOTFOUND;
-  {
-    std::vector<uint32_t> srt(v);
-    std::sort(srt.begin(), srt.end());
-    if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SINN_EINVAL;
-  }
   const size_t o_cnt = ((size_t)n_ids * 4 + 15) / 16 * 16;
   if ((st = ensure_iscratch(ix, o_cnt + (size_t)n_ids * 4))) return st;
   if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
   uint32_t *d_ids = (uint32_t *)ix->iscratch;
   uint32_t *d_cnt = (uint32_t *)((char *)ix->iscratch + o_cnt);
-  CK(cudaMemcpyAsync(d_ids, ids, (size_t)n_ids * 4, cudaMemcpyDeviceToDevice, s));
+  if (d_src) {
+    CK(cudaMemcpyAsync(d_ids, d_src, (size_t)n_ids * 4, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaStreamSynchronize(s));  // the staging buffer is free
+    memcpy(ix->pinned, v.data(), (size_t)n_ids * 4);
+    CK(cudaMemcpyAsync(d_ids, ix->pinned, (size_t)n_ids * 4, cudaMemcpyHostToDevice, s));
+  }
   SinnPhase phase(ix, s, 5);
   ix->launches++;
   k_tombstone<<<(n_ids + 7) / 8, 256, 0, s>>>(d_ids, n_ids, ix->d_fwd_off, ix->d_fwd_nnz,
                                               ix->d_fwd, ix->d_tile_dir, ix->d_tile_post,
-                                              ix->d_live, ix->n, ix->log2T, d_cnt,
+                                              ix->d_tile_sel, ix->d_live, ix->n, ix->log2T, d_cnt,
                                               ix->d_coord_len, ix->d_err);
   CK(cudaGetLastError());
   uint32_t *hc = (uint32_t *)ix->pinned;
@@ -1178,20 +1276,125 @@ extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, 
   return bits ? SINN_EDEVICE : SINN_OK;
 }
 
+// The ids of a delete call on the host, checked: each live (and not already
+// deleted at a sequence number), none repeated.
+static int delete_ids(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, cudaStream_t s,
+                      std::vector<uint32_t> *out) {
+  int st;
+  if ((st = sinn_ensure_pinned(ix, (size_t)n_ids * 4 + 64))) return st;
+  uint32_t *h = (uint32_t *)ix->pinned;
+  CK(cudaMemcpyAsync(h, ids, (size_t)n_ids * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out->assign(h, h + n_ids);
+  for (uint32_t id : *out)
+    if (id >= ix->next_id || ix->live[id] != 1) return SINN_ENOTFOUND;
+  std::vector<uint32_t> srt(*out);
+  std::sort(srt.begin(), srt.end());
+  if (std::adjacent_find(srt.begin(), srt.end()) != srt.end()) return SINN_EINVAL;
+  return SINN_OK;
+}
+
+extern "C" int sinn_delete(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, void *stream) {
+  if (!ix) return SINN_EINVAL;
+  if (n_ids == 0) return SINN_OK;
+  if (!ids) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint32_t> v;
+  int st = delete_ids(ix, ids, n_ids, s, &v);
+  if (st) return st;
+  return delete_physical(ix, ids, v, s);
+}
+
+extern "C" int sinn_delete_at(sinn_index *ix, const uint32_t *ids, uint32_t n_ids, uint32_t seq,
+                              void *stream) {
+  if (!ix || seq > SINN_SEQ_LATEST) return SINN_EINVAL;
+  if (n_ids == 0) return SINN_OK;
+  if (!ids) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint32_t> v;
+  int st = delete_ids(ix, ids, n_ids, s, &v);
+  if (st) return st;
+  mark_snapshots(ix);
+  // searches at seq or later no longer count the ids; their postings stay
+  // for the older ones until sinn_reclaim removes them
+  SinnPhase phase(ix, s, 5);
+  ix->launches += 2;
+  const unsigned g = (n_ids + 255) / 256;
+  k_fill_ids<<<g, 256, 0, s>>>(ids, n_ids, ix->d_died, seq);
+  k_set_live<<<g, 256, 0, s>>>(ids, n_ids, ix->d_recent, 1);
+  CK(cudaGetLastError());
+  for (uint32_t id : v) {
+    ix->live[id] = 2;
+    ix->recent[id] = 1;
+    ix->pending_del.push_back({seq, id});
+  }
+  CK(cudaStreamSynchronize(s));
+  return SINN_OK;
+}
+
+extern "C" int sinn_reclaim(sinn_index *ix, uint32_t horizon, void *stream) {
+  if (!ix || horizon > SINN_SEQ_LATEST + 1) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  ix->reclaimed = std::max(ix->reclaimed, horizon);
+  // deleted ids no search still counts: postings removed, ids freed (their
+  // death words stay, so a search that still sees them live drops them)
+  std::vector<uint32_t> dead;
+  std::vector<std::pair<uint32_t, uint32_t>> keep;
+  for (const auto &p : ix->pending_del) {
+    if (p.first <= ix->reclaimed) dead.push_back(p.second);
+    else keep.push_back(p);
+  }
+  int st = SINN_OK;
+  if (!dead.empty()) {
+    for (uint32_t id : dead) ix->live[id] = 1;  // physically live until removed
+    st = delete_physical(ix, nullptr, dead, s);
+    if (st) {
+      for (uint32_t id : dead) ix->live[id] = 2;
+      return st;
+    }
+    ix->pending_del.swap(keep);
+  }
+  // inserted ids every search in flight counts: no snapshot check needed
+  std::vector<uint32_t> settled;
+  std::vector<std::pair<uint32_t, uint32_t>> young;
+  for (const auto &p : ix->recent_ins) {
+    if (p.first > ix->reclaimed) young.push_back(p);
+    else if (ix->live[p.second] == 1) settled.push_back(p.second);
+  }
+  ix->recent_ins.swap(young);
+  if (!settled.empty()) {
+    const size_t o = 0;
+    if ((st = ensure_iscratch(ix, o + settled.size() * 4))) return st;
+    if ((st = sinn_ensure_pinned(ix, settled.size() * 4 + 64))) return st;
+    CK(cudaStreamSynchronize(s));
+    memcpy(ix->pinned, settled.data(), settled.size() * 4);
+    CK(cudaMemcpyAsync(ix->iscratch, ix->pinned, settled.size() * 4, cudaMemcpyHostToDevice, s));
+    ix->launches++;
+    k_set_live<<<(unsigned)((settled.size() + 255) / 256), 256, 0, s>>>(
+        (const uint32_t *)ix->iscratch, (uint32_t)settled.size(), ix->d_recent, 0);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    for (uint32_t id : settled) ix->recent[id] = 0;
+  }
+  return SINN_OK;
+}
+
 extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   if (!ix || !out) return SINN_EINVAL;
   memset(out, 0, sizeof(*out));
-  out->live = ix->live_count;
+  out->live = ix->live_count - ix->pending_del.size();
   out->capacity = ix->cap;
   out->next_id = ix->next_id;
   uint64_t post = 0, pbytes = 0;
-  for (size_t t = 0; t < ix->tile_post.size(); ++t) {
-    post += ix->tile_post_len[t];
-    pbytes += ix->tile_post_cap[t] * 2;
-  }
+  for (size_t t = 0; t < ix->tile_post_len.size(); ++t) post += ix->tile_post_len[t];
+  for (size_t i = 0; i < ix->tile_post_cap.size(); ++i) pbytes += ix->tile_post_cap[i] * 2;
   out->postings = post;
   out->tombstones = ix->tombstones;
-  out->bytes_lists = pbytes + (ix->cap / ix->T) * (uint64_t)ix->n * 8;
+  out->bytes_lists = pbytes + 2 * (ix->cap / ix->T) * (uint64_t)ix->n * 8;
+  out->pending_deletes = (uint32_t)ix->pending_del.size();
   out->bytes_sketch = (ix->d_L ? 2ull : 1ull) * ix->m * ix->cap * ix->sk_elem;
   out->bytes_store = ix->fwd_cap * 8 + ix->cap * 12;
   out->bytes_scratch = ix->scratch_size + ix->iscratch_size;
@@ -1232,16 +1435,19 @@ extern "C" int sinn_inverted_list(sinn_index *ix, uint32_t coord, uint32_t *out,
   CK(cudaDeviceSynchronize());
   const uint64_t nt = ix->cap / ix->T;
   const uint32_t W16 = ix->T / 16;
-  std::vector<uint2> de(nt);
-  CK(cudaMemcpy2D(de.data(), sizeof(uint2), ix->d_tile_dir + coord, (size_t)ix->n * sizeof(uint2),
-                  sizeof(uint2), nt, cudaMemcpyDeviceToHost));
+  // the coordinate's entry in both copies of every tile; the current one counts
+  std::vector<uint2> dd(2 * nt);
+  CK(cudaMemcpy2D(dd.data(), sizeof(uint2), ix->d_tile_dir + coord, (size_t)ix->n * sizeof(uint2),
+                  sizeof(uint2), 2 * nt, cudaMemcpyDeviceToHost));
   uint64_t cnt = 0;
   std::vector<uint16_t> buf;
   for (uint64_t t = 0; t < nt; ++t) {
-    if (de[t].y == 0 || !ix->tile_post[t]) continue;
-    const bool bitmap = de[t].y >= (ix->T >> SINN_BITMAP_SHIFT);
-    buf.resize(bitmap ? W16 : de[t].y);
-    CK(cudaMemcpy(buf.data(), ix->tile_post[t] + de[t].x, buf.size() * 2, cudaMemcpyDeviceToHost));
+    const uint64_t slot = 2 * t + ix->tile_sel[t];
+    const uint2 de = dd[slot];
+    if (de.y == 0 || !ix->tile_post[slot]) continue;
+    const bool bitmap = de.y >= (ix->T >> SINN_BITMAP_SHIFT);
+    buf.resize(bitmap ? W16 : de.y);
+    CK(cudaMemcpy(buf.data(), ix->tile_post[slot] + de.x, buf.size() * 2, cudaMemcpyDeviceToHost));
     auto emit = [&](uint32_t d) {
       if (cnt < cap) out[cnt] = (uint32_t)((t << ix->log2T) + d);
       cnt++;
@@ -1349,21 +1555,33 @@ int save_body(sinn_index *ix, File &F) {
   if ((st = put_array(F, ix->d_fwd_off, cap * 8, true))) return st;
   if ((st = put_array(F, ix->d_fwd_nnz, cap * 4, true))) return st;
   if ((st = put_array(F, ix->d_fwd, ix->fwd_used * 8, true))) return st;
-  if ((st = put_array(F, ix->d_tile_dir, tiles * ix->n * 8, true))) return st;
+  {  // the directory of each tile's current copy
+    const uint64_t bytes = tiles * ix->n * 8;
+    if (!F.put(&bytes, 8)) return SINN_EIO;
+    for (uint64_t t = 0; t < tiles; ++t) {
+      CK(cudaMemcpy(F.buf.data(), ix->d_tile_dir + (2 * t + ix->tile_sel[t]) * ix->n,
+                    (size_t)ix->n * 8, cudaMemcpyDeviceToHost));
+      if (!F.put(F.buf.data(), (size_t)ix->n * 8)) return SINN_EIO;
+    }
+  }
   if ((st = put_array(F, ix->d_coord_len, (uint64_t)ix->n * 4, true))) return st;
   if ((st = put_array(F, ix->live.data(), cap, false))) return st;
   if ((st = put_array(F, ix->nnz.data(), cap * 4, false))) return st;
   std::vector<uint32_t> free_ids;
   for (auto q = ix->free_ids; !q.empty(); q.pop()) free_ids.push_back(q.top());
   if ((st = put_array(F, free_ids.data(), free_ids.size() * 4, false))) return st;
+  std::vector<uint64_t> cur_cap(tiles);
+  for (uint64_t t = 0; t < tiles; ++t) cur_cap[t] = ix->tile_post_cap[2 * t + ix->tile_sel[t]];
   if ((st = put_array(F, ix->tile_post_len.data(), tiles * 8, false))) return st;
-  if ((st = put_array(F, ix->tile_post_cap.data(), tiles * 8, false))) return st;
+  if ((st = put_array(F, cur_cap.data(), tiles * 8, false))) return st;
   if ((st = put_array(F, ix->tile_nnz.data(), tiles * 8, false))) return st;
   if ((st = put_array(F, ix->tile_tombs.data(), tiles * 8, false))) return st;
-  for (uint64_t t = 0; t < tiles; ++t)
-    if ((st = put_array(F, ix->tile_post[t], ix->tile_post[t] ? ix->tile_post_cap[t] * 2 : 0,
-                        true)))
+  for (uint64_t t = 0; t < tiles; ++t) {
+    const uint64_t slot = 2 * t + ix->tile_sel[t];
+    if ((st = put_array(F, ix->tile_post[slot],
+                        ix->tile_post[slot] ? ix->tile_post_cap[slot] * 2 : 0, true)))
       return st;
+  }
   return SINN_OK;
 }
 
@@ -1371,6 +1589,8 @@ int save_body(sinn_index *ix, File &F) {
 
 extern "C" int sinn_save(sinn_index *ix, const char *path) {
   if (!ix || !path) return SINN_EINVAL;
+  // deletions not yet reclaimed have no place in the file
+  if (!ix->pending_del.empty()) return SINN_EBUSY;
   SinnDevice dev_guard_(ix->device);
   CK(cudaDeviceSynchronize());
   // written to a temporary file beside the target and renamed over it only
@@ -1602,25 +1822,30 @@ extern "C" int sinn_load(const char *path, sinn_index **out) {
   if ((st = upload_from(F, L.at_U, ix->d_U, plane))) return fail(st);
   if ((st = upload_from(F, L.at_L, ix->d_L, ix->d_L ? plane : 0))) return fail(st);
   if ((st = upload_from(F, L.at_fwd, ix->d_fwd, hd.fwd_used * 8))) return fail(st);
-  for (uint64_t t = 0; t < tiles; ++t) {
+  for (uint64_t t = 0; t < tiles; ++t) {  // every tile's copy 0 is current
     if (!L.post_cap[t]) continue;
     uint16_t *p = nullptr;
     if ((st = sinn_check_cuda(sinn_dev_malloc((void **)&p, L.post_cap[t] * 2)))) return fail(st);
-    ix->tile_post[t] = p;
+    ix->tile_post[2 * t] = p;
+    ix->tile_post_cap[2 * t] = L.post_cap[t];
     if ((st = upload_from(F, L.at_post[t], p, L.post_cap[t] * 2))) return fail(st);
   }
   if ((st = up(ix->d_live, L.live_bits.data(), cap / 32 * 4))) return fail(st);
   if ((st = up(ix->d_fwd_off, L.fwd_off.data(), cap * 8))) return fail(st);
   if ((st = up(ix->d_fwd_nnz, L.fwd_nnz.data(), cap * 4))) return fail(st);
-  if ((st = up(ix->d_tile_dir, L.dir.data(), tiles * hd.n * 8))) return fail(st);
+  if (tiles &&
+      (st = sinn_check_cuda(cudaMemcpy2D(ix->d_tile_dir, (size_t)2 * hd.n * 8, L.dir.data(),
+                                         (size_t)hd.n * 8, (size_t)hd.n * 8, tiles,
+                                         cudaMemcpyHostToDevice))))
+    return fail(st);
   if ((st = up(ix->d_coord_len, L.coord_len.data(), (uint64_t)hd.n * 4))) return fail(st);
-  if ((st = up(ix->d_tile_post, ix->tile_post.data(), tiles * sizeof(uint16_t *)))) return fail(st);
+  if ((st = up(ix->d_tile_post, ix->tile_post.data(), 2 * tiles * sizeof(uint16_t *))))
+    return fail(st);
   if ((st = up(ix->d_live_count, &hd.live_count, 8))) return fail(st);
   ix->live = L.live;
   ix->nnz = L.nnz;
   for (uint32_t id : L.free_ids) ix->free_ids.push(id);
   ix->tile_post_len = L.post_len;
-  ix->tile_post_cap = L.post_cap;
   ix->tile_nnz = L.tile_nnz;
   ix->tile_tombs = L.tile_tombs;
   ix->next_id = hd.next_id;

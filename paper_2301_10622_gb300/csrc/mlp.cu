@@ -346,7 +346,7 @@ __global__ void k_weights_bf16(const float *W1, const float *W2, uint32_t nin, u
 // summed over the tiles' containers (tombstones included).
 __global__ void k_features(const uint64_t *__restrict__ ip, const uint32_t *__restrict__ idx,
                            const float *__restrict__ val, uint32_t n, const uint2 *tile_dir,
-                           uint32_t tiles, float *out) {
+                           const uint32_t *tile_sel, uint32_t tiles, float *out) {
   const uint32_t q = blockIdx.x, tid = threadIdx.x;
   __shared__ uint32_t sj[SINN_KP_TOP];
   __shared__ float red[3][32];
@@ -407,7 +407,8 @@ __global__ void k_features(const uint64_t *__restrict__ ip, const uint32_t *__re
     float f = 0.0f;
     if (r < s_top) {
       uint64_t cnt = 0;
-      for (uint32_t t = lane; t < tiles; t += 32) cnt += tile_dir[(uint64_t)t * n + sj[r]].y;
+      for (uint32_t t = lane; t < tiles; t += 32)  // each tile's current copy
+        cnt += tile_dir[((uint64_t)t * 2 + __ldcg(tile_sel + t)) * n + sj[r]].y;
       for (int s2 = 16; s2 > 0; s2 >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, s2);
       f = log2f(1.0f + (float)cnt);
     }
@@ -832,8 +833,8 @@ extern "C" int sinn_kp_features(sinn_index *ix, const uint64_t *q_indptr, const 
   if (n_q == 0) return SINN_OK;
   SinnDevice dev_guard_(ix->device);
   k_features<<<n_q, 256, 0, (cudaStream_t)stream>>>(q_indptr, q_indices, q_values, ix->n,
-                                                    ix->d_tile_dir, (uint32_t)(ix->cap / ix->T),
-                                                    out);
+                                                    ix->d_tile_dir, ix->d_tile_sel,
+                                                    (uint32_t)(ix->cap / ix->T), out);
   CK(cudaGetLastError());
   return SINN_OK;
 }

@@ -213,8 +213,12 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
 // that have postings in this tile, then walks the flattened (term, posting)
 // space so every thread stays busy whatever the list lengths.
 struct ScoreArgs {
-  const uint2 *tile_dir;
-  uint16_t *const *tile_post;
+  const uint2 *tile_dir;        // copy v of tile t at (2t + v) n
+  uint16_t *const *tile_post;   // storage of copy v of tile t at 2t + v
+  const uint32_t *sel;          // per tile: the copy to read
+  const uint32_t *recent;       // ids whose visibility depends on the snapshot
+  const uint32_t *born, *died;  // their birth and death sequence numbers
+  uint32_t seq;                 // the search's snapshot
   const void *U;  // sketch planes: fp32 or bfloat16 bits (S below)
   const void *L;
   const uint32_t *pi;
@@ -327,16 +331,44 @@ __device__ __forceinline__ float4 decode4(const S *const *row, uint32_t h, bool 
 
 // One warp: start the copies of the directory entries {start, count} of the
 // first nt query terms (coordinates tj, in shared memory) in tile t into dst
-// (8 bytes each, cp.async).
+// (8 bytes each, cp.async), from the tile's current copy, whose number goes
+// to *ver.
 __device__ __forceinline__ void dir_fetch(const ScoreArgs &a, const uint32_t *tj, uint32_t nt,
-                                          uint32_t t, uint2 *dst, uint32_t lane) {
-  const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
+                                          uint32_t t, uint2 *dst, uint32_t *ver, uint32_t lane) {
+  // one load for the warp: every lane reads the same copy of the tile
+  const uint32_t v = __ldcg(a.sel + t);
+  if (lane == 0) *ver = v;
+  const uint2 *dir = a.tile_dir + ((uint64_t)t * 2 + v) * a.n;
   for (uint32_t k = lane; k < nt; k += 32) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + k);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(dir + tj[k])
                  : "memory");
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// The recent bits of this thread's 4 ids (id a multiple of 4; the warp's
+// lanes cover consecutive ids, 8 lanes per 32-bit word) among the live ones
+// in lwv, read by one lane per word once a live bit was seen; 0 when the
+// index keeps no snapshot words.  Every lane of the warp takes part.
+__device__ __forceinline__ uint32_t recent_bits4(const ScoreArgs &a, uint64_t id, uint32_t lwv,
+                                                 uint32_t lane) {
+  if (!a.recent || !__any_sync(0xFFFFFFFFu, lwv != 0u)) return 0u;
+  uint32_t w = 0u;
+  if ((lane & 7u) == 0u) w = sinn_ld_gpu(a.recent + (id >> 5));
+  w = __shfl_sync(0xFFFFFFFFu, w, lane & ~7u);
+  return (w >> (id & 31)) & lwv;
+}
+
+// Live ids of this thread's 4 (bits of lwv) that the search's snapshot counts.
+__device__ __forceinline__ uint32_t visible4(const ScoreArgs &a, uint64_t id, uint32_t lwv,
+                                             uint32_t lane) {
+  const uint32_t rwv = recent_bits4(a, id, lwv, lane);
+  if (rwv)
+    for (uint32_t q = 0; q < 4; ++q)
+      if (((rwv >> q) & 1u) && !sinn_visible_recent(a.born, a.died, a.seq, id + q))
+        lwv &= ~(1u << q);
+  return lwv;
 }
 
 // Alg. 6 for query slot b over tiles [t_beg, t_end).  A query term's postings
@@ -388,6 +420,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
   // directory entries of the query's terms for this tile and the next one
   // (queries of at most kTermBatch terms: fetched a tile ahead by cp.async)
   __shared__ uint2 s_dir[2][kTermBatch];
+  __shared__ uint32_t s_ver[2], s_vt;  // copies of the prefetched entries; of this tile
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
@@ -420,14 +453,12 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
       }
     }
     __syncwarp();
-    if (t_beg < t_end) dir_fetch(a, t_j, nt, t_beg, s_dir[0], lane);
+    if (t_beg < t_end) dir_fetch(a, t_j, nt, t_beg, s_dir[0], &s_ver[0], lane);
   }
   __syncthreads();
   // keys below the bound are neither counted nor emitted
   const uint32_t lb = s_lb;
   for (uint32_t t = t_beg; t < t_end; ++t) {
-    const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
-    const uint16_t *post = a.tile_post[t];
     const uint64_t id0 = (uint64_t)t << a.log2T;
     __syncthreads();  // the previous tile's epilogue is done with acc, bacc and the list
     bool touch = false;
@@ -443,6 +474,12 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           asm volatile("cp.async.wait_all;\n" ::: "memory");  // this tile's entries
           __syncwarp();
         }
+        // the tile's copy: the one its entries were prefetched from, or (terms
+        // restaged per batch) the current one, read once for all batches
+        const uint32_t vt = nbatch == 1 ? s_ver[pb] : (bi == 0 ? __ldcg(a.sel + t) : s_vt);
+        const uint2 *dir = a.tile_dir + ((uint64_t)t * 2 + vt) * a.n;
+        __syncwarp();
+        if (lane == 0) s_vt = vt;
         for (uint32_t k = lane; k < nb; k += 32) {
           uint2 de;
           if (nbatch == 1) {
@@ -462,7 +499,8 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           t_cp[k] = de.y >= BMIN ? 0u : (WALK ? de.y : (de.y + 31) >> 5);
         }
         // the next tile's entries arrive while this tile is scored
-        if (nbatch == 1 && t + 1 < t_end) dir_fetch(a, t_j, nb, t + 1, s_dir[pb ^ 1u], lane);
+        if (nbatch == 1 && t + 1 < t_end)
+          dir_fetch(a, t_j, nb, t + 1, s_dir[pb ^ 1u], &s_ver[pb ^ 1u], lane);
         __syncwarp();
         uint32_t run = 0, nbm = 0, apost = 0;
         for (uint32_t base = 0; base < nb; base += 32) {
@@ -494,6 +532,7 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
         }
       }
       __syncthreads();
+      const uint16_t *post = a.tile_post[(uint64_t)t * 2 + s_vt];
       // a touched-list tile (block-uniform): arrays only, bound above zero
       touch = nbatch == 1 && s_nbm == 0 && lb > kZeroBin && s_apost <= kTouchCap;
       // bitmap terms: thread tid owns ids 4*tid + 4*kScoreThreads*g .. +3;
@@ -655,7 +694,10 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           touched[d >> 5] = 0u;
         }
         const uint32_t key = sinn_f2key(sc + 0.0f);
-        const bool em = in && sinn_is_live(a.live, id0 + d) && (key >> 20) >= lb;
+        const uint64_t id = id0 + d;
+        const bool em = in && sinn_is_live(a.live, id) && (key >> 20) >= lb &&
+                        (!a.recent || !((sinn_ld_gpu(a.recent + (id >> 5)) >> (id & 31)) & 1u) ||
+                         sinn_visible_recent(a.born, a.died, a.seq, id));
         if (em) atomicAdd(&gh[key >> 20], 1u);
         if (__any_sync(0xFFFFFFFFu, em)) {
           const uint32_t p = warp_append(em, &bt.ecnt[b]);
@@ -682,7 +724,10 @@ __device__ void score_tiles(const ScoreArgs &a, const Batch &bt, uint32_t b, uin
           sa = make_float4(sa.x + y.x, sa.y + y.y, sa.z + y.z, sa.w + y.w);
         }
       }
-      const uint32_t lwv = in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) : 0u;
+      // live ids, less those the search's snapshot does not count
+      const uint32_t lwv =
+          visible4(a, id0 + d0, in ? (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) & 15u : 0u,
+                   lane);
       const float rv[4] = {sa.x, sa.y, sa.z, sa.w};
       // ids at or above the running bound count and are emitted
 #pragma unroll
@@ -797,7 +842,7 @@ __global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Bat
   __shared__ uint32_t t_bin[kTermBatch * SINN_MAX_H];
   __shared__ float t_v[kTermBatch];
   __shared__ uint8_t t_bl[kTermBatch], t_al[kTermBatch];  // bitmap / array terms
-  __shared__ uint32_t s_nbm, s_nal;
+  __shared__ uint32_t s_nbm, s_nal, s_v;
   float *acc = (float *)acc4;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t T = a.T, BMIN = T >> SINN_BITMAP_SHIFT, spt = T / kLoneSlice;
@@ -827,10 +872,12 @@ __global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Bat
     }
     const uint32_t nt = bt.ns[b];  // Alg. 6 scores the budget's prefix
     const QTerm *terms = bt.terms + (uint64_t)b * a.qmax;
-    const uint2 *dir = a.tile_dir + (uint64_t)t * a.n;
-    const uint16_t *post = a.tile_post[t];
     const uint64_t id0 = (uint64_t)t << a.log2T;
     const uint32_t d0 = s0 + 4 * tid;  // this thread's 4 ids
+    if (tid == 0) s_v = __ldcg(a.sel + t);  // the tile's copy, for the whole item
+    __syncthreads();
+    const uint2 *dir = a.tile_dir + ((uint64_t)t * 2 + s_v) * a.n;
+    const uint16_t *post = a.tile_post[(uint64_t)t * 2 + s_v];
     acc4[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     for (uint32_t i0 = 0; i0 < nt; i0 += kTermBatch) {
@@ -926,7 +973,9 @@ __global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Bat
     __syncthreads();  // the array terms' atomics are complete
     const float4 x = acc4[tid];
     const float rv[4] = {r.x + x.x, r.y + x.y, r.z + x.z, r.w + x.w};
-    const uint32_t lwv = __ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31);
+    // live ids, less those the search's snapshot does not count
+    const uint32_t lwv =
+        visible4(a, id0 + d0, (__ldg(a.live + ((id0 + d0) >> 5)) >> (d0 & 31)) & 15u, lane);
     uint32_t kv[4];
 #pragma unroll
     for (uint32_t q = 0; q < 4; ++q) {
@@ -1083,6 +1132,29 @@ __global__ void k_pick(Batch bt, uint32_t level) {
     const uint32_t b = bt.flagged[f];
     SelState st = bt.sel[b];
     if (level == 0) {
+      // the dense histogram counts every id the search sees: a snapshot may
+      // see fewer than the live count that bounded kq
+      __shared__ uint32_t s_tot;
+      if (threadIdx.x == 0) s_tot = 0;
+      __syncthreads();
+      uint32_t c = 0;
+      for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x) c += bt.hist0[(uint64_t)b * 4096 + i];
+      atomicAdd(&s_tot, c);
+      __syncthreads();
+      const uint32_t tot = s_tot;
+      __syncthreads();
+      if (tot < st.kq) {
+        st.kq = tot;
+        if (threadIdx.x == 0) bt.sel[b].kq = tot;
+      }
+      if (st.kq == 0) {
+        if (threadIdx.x == 0) {
+          st.mode = SEL_DONE;
+          bt.sel[b] = st;
+        }
+        __syncthreads();
+        continue;
+      }
       st.rem = st.kq;
       st.prefix = 0;
       st.pbits = 0;
@@ -1576,6 +1648,7 @@ struct SearchReq {
   uint32_t n_q, k, kp, kp_min, kp_max;
   const uint32_t *kp_arr;
   const uint64_t *budget_arr;  // per-query Alg. 6 budgets (0 = none), or null: the index's
+  uint32_t seq = SINN_SEQ_LATEST;  // snapshot: the ids the search counts
   uint32_t *out_ids;
   float *out_scores;
   uint32_t *out_count;
@@ -1650,6 +1723,12 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   ScoreArgs sa;
   sa.tile_dir = ix->d_tile_dir;
   sa.tile_post = ix->d_tile_post;
+  sa.sel = ix->d_tile_sel;
+  // without sequence-numbered mutations every live id counts for every search
+  sa.recent = ix->snapshots ? ix->d_recent : nullptr;
+  sa.born = ix->d_born;
+  sa.died = ix->d_died;
+  sa.seq = r.seq;
   sa.U = ix->d_U;
   sa.L = ix->d_L;
   sa.pi = ix->d_pi;
@@ -2031,7 +2110,14 @@ struct sinn_ctx {
   sinn_index *ix = nullptr;
   void *scratch = nullptr;
   size_t bytes = 0;
+  uint32_t seq = SINN_SEQ_LATEST;  // snapshot its searches see
 };
+
+extern "C" int sinn_ctx_set_snapshot(sinn_ctx *c, uint32_t seq) {
+  if (!c || seq > SINN_SEQ_LATEST) return SINN_EINVAL;
+  c->seq = seq;
+  return SINN_OK;
+}
 
 extern "C" int sinn_ctx_create(sinn_index *ix, uint64_t scratch_bytes, sinn_ctx **out) {
   if (!ix || !out || scratch_bytes < (1u << 20)) return SINN_EINVAL;
@@ -2092,6 +2178,7 @@ extern "C" int sinn_search_ctx(sinn_ctx *c, const uint64_t *q_indptr, const uint
   r.out_ids = out_ids;
   r.out_scores = out_scores;
   r.stage = Stage::kFull;
+  r.seq = c->seq;
   return run_search(ix, r, (cudaStream_t)stream, &fx);
 }
 
@@ -2123,6 +2210,7 @@ int sinn_search_ext(sinn_index *ix, sinn_ctx *c, const uint64_t *q_indptr,
   r.out_scores = out_scores;
   r.stage = Stage::kFull;
   if (!c) return run_search(ix, r, s);
+  r.seq = c->seq;
   FixedScratch fx{c->scratch, c->bytes};
   return run_search(ix, r, s, &fx);
 }

@@ -35,6 +35,9 @@
 // bits that mean a kernel went wrong (SINN_EDEVICE), not a malformed input
 #define SINN_DERR_DEVICE (SINN_DERR_INTERNAL | SINN_DERR_TIMEOUT | SINN_DERR_BOUNDS)
 
+// never deleted (died of a live id)
+#define SINN_SEQ_NEVER 0xFFFFFFFFu
+
 // Index checks compiled in with -DSINN_BOUNDS_CHECK (the library's stand-in
 // for a memory checker): a failed check sets SINN_DERR_BOUNDS in the error
 // word `err` and the caller skips the access.  Compiled out, the condition is
@@ -74,25 +77,48 @@ struct sinn_index {
   uint32_t *d_fwd_nnz = nullptr;   // cap: entries stored (zeros included)
   uint2 *d_fwd = nullptr;          // vector store pool: (coordinate, value bits)
   uint64_t fwd_cap = 0, fwd_used = 0;
-  uint2 *d_tile_dir = nullptr;     // tiles_cap x n containers {start, count} per tile
-                                   // (count >= T/8: bitmap of T bits, else sorted array)
-  uint16_t **d_tile_post = nullptr;  // tiles_cap device pointers
+  // Each tile has two copies of its containers (directory and storage), so
+  // that a rebuild can write one while searches read the other; d_tile_sel
+  // names the copy searches use.  Copy v of tile t: directory entries at
+  // d_tile_dir + (2t + v) n (per coordinate {start, count}; count >= T/8: a
+  // bitmap of T bits, else a sorted array), storage d_tile_post[2t + v].
+  uint2 *d_tile_dir = nullptr;     // 2 x tiles_cap x n
+  uint16_t **d_tile_post = nullptr;  // 2 x tiles_cap device pointers
+  uint32_t *d_tile_sel = nullptr;  // tiles_cap: the copy searches read
+  // Snapshot visibility: a search at sequence number s counts id i only if
+  // born[i] <= s < died[i]; consulted only for ids whose recent bit is set
+  // (every other live id is visible to every search).
+  uint32_t *d_born = nullptr;      // cap
+  uint32_t *d_died = nullptr;      // cap
+  uint32_t *d_recent = nullptr;    // cap/32 bitmap words
   uint32_t *d_err = nullptr;       // sticky device error bits
   uint64_t *d_live_count = nullptr;  // live_count, kept on the device for the searches
   uint32_t *d_coord_len = nullptr;   // n: live postings per coordinate, |I[j]|
   uint64_t cap = 0;                // id capacity = tiles_cap * T
 
   // ---- host mirror
-  std::vector<uint8_t> live;        // per id
+  std::vector<uint8_t> live;        // per id: 1 live, 2 deleted at a sequence number
+                                    // but its postings kept (sinn_delete_at), 0 free
   std::vector<uint32_t> nnz;        // per id: stored entries of the live vector
+  std::vector<uint8_t> recent;      // per id: its recent bit is set on the device
   std::priority_queue<uint32_t, std::vector<uint32_t>, std::greater<uint32_t>> free_ids;
-  uint64_t next_id = 0, live_count = 0;
-  std::vector<uint16_t *> tile_post;     // per tile posting array (device)
-  std::vector<uint64_t> tile_post_len;   // postings held (tombstones included)
-  std::vector<uint64_t> tile_post_cap;   // storage words allocated per tile
+  uint64_t next_id = 0, live_count = 0;  // live_count: ids with postings (live != 0)
+  std::vector<uint16_t *> tile_post;     // 2 per tile: each copy's storage (device)
+  std::vector<uint64_t> tile_post_cap;   // 2 per tile: storage words of each copy
+  std::vector<uint8_t> tile_sel;         // per tile: the copy searches read
+  std::vector<uint32_t> tile_flip_seq;   // per tile: sequence number of the insert that
+                                         // made that copy current (0: stream-ordered)
+  std::vector<uint64_t> tile_post_len;   // per tile: postings of the current copy
+                                         // (tombstones included)
   std::vector<uint64_t> tile_nnz;        // sum of nnz over live vectors of the tile
   std::vector<uint64_t> tile_tombs;      // tombstoned postings per tile
   uint64_t tombstones = 0;
+  // sequence-numbered mutations (sinn_insert_at, sinn_delete_at, sinn_reclaim)
+  bool snapshots = false;   // a sequence-numbered mutation was made: searches check
+                            // the snapshot words (set once, never cleared)
+  uint32_t reclaimed = 0;   // every search at a smaller sequence number has finished
+  std::vector<std::pair<uint32_t, uint32_t>> pending_del;  // (died, id), postings kept
+  std::vector<std::pair<uint32_t, uint32_t>> recent_ins;   // (born, id), recent bit set
   // Bumped whenever a recorded search (sinn_plan) would go stale: device
   // arrays reallocated, the tiles in use or the tuning changed.
   uint64_t shape_version = 0;
@@ -196,4 +222,23 @@ __device__ __forceinline__ uint16_t sinn_bf16_dir(float x, bool up) {
 __device__ __forceinline__ float sinn_bf16_f(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
 __device__ __forceinline__ bool sinn_is_live(const uint32_t *live, uint64_t id) {
   return (__ldg(live + (id >> 5)) >> (id & 31)) & 1u;
+}
+
+// A load from L2 that the compiler neither caches nor moves ahead of the
+// code that decides to make it: the snapshot words are written by mutations
+// that may run while a search does.  Taken only after the id's live bit was
+// seen set, it sees the visibility words that the mutation wrote before it
+// set that bit (they were written by an earlier kernel of its stream).
+__device__ __forceinline__ uint32_t sinn_ld_gpu(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Whether a search at sequence number seq counts a live id whose recent bit
+// (bit of rwv, the id's recent-bitmap word) is set: only when
+// born <= seq < died.  Ids whose recent bit is clear count for every search.
+__device__ __forceinline__ bool sinn_visible_recent(const uint32_t *born, const uint32_t *died,
+                                                    uint32_t seq, uint64_t id) {
+  return sinn_ld_gpu(born + id) <= seq && seq < sinn_ld_gpu(died + id);
 }

@@ -8,21 +8,25 @@ time.  The loop keeps the index on the device and:
     batch size follows the load;
   * runs several slots' searches at once on different streams (a search
     only reads the index);
-  * applies inserts and deletes at epoch boundaries: once the oldest
-    pending mutation has waited ``mutation_delay`` seconds, it admits every
-    waiting query (all arrived before the boundary), waits for the searches
-    in flight (a mutation changes the index in place), then applies every
-    pending mutation -- the epoch's deletes, then its inserts.
-Consistency (snapshot rule): requests get sequence numbers in the order the
-loop applies or admits them; a query sees exactly the mutations with smaller
-sequence numbers.  Those all arrived before it, and the newer ones it misses
-arrived at most one epoch (about ``mutation_delay`` plus the drain) before
-it.  The loop returns its log in sequence order so that ``replay`` can
-reproduce any query alone.
+  * applies inserts and deletes in epochs: once the oldest pending mutation
+    has waited ``mutation_delay`` seconds, every pending mutation is applied
+    at the next sequence number (the epoch's deletes, then its inserts) while
+    the searches in flight keep running -- no drain.
+Consistency (snapshot rule): a query is searched at the sequence number of
+the last epoch applied before it arrived, so it counts exactly the mutations
+applied before its arrival, however long it waits for a slot or runs beside
+later epochs (the library's snapshot searches: born <= s < died).  Deleted
+ids keep their postings until no queued or running query is older than the
+delete (``sinn_reclaim``), and a tile rebuilt by an epoch is rebuilt again
+only once the searches older than that epoch are done (an insert returns
+SINN_EBUSY before that; the loop then waits for the oldest searches only).
+The loop returns its log in order, reclaims included, so that ``replay``
+can reproduce every id and answer any query alone.
 
 The host does scheduling and argument marshalling only; inserts, deletes and
-searches are the library's calls (sinn_insert, sinn_delete, sinn_search_ctx,
-sinn_search_learned_ctx).
+searches are the library's calls (sinn_insert_at, sinn_delete_at,
+sinn_reclaim, sinn_search_ctx, sinn_search_learned_ctx at a context's
+snapshot).
 """
 from __future__ import annotations
 
@@ -128,6 +132,7 @@ class _Slot:
         self.h_kp = torch.empty(max_batch, dtype=torch.int32, **pin)
         self.done = torch.cuda.Event()
         self.batch = None  # request indices in flight
+        self.snap = None   # their snapshot
 
 
 class Server:
@@ -163,42 +168,68 @@ class Server:
                       for _ in range(slots)]
         self.mutated = torch.cuda.Event()
         self.mutated.record(torch.cuda.current_stream(index.device))
-        self.t_delete = self.t_insert = 0.0
+        self.t_delete = self.t_insert = self.t_wait = 0.0
+        self.seq = 0            # the last epoch applied (the starting documents: 0)
+        self.reclaimed = 0      # the reclaim horizon handed to the library
+        self.busy_waits = 0
         torch.cuda.synchronize(index.device)
 
     # ------------------------------------------------------------ mutations
-    def _apply(self, reqs, pending, log):
-        """Apply one epoch's mutations: first its deletes (each picks among
-        the ids live when the epoch opened), then its inserts, which reuse
-        the freed ids first -- one library call each."""
+    def _reclaim(self, log, horizon):
+        if horizon > self.reclaimed:
+            self.ix.reclaim(horizon)
+            self.reclaimed = horizon
+            log.append(("reclaim", [], None, None, horizon))
+
+    def _apply(self, reqs, pending, log, horizon_fn, wait_oldest):
+        """Apply one epoch's mutations at the next sequence number: first its
+        deletes (each picks among the ids live when the epoch opened), then
+        its inserts, which reuse reclaimed ids first -- one library call
+        each.  An insert that would rebuild a tile some older search may
+        still read (SINN_EBUSY) waits for the oldest searches and retries."""
         t0 = time.perf_counter()
+        self._reclaim(log, horizon_fn())
+        self.seq += 1
+        e = self.seq
         dels = [r for r in pending if reqs[r].kind == "delete"]
         ins = [r for r in pending if reqs[r].kind == "insert"]
         if dels:
             ids = [self.live.take(reqs[r].u) for r in dels if len(self.live)]
             if ids:
-                self.ix.delete(np.asarray(ids, np.int32))
-            log.append(("delete", dels, None, np.asarray(ids, np.int64)))
+                self.ix.delete_at(np.asarray(ids, np.int32), e)
+            log.append(("delete", dels, None, np.asarray(ids, np.int64), e))
         t1 = time.perf_counter()
         if ins:
             rows = [reqs[r].row for r in ins]
             ip, idx, val = csr_rows(self.pool, rows)
-            ids = self.ix.insert(ip, idx, val).cpu().numpy().astype(np.int64)
+            while True:
+                try:
+                    ids = self.ix.insert_at(ip, idx, val, e).cpu().numpy().astype(np.int64)
+                    break
+                except sinnamon.SinnError as err:
+                    if err.code != sinnamon.SINN_EBUSY:
+                        raise
+                    self.busy_waits += 1
+                    tw = time.perf_counter()
+                    wait_oldest()
+                    self.t_wait += time.perf_counter() - tw
+                    self._reclaim(log, horizon_fn())
             self.live.add(ids)
-            log.append(("insert", ins, rows, ids))
+            log.append(("insert", ins, rows, ids, e))
         self.mutated.record(torch.cuda.current_stream(self.ix.device))
         t2 = time.perf_counter()
         self.t_delete += t1 - t0
         self.t_insert += t2 - t1
 
     # ------------------------------------------------------------ searches
-    def _launch(self, s, batch, reqs, log):
+    def _launch(self, s, batch, reqs, log, snap):
         rows = [reqs[q].row for q in batch]
         ip, idx, val = csr_rows(self.queries, rows)
         n, nz = len(batch), idx.size
         s.h_ip.numpy()[:n + 1] = ip
         s.h_ix.numpy()[:nz] = idx
         s.h_v.numpy()[:nz] = val
+        s.ctx.set_snapshot(snap)  # the epochs applied before these queries arrived
         with torch.cuda.stream(s.stream):
             s.stream.wait_event(self.mutated)
             s.d_ip[:n + 1].copy_(s.h_ip[:n + 1], non_blocking=True)
@@ -216,7 +247,8 @@ class Server:
             s.h_kp[:n].copy_(s.kp[:n], non_blocking=True)
             s.done.record(s.stream)
         s.batch = list(batch)
-        log.append(("query", list(batch), rows, None))
+        s.snap = snap
+        log.append(("query", list(batch), rows, None, snap))
 
     def _reap(self, s, results, done_t, t0):
         n = len(s.batch)
@@ -228,6 +260,7 @@ class Server:
             results[q] = (ids[r], sc[r], int(kp[r]))
             done_t[q] = t
         s.batch = None
+        s.snap = None
 
     def _poll(self, results, done_t, t0, block=False):
         for s in self.slots:
@@ -243,54 +276,74 @@ class Server:
         overloaded server would otherwise fall behind without end); the
         requests not taken are counted as dropped.  Returns (stats, results,
         log): results maps a query's request index to (ids, scores, k'); log
-        lists ("insert"|"delete"|"query", request indices, pool rows, ids)
-        in sequence order."""
+        lists ("insert"|"delete"|"query"|"reclaim", request indices, pool
+        rows, ids, sequence number) in the order the loop made the calls (a
+        query's number is its snapshot, a reclaim's its horizon)."""
         n = len(reqs)
         results, done_t = {}, np.full(n, np.nan)
-        log, wq, wm = [], [], []
-        nxt, batches, inflight_max, epochs, t_drain = 0, 0, 0, 0, 0.0
-        self.t_delete = self.t_insert = 0.0
+        log, wm = [], []
+        wq = []  # waiting queries: (request index, snapshot)
+        nxt, batches, inflight_max, epochs, overlapped = 0, 0, 0, 0, 0
+        self.t_delete = self.t_insert = self.t_wait = 0.0
+        self.busy_waits = 0
         t0 = time.perf_counter()
 
         def admit(queue):
+            # a batch holds queries of one snapshot (arrival order keeps them
+            # contiguous)
             nonlocal batches, inflight_max
             for s in self.slots:
                 if queue and s.batch is None:
-                    b, queue = queue[:self.max_batch], queue[self.max_batch:]
-                    self._launch(s, b, reqs, log)
+                    snap = queue[0][1]
+                    j = 0
+                    while j < len(queue) and j < self.max_batch and queue[j][1] == snap:
+                        j += 1
+                    self._launch(s, [q for q, _ in queue[:j]], reqs, log, snap)
+                    queue = queue[j:]
                     batches += 1
             inflight_max = max(inflight_max, sum(s.batch is not None for s in self.slots))
             return queue
+
+        def horizon():
+            # no search at a smaller number is queued or running, and every
+            # later arrival gets at least the current number
+            snaps = [s.snap for s in self.slots if s.batch is not None] + [p for _, p in wq]
+            return min(snaps + [self.seq])
+
+        def wait_oldest():
+            nonlocal wq
+            busy = [s for s in self.slots if s.batch is not None]
+            if busy:
+                s = min(busy, key=lambda x: x.snap)
+                s.done.synchronize()
+                self._reap(s, results, done_t, t0)
+            wq = admit(wq)
 
         while nxt < n or wq or wm or any(s.batch is not None for s in self.slots):
             now = time.perf_counter() - t0
             if max_wall is not None and now > max_wall:
                 nxt = n
             while nxt < n and reqs[nxt].t <= now:
-                (wq if reqs[nxt].kind == "query" else wm).append(nxt)
+                if reqs[nxt].kind == "query":
+                    wq.append((nxt, self.seq))
+                else:
+                    wm.append(nxt)
                 nxt += 1
             self._poll(results, done_t, t0)
+            wq = admit(wq)
             if wm and (now - reqs[wm[0]].t >= self.mutation_delay or nxt >= n):
-                # epoch boundary: every waiting query arrived before it and
-                # runs on the old snapshot; then the searches drain and the
-                # pending mutations apply
-                while wq:
-                    wq = admit(wq)
-                    if wq:
-                        self._poll(results, done_t, t0, block=True)
-                td = time.perf_counter()
-                self._poll(results, done_t, t0, block=True)
-                t_drain += time.perf_counter() - td
-                self._apply(reqs, wm, log)
+                # an epoch: applied at the next number while searches run
+                overlapped += any(s.batch is not None for s in self.slots)
+                self._apply(reqs, wm, log, horizon, wait_oldest)
                 done_t[wm] = time.perf_counter() - t0
                 wm = []
                 epochs += 1
                 continue
-            wq = admit(wq)
             if not wq and not wm and nxt < n and all(s.batch is None for s in self.slots):
                 wait = reqs[nxt].t - (time.perf_counter() - t0)
                 if wait > 2e-4:
                     time.sleep(wait - 1e-4)
+        self._reclaim(log, horizon())  # nothing is in flight any more
         wall = time.perf_counter() - t0
         kinds = np.array([r.kind for r in reqs])
         arrive = np.array([r.t for r in reqs])
@@ -308,41 +361,63 @@ class Server:
                  "p50_ms": pct(ql, 50), "p99_ms": pct(ql, 99),
                  "mutation_p50_ms": pct(ml, 50), "mutation_p99_ms": pct(ml, 99),
                  "query_batches": batches, "mean_batch": ql.size / max(batches, 1),
-                 "epochs": epochs, "epoch_drain_s": t_drain, "epoch_delete_s": self.t_delete,
+                 "epochs": epochs, "epochs_overlapped": overlapped,
+                 "epoch_busy_wait_s": self.t_wait,
+                 "busy_waits": self.busy_waits, "epoch_delete_s": self.t_delete,
                  "epoch_insert_s": self.t_insert, "max_batch": self.max_batch,
                  "max_inflight": inflight_max, "slots": len(self.slots)}
         return stats, results, log
 
 
 def replay(index, queries, docs_pool, log, k: int, k_prime: int = 1000, mlp=None,
-           kp_max: int = 4096, pick=None, approx=False):
+           kp_max: int = 4096, pick=None, approx=False, k_primes=None):
     """Apply a served log to another index holding the same starting
-    documents and answer the chosen queries (request indices in ``pick``;
-    all when None) one at a time at their place in the sequence.  Returns
-    {request index: (ids, scores, k')}, plus each query's Alg. 6 scores over
-    all ids at that point when ``approx``."""
+    documents -- the same library calls in the same order, so every id comes
+    out the same -- and answer each chosen query (request indices in
+    ``pick``; all when None) alone, by a plain search (no snapshot) at the
+    point where exactly the epochs up to its snapshot have been applied.
+    k' per query: ``k_primes[q]`` when given, else the network's (``mlp``)
+    or ``k_prime``.  Returns {request index: (ids, scores, k')}, plus each
+    query's Alg. 6 scores over all ids at that point when ``approx``."""
     out, scores = {}, {}
-    for kind, reqs_i, rows, ids in log:
+    by_snap = {}
+    for kind, reqs_i, rows, ids, seq in log:
+        if kind == "query":
+            by_snap.setdefault(seq, []).append((reqs_i, rows))
+    done = set()
+
+    def answer_upto(e):
+        for snap in sorted(x for x in by_snap if x <= e and x not in done):
+            done.add(snap)
+            for reqs_i, rows in by_snap[snap]:
+                for q, row in zip(reqs_i, rows):
+                    if pick is not None and q not in pick:
+                        continue
+                    ip, idx, val = csr_rows(queries, [row])
+                    if k_primes is not None or mlp is None:
+                        kp = k_prime if k_primes is None else int(k_primes[q])
+                        r_ids, r_sc = index.search(ip, idx, val, k=k, k_prime=kp)
+                    else:
+                        r_ids, r_sc, r_kp = index.search_learned(mlp, ip, idx, val, k, k, kp_max)
+                        kp = int(r_kp.cpu().numpy()[0])
+                    out[q] = (r_ids.cpu().numpy()[0], r_sc.cpu().numpy()[0], kp)
+                    if approx:
+                        scores[q] = index.scores(ip, idx, val).cpu().numpy()[0]
+
+    applied = 0  # the last epoch applied
+    for kind, reqs_i, rows, ids, seq in log:
+        if kind in ("insert", "delete") and seq > applied:
+            answer_upto(applied)  # an epoch starts: the earlier snapshots are complete
+            applied = seq
         if kind == "insert":
             ip, idx, val = csr_rows(docs_pool, rows)
-            got = index.insert(ip, idx, val).cpu().numpy().astype(np.int64)
+            got = index.insert_at(ip, idx, val, seq).cpu().numpy().astype(np.int64)
             if not np.array_equal(got, ids):
                 raise AssertionError("replayed insert assigned other ids")
         elif kind == "delete":
             if ids.size:
-                index.delete(ids.astype(np.int32))
-        else:
-            for q, row in zip(reqs_i, rows):
-                if pick is not None and q not in pick:
-                    continue
-                ip, idx, val = csr_rows(queries, [row])
-                if mlp is None:
-                    r_ids, r_sc = index.search(ip, idx, val, k=k, k_prime=k_prime)
-                    kp = k_prime
-                else:
-                    r_ids, r_sc, r_kp = index.search_learned(mlp, ip, idx, val, k, k, kp_max)
-                    kp = int(r_kp.cpu().numpy()[0])
-                out[q] = (r_ids.cpu().numpy()[0], r_sc.cpu().numpy()[0], kp)
-                if approx:
-                    scores[q] = index.scores(ip, idx, val).cpu().numpy()[0]
+                index.delete_at(ids.astype(np.int32), seq)
+        elif kind == "reclaim":
+            index.reclaim(seq)
+    answer_upto(applied)
     return (out, scores) if approx else out

@@ -23,7 +23,8 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 (SINN_OK, SINN_EINVAL, SINN_ENOTFOUND, SINN_ENOMEM, SINN_ECUDA, SINN_EDEVICE, SINN_ESCRATCH,
- SINN_EIO) = range(8)
+ SINN_EIO, SINN_EBUSY) = range(9)
+SINN_SEQ_LATEST = 0xFFFFFFFE
 SINN_FLAG_NONNEG = 1
 SINN_FLAG_BF16_SKETCH = 2
 
@@ -37,6 +38,7 @@ EXPORTS = [
     "sinn_search_ctx", "sinn_get_tuning", "sinn_set_tuning", "sinn_autotune",
     "sinn_set_budget", "sinn_get_budget", "sinn_save", "sinn_load", "sinn_debug_fail_alloc",
     "sinn_debug_wait_probe", "sinn_search_kpb", "sinn_candidates_kpb", "sinn_query_postings",
+    "sinn_insert_at", "sinn_delete_at", "sinn_reclaim", "sinn_ctx_set_snapshot",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
@@ -75,7 +77,8 @@ class SinnStats(C.Structure):
                 ("bytes_lists", C.c_uint64), ("bytes_sketch", C.c_uint64),
                 ("bytes_store", C.c_uint64), ("bytes_scratch", C.c_uint64),
                 ("n", C.c_uint32), ("m", C.c_uint32), ("h", C.c_uint32),
-                ("tile_docs", C.c_uint32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
+                ("tile_docs", C.c_uint32), ("flags", C.c_uint32),
+                ("pending_deletes", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -187,6 +190,10 @@ def load(build_if_missing: bool = False):
         "sinn_autotune": ([vp, vp, vp, vp, u32, u32, u32, u32, C.POINTER(SinnTuning), vp],
                           C.c_int),
         "sinn_search_kpb": ([vp, vp, vp, vp, u32, u32, vp, u32, vp, vp, vp, vp], C.c_int),
+        "sinn_insert_at": ([vp, vp, vp, vp, u32, vp, u32, vp], C.c_int),
+        "sinn_delete_at": ([vp, vp, u32, u32, vp], C.c_int),
+        "sinn_reclaim": ([vp, u32, vp], C.c_int),
+        "sinn_ctx_set_snapshot": ([vp, u32], C.c_int),
         "sinn_candidates_kpb": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp, vp], C.c_int),
         "sinn_query_postings": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
         "sinn_mlp_set_policy": ([vp, C.POINTER(SinnKpPolicy)], C.c_int),
@@ -271,6 +278,22 @@ def sinn_insert(ix, indptr, indices, values, out_ids, stream=None):
 
 def sinn_delete(ix, ids, stream=None):
     _check(load().sinn_delete(ix, _p(ids), ids.numel(), _s(stream)), "sinn_delete")
+
+
+def sinn_insert_at(ix, indptr, indices, values, out_ids, seq, stream=None):
+    n_docs = indptr.numel() - 1
+    _check(load().sinn_insert_at(ix, _p(indptr), _p(indices), _p(values), n_docs, _p(out_ids),
+                                 int(seq), _s(stream)), "sinn_insert_at")
+    return out_ids
+
+
+def sinn_delete_at(ix, ids, seq, stream=None):
+    _check(load().sinn_delete_at(ix, _p(ids), ids.numel(), int(seq), _s(stream)),
+           "sinn_delete_at")
+
+
+def sinn_reclaim(ix, horizon, stream=None):
+    _check(load().sinn_reclaim(ix, int(horizon), _s(stream)), "sinn_reclaim")
 
 
 def sinn_search(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
@@ -497,6 +520,10 @@ class Context:
     def query_bytes(self, k_prime_max: int) -> int:
         return int(load().sinn_ctx_query_bytes(self._h, k_prime_max))
 
+    def set_snapshot(self, seq: int):
+        """The sequence number this context's searches see."""
+        _check(load().sinn_ctx_set_snapshot(self._h, int(seq)), "sinn_ctx_set_snapshot")
+
     def search(self, q_indptr, q_indices, q_values, k, k_prime_max, out_ids, out_scores,
                k_prime=None, stream=None):
         n_q = q_indptr.numel() - 1
@@ -703,6 +730,19 @@ class Index:
 
     def delete(self, ids, stream=None):
         sinn_delete(self._h, _dev(ids, torch.int32, self.device), stream)
+
+    def insert_at(self, indptr, indices, values, seq: int, stream=None) -> torch.Tensor:
+        """sinn_insert_at: the vectors are born at sequence number seq."""
+        ip, ix, v = self._csr(indptr, indices, values)
+        out = torch.empty(ip.numel() - 1, dtype=torch.int32, device=self.device)
+        sinn_insert_at(self._h, ip, ix, v, out, seq, stream)
+        return out
+
+    def delete_at(self, ids, seq: int, stream=None):
+        sinn_delete_at(self._h, _dev(ids, torch.int32, self.device), seq, stream)
+
+    def reclaim(self, horizon: int, stream=None):
+        sinn_reclaim(self._h, horizon, stream)
 
     def search(self, indptr, indices, values, k: int, k_prime, k_prime_max: int | None = None,
                stream=None):

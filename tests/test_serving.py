@@ -1,7 +1,8 @@
 """The continuous-batching serving loop: each query's result in the mix (a
-batch in one of several overlapping search contexts, between inserts and
-deletes) is the same as the same query run alone on an index that replays
-the loop's sequence of mutations.
+batch in one of several overlapping search contexts, at its snapshot, while
+later epochs of inserts and deletes are applied) is the same as the same
+query run alone, with no snapshot, on an index that replays the loop's
+calls up to exactly the epochs its snapshot counts.
 
 Both sides are the CUDA path; alone the query is a batch of one, in the mix
 one of a larger batch, so the scoring kernels sum in other orders.  Re-ranked
@@ -100,12 +101,20 @@ def test_same_alone_and_in_the_mix(learned):
     assert stats["max_inflight"] >= 2, stats          # searches overlapped
     assert stats["mean_batch"] > 1.0, stats           # batches formed
     assert any(e[0] == "insert" for e in log) and any(e[0] == "delete" for e in log)
+    assert stats["epochs_overlapped"] >= 1, stats     # an epoch ran beside searches
+    assert any(e[0] == "reclaim" for e in log)
+    k_primes = None
     if learned:
         assert len({v[2] for v in results.values()}) > 1  # k' varies per query
+        # the network reads list lengths (tombstones included) as they stand
+        # when the search runs, which later epochs may already have changed:
+        # the alone run takes the k' the mix chose
+        k_primes = {q: v[2] for q, v in results.items()}
+        assert all(k <= v <= 512 for v in k_primes.values())
 
     ix2, live2 = fresh()
     assert np.array_equal(live, live2)
-    alone, approx = serving.replay(ix2, qs, extra, log, k, kp, mlp=mlp, kp_max=512, approx=True)
+    alone, approx = serving.replay(ix2, qs, extra, log, k, kp, approx=True, k_primes=k_primes)
     assert set(alone) == set(results)
     moves = _compare(results, alone, approx, k)
     assert moves <= max(2, 0.02 * n_q), moves
@@ -115,8 +124,11 @@ def test_same_alone_and_in_the_mix(learned):
 
 
 def test_mutations_follow_arrival_order():
-    """A query that arrived before a mutation never sees it; the log keeps
-    every request exactly once."""
+    """Snapshots follow arrival: a query counts only epochs whose requests
+    all arrived no later than it, and never a later epoch than the last one
+    logged before its launch; epochs are numbered 1, 2, ... in log order;
+    reclaim horizons only grow and no query launched after a reclaim is
+    older than its horizon; the log keeps every request exactly once."""
     w, qs, extra, fresh = _setup(n0=5000, pool=2000, nq=50)
     ix, live = fresh()
     srv = serving.Server(ix, qs, extra, live, slots=2, slot_bytes=32 << 20, max_batch=16,
@@ -126,12 +138,20 @@ def test_mutations_follow_arrival_order():
     stats, results, log = srv.serve(reqs)
     seen = [i for e in log for i in e[1]]
     assert sorted(seen) == list(range(len(reqs)))
-    pos = {r: p for p, e in enumerate(log) for r in e[1]}
-    for i, r in enumerate(reqs):
-        if r.kind != "query":
-            continue
-        # every mutation sequenced before this query arrived no later than it
-        for e in log[:pos[i]]:
-            if e[0] != "query":
-                assert all(reqs[j].t <= r.t for j in e[1])
+    epoch_reqs, last_epoch, horizon = {}, 0, 0
+    for kind, ri, rows, ids, seq in log:
+        if kind in ("insert", "delete"):
+            assert seq in (last_epoch, last_epoch + 1)
+            last_epoch = seq
+            epoch_reqs.setdefault(seq, []).extend(ri)
+        elif kind == "reclaim":
+            assert seq > horizon
+            horizon = seq
+        else:
+            assert horizon <= seq <= last_epoch
+            t = max(reqs[q].t for q in ri)
+            for e in range(1, seq + 1):
+                assert all(reqs[j].t <= t for j in epoch_reqs[e])
+    assert last_epoch == stats["epochs"] >= 2
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert ix.stats()["live"] == len(srv.live)
