@@ -36,8 +36,11 @@ METRIC = "queries/s at recall@10>=0.9 (batched search with learned per-query k' 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
+_T_START = time.time()
+
+
 def log(*a):
-    print(*a, file=sys.stderr, flush=True)
+    print(f"[{time.time() - _T_START:7.1f}s]", *a, file=sys.stderr, flush=True)
 
 
 def job_throughput(elapsed_s: float, units: float, device=None):
@@ -66,8 +69,12 @@ def _synth_key():
 
 
 def cached(name, fn):
-    """Generated inputs are cached in /tmp under their name (which carries
-    the size and seed) and the generator's hash; regenerated when absent."""
+    """With SINN_BENCH_CACHE=1, generated inputs are cached in /tmp under
+    their name (which carries the size and seed) and the generator's hash,
+    and regenerated when absent; otherwise every run generates them (on a
+    fresh machine writing the cache costs more than it saves)."""
+    if os.environ.get("SINN_BENCH_CACHE", "0") != "1":
+        return fn()
     path = f"/tmp/sinn_bench_{name}_{_synth_key()}.npz"
     if os.path.exists(path):
         z = np.load(path)
@@ -223,11 +230,13 @@ def cpu_baseline(ora, w, qs, target_s, k, kp):
                               "sample": f"first {s1} queries, {dt1:.1f}s on 1 thread"}}
 
 
-def recall_at_10(ora, qs_sample, gpu_ids, threads):
-    """recall@10 of the GPU's top-10 against the FP64 exact top-10 (LinScan);
-    a returned id whose exact score ties the exact 10th score counts as a hit."""
-    ex = ora.linscan_topk(qs_sample.indptr, qs_sample.indices, qs_sample.values, k=10,
-                          threads=threads)
+def recall_at_10(ora, qs_sample, gpu_ids, threads, ex=None):
+    """recall@10 of the GPU's top-10 against the FP64 exact top-10 (LinScan,
+    or ``ex``: its result for these queries computed before); a returned id
+    whose exact score ties the exact 10th score counts as a hit."""
+    if ex is None:
+        ex = ora.linscan_topk(qs_sample.indptr, qs_sample.indices, qs_sample.values, k=10,
+                              threads=threads)
     hits = 0
     for r in range(qs_sample.rows):
         truth = set(int(x) for x in ex["ids"][r])
@@ -716,15 +725,19 @@ def run_ours(args):
             ora = oracle_index(w, live_docs)
             nr = min(args.recall_queries, qs.rows)
             samp = qs.slice(0, nr)
+            cores = os.cpu_count() or 1
+            truth = ora.linscan_topk(samp.indptr, samp.indices, samp.values, k=10,
+                                     threads=cores)
             extras["recall_at_10"] = recall_at_10(ora, samp, out_ids.cpu().numpy()[:nr],
-                                                  os.cpu_count() or 1)
+                                                  cores, truth)
             extras["recall_at_10_fixed_kprime"] = recall_at_10(
-                ora, samp, fx_ids.cpu().numpy()[:nr], os.cpu_count() or 1)
+                ora, samp, fx_ids.cpu().numpy()[:nr], cores, truth)
             extras["recall_queries"] = nr
             extras["cpu_baseline"] = cpu_baseline(ora, w, qs, args.cpu_seconds, k, kp)
         if not args.skip_variants:
-            extras.update(run_variants(args, w, docs, ix, (g_qip, g_qix, g_qv), qs, k, kp,
-                                       float(P_full.mean()), ora, T))
+            extras.update(run_variants(args, w, live_docs if ora is not None else docs, ix,
+                                       (g_qip, g_qix, g_qv), qs, k, kp, float(P_full.mean()),
+                                       ora, T, truth if ora is not None else None))
         if args.serve_seconds > 0:
             extras["serving"] = run_serving(args, w, ix, qs, docs.rows, mlp, k, kp)
         if ora is not None:
@@ -783,6 +796,15 @@ def run_mixed(args, dev):
     from paper_2301_10622_gb300 import sinnamon
     w, docs, _, qs = make_inputs(args, 0, workload="mixed", n_docs=args.mixed_docs)
     k, kp = w.k, w.k_prime
+    ora_job = pool = None
+    if not args.skip_oracle:
+        # the checker's index builds on one host thread (the C call releases
+        # the interpreter lock) while the device part runs
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        oracle.build()
+        pool = ThreadPoolExecutor(1)
+        ora_job = pool.submit(oracle_index, w, docs)
     t0 = time.time()
     ix = build_index(sinnamon, w, docs, dev, 4096, args.scratch_gb)
     torch.cuda.synchronize()
@@ -828,10 +850,9 @@ def run_mixed(args, dev):
                         "postings_per_query": float(P.mean())}}
     out["plain"] = plain_search(sinnamon, ix.handle, qs, g[1], g[2], k, kp, dev,
                                 min(100, args.plain_queries), alg)
-    if not args.skip_oracle:
-        import oracle
-        oracle.build()
-        ora = oracle_index(w, docs)
+    if ora_job is not None:
+        ora = ora_job.result()
+        pool.shutdown()
         nr = min(args.mixed_recall_queries, qs.rows)
         out["recall_at_10"] = recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr],
                                            os.cpu_count() or 1)
@@ -842,11 +863,12 @@ def run_mixed(args, dev):
     return out
 
 
-def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs):
+def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs, truth):
     """The paper's variants, untimed extras: Alg. 6 with an anytime budget
     (half and a quarter of the mean postings per query) on the bench's
-    index, and a SINNAMON+ index (U only) of the original collection; each
-    searched with fixed k' as one batch."""
+    index, and SINNAMON+ (U only) and bfloat16-bin indexes of the same
+    collection (``docs``, in id order); each searched with fixed k' as one
+    batch, recall against the exact top-10 ``truth`` of the first queries."""
     import torch
     from paper_2301_10622_gb300 import sinnamon
     out = {}
@@ -873,8 +895,8 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs)
         budget = int(mean_postings * frac)
         ix.set_budget(budget)
         qps, ids = timed(ix)
-        rec = (recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1)
-               if ora is not None else None)
+        rec = (recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1,
+                            truth) if ora is not None else None)
         runs.append({"budget_postings": budget, "fraction_of_mean_postings": frac,
                      "qps": qps, "k_prime": kp, "recall_at_10": rec})
     ix.set_budget(0)
@@ -890,7 +912,7 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs)
                             "bytes_sketch": plus.stats()["bytes_sketch"],
                             "bytes_sketch_full": ix.stats()["bytes_sketch"]}
     plus.close()
-    # bfloat16 bins (upper rounded up, lower down) on the original collection
+    # bfloat16 bins (upper rounded up, lower down)
     bf = sinnamon.Index(w.n, w.m, w.h, device=q[0].device, tile_docs=tile_docs,
                         capacity_hint=docs.rows, scratch_bytes=args.scratch_gb << 30,
                         flags=sinnamon.SINN_FLAG_BF16_SKETCH)
@@ -899,11 +921,9 @@ def run_variants(args, w, docs, ix, q, qs, k, kp, mean_postings, ora, tile_docs)
         bf.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
     qps, ids = timed(bf)
     rec = None
-    if ora is not None:  # recall against the original collection's exact top-10
-        import oracle
-        o0 = oracle_index(w, docs)
-        rec = recall_at_10(o0, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1)
-        o0.close()
+    if ora is not None:  # the same collection and ids as the bench's index
+        rec = recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr], os.cpu_count() or 1,
+                           truth)
     out["bf16_sketch"] = {"qps": qps, "k_prime": kp, "docs": docs.rows, "recall_at_10": rec,
                           "bytes_sketch": bf.stats()["bytes_sketch"]}
     bf.close()
@@ -974,7 +994,7 @@ def reconstruct(docs, parts, dels, executed):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="text")

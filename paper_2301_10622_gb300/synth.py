@@ -16,13 +16,20 @@ Distribution readings (the workload descriptions give only the family names):
     coordinates are drawn one after another without replacement (each draw is
     proportional to the weights of the coordinates not yet taken).
   * uniform coordinates: a uniformly random subset of the given size.
-The random generator is numpy's PCG64 seeded with the given seed.
+The random generator is numpy's PCG64 seeded with the given seed.  A
+collection of more than ``BLOCK_ROWS`` rows is drawn in blocks of that many
+rows, block b from its own PCG64 stream (the seed's SeedSequence, child b), on
+several threads; the rows do not depend on the number of threads.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
+
+BLOCK_ROWS = 1 << 18
 
 
 @dataclass
@@ -222,29 +229,53 @@ def _counts(rng, spec, rows, n):
     raise ValueError(spec)
 
 
-def _vectors(rng, rows, n, coords, nnz_spec, values):
-    counts = _counts(rng, nnz_spec, rows, n)
+def _fill(rng, counts, n, coords, values):
     if coords == "zipf":
         ip, idx = zipf_coords(rng, counts, n)
     else:
         ip, idx = uniform_coords(rng, counts, n)
     nnz = int(ip[-1])
     val = normal_values(rng, nnz) if values == "normal" else lognormal_values(rng, nnz)
+    return ip, idx, val
+
+
+def _vectors(seed, rows, n, coords, nnz_spec, values):
+    if rows <= BLOCK_ROWS:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        ip, idx, val = _fill(rng, _counts(rng, nnz_spec, rows, n), n, coords, values)
+        return CSR(ip, idx, val)
+    nb = (rows + BLOCK_ROWS - 1) // BLOCK_ROWS
+    rngs = [np.random.Generator(np.random.PCG64(c))
+            for c in np.random.SeedSequence(seed).spawn(nb)]
+    counts = [_counts(rngs[b], nnz_spec, min(BLOCK_ROWS, rows - b * BLOCK_ROWS), n)
+              for b in range(nb)]
+    ip = _indptr(np.concatenate(counts))
+    idx = np.empty(int(ip[-1]), np.uint32)
+    val = np.empty(int(ip[-1]), np.float32)
+
+    def block(b):
+        _, bi, bv = _fill(rngs[b], counts[b], n, coords, values)
+        o = int(ip[b * BLOCK_ROWS])
+        idx[o:o + bi.size] = bi
+        val[o:o + bv.size] = bv
+
+    with ThreadPoolExecutor(max(1, min(nb, os.cpu_count() or 1))) as ex:
+        list(ex.map(block, range(nb)))
     return CSR(ip, idx, val)
 
 
 def make_docs(w: Workload, n_docs: int | None = None, seed: int | None = None) -> CSR:
     """Documents of workload w (seed default: 1000 + workload number)."""
     rows = w.n_docs if n_docs is None else n_docs
-    rng = np.random.Generator(np.random.PCG64(_seed(w, 1000) if seed is None else seed))
-    return _vectors(rng, rows, w.n, w.doc_coords, w.doc_nnz, w.doc_values)
+    return _vectors(_seed(w, 1000) if seed is None else seed, rows, w.n, w.doc_coords,
+                    w.doc_nnz, w.doc_values)
 
 
 def make_queries(w: Workload, n_q: int | None = None, seed: int | None = None) -> CSR:
     """Queries of workload w (seed default: 2000 + workload number)."""
     rows = w.n_queries if n_q is None else n_q
-    rng = np.random.Generator(np.random.PCG64(_seed(w, 2000) if seed is None else seed))
-    return _vectors(rng, rows, w.n, w.q_coords or w.doc_coords, w.q_nnz, w.q_values)
+    return _vectors(_seed(w, 2000) if seed is None else seed, rows, w.n,
+                    w.q_coords or w.doc_coords, w.q_nnz, w.q_values)
 
 
 def _seed(w: Workload, base: int) -> int:
