@@ -50,6 +50,7 @@ constexpr uint32_t kBmGroups = 2;       // 4-id groups per thread a bitmap term 
 constexpr uint32_t kFbBlocks = 1024;    // blocks of the fallback kernels
 constexpr uint32_t kTouchCap = 2048;    // ids a touched-list tile may list
 constexpr uint32_t kZeroBin = 0x800u;   // key bin (top 12 bits) of a zero score
+constexpr uint32_t kFuseQueries = 4;    // launches of at most this many queries fuse steps
 
 enum SelMode : uint32_t { SEL_DONE = 0, SEL_L1 = 1, SEL_L2 = 2, SEL_COMPACT = 3, SEL_TIES = 4 };
 
@@ -87,8 +88,10 @@ struct Batch {  // device scratch views of one launch
   uint32_t *ecnt;   // B: emitted count (may exceed kEmitCap: overflow)
   uint32_t *bound;  // B: lower-bound bin of the k'-th best key
   uint32_t *tdone;  // B: tiles finished
+  uint32_t *rdone;  // B: re-rank blocks finished
   uint32_t *flagged;  // B: queries taking the dense fallback
   uint32_t *nflag;    // 1
+  uint32_t *tick;     // 4: blocks finished of the kernels that end in a pick or refine
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -104,6 +107,22 @@ __device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t *counter) {
   if ((threadIdx.x & 31) == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
   return base + __popc(m & lanemask_lt());
+}
+
+// True in every thread of the block that is the last of `total` blocks to
+// count on *ctr (zeroed by the query prep); every block fences its writes
+// before counting, and the last one fences after, so it sees them all.
+// Reads of data other blocks wrote in the same launch go through L2
+// (__ldcg): this SM's L1 may hold older copies.
+__device__ bool last_block(uint32_t *ctr, uint32_t total) {
+  __shared__ uint32_t s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) + 1u == total ? 1u : 0u;
+  __syncthreads();
+  const bool last = s_last != 0u;
+  if (last) __threadfence();
+  return last;
 }
 
 // --------------------------------------------------------------- query prep
@@ -132,10 +151,12 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
     bt.ecnt[b] = 0u;
     bt.bound[b] = 0u;
     bt.tdone[b] = 0u;
+    bt.rdone[b] = 0u;
     if (dense_all) bt.flagged[b] = b;  // every query of the launch scores densely
     if (b == 0) {
       *bt.nflag = dense_all ? gridDim.x : 0u;
       *(unsigned long long *)(((uintptr_t)(bt.nflag + 1) + 7) & ~(uintptr_t)7) = 0ull;
+      for (uint32_t i = 0; i < 4; ++i) bt.tick[i] = 0u;
     }
   }
   const uint64_t s = q_indptr[q], e = q_indptr[q + 1];
@@ -832,8 +853,11 @@ __device__ __forceinline__ void lone_fma(float4 &r, uint32_t bits, float4 x, flo
   if (bits & 8u) r.w = fmaf(v, x.w, r.w);
 }
 
+__device__ __noinline__ void pick_all(Batch bt, uint32_t level);
+
 template <int H, typename S>
-__global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Batch bt) {
+__global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Batch bt,
+                                                                uint32_t fuse_pick) {
   constexpr uint32_t HS = H > 0 ? (uint32_t)H : (uint32_t)SINN_MAX_H;
   constexpr uint32_t NW = kLoneThreads / 32;
   __shared__ float4 acc4[kLoneSlice / 4];  // array terms of the slice (atomics)
@@ -988,13 +1012,15 @@ __global__ void __launch_bounds__(kLoneThreads, 8) k_score_lone(ScoreArgs a, Bat
   }
   __syncthreads();
   if (cur != 0xFFFFFFFFu) flush();
+  // with fuse_pick, the launch's last block makes the level-0 picks
+  if (fuse_pick && last_block(bt.tick, gridDim.x)) pick_all(bt, 0);
 }
 
 // Kernels specialised for h = 1 and h = 2 (the common sketch shapes); other h
 // use the general loop.
 struct ScoreKernels {
   void (*emit)(ScoreArgs, Batch);
-  void (*dense)(ScoreArgs, Batch);
+  void (*dense)(ScoreArgs, Batch, uint32_t);
   void (*persistent)(ScoreArgs, Batch, uint32_t, unsigned long long *);
 };
 
@@ -1016,17 +1042,20 @@ ScoreKernels score_kernels(uint32_t h, bool bf16, bool walk) {
 
 // ------------------------------------------------------------------ select
 // Find, scanning bins from the top, the bin where the running count reaches
-// rem.  Returns (bin, count above the bin).  Block of 128 threads.
+// rem.  Returns (bin, count above the bin).  Block of at least 128 threads
+// (the first 128 read); the counts are read from L2.
 __device__ void find_bin(const uint32_t *hist, uint32_t nb, uint32_t rem, uint32_t *out_bin,
                          uint32_t *out_above) {
   __shared__ uint32_t sums[128];
   __shared__ uint32_t res[2];
   const uint32_t tid = threadIdx.x, per = nb / 128;
-  // thread tid owns bins [nb - (tid+1)*per, nb - tid*per), highest first
-  const uint32_t hi = nb - tid * per;
-  uint32_t s = 0;
-  for (uint32_t i = 0; i < per; ++i) s += hist[hi - 1 - i];
-  sums[tid] = s;
+  if (tid < 128) {
+    // thread tid owns bins [nb - (tid+1)*per, nb - tid*per), highest first
+    const uint32_t hi = nb - tid * per;
+    uint32_t s = 0;
+    for (uint32_t i = 0; i < per; ++i) s += __ldcg(hist + hi - 1 - i);
+    sums[tid] = s;
+  }
   __syncthreads();
   if (tid == 0) {
     uint32_t run = 0, found = 0;
@@ -1034,7 +1063,7 @@ __device__ void find_bin(const uint32_t *hist, uint32_t nb, uint32_t rem, uint32
       if (run + sums[w] >= rem) {
         uint32_t top = nb - w * per;
         for (uint32_t i = 0; i < per; ++i) {
-          uint32_t c = hist[top - 1 - i];
+          uint32_t c = __ldcg(hist + top - 1 - i);
           if (run + c >= rem) {
             res[0] = top - 1 - i;
             res[1] = run;
@@ -1125,64 +1154,77 @@ __global__ void k_fb_reset(Batch bt) {
   }
 }
 
+// Dense-path pick at a level for flagged query b (one block; the counts
+// may come from the same launch, so they are read from L2).
+__device__ void pick_one(Batch bt, uint32_t b, uint32_t level) {
+  SelState st = bt.sel[b];
+  if (level == 0) {
+    // the dense histogram counts every id the search sees: a snapshot may
+    // see fewer than the live count that bounded kq
+    __shared__ uint32_t s_tot;
+    if (threadIdx.x == 0) s_tot = 0;
+    __syncthreads();
+    uint32_t c = 0;
+    for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x)
+      c += __ldcg(bt.hist0 + (uint64_t)b * 4096 + i);
+    atomicAdd(&s_tot, c);
+    __syncthreads();
+    const uint32_t tot = s_tot;
+    __syncthreads();
+    if (tot < st.kq) {
+      st.kq = tot;
+      if (threadIdx.x == 0) bt.sel[b].kq = tot;
+    }
+    if (st.kq == 0) {
+      if (threadIdx.x == 0) {
+        st.mode = SEL_DONE;
+        bt.sel[b] = st;
+      }
+      __syncthreads();
+      return;
+    }
+    st.rem = st.kq;
+    st.prefix = 0;
+    st.pbits = 0;
+  } else if ((level == 1 && st.mode != SEL_L1) || (level == 2 && st.mode != SEL_L2)) {
+    return;
+  }
+  const uint32_t nb = level == 2 ? 256u : 4096u;
+  const uint32_t *h = level == 0 ? bt.hist0 + (uint64_t)b * 4096
+                                 : level == 1 ? bt.hist1 + (uint64_t)b * 4096
+                                              : bt.hist2 + (uint64_t)b * 256;
+  uint32_t bin, above;
+  find_bin(h, nb, st.rem, &bin, &above);
+  if (threadIdx.x == 0) {
+    const uint32_t digits = level == 2 ? 8u : 12u;
+    st.prefix = (st.prefix << digits) | bin;
+    st.pbits += digits;
+    st.rem -= above;
+    st.cnt = __ldcg(h + bin);
+    if (st.cnt <= kBoundCap) st.mode = SEL_COMPACT;
+    else st.mode = level == 0 ? SEL_L1 : level == 1 ? SEL_L2 : SEL_TIES;
+    bt.sel[b] = st;
+  }
+  __syncthreads();
+}
+
+// The pick at a level for every flagged query, by one block (the last of a
+// launch that produced the counts).
+__device__ __noinline__ void pick_all(Batch bt, uint32_t level) {
+  const uint32_t nf = __ldcg(bt.nflag);
+  for (uint32_t f = 0; f < nf; ++f) pick_one(bt, __ldcg(bt.flagged + f), level);
+}
+
 // Dense-path pick at a level for the flagged queries.
 __global__ void k_pick(Batch bt, uint32_t level) {
   const uint32_t nf = *bt.nflag;
-  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
-    const uint32_t b = bt.flagged[f];
-    SelState st = bt.sel[b];
-    if (level == 0) {
-      // the dense histogram counts every id the search sees: a snapshot may
-      // see fewer than the live count that bounded kq
-      __shared__ uint32_t s_tot;
-      if (threadIdx.x == 0) s_tot = 0;
-      __syncthreads();
-      uint32_t c = 0;
-      for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x) c += bt.hist0[(uint64_t)b * 4096 + i];
-      atomicAdd(&s_tot, c);
-      __syncthreads();
-      const uint32_t tot = s_tot;
-      __syncthreads();
-      if (tot < st.kq) {
-        st.kq = tot;
-        if (threadIdx.x == 0) bt.sel[b].kq = tot;
-      }
-      if (st.kq == 0) {
-        if (threadIdx.x == 0) {
-          st.mode = SEL_DONE;
-          bt.sel[b] = st;
-        }
-        __syncthreads();
-        continue;
-      }
-      st.rem = st.kq;
-      st.prefix = 0;
-      st.pbits = 0;
-    } else if ((level == 1 && st.mode != SEL_L1) || (level == 2 && st.mode != SEL_L2)) {
-      continue;
-    }
-    const uint32_t nb = level == 2 ? 256u : 4096u;
-    const uint32_t *h = level == 0 ? bt.hist0 + (uint64_t)b * 4096
-                                   : level == 1 ? bt.hist1 + (uint64_t)b * 4096
-                                                : bt.hist2 + (uint64_t)b * 256;
-    uint32_t bin, above;
-    find_bin(h, nb, st.rem, &bin, &above);
-    if (threadIdx.x == 0) {
-      const uint32_t digits = level == 2 ? 8u : 12u;
-      st.prefix = (st.prefix << digits) | bin;
-      st.pbits += digits;
-      st.rem -= above;
-      st.cnt = h[bin];
-      if (st.cnt <= kBoundCap) st.mode = SEL_COMPACT;
-      else st.mode = level == 0 ? SEL_L1 : level == 1 ? SEL_L2 : SEL_TIES;
-      bt.sel[b] = st;
-    }
-    __syncthreads();
-  }
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) pick_one(bt, bt.flagged[f], level);
 }
 
 // Histogram of the next digit over dense keys matching the current prefix.
-__global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t level) {
+// With fuse set, the launch's last block then makes the level's pick.
+__global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t level,
+                             uint32_t fuse) {
   __shared__ uint32_t hist[4096];
   const uint32_t nf = *bt.nflag;
   const uint64_t chunks = (span + kChunk - 1) / kChunk;
@@ -1210,14 +1252,19 @@ __global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t lev
       if (hist[i]) atomicAdd(&gh[i], hist[i]);
     __syncthreads();
   }
+  if (fuse && last_block(bt.tick + level, gridDim.x)) pick_all(bt, level);
 }
 
 // Dense-path collection: keys above the boundary bin are candidates; in
 // COMPACT mode the boundary bin's keys are buffered too.  A block takes a
 // chunk of kChunk keys, 8 per thread, counts its hits, reserves room for the
 // whole block with one atomic per list and writes them.
+__device__ void refine_one(Batch bt, uint32_t b, uint64_t cap, uint64_t span, uint32_t kpmax);
+
+// With refine_nb > 0, the launch's last block then refines queries
+// 0 .. refine_nb - 1 (the work of k_refine).
 __global__ void __launch_bounds__(256) k_compact(Batch bt, uint64_t cap, uint64_t span,
-                                                 uint32_t kpmax) {
+                                                 uint32_t kpmax, uint32_t refine_nb) {
   constexpr uint32_t PER = kChunk / 256;
   __shared__ uint32_t wsum[2][8], s_base[2];
   const uint32_t nf = *bt.nflag;
@@ -1296,11 +1343,14 @@ __global__ void __launch_bounds__(256) k_compact(Batch bt, uint64_t cap, uint64_
     }
     __syncthreads();  // wsum and s_base are reused by the next chunk
   }
+  if (refine_nb && last_block(bt.tick + 3, gridDim.x))
+    for (uint32_t b = 0; b < refine_nb; ++b) refine_one(bt, b, cap, span, kpmax);
 }
 
 // Block-level selection of the r largest of n distinct 64-bit keys held in
-// global memory: one 8-bit digit per pass from the top, stopping early once
-// the prefix pins down exactly r keys.  Returns (prefix, mask): the selected
+// global memory (read from L2: they may come from the same launch): one
+// 8-bit digit per pass from the top, stopping early once the prefix pins
+// down exactly r keys.  Returns (prefix, mask): the selected
 // keys are those with (key & mask) >= prefix.
 __device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
                                  uint64_t *out_prefix, uint64_t *out_mask) {
@@ -1319,7 +1369,7 @@ __device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
     __syncthreads();
     const uint64_t pre = s_prefix, msk = s_mask;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t k = keys[i];
+      const uint64_t k = __ldcg(keys + i);
       if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255u], 1u);
     }
     __syncthreads();
@@ -1363,14 +1413,16 @@ __device__ void block_select_u64(const uint64_t *keys, uint32_t n, uint32_t r,
   __syncthreads();
 }
 
-// Rest of the boundary bin: the rem best of its keys (COMPACT), or in TIES
-// mode the rem smallest ids whose key equals the boundary value exactly.
-__global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t span,
-                                                uint32_t kpmax) {
-  const uint32_t b = blockIdx.x;
+// Rest of the boundary bin of query b: the rem best of its keys (COMPACT), or
+// in TIES mode the rem smallest ids whose key equals the boundary value
+// exactly.  One block of up to 512 threads; the state and the boundary keys
+// may come from the same launch (read from L2).
+__device__ void refine_one(Batch bt, uint32_t b, uint64_t cap, uint64_t span, uint32_t kpmax) {
   __shared__ SelState st;
   __shared__ uint32_t s_base, wsum[16];
-  if (threadIdx.x == 0) st = bt.sel[b];
+  __syncthreads();  // st and s_base may still be read for the previous query
+  if (threadIdx.x < sizeof(SelState) / 4)
+    ((uint32_t *)&st)[threadIdx.x] = __ldcg((const uint32_t *)&bt.sel[b] + threadIdx.x);
   __syncthreads();
   if (st.mode != SEL_COMPACT && st.mode != SEL_TIES) return;
   uint64_t *cand = bt.cand + (uint64_t)b * kpmax;
@@ -1382,7 +1434,7 @@ __global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t
     block_select_u64(bnd, nb, st.rem, &pre, &msk);
     for (uint32_t i0 = 0; i0 < nb; i0 += blockDim.x) {
       const uint32_t i = i0 + threadIdx.x;
-      const uint64_t k = i < nb ? bnd[i] : 0ull;
+      const uint64_t k = i < nb ? __ldcg(bnd + i) : 0ull;
       const bool take = i < nb && (k & msk) >= pre;
       const uint32_t p = warp_append(take, ncand);
       if (take && p < kpmax) cand[p] = k;
@@ -1418,6 +1470,11 @@ __global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t
   }
 }
 
+__global__ void __launch_bounds__(512) k_refine(Batch bt, uint64_t cap, uint64_t span,
+                                                uint32_t kpmax) {
+  refine_one(bt, blockIdx.x, cap, span, kpmax);
+}
+
 // ------------------------------------------------------------------ re-rank
 struct RerankArgs {
   const uint64_t *fwd_off;
@@ -1441,16 +1498,66 @@ __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
   return (c * 0x9E3779B1u) >> 7 & mask;
 }
 
-// Alg. 7, re-rank: exact <q, x_v> from the vector store for each candidate v.
-// The query lives in a shared-memory hash table; one warp per candidate, lanes
-// over the vector's entries, fixed-order reduction.
-__global__ void k_rerank(RerankArgs a, Batch bt) {
-  extern __shared__ uint32_t hs[];
-  const uint32_t b = blockIdx.y;
-  const SelState st = bt.sel[b];
-  const uint32_t kq = n_selected(st, a.kpmax);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && st.ncand != st.kq) atomicOr(a.err, SINN_DERR_INTERNAL);
-  if (blockIdx.x * (blockDim.x >> 5) >= kq) return;
+// Alg. 7, result: best k of query b's re-ranked candidates, sorted best
+// first.  One block; the re-ranked keys may come from the same launch (read
+// from L2).
+__device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint32_t q0,
+                          uint32_t *out_ids, float *out_scores) {
+  __shared__ uint64_t sk[SINN_MAX_K];
+  __shared__ uint32_t s_cnt;
+  const uint32_t kq = n_selected(bt.sel[b], kpmax);
+  const uint32_t r = min(k, kq);
+  const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
+  uint64_t pre = 0, msk = 0;
+  if (kq > 0) block_select_u64(ek, kq, r, &pre, &msk);
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kq; i += blockDim.x) {
+    const uint64_t key = __ldcg(ek + i);
+    if ((key & msk) >= pre) {
+      const uint32_t p = atomicAdd(&s_cnt, 1u);
+      if (p < SINN_MAX_K) sk[p] = key;
+    }
+  }
+  // bitonic sort, descending, of the r keys padded to the next power of two
+  uint32_t P = 1;
+  while (P < r) P <<= 1;
+  for (uint32_t i = r + threadIdx.x; i < P; i += blockDim.x) sk[i] = 0ull;
+  __syncthreads();
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t j = i ^ stride;
+        if (j > i) {
+          const bool desc = (i & size) == 0;
+          const uint64_t x = sk[i], y = sk[j];
+          if (desc ? (x < y) : (x > y)) {
+            sk[i] = y;
+            sk[j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const uint64_t ob = (uint64_t)(q0 + b) * k;
+  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+    if (i < r) {
+      out_ids[ob + i] = ~(uint32_t)sk[i];
+      out_scores[ob + i] = sinn_key2f((uint32_t)(sk[i] >> 32));
+    } else {
+      out_ids[ob + i] = 0xFFFFFFFFu;
+      out_scores[ob + i] = -INFINITY;
+    }
+  }
+}
+
+// One block's share of query b's re-rank (Alg. 7: exact <q, x_v> from the
+// vector store for each candidate v).  The query lives in a shared-memory
+// hash table; one warp per candidate, lanes over the vector's entries,
+// fixed-order reduction.
+__device__ void rerank_part(const RerankArgs &a, Batch bt, uint32_t b, uint32_t kq,
+                            uint32_t *hs) {
   const uint32_t nt = bt.nt[b];
   uint32_t tsz = 64;
   while (tsz < 2 * nt) tsz <<= 1;
@@ -1513,57 +1620,16 @@ __global__ void k_rerank(RerankArgs a, Batch bt) {
   }
 }
 
-// Alg. 7, result: best k of the re-ranked candidates, sorted best first.
-__global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32_t k, uint32_t q0,
-                                                uint32_t *out_ids, float *out_scores) {
-  __shared__ uint64_t sk[SINN_MAX_K];
-  __shared__ uint32_t s_cnt;
-  const uint32_t b = blockIdx.x;
-  const uint32_t kq = n_selected(bt.sel[b], kpmax);
-  const uint32_t r = min(k, kq);
-  const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
-  uint64_t pre = 0, msk = 0;
-  if (kq > 0) block_select_u64(ek, kq, r, &pre, &msk);
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kq; i += blockDim.x) {
-    const uint64_t key = ek[i];
-    if ((key & msk) >= pre) {
-      const uint32_t p = atomicAdd(&s_cnt, 1u);
-      if (p < SINN_MAX_K) sk[p] = key;
-    }
-  }
-  // bitonic sort, descending, of the r keys padded to the next power of two
-  uint32_t P = 1;
-  while (P < r) P <<= 1;
-  for (uint32_t i = r + threadIdx.x; i < P; i += blockDim.x) sk[i] = 0ull;
-  __syncthreads();
-  for (uint32_t size = 2; size <= P; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-        const uint32_t j = i ^ stride;
-        if (j > i) {
-          const bool desc = (i & size) == 0;
-          const uint64_t x = sk[i], y = sk[j];
-          if (desc ? (x < y) : (x > y)) {
-            sk[i] = y;
-            sk[j] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  const uint64_t ob = (uint64_t)(q0 + b) * k;
-  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
-    if (i < r) {
-      out_ids[ob + i] = ~(uint32_t)sk[i];
-      out_scores[ob + i] = sinn_key2f((uint32_t)(sk[i] >> 32));
-    } else {
-      out_ids[ob + i] = 0xFFFFFFFFu;
-      out_scores[ob + i] = -INFINITY;
-    }
-  }
+// Alg. 7, re-rank, then (the last of a query's blocks to finish) its best k.
+__global__ void k_rerank(RerankArgs a, Batch bt, uint32_t k, uint32_t q0, uint32_t *out_ids,
+                         float *out_scores) {
+  extern __shared__ uint32_t hs[];
+  const uint32_t b = blockIdx.y;
+  const SelState st = bt.sel[b];
+  const uint32_t kq = n_selected(st, a.kpmax);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st.ncand != st.kq) atomicOr(a.err, SINN_DERR_INTERNAL);
+  if (blockIdx.x * (blockDim.x >> 5) < kq) rerank_part(a, bt, b, kq, hs);
+  if (last_block(bt.rdone + b, gridDim.x)) final_one(bt, b, a.kpmax, k, q0, out_ids, out_scores);
 }
 
 __global__ void k_keys_to_scores(const uint32_t *__restrict__ keys, uint64_t cnt, float *out) {
@@ -1610,7 +1676,7 @@ Layout layout_for(const sinn_index *ix, uint32_t B, uint32_t kpmax) {
   L.bnd = o;     o = align256(o + (size_t)B * kBoundCap * 8);
   L.ekeys = o;   o = align256(o + (size_t)B * kpmax * 8);
   L.elist = o;   o = align256(o + (size_t)B * kEmitCap * 8);
-  L.ctr = o;     o = align256(o + ((size_t)3 * B + 4) * 4);
+  L.ctr = o;     o = align256(o + ((size_t)4 * B + 8) * 4);
   L.flagged = o; o = align256(o + (size_t)B * 4);
   L.total = o;
   return L;
@@ -1634,7 +1700,9 @@ Batch views(void *base, const Layout &L, uint32_t B) {
   bt.ecnt = (uint32_t *)(p + L.ctr);
   bt.bound = bt.ecnt + B;
   bt.tdone = bt.bound + B;
-  bt.nflag = bt.tdone + B;
+  bt.rdone = bt.tdone + B;
+  bt.nflag = bt.rdone + B;  // then the persistent kernel's 8-byte counter
+  bt.tick = bt.nflag + 4;
   bt.flagged = (uint32_t *)(p + L.flagged);
   return bt;
 }
@@ -1764,6 +1832,10 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
   const uint32_t fb_score_blocks = (uint32_t)std::max(1, sms) * ix->tune.dense_blocks_per_sm;
   for (uint32_t q0 = 0; q0 < r.n_q; q0 += (uint32_t)B) {
     const uint32_t nb = (uint32_t)std::min<uint64_t>(B, r.n_q - q0);
+    // a launch of a few queries ends its scoring, histogram and compaction
+    // kernels with the next step's pick or refine (the last block to finish
+    // makes it for every query, one after another) instead of launching it
+    const uint32_t fuse = nb <= kFuseQueries ? 1u : 0u;
     {
       SinnPhase ph(ix, s, 0);
       ix->launches++;
@@ -1781,7 +1853,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     }
     if (r.stage == Stage::kScores) {  // dense keys for every query
       ix->launches += 1 + nb;
-      sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
+      sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt, 0u);
       for (uint32_t b = 0; b < nb; ++b) {
         uint64_t cnt = ix->cap;
         k_keys_to_scores<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
@@ -1795,7 +1867,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       SinnPhase ph(ix, s, 1);
       if (dense_all) {
         ix->launches++;
-        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
+        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt, fuse);
       } else {
         ix->launches++;
         if (ix->tune.persistent_blocks_per_sm) {
@@ -1819,23 +1891,30 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
         k_pick_list<<<nb, 128, 0, s>>>(bt);
         k_compact_list<<<nb, 512, 0, s>>>(bt, kpmax);
         k_fb_reset<<<std::min(nb, kFbBlocks), 256, 0, s>>>(bt);
-        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt);
+        sk.dense<<<fb_score_blocks, kLoneThreads, 0, s>>>(sa, bt, fuse);
       }
-      ix->launches += 7;
       // grids no larger than the work (the flagged queries are at most nb)
       const uint32_t gq = std::min(nb, kFbBlocks);
       const uint32_t gc = (uint32_t)std::min<uint64_t>(
           (uint64_t)nb * ((span + kChunk - 1) / kChunk), (uint64_t)fb_score_blocks * 2);
-      k_pick<<<gq, 128, 0, s>>>(bt, 0);
       // the finer levels only run for a boundary bin too large to buffer
       // (massive ties): a smaller grid keeps the common no-op launch cheap
       const uint32_t gh = std::min<uint32_t>(gc, nb * 64);
-      k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1);
-      k_pick<<<gq, 128, 0, s>>>(bt, 1);
-      k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 2);
-      k_pick<<<gq, 128, 0, s>>>(bt, 2);
-      k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax);
-      k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, span, kpmax);
+      if (fuse) {
+        ix->launches += 3;
+        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1, 1u);
+        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 2, 1u);
+        k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax, nb);
+      } else {
+        ix->launches += 7;
+        k_pick<<<gq, 128, 0, s>>>(bt, 0);
+        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1, 0u);
+        k_pick<<<gq, 128, 0, s>>>(bt, 1);
+        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 2, 0u);
+        k_pick<<<gq, 128, 0, s>>>(bt, 2);
+        k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax, 0u);
+        k_refine<<<nb, 512, 0, s>>>(bt, ix->cap, span, kpmax);
+      }
       CK(cudaGetLastError());
     }
     if (r.stage == Stage::kCandidates) {
@@ -1846,7 +1925,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     }
     {
       SinnPhase ph(ix, s, 3);
-      ix->launches += 2;
+      ix->launches += 1;
       // blocks per query: the tuning's count, or (0) about 64 candidates each
       // (for a launch of few queries, enough blocks to fill the GPU, down to
       // one warp per candidate)
@@ -1854,8 +1933,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       if (!ix->tune.rerank_blocks)
         rb = std::max<uint32_t>(rb, ((uint32_t)sms * 8 + nb - 1) / nb);
       k_rerank<<<dim3(std::min<uint32_t>(rb, (kpmax + 7) / 8), nb), 256,
-                 (size_t)tsz * 8, s>>>(ra, bt);
-      k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
+                 (size_t)tsz * 8, s>>>(ra, bt, r.k, q0, r.out_ids, r.out_scores);
       CK(cudaGetLastError());
     }
   }
