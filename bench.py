@@ -791,20 +791,21 @@ def run_mixed(args, dev):
     """The mixed-sign workload (8.8M documents, uniform coordinates, N(0,1)
     values, m = 64, h = 2: both sketch planes read) as an extra line: its
     batched fixed-k' search of 10,000 queries, one-query searches, the
-    scorer's roofline, and recall@10 against the FP64 oracle on a sample."""
+    scorer's roofline, the insert and delete phases of churn steps, and
+    recall@10 against the FP64 oracle on a sample."""
     import torch
     from paper_2301_10622_gb300 import sinnamon
-    w, docs, _, qs = make_inputs(args, 0, workload="mixed", n_docs=args.mixed_docs)
+    w, docs, pool, qs = make_inputs(args, 0, workload="mixed", n_docs=args.mixed_docs)
     k, kp = w.k, w.k_prime
-    ora_job = pool = None
+    ora_job = ex = None
     if not args.skip_oracle:
         # the checker's index builds on one host thread (the C call releases
         # the interpreter lock) while the device part runs
         import oracle
         from concurrent.futures import ThreadPoolExecutor
         oracle.build()
-        pool = ThreadPoolExecutor(1)
-        ora_job = pool.submit(oracle_index, w, docs)
+        ex = ThreadPoolExecutor(1)
+        ora_job = ex.submit(oracle_index, w, docs)
     t0 = time.time()
     ix = build_index(sinnamon, w, docs, dev, 4096, args.scratch_gb)
     torch.cuda.synchronize()
@@ -850,9 +851,24 @@ def run_mixed(args, dev):
                         "postings_per_query": float(P.mean())}}
     out["plain"] = plain_search(sinnamon, ix.handle, qs, g[1], g[2], k, kp, dev,
                                 min(100, args.plain_queries), alg)
+    # streaming churn: steps of `churn` deletes of random live ids and as many
+    # inserts (which take the freed ids), timed by phase
+    rng = np.random.default_rng(77)
+    churn = []
+    for si in range(4):
+        d = torch.from_numpy(rng.choice(docs.rows, args.churn, replace=False).astype(np.int32))
+        part = pool.slice(si * args.churn, (si + 1) * args.churn)
+        sinnamon.sinn_timing_start(ix.handle)
+        ix.delete(d.to(dev))
+        ix.insert(part.indptr.astype(np.int64), part.indices.astype(np.int32), part.values)
+        torch.cuda.synchronize()
+        churn.append(sinnamon.sinn_timing_stop(ix.handle)["ms"])
+    out["churn"] = {"per_step": args.churn, "steps": len(churn) - 1,
+                    "insert_ms": float(np.median([c["insert"] for c in churn[1:]])),
+                    "delete_ms": float(np.median([c["delete"] for c in churn[1:]]))}
     if ora_job is not None:
         ora = ora_job.result()
-        pool.shutdown()
+        ex.shutdown()
         nr = min(args.mixed_recall_queries, qs.rows)
         out["recall_at_10"] = recall_at_10(ora, qs.slice(0, nr), ids.cpu().numpy()[:nr],
                                            os.cpu_count() or 1)

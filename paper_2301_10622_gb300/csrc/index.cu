@@ -234,41 +234,96 @@ __device__ uint32_t block_scan_value(uint32_t x, uint32_t *part, uint32_t *total
   return r;
 }
 
-// Rebuild of the postings of a group of tiles from the vector store, in four
-// passes.  For every live id of a tile and each of its non-zero coordinates
-// j, the tile-local id lands in container (tile, j): a bitmap of T bits when
-// the tile has at least T >> SINN_BITMAP_SHIFT postings of j, else an array
-// of 16-bit local ids in ascending order.  Tombstones disappear: only live
-// vectors contribute.
-//   count   one warp per id slot: postings per (tile, coordinate)
-//   plan    one block per tile: container kinds, array starts by a scan in
-//           coordinate order, bitmap slots from the back of the storage in
-//           the same order; the directory is written and the bitmaps zeroed
-//   scatter one warp per id slot: bitmap bits, array slots by atomic cursors
-//   sort    one warp per (tile, coordinate): each array is put in ascending
-//           order through a bitmap of the tile's local ids
+// Rebuild of the postings of a group of tiles into each tile's other copy,
+// merging the copy searches read now with the batch's new vectors (Alg. 5:
+// the new vectors' postings appended to their lists; Sec. 4.3: tombstones
+// dropped).  Container (tile, j) of the new copy holds the current
+// container's postings that are not tombstones plus the tile-local ids of
+// the new vectors with a non-zero at j: a bitmap of T bits when that makes
+// at least T >> SINN_BITMAP_SHIFT postings, else an array of 16-bit local
+// ids in ascending order.  Only the new vectors are read from the store.
+//   count_old  one warp per (tile, 32 coordinates): each lane counts the live
+//              postings of its coordinate's array; the warp counts each
+//              bitmap together
+//   count_new  one warp per new vector: its postings per coordinate
+//   plan       one block per tile: container kinds, array starts by a scan in
+//              coordinate order, bitmap slots from the back of the storage in
+//              the same order; the directory is written and the bitmaps zeroed
+//   merge_old  as count_old: the live postings into the new containers, in
+//              order (array to array or bitmap, bitmap to bitmap or array)
+//   merge_new  one warp per new vector: bitmap bits, or array slots after the
+//              old postings by atomic cursors; each array so extended is
+//              listed once
+//   sort       one warp per listed array: ascending order again
 struct RebuildArgs {
-  const uint32_t *tiles;      // tile per group entry
+  const uint32_t *tiles;      // tile per group entry (ascending)
   const uint32_t *ver;        // copy (0 or 1) of the tile the entry rebuilds into
   uint16_t *const *new_post;  // storage per group entry
   const uint64_t *post_cap;   // storage size per entry (16-bit words, multiple of T/16)
   uint32_t *cnt;              // n per entry: counts, then array cursors
   uint32_t *out_len;          // postings per entry
-  uint32_t nb, n, T, log2T;
+  const uint2 *dir;           // every tile's directories (copy v of tile t at (2t + v) n)
+  uint16_t *const *post;      // every tile's storage (copy v of tile t at 2t + v)
+  const uint32_t *new_ids;    // the new vectors of the group's tiles
+  uint32_t *dirty;            // nb * n bits: arrays the new vectors extend
+  uint32_t *dlist;            // those arrays, as entry * n + coordinate
+  uint32_t *dcount;           // their number
+  uint32_t dcap;              // room in dlist
+  uint32_t n_new, nb, n, T, log2T;
   uint32_t *err;              // device error word (bounds-check builds)
 };
 
-__global__ void __launch_bounds__(256)
-    k_rb_count(RebuildArgs a, const uint32_t *__restrict__ live,
-               const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
-               const uint2 *__restrict__ fwd) {
-  const uint32_t lane = threadIdx.x & 31;
+// Group entry of tile t (entries are ascending), or -1.
+__device__ __forceinline__ int rb_entry(const RebuildArgs &a, uint32_t t) {
+  uint32_t lo = 0, hi = a.nb;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.tiles[mid] < t) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < a.nb && a.tiles[lo] == t) ? (int)lo : -1;
+}
+
+__global__ void __launch_bounds__(256) k_rb_count_old(RebuildArgs a) {
+  const uint32_t lane = threadIdx.x & 31, BMIN = a.T >> SINN_BITMAP_SHIFT, W128 = a.T >> 7;
+  const uint32_t nch = (a.n + 31) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-       w < (uint64_t)a.nb * a.T; w += nwarps) {
-    const uint32_t i = (uint32_t)(w >> a.log2T), d = (uint32_t)(w & (a.T - 1));
-    const uint64_t id = ((uint64_t)a.tiles[i] << a.log2T) + d;
-    if (!sinn_is_live(live, id)) continue;
+       w < (uint64_t)a.nb * nch; w += nwarps) {
+    const uint32_t i = (uint32_t)(w / nch), c = (uint32_t)(w % nch) * 32 + lane;
+    const uint32_t t = a.tiles[i], ov = 1u - a.ver[i];  // the copy searches read now
+    const uint2 de = c < a.n ? a.dir[((uint64_t)t * 2 + ov) * a.n + c] : make_uint2(0u, 0u);
+    const uint16_t *po = a.post[(uint64_t)t * 2 + ov];
+    uint32_t live = 0;
+    if (de.y > 0 && de.y < BMIN)
+      for (uint32_t e = 0; e < de.y; ++e) live += (po[de.x + e] & SINN_TOMB) ? 0u : 1u;
+    uint32_t bms = __ballot_sync(0xFFFFFFFFu, de.y >= BMIN);
+    while (bms) {  // deletes clear bitmap bits: the live postings are the set bits
+      const uint32_t src = __ffs(bms) - 1;
+      bms &= bms - 1;
+      const uint4 *wd = (const uint4 *)(po + __shfl_sync(0xFFFFFFFFu, de.x, src));
+      uint32_t pc = 0;
+      for (uint32_t k = lane; k < W128; k += 32) {
+        const uint4 q = wd[k];
+        pc += __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
+      }
+      for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xFFFFFFFFu, pc, o);
+      if (lane == src) live = pc;
+    }
+    if (c < a.n) a.cnt[(uint64_t)i * a.n + c] = live;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_rb_count_new(RebuildArgs a, const uint64_t *__restrict__ fwd_off,
+                   const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < a.n_new;
+       w += nwarps) {
+    const uint32_t id = a.new_ids[w];
+    const int i = rb_entry(a, id >> a.log2T);
+    if (!SINN_IN_BOUNDS(i >= 0, a.err)) continue;
     const uint64_t fo = fwd_off[id];
     const uint32_t nz = fwd_nnz[id];
     uint32_t *cnt = a.cnt + (uint64_t)i * a.n;
@@ -328,54 +383,137 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-__global__ void __launch_bounds__(256)
-    k_rb_scatter(RebuildArgs a, const uint32_t *__restrict__ live,
-                 const uint64_t *__restrict__ fwd_off, const uint32_t *__restrict__ fwd_nnz,
-                 const uint2 *__restrict__ fwd, const uint2 *__restrict__ tile_dir) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t BMIN = a.T >> SINN_BITMAP_SHIFT;
+__global__ void __launch_bounds__(256) k_rb_merge_old(RebuildArgs a) {
+  const uint32_t lane = threadIdx.x & 31, BMIN = a.T >> SINN_BITMAP_SHIFT;
+  const uint32_t W128 = a.T >> 7, W32 = a.T >> 5, wpl = W32 >> 5;
+  const uint32_t nch = (a.n + 31) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-       w < (uint64_t)a.nb * a.T; w += nwarps) {
-    const uint32_t i = (uint32_t)(w >> a.log2T), d = (uint32_t)(w & (a.T - 1));
-    const uint32_t t = a.tiles[i];
-    const uint64_t id = ((uint64_t)t << a.log2T) + d;
-    if (!sinn_is_live(live, id)) continue;
-    const uint64_t fo = fwd_off[id];
-    const uint32_t nz = fwd_nnz[id];
-    uint32_t *cur = a.cnt + (uint64_t)i * a.n;
-    const uint2 *dir = tile_dir + ((uint64_t)t * 2 + a.ver[i]) * a.n;
-    uint16_t *post = a.new_post[i];
-    for (uint32_t e = lane; e < nz; e += 32) {
-      const uint2 pr = fwd[fo + e];
-      if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
-      const uint2 de = dir[pr.x];
-      if (de.y >= BMIN) {
-        if (SINN_IN_BOUNDS((uint64_t)de.x + a.T / 16 <= a.post_cap[i], a.err))
-          atomicOr((uint32_t *)(post + de.x) + (d >> 5), 1u << (d & 31));
+       w < (uint64_t)a.nb * nch; w += nwarps) {
+    const uint32_t i = (uint32_t)(w / nch), c = (uint32_t)(w % nch) * 32 + lane;
+    const uint32_t t = a.tiles[i], v = a.ver[i], ov = 1u - v;
+    const bool in = c < a.n;
+    const uint2 de = in ? a.dir[((uint64_t)t * 2 + ov) * a.n + c] : make_uint2(0u, 0u);
+    const uint2 dn = in ? a.dir[((uint64_t)t * 2 + v) * a.n + c] : make_uint2(0u, 0u);
+    const uint16_t *po = a.post[(uint64_t)t * 2 + ov];
+    uint16_t *pn = a.new_post[i];
+    const uint64_t pcap = a.post_cap[i];
+    (void)pcap;  // read by the bounds checks only
+    uint32_t *cur = a.cnt + (uint64_t)i * a.n + c;
+    const bool old_bm = de.y >= BMIN, new_bm = dn.y >= BMIN;
+    // an old array: its lane alone, in order
+    if (de.y > 0 && !old_bm) {
+      if (new_bm) {
+        uint32_t *bm = (uint32_t *)(pn + dn.x);
+        if (SINN_IN_BOUNDS((uint64_t)dn.x + a.T / 16 <= pcap, a.err))
+          for (uint32_t e = 0; e < de.y; ++e) {
+            const uint32_t x = po[de.x + e];
+            if (!(x & SINN_TOMB)) bm[(x & 0x7FFFu) >> 5] |= 1u << (x & 31u);
+          }
       } else {
-        const uint32_t at = atomicAdd(&cur[pr.x], 1u);
-        if (SINN_IN_BOUNDS(at < de.x + de.y && at < a.post_cap[i], a.err)) post[at] = (uint16_t)d;
+        uint32_t at = *cur;
+        for (uint32_t e = 0; e < de.y; ++e) {
+          const uint32_t x = po[de.x + e];
+          if (x & SINN_TOMB) continue;
+          if (SINN_IN_BOUNDS(at < dn.x + dn.y && at < pcap, a.err)) pn[at] = (uint16_t)x;
+          ++at;
+        }
+        *cur = at;
+      }
+    }
+    // an old bitmap: the warp together (an array it turns into starts at
+    // its coordinate's cursor)
+    const uint32_t cur0 = (old_bm && dn.y > 0 && !new_bm) ? *cur : 0u;
+    uint32_t bms = __ballot_sync(0xFFFFFFFFu, old_bm);
+    while (bms) {
+      const uint32_t src = __ffs(bms) - 1;
+      bms &= bms - 1;
+      const uint32_t ox = __shfl_sync(0xFFFFFFFFu, de.x, src);
+      const uint32_t nx = __shfl_sync(0xFFFFFFFFu, dn.x, src);
+      const uint32_t ny = __shfl_sync(0xFFFFFFFFu, dn.y, src);
+      if (ny >= BMIN) {  // bitmap to bitmap: the words as they are
+        if (!SINN_IN_BOUNDS((uint64_t)nx + a.T / 16 <= pcap, a.err)) continue;
+        const uint4 *src4 = (const uint4 *)(po + ox);
+        uint4 *dst4 = (uint4 *)(pn + nx);
+        for (uint32_t k = lane; k < W128; k += 32) dst4[k] = src4[k];
+      } else if (ny > 0) {  // bitmap to array (deletes took it below the threshold)
+        const uint32_t *wd = (const uint32_t *)(po + ox);
+        uint32_t mine = 0;
+        for (uint32_t j = 0; j < wpl; ++j) mine += __popc(wd[lane * wpl + j]);
+        uint32_t inc = mine;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+          if (lane >= (uint32_t)d) inc += y;
+        }
+        const uint32_t base = __shfl_sync(0xFFFFFFFFu, cur0, src);
+        uint32_t at = base + inc - mine;
+        for (uint32_t j = 0; j < wpl; ++j) {
+          uint32_t bits = wd[lane * wpl + j];
+          while (bits) {
+            const uint32_t b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (SINN_IN_BOUNDS(at < nx + ny && at < pcap, a.err))
+              pn[at] = (uint16_t)(((lane * wpl + j) << 5) + b);
+            ++at;
+          }
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        if (lane == src) *cur = base + total;
       }
     }
   }
 }
 
-// Sorts each array container of the rebuilt tiles: up to 32 postings in
-// registers (a bitonic network), more through a T-bit bitmap in shared
-// memory.  Dynamic shared memory: T/32 words per warp.
 __global__ void __launch_bounds__(256)
-    k_rb_sort(RebuildArgs a, const uint2 *__restrict__ tile_dir) {
+    k_rb_merge_new(RebuildArgs a, const uint64_t *__restrict__ fwd_off,
+                   const uint32_t *__restrict__ fwd_nnz, const uint2 *__restrict__ fwd) {
+  const uint32_t lane = threadIdx.x & 31, BMIN = a.T >> SINN_BITMAP_SHIFT;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < a.n_new;
+       w += nwarps) {
+    const uint32_t id = a.new_ids[w];
+    const int i = rb_entry(a, id >> a.log2T);
+    if (i < 0) continue;  // reported by the count
+    const uint32_t t = a.tiles[i], d = id & (a.T - 1);
+    const uint2 *dir = a.dir + ((uint64_t)t * 2 + a.ver[i]) * a.n;
+    uint16_t *pn = a.new_post[i];
+    uint32_t *cur = a.cnt + (uint64_t)i * a.n;
+    const uint64_t fo = fwd_off[id];
+    const uint32_t nz = fwd_nnz[id];
+    for (uint32_t e = lane; e < nz; e += 32) {
+      const uint2 pr = fwd[fo + e];
+      if ((pr.y & 0x7FFFFFFFu) == 0u) continue;
+      const uint2 dn = dir[pr.x];
+      if (dn.y >= BMIN) {
+        if (SINN_IN_BOUNDS((uint64_t)dn.x + a.T / 16 <= a.post_cap[i], a.err))
+          atomicOr((uint32_t *)(pn + dn.x) + (d >> 5), 1u << (d & 31));
+      } else {
+        const uint32_t at = atomicAdd(&cur[pr.x], 1u);
+        if (SINN_IN_BOUNDS(at < dn.x + dn.y && at < a.post_cap[i], a.err)) pn[at] = (uint16_t)d;
+        // the array's order is restored by the sort (listed once)
+        const uint32_t key = (uint32_t)i * a.n + pr.x, bit = 1u << (key & 31);
+        if (!(atomicOr(&a.dirty[key >> 5], bit) & bit)) {
+          const uint32_t p = atomicAdd(a.dcount, 1u);
+          if (SINN_IN_BOUNDS(p < a.dcap, a.err)) a.dlist[p] = key;
+        }
+      }
+    }
+  }
+}
+
+// Sorts the listed array containers of the rebuilt tiles: up to 32 postings
+// in registers (a bitonic network), more through a T-bit bitmap in shared
+// memory.  Dynamic shared memory: T/32 words per warp.
+__global__ void __launch_bounds__(256) k_rb_sort(RebuildArgs a) {
   extern __shared__ uint32_t sm[];
   const uint32_t lane = threadIdx.x & 31, words = a.T >> 5, wpl = words >> 5;
-  const uint32_t BMIN = a.T >> SINN_BITMAP_SHIFT;
   uint32_t *bm = sm + (threadIdx.x >> 5) * words;
+  const uint32_t nl = min(*a.dcount, a.dcap);
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-       w < (uint64_t)a.nb * a.n; w += nwarps) {
-    const uint32_t i = (uint32_t)(w / a.n), c = (uint32_t)(w % a.n);
-    const uint2 de = tile_dir[((uint64_t)a.tiles[i] * 2 + a.ver[i]) * a.n + c];
-    if (de.y < 2 || de.y >= BMIN) continue;  // warp-uniform
+  for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < nl; w += nwarps) {
+    const uint32_t key = a.dlist[w], i = key / a.n, c = key % a.n;
+    const uint2 de = a.dir[((uint64_t)a.tiles[i] * 2 + a.ver[i]) * a.n + c];
+    if (de.y < 2) continue;  // warp-uniform
     uint16_t *seg = a.new_post[i] + de.x;
     if (de.y <= 32) {
       // one posting per lane, sorted by a bitonic network over the warp
@@ -902,7 +1040,7 @@ static int tile_alloc(sinn_index *ix, uint32_t t, uint64_t nnz, cudaStream_t s, 
   const uint64_t slot = (uint64_t)t * 2 + (1u - ix->tile_sel[t]);
   if (ix->tile_post[slot] && ix->tile_post_cap[slot] >= need &&
       ix->tile_post_cap[slot] <= 2 * need) {
-    *out = {nullptr, ix->tile_post_cap[slot]};  // the rebuild reads only the store
+    *out = {nullptr, ix->tile_post_cap[slot]};  // no search reads that copy
     return SINN_OK;
   }
   const uint64_t cap = need + need / 4 / W16 * W16;
@@ -912,20 +1050,30 @@ static int tile_alloc(sinn_index *ix, uint32_t t, uint64_t nnz, cudaStream_t s, 
   return SINN_OK;
 }
 
-// Device scratch of a rebuild of nb tiles: counts, tiles, target copies,
-// storage pointers, storage sizes, lengths.
+// Device scratch of a rebuild of nb tiles with up to n_new new vectors:
+// counts, tiles, target copies, storage pointers, storage sizes, lengths,
+// the extended-array marks, their list (room for `dcap`) and count, the new
+// vectors' ids.
 struct RebuildLayout {
-  size_t o_cn, o_tl, o_vr, o_pt, o_pc, o_ln, bytes;
+  size_t o_cn, o_tl, o_vr, o_pt, o_pc, o_ln, o_dm, o_dc, o_dl, o_id, bytes;
+  uint32_t dcap;
 };
-static RebuildLayout rebuild_layout(const sinn_index *ix, uint32_t nb) {
+static RebuildLayout rebuild_layout(const sinn_index *ix, uint32_t nb, uint64_t n_new,
+                                    uint64_t new_entries) {
   RebuildLayout L;
+  const uint64_t pairs = (uint64_t)nb * ix->n;
+  L.dcap = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(pairs, new_entries));
   L.o_cn = 0;
-  L.o_tl = L.o_cn + (size_t)nb * ix->n * 4;
+  L.o_tl = L.o_cn + (size_t)pairs * 4;
   L.o_vr = L.o_tl + (size_t)nb * 4;
   L.o_pt = (L.o_vr + (size_t)nb * 4 + 15) / 16 * 16;
   L.o_pc = L.o_pt + (size_t)nb * 8;
   L.o_ln = L.o_pc + (size_t)nb * 8;
-  L.bytes = L.o_ln + (size_t)nb * 4;
+  L.o_dm = (L.o_ln + (size_t)nb * 4 + 15) / 16 * 16;
+  L.o_dc = L.o_dm + (size_t)(pairs + 31) / 32 * 4;
+  L.o_dl = (L.o_dc + 4 + 15) / 16 * 16;
+  L.o_id = L.o_dl + (size_t)L.dcap * 4;
+  L.bytes = L.o_id + (size_t)std::max<uint64_t>(n_new, 1) * 4;
   return L;
 }
 
@@ -935,14 +1083,17 @@ static uint32_t rebuild_group_tiles(const sinn_index *ix, size_t tiles) {
   return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (1ull << 30) / per));
 }
 
-// Rebuild the postings of a group of tiles (sorted, unique) from the store
-// into each tile's other copy, with the storage `pre` gives per tile
-// (allocated here if pre is null), then make those copies the ones searches
-// read.  A search already reading a tile keeps its copy intact; flip_seq is
-// the sequence number recorded for the switch.
+// Rebuild the postings of a group of tiles (sorted, unique) into each tile's
+// other copy -- the current copy's live postings and those of the new
+// vectors `new_ids` (host, n_new ids in these tiles, new_entries store
+// entries between them) -- with the storage `pre` gives per tile (allocated
+// here if pre is null), then make those copies the ones searches read.  A
+// search already reading a tile keeps its copy intact; flip_seq is the
+// sequence number recorded for the switch.
 static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cudaStream_t s,
-                         const TileAlloc *pre, uint32_t flip_seq) {
-  const RebuildLayout RL = rebuild_layout(ix, nb);
+                         const TileAlloc *pre, uint32_t flip_seq, const uint32_t *new_ids,
+                         uint32_t n_new, uint64_t new_entries) {
+  const RebuildLayout RL = rebuild_layout(ix, nb, n_new, new_entries);
   int st = ensure_iscratch(ix, RL.bytes);
   if (st) return st;
   std::vector<uint16_t *> newp(nb);
@@ -963,7 +1114,7 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
     newp[i] = ta.p ? ta.p : ix->tile_post[slot];
     pcap[i] = ta.cap;
   }
-  const size_t hb = (size_t)nb * (4 + 4 + 8 + 8);
+  const size_t hb = (size_t)nb * (4 + 4 + 8 + 8) + (size_t)n_new * 4;
   CK(cudaStreamSynchronize(s));  // earlier copies may still read the staging buffer
   if ((st = sinn_ensure_pinned(ix, hb))) return st;
   char *hp = (char *)ix->pinned;
@@ -971,13 +1122,18 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   memcpy(hp + (size_t)nb * 4, ver.data(), (size_t)nb * 4);
   memcpy(hp + (size_t)nb * 8, newp.data(), (size_t)nb * 8);
   memcpy(hp + (size_t)nb * 16, pcap.data(), (size_t)nb * 8);
+  if (n_new) memcpy(hp + (size_t)nb * 24, new_ids, (size_t)n_new * 4);
   char *sp = (char *)ix->iscratch;
   CK(cudaMemcpyAsync(sp + RL.o_tl, hp, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sp + RL.o_vr, hp + (size_t)nb * 4, (size_t)nb * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sp + RL.o_pt, hp + (size_t)nb * 8, (size_t)nb * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sp + RL.o_pc, hp + (size_t)nb * 16, (size_t)nb * 8, cudaMemcpyHostToDevice,
                      s));
-  CK(cudaMemsetAsync(sp + RL.o_cn, 0, (size_t)nb * ix->n * 4, s));
+  if (n_new)
+    CK(cudaMemcpyAsync(sp + RL.o_id, hp + (size_t)nb * 24, (size_t)n_new * 4,
+                       cudaMemcpyHostToDevice, s));
+  // the marks and the list count start at zero (the counts are written whole)
+  CK(cudaMemsetAsync(sp + RL.o_dm, 0, RL.o_dl - RL.o_dm, s));
   RebuildArgs a;
   a.tiles = (const uint32_t *)(sp + RL.o_tl);
   a.ver = (const uint32_t *)(sp + RL.o_vr);
@@ -985,6 +1141,14 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   a.post_cap = (const uint64_t *)(sp + RL.o_pc);
   a.cnt = (uint32_t *)(sp + RL.o_cn);
   a.out_len = (uint32_t *)(sp + RL.o_ln);
+  a.dir = ix->d_tile_dir;
+  a.post = ix->d_tile_post;
+  a.new_ids = (const uint32_t *)(sp + RL.o_id);
+  a.dirty = (uint32_t *)(sp + RL.o_dm);
+  a.dcount = (uint32_t *)(sp + RL.o_dc);
+  a.dlist = (uint32_t *)(sp + RL.o_dl);
+  a.dcap = RL.dcap;
+  a.n_new = n_new;
   a.nb = nb;
   a.n = ix->n;
   a.T = ix->T;
@@ -992,16 +1156,25 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   a.err = ix->d_err;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  // grids: a warp per (tile, 32 coordinates), per new vector, per listed
+  // array, each at most 32 blocks per SM
   const uint64_t cap_blocks = (uint64_t)std::max(1, sms) * 32;
-  const uint64_t slot_blocks = std::min<uint64_t>(((uint64_t)nb * ix->T + 7) / 8, cap_blocks);
-  const uint64_t pair_blocks = std::min<uint64_t>(((uint64_t)nb * ix->n + 7) / 8, cap_blocks);
-  ix->launches += 5;
-  k_rb_count<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
-                                                   ix->d_fwd);
+  const uint64_t chunk_blocks =
+      std::min<uint64_t>(((uint64_t)nb * ((ix->n + 31) / 32) + 7) / 8, cap_blocks);
+  const uint64_t new_blocks = std::min<uint64_t>(((uint64_t)n_new + 7) / 8, cap_blocks);
+  const uint64_t sort_blocks = std::min<uint64_t>(((uint64_t)RL.dcap + 7) / 8, cap_blocks);
+  ix->launches += 5 + (n_new ? 3 : 0);
+  k_rb_count_old<<<(unsigned)chunk_blocks, 256, 0, s>>>(a);
+  if (n_new)
+    k_rb_count_new<<<(unsigned)new_blocks, 256, 0, s>>>(a, ix->d_fwd_off, ix->d_fwd_nnz,
+                                                        ix->d_fwd);
   k_rb_plan<<<nb, 1024, 0, s>>>(a, ix->d_tile_dir, ix->d_tile_post, ix->d_err);
-  k_rb_scatter<<<(unsigned)slot_blocks, 256, 0, s>>>(a, ix->d_live, ix->d_fwd_off, ix->d_fwd_nnz,
-                                                     ix->d_fwd, ix->d_tile_dir);
-  k_rb_sort<<<(unsigned)pair_blocks, 256, (size_t)8 * (ix->T / 32) * 4, s>>>(a, ix->d_tile_dir);
+  k_rb_merge_old<<<(unsigned)chunk_blocks, 256, 0, s>>>(a);
+  if (n_new) {
+    k_rb_merge_new<<<(unsigned)new_blocks, 256, 0, s>>>(a, ix->d_fwd_off, ix->d_fwd_nnz,
+                                                        ix->d_fwd);
+    k_rb_sort<<<(unsigned)sort_blocks, 256, (size_t)8 * (ix->T / 32) * 4, s>>>(a);
+  }
   k_rb_flip<<<(nb + 255) / 256, 256, 0, s>>>(a, ix->d_tile_sel);
   CK(cudaGetLastError());
   for (uint32_t i = 0; i < nb; ++i) {
@@ -1029,17 +1202,25 @@ static int rebuild_group(sinn_index *ix, const uint32_t *tiles, uint32_t nb, cud
   return SINN_OK;
 }
 
-// Rebuild the postings of the given tiles (sorted, unique), in groups whose
-// per-coordinate counts fit 1 GiB of scratch, into the storage `pre` gives
-// per tile (or allocated as they go if pre is null).
+// Rebuild the postings of the given tiles (sorted, unique) with the new
+// vectors `new_ids` (each in one of them; new_entries store entries in
+// all), in groups whose per-coordinate counts fit 1 GiB of scratch, into
+// the storage `pre` gives per tile (or allocated as they go if pre is null).
 static int rebuild_tiles(sinn_index *ix, const std::vector<uint32_t> &tiles, cudaStream_t s,
-                         const std::vector<TileAlloc> *pre, uint32_t flip_seq) {
+                         const std::vector<TileAlloc> *pre, uint32_t flip_seq,
+                         const std::vector<uint32_t> &new_ids, uint64_t new_entries) {
   if (tiles.empty()) return SINN_OK;
   const uint32_t g = rebuild_group_tiles(ix, tiles.size());
+  std::vector<uint32_t> ids(new_ids);
+  std::sort(ids.begin(), ids.end());  // by tile: each group's ids are one run
+  size_t k = 0;
   for (size_t g0 = 0; g0 < tiles.size(); g0 += g) {
     const uint32_t nb = (uint32_t)std::min<size_t>(g, tiles.size() - g0);
+    const uint32_t last = tiles[g0 + nb - 1];
+    const size_t k0 = k;
+    while (k < ids.size() && (ids[k] >> ix->log2T) <= last) ++k;
     int st = rebuild_group(ix, tiles.data() + g0, nb, s, pre ? pre->data() + g0 : nullptr,
-                           flip_seq);
+                           flip_seq, ids.data() + k0, (uint32_t)(k - k0), new_entries);
     if (st) return st;
   }
   return SINN_OK;
@@ -1138,10 +1319,10 @@ static int insert_impl(sinn_index *ix, const uint64_t *indptr, const uint32_t *i
                                              (uint32_t)tiles.size());
     const size_t o_off0 = ((size_t)n_docs * 4 + 15) / 16 * 16;
     if ((st = ensure_iscratch(ix, std::max(o_off0 + (size_t)n_docs * 8,
-                                           rebuild_layout(ix, gmax).bytes))))
+                                           rebuild_layout(ix, gmax, n_docs, total).bytes))))
       return st;
     if ((st = sinn_ensure_pinned(ix, std::max(ipb + (size_t)n_docs * 12 + 64,
-                                              (size_t)gmax * 24))))
+                                              (size_t)gmax * 24 + (size_t)n_docs * 4))))
       return st;
     pre.resize(tiles.size());
     for (size_t i = 0; i < tiles.size(); ++i) {
@@ -1208,7 +1389,7 @@ static int insert_impl(sinn_index *ix, const uint64_t *indptr, const uint32_t *i
   ix->launches++;
   k_store_u64<<<1, 1, 0, s>>>(ix->d_live_count, ix->live_count);
   CK(cudaGetLastError());
-  if ((st = rebuild_tiles(ix, tiles, s, &pre, at ? seq : 0u))) return st;
+  if ((st = rebuild_tiles(ix, tiles, s, &pre, at ? seq : 0u, ids, total))) return st;
   uint32_t bits = 0;
   if ((st = read_and_clear_err(ix, s, &bits))) return st;
   return bits ? SINN_EDEVICE : SINN_OK;
