@@ -141,11 +141,15 @@ __global__ void k_qprep(const uint64_t *__restrict__ q_indptr, const uint32_t *_
   // the slot's selection state starts empty: histograms, emitted count,
   // running bound, tiles done; block 0 also resets the launch's counters
   // (flagged queries, the persistent kernel's work counter)
-  for (uint32_t i = threadIdx.x; i < 4096 + 4096 + 256; i += blockDim.x) {
-    const uint32_t which = i < 4096 ? 0 : (i < 8192 ? 1 : 2);
-    uint32_t *h = which == 0 ? bt.hist0 + (uint64_t)b * 4096
-                             : which == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
-    h[i - (which == 0 ? 0u : which == 1 ? 4096u : 8192u)] = 0u;
+  {
+    uint4 *h0 = (uint4 *)(bt.hist0 + (uint64_t)b * 4096), *h1 = (uint4 *)(bt.hist1 + (uint64_t)b * 4096);
+    uint4 *h2 = (uint4 *)(bt.hist2 + (uint64_t)b * 256);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) {
+      h0[i] = z;
+      h1[i] = z;
+    }
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) h2[i] = z;
   }
   if (threadIdx.x == 0) {
     bt.ecnt[b] = 0u;
@@ -1226,13 +1230,22 @@ __global__ void k_pick(Batch bt, uint32_t level) {
 __global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t level,
                              uint32_t fuse) {
   __shared__ uint32_t hist[4096];
+  __shared__ uint32_t s_any;
   const uint32_t nf = *bt.nflag;
   const uint64_t chunks = (span + kChunk - 1) / kChunk;
   const uint32_t nb = level == 1 ? 4096u : 256u;
-  for (uint64_t w = blockIdx.x; w < nf * chunks; w += gridDim.x) {
+  const SelMode want = level == 1 ? SEL_L1 : SEL_L2;
+  // the level is needed only for a boundary bin too large to buffer: look
+  // once before walking the keys
+  if (threadIdx.x == 0) s_any = 0u;
+  __syncthreads();
+  for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x)
+    if (bt.sel[bt.flagged[f]].mode == want) s_any = 1u;
+  __syncthreads();
+  for (uint64_t w = blockIdx.x; s_any && w < nf * chunks; w += gridDim.x) {
     const uint32_t b = bt.flagged[w / chunks];
     const SelState st = bt.sel[b];
-    if (st.mode != (level == 1 ? SEL_L1 : SEL_L2)) continue;
+    if (st.mode != want) continue;
     for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const uint32_t shift_p = 32 - st.pbits;  // 20 or 8
@@ -1620,16 +1633,24 @@ __device__ void rerank_part(const RerankArgs &a, Batch bt, uint32_t b, uint32_t 
   }
 }
 
-// Alg. 7, re-rank, then (the last of a query's blocks to finish) its best k.
-__global__ void k_rerank(RerankArgs a, Batch bt, uint32_t k, uint32_t q0, uint32_t *out_ids,
-                         float *out_scores) {
+// Alg. 7, re-rank; with fuse set, the last of a query's blocks to finish
+// then takes its best k (otherwise k_final does).
+__global__ void k_rerank(RerankArgs a, Batch bt, uint32_t fuse, uint32_t k, uint32_t q0,
+                         uint32_t *out_ids, float *out_scores) {
   extern __shared__ uint32_t hs[];
   const uint32_t b = blockIdx.y;
   const SelState st = bt.sel[b];
   const uint32_t kq = n_selected(st, a.kpmax);
   if (blockIdx.x == 0 && threadIdx.x == 0 && st.ncand != st.kq) atomicOr(a.err, SINN_DERR_INTERNAL);
   if (blockIdx.x * (blockDim.x >> 5) < kq) rerank_part(a, bt, b, kq, hs);
-  if (last_block(bt.rdone + b, gridDim.x)) final_one(bt, b, a.kpmax, k, q0, out_ids, out_scores);
+  if (fuse && last_block(bt.rdone + b, gridDim.x))
+    final_one(bt, b, a.kpmax, k, q0, out_ids, out_scores);
+}
+
+// Alg. 7, result, for a launch of many queries: one block per query.
+__global__ void __launch_bounds__(1024) k_final(Batch bt, uint32_t kpmax, uint32_t k, uint32_t q0,
+                                                uint32_t *out_ids, float *out_scores) {
+  final_one(bt, blockIdx.x, kpmax, k, q0, out_ids, out_scores);
 }
 
 __global__ void k_keys_to_scores(const uint32_t *__restrict__ keys, uint64_t cnt, float *out) {
@@ -1925,7 +1946,7 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
     }
     {
       SinnPhase ph(ix, s, 3);
-      ix->launches += 1;
+      ix->launches += fuse ? 1 : 2;
       // blocks per query: the tuning's count, or (0) about 64 candidates each
       // (for a launch of few queries, enough blocks to fill the GPU, down to
       // one warp per candidate)
@@ -1933,7 +1954,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       if (!ix->tune.rerank_blocks)
         rb = std::max<uint32_t>(rb, ((uint32_t)sms * 8 + nb - 1) / nb);
       k_rerank<<<dim3(std::min<uint32_t>(rb, (kpmax + 7) / 8), nb), 256,
-                 (size_t)tsz * 8, s>>>(ra, bt, r.k, q0, r.out_ids, r.out_scores);
+                 (size_t)tsz * 8, s>>>(ra, bt, fuse, r.k, q0, r.out_ids, r.out_scores);
+      if (!fuse) k_final<<<nb, 1024, 0, s>>>(bt, kpmax, r.k, q0, r.out_ids, r.out_scores);
       CK(cudaGetLastError());
     }
   }
