@@ -128,8 +128,10 @@ def _delete_at(ix, book, ids, seq):
     book.delete(ids, seq)
 
 
-def test_snapshots_see_their_epoch_and_reclaim_reuses_ids():
+@pytest.mark.parametrize("walk", [0, 1])
+def test_snapshots_see_their_epoch_and_reclaim_reuses_ids(walk):
     w, ix, book, extra, qs = _setup()
+    ix.set_tuning(array_walk=walk, emit_min_batch=1)  # batched scorers, either walk
     rng = np.random.default_rng(3)
     k, kp = 10, 150
     ctx = sinnamon.Context(ix, 64 << 20)
