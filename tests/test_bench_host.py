@@ -119,3 +119,36 @@ def test_clock_summary_reads_throttle_reasons():
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_recall_counts_ties_from_the_exact_list():
+    """recall@10: an id of the exact top 10 is a hit; a missed id is a hit
+    exactly when its exact score ties the 10th (taken from the exact list,
+    or from the dense exact scores when the whole list ties the 10th)."""
+    class FakeOracle:
+        def __init__(self, ids, scores, dense):
+            self.ids, self.scores, self.dense, self.dense_calls = ids, scores, dense, 0
+
+        def linscan_topk(self, ip, ix, v, k, threads):
+            return {"ids": self.ids[:, :k], "scores": self.scores[:, :k]}
+
+        def exact_scores(self, qi, qv):
+            self.dense_calls += 1
+            return self.dense
+
+    D = bench.TRUTH_DEPTH
+    ids = np.arange(D, dtype=np.int64)[None, :]
+    sc = np.linspace(10.0, 1.0, D)[None, :]
+    sc[0, 10] = sc[0, 9]                    # id 10 ties the 10th
+    qs = _csr([[(0, 1.0)]])
+    ora = FakeOracle(ids, sc, None)
+    got = np.array([[0, 1, 2, 3, 4, 5, 6, 7, 10, 11]])   # 8 of the top 10, the tie, a miss
+    assert bench.recall_at_10(ora, qs, got, 1) == 0.9
+    assert bench.recall_at_10(ora, qs, np.array([[0, 1, 2, 3, 4, 5, 6, 7, 8, 500]]), 1) == 0.9
+    assert ora.dense_calls == 0             # the list ends below the tie: 500 is a miss
+    flat = np.full((1, D), 3.0)
+    dense = np.zeros(1000)
+    dense[500] = 3.0
+    ora2 = FakeOracle(ids, flat, dense)     # every listed score ties the 10th
+    assert bench.recall_at_10(ora2, qs, np.array([[0, 1, 2, 3, 4, 5, 6, 7, 8, 500]]), 1) == 1.0
+    assert ora2.dense_calls == 1
