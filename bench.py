@@ -363,12 +363,15 @@ def dram_figures(fig, launch_ms, peak, units_per_launch, docs):
     """DRAM bytes per launch from a profile's counters, scaled to this run's
     units per launch; the DRAM fraction of peak over the live launch time;
     and the L1 / L2 throughput fractions the profile read.  None entries
-    when the profile does not match this kernel or this index size."""
+    when the profile does not match this kernel or this index size, and no
+    traffic when this run's launches hold more than 10% more or fewer units
+    than the profiled ones (a launch streams the index about once, so its
+    traffic is not proportional to its queries)."""
     out = {"traffic": None, "dram_frac": None, "l1_frac": None, "l2_frac": None}
     if not fig or fig.get("docs_in_index") != docs:
         return out
     per, q = fig.get("traffic_bytes_per_launch"), fig.get("queries_per_launch")
-    if per and q and launch_ms:
+    if per and q and launch_ms and abs(units_per_launch - q) <= 0.1 * q:
         t = per * units_per_launch / q
         out["traffic"] = t
         out["dram_frac"] = t / (launch_ms / 1000.0) / 1e9 / peak

@@ -166,6 +166,9 @@ class Server:
             mlp.forward(torch.zeros((1, sinnamon.KP_FEATURES), device=index.device))
         self.slots = [_Slot(index, slot_bytes, self.max_batch, max_nnz, k, mlp)
                       for _ in range(slots)]
+        # mutations run on a stream of their own, ordered before later
+        # searches by an event and beside the ones in flight
+        self.mstream = torch.cuda.Stream(device=index.device)
         self.mutated = torch.cuda.Event()
         self.mutated.record(torch.cuda.current_stream(index.device))
         self.t_delete = self.t_insert = self.t_wait = 0.0
@@ -177,7 +180,8 @@ class Server:
     # ------------------------------------------------------------ mutations
     def _reclaim(self, log, horizon):
         if horizon > self.reclaimed:
-            self.ix.reclaim(horizon)
+            with torch.cuda.stream(self.mstream):
+                self.ix.reclaim(horizon, stream=self.mstream)
             self.reclaimed = horizon
             log.append(("reclaim", [], None, None, horizon))
 
@@ -196,7 +200,8 @@ class Server:
         if dels:
             ids = [self.live.take(reqs[r].u) for r in dels if len(self.live)]
             if ids:
-                self.ix.delete_at(np.asarray(ids, np.int32), e)
+                with torch.cuda.stream(self.mstream):
+                    self.ix.delete_at(np.asarray(ids, np.int32), e, stream=self.mstream)
             log.append(("delete", dels, None, np.asarray(ids, np.int64), e))
         t1 = time.perf_counter()
         if ins:
@@ -204,7 +209,9 @@ class Server:
             ip, idx, val = csr_rows(self.pool, rows)
             while True:
                 try:
-                    ids = self.ix.insert_at(ip, idx, val, e).cpu().numpy().astype(np.int64)
+                    with torch.cuda.stream(self.mstream):
+                        got = self.ix.insert_at(ip, idx, val, e, stream=self.mstream)
+                        ids = got.cpu().numpy().astype(np.int64)
                     break
                 except sinnamon.SinnError as err:
                     if err.code != sinnamon.SINN_EBUSY:
@@ -216,7 +223,7 @@ class Server:
                     self._reclaim(log, horizon_fn())
             self.live.add(ids)
             log.append(("insert", ins, rows, ids, e))
-        self.mutated.record(torch.cuda.current_stream(self.ix.device))
+        self.mutated.record(self.mstream)
         t2 = time.perf_counter()
         self.t_delete += t1 - t0
         self.t_insert += t2 - t1

@@ -94,11 +94,14 @@ def test_profile_figures_scale_and_check_their_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     fig = bench.profile_figures("k_score_emit_text")
     assert fig["traffic_bytes_per_launch"] == 1e6 and fig["docs_in_index"] == 5000
-    # 50 queries per launch: half the bytes; 1 ms per launch at 1000 GB/s peak
-    d = bench.dram_figures(fig, 1.0, 1000.0, 50, 5000)
-    assert d["traffic"] == pytest.approx(500000.0)
-    assert d["dram_frac"] == pytest.approx(500000.0 / 1e-3 / 1e9 / 1000.0)
+    # 95 queries per launch: 0.95 of the bytes; 1 ms per launch at 1000 GB/s peak
+    d = bench.dram_figures(fig, 1.0, 1000.0, 95, 5000)
+    assert d["traffic"] == pytest.approx(950000.0)
+    assert d["dram_frac"] == pytest.approx(950000.0 / 1e-3 / 1e9 / 1000.0)
     assert d["l2_frac"] == 0.5 and d["l1_frac"] is None
+    # launches half the profiled size: no scaled traffic, the fractions stay
+    d = bench.dram_figures(fig, 1.0, 1000.0, 50, 5000)
+    assert d["traffic"] is None and d["dram_frac"] is None and d["l2_frac"] == 0.5
     assert bench.dram_figures(fig, 1.0, 1000.0, 50, 6000)["traffic"] is None  # another size
     (src / "search.cu").write_text("__global__ void k() { int x; }\n")
     assert bench.profile_figures("k_score_emit_text") is None                  # kernel changed
