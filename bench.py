@@ -405,8 +405,11 @@ def config_dict(args, w, docs, qs, tile_docs, index_gb=0.0):
 
 # ------------------------------------------------------------------- ours
 
-def build_index(sinnamon, w, docs, dev, T, scratch_gb, flags=0):
-    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
+def build_index(sinnamon, w, docs, dev, T, scratch_gb, flags=0, extra_ids=0):
+    """The collection indexed in batches of 200k; room for extra_ids more ids
+    is reserved up front (growing the id capacity later pauses the device)."""
+    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T,
+                        capacity_hint=docs.rows + extra_ids,
                         scratch_bytes=scratch_gb << 30, flags=flags)
     for a in range(0, docs.rows, 200_000):
         part = docs.slice(a, min(docs.rows, a + 200_000))
@@ -530,7 +533,12 @@ def run_ours(args):
         tile_choice = {str(t): round(r["ms"], 3) for t, r in res.items()}
         log(f"tile size {T} chosen in {time.time() - t0:.1f}s: {tile_choice}")
     t0 = time.time()
-    ix = build_index(sinnamon, w, docs, dev, T, args.scratch_gb)
+    # the serving leg's net inserts get their ids reserved with the index
+    serve_growth = 0
+    if args.serve_seconds > 0:
+        r_ins, r_del, _ = (float(x) for x in args.serve_rates.split(","))
+        serve_growth = int(max(0.0, r_ins - r_del) * args.serve_seconds * 1.2) + 4096
+    ix = build_index(sinnamon, w, docs, dev, T, args.scratch_gb, extra_ids=serve_growth)
     torch.cuda.synchronize()
     st = ix.stats()
     log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
