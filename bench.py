@@ -405,11 +405,8 @@ def config_dict(args, w, docs, qs, tile_docs, index_gb=0.0):
 
 # ------------------------------------------------------------------- ours
 
-def build_index(sinnamon, w, docs, dev, T, scratch_gb, flags=0, extra_ids=0):
-    """The collection indexed in batches of 200k; room for extra_ids more ids
-    is reserved up front (growing the id capacity later pauses the device)."""
-    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T,
-                        capacity_hint=docs.rows + extra_ids,
+def build_index(sinnamon, w, docs, dev, T, scratch_gb, flags=0):
+    ix = sinnamon.Index(w.n, w.m, w.h, device=dev, tile_docs=T, capacity_hint=docs.rows,
                         scratch_bytes=scratch_gb << 30, flags=flags)
     for a in range(0, docs.rows, 200_000):
         part = docs.slice(a, min(docs.rows, a + 200_000))
@@ -533,12 +530,7 @@ def run_ours(args):
         tile_choice = {str(t): round(r["ms"], 3) for t, r in res.items()}
         log(f"tile size {T} chosen in {time.time() - t0:.1f}s: {tile_choice}")
     t0 = time.time()
-    # the serving leg's net inserts get their ids reserved with the index
-    serve_growth = 0
-    if args.serve_seconds > 0:
-        r_ins, r_del, _ = (float(x) for x in args.serve_rates.split(","))
-        serve_growth = int(max(0.0, r_ins - r_del) * args.serve_seconds * 1.2) + 4096
-    ix = build_index(sinnamon, w, docs, dev, T, args.scratch_gb, extra_ids=serve_growth)
+    ix = build_index(sinnamon, w, docs, dev, T, args.scratch_gb)
     torch.cuda.synchronize()
     st = ix.stats()
     log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
@@ -985,6 +977,10 @@ def run_serving(args, w, ix, qs, n_live, mlp, k, kp):
                                                                        seed=5001))
     reqs = serving.poisson_stream(args.serve_seconds, {"insert": r_ins, "delete": r_del,
                                                        "query": r_q}, spool.rows, qs.rows)
+    # room for the stream's inserts up front: growing the id capacity or the
+    # vector store mid-stream would pause the device
+    n_ins = sum(r.kind == "insert" for r in reqs)
+    ix.reserve(n_ins + 4096, int(spool.nnz / max(spool.rows, 1) * n_ins * 1.2) + (1 << 16))
     srv = serving.Server(ix, qs, spool, np.arange(n_live), slots=args.serve_slots,
                          slot_bytes=int(args.serve_slot_gb * (1 << 30)), k=k, k_prime=kp,
                          mlp=mlp, kp_max=args.kp_max, mutation_delay=args.serve_delay)

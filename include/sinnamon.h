@@ -279,6 +279,16 @@ int sinn_sync(sinn_index *ix, void *stream);
 /* Fill *out with the counters above (host). */
 int sinn_stats(sinn_index *ix, sinn_stats_t *out);
 
+/* Make room ahead of inserts: id slots for more_ids fresh ids beyond those
+ * handed out so far (next_id) and vector-store room for more_entries
+ * (coordinate, value) entries beyond those it holds, so that inserts up to
+ * those sizes allocate no id-capacity arrays and no store (growing either
+ * waits for every stream of the device, which a serving loop would feel as
+ * a pause).  Room already there is kept; nothing else changes.  SINN_ENOMEM
+ * (and no change to the part that failed) if an allocation fails; the id
+ * capacity is limited as for inserts. */
+int sinn_reserve(sinn_index *ix, uint64_t more_ids, uint64_t more_entries);
+
 /* Alg. 6's anytime budget T, counted in postings (the scoring time is
  * proportional to them): each query's terms run in Alg. 6 order and scoring
  * stops after the first term at which the live postings of the lists scored

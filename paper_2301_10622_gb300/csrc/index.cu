@@ -1563,6 +1563,15 @@ extern "C" int sinn_reclaim(sinn_index *ix, uint32_t horizon, void *stream) {
   return SINN_OK;
 }
 
+extern "C" int sinn_reserve(sinn_index *ix, uint64_t more_ids, uint64_t more_entries) {
+  if (!ix) return SINN_EINVAL;
+  SinnDevice dev_guard_(ix->device);
+  if (more_ids > 0xFFFFFFFEull || more_entries > (1ull << 40)) return SINN_ENOMEM;
+  int st = grow_capacity(ix, ix->next_id + more_ids);
+  if (st) return st;
+  return grow_store(ix, ix->fwd_used + more_entries);
+}
+
 extern "C" int sinn_stats(sinn_index *ix, sinn_stats_t *out) {
   if (!ix || !out) return SINN_EINVAL;
   memset(out, 0, sizeof(*out));

@@ -30,6 +30,7 @@ snapshot).
 """
 from __future__ import annotations
 
+import gc
 import time
 from dataclasses import dataclass
 
@@ -286,11 +287,25 @@ class Server:
         lists ("insert"|"delete"|"query"|"reclaim", request indices, pool
         rows, ids, sequence number) in the order the loop made the calls (a
         query's number is its snapshot, a reclaim's its horizon)."""
+        # the interpreter's cyclic collector is paused while serving: a full
+        # collection over the requests, results and log objects stalls the
+        # loop for tens of milliseconds, which every queued query would wait
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(reqs, max_wall)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _serve(self, reqs, max_wall):
         n = len(reqs)
         results, done_t = {}, np.full(n, np.nan)
         log, wm = [], []
         wq = []  # waiting queries: (request index, snapshot)
         nxt, batches, inflight_max, epochs, overlapped = 0, 0, 0, 0, 0
+        epoch_max = 0.0  # the longest epoch, host time
+        self.launch_max = 0.0  # the longest batch launch, host time
         self.t_delete = self.t_insert = self.t_wait = 0.0
         self.busy_waits = 0
         t0 = time.perf_counter()
@@ -305,7 +320,9 @@ class Server:
                     j = 0
                     while j < len(queue) and j < self.max_batch and queue[j][1] == snap:
                         j += 1
+                    tl = time.perf_counter()
                     self._launch(s, [q for q, _ in queue[:j]], reqs, log, snap)
+                    self.launch_max = max(self.launch_max, time.perf_counter() - tl)
                     queue = queue[j:]
                     batches += 1
             inflight_max = max(inflight_max, sum(s.batch is not None for s in self.slots))
@@ -341,7 +358,9 @@ class Server:
             if wm and (now - reqs[wm[0]].t >= self.mutation_delay or nxt >= n):
                 # an epoch: applied at the next number while searches run
                 overlapped += any(s.batch is not None for s in self.slots)
+                te = time.perf_counter()
                 self._apply(reqs, wm, log, horizon, wait_oldest)
+                epoch_max = max(epoch_max, time.perf_counter() - te)
                 done_t[wm] = time.perf_counter() - t0
                 wm = []
                 epochs += 1
@@ -369,6 +388,7 @@ class Server:
                  "mutation_p50_ms": pct(ml, 50), "mutation_p99_ms": pct(ml, 99),
                  "query_batches": batches, "mean_batch": ql.size / max(batches, 1),
                  "epochs": epochs, "epochs_overlapped": overlapped,
+                 "epoch_max_ms": 1000.0 * epoch_max, "launch_max_ms": 1000.0 * self.launch_max,
                  "epoch_busy_wait_s": self.t_wait,
                  "busy_waits": self.busy_waits, "epoch_delete_s": self.t_delete,
                  "epoch_insert_s": self.t_insert, "max_batch": self.max_batch,

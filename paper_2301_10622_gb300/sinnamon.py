@@ -39,6 +39,7 @@ EXPORTS = [
     "sinn_set_budget", "sinn_get_budget", "sinn_save", "sinn_load", "sinn_debug_fail_alloc",
     "sinn_debug_wait_probe", "sinn_search_kpb", "sinn_candidates_kpb", "sinn_query_postings",
     "sinn_insert_at", "sinn_delete_at", "sinn_reclaim", "sinn_ctx_set_snapshot",
+    "sinn_reserve",
     # sinnamon_kprime.h
     "sinn_kp_features", "sinn_mlp_create", "sinn_mlp_destroy", "sinn_mlp_num_params",
     "sinn_mlp_params", "sinn_mlp_set_params", "sinn_mlp_set_normalizer", "sinn_mlp_forward",
@@ -193,6 +194,7 @@ def load(build_if_missing: bool = False):
         "sinn_insert_at": ([vp, vp, vp, vp, u32, vp, u32, vp], C.c_int),
         "sinn_delete_at": ([vp, vp, u32, u32, vp], C.c_int),
         "sinn_reclaim": ([vp, u32, vp], C.c_int),
+        "sinn_reserve": ([vp, u64, u64], C.c_int),
         "sinn_ctx_set_snapshot": ([vp, u32], C.c_int),
         "sinn_candidates_kpb": ([vp, vp, vp, vp, u32, u32, vp, vp, vp, vp, vp], C.c_int),
         "sinn_query_postings": ([vp, vp, vp, vp, u32, vp, vp], C.c_int),
@@ -294,6 +296,10 @@ def sinn_delete_at(ix, ids, seq, stream=None):
 
 def sinn_reclaim(ix, horizon, stream=None):
     _check(load().sinn_reclaim(ix, int(horizon), _s(stream)), "sinn_reclaim")
+
+
+def sinn_reserve(ix, more_ids, more_entries):
+    _check(load().sinn_reserve(ix, int(more_ids), int(more_entries)), "sinn_reserve")
 
 
 def sinn_search(ix, q_indptr, q_indices, q_values, k, k_prime, out_ids, out_scores,
@@ -743,6 +749,11 @@ class Index:
 
     def reclaim(self, horizon: int, stream=None):
         sinn_reclaim(self._h, horizon, stream)
+
+    def reserve(self, more_ids: int, more_entries: int):
+        """sinn_reserve: room for more_ids fresh ids and more_entries store
+        entries beyond those in use."""
+        sinn_reserve(self._h, more_ids, more_entries)
 
     def search(self, indptr, indices, values, k: int, k_prime, k_prime_max: int | None = None,
                stream=None):

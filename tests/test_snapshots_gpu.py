@@ -245,3 +245,25 @@ def test_sequence_arguments_are_checked():
     for s in (1, sinnamon.SINN_SEQ_LATEST):
         ctx.set_snapshot(s)
         _check(*_ctx_search(ctx, _dev_csr(qs, ix.device), 5, 50), book, w, 1, qs, 5, 50)
+
+
+def test_reserve_makes_room_ahead():
+    """sinn_reserve grows the id capacity and the vector store once; inserts
+    within the reserved sizes then allocate neither, and the index holds and
+    returns the same as without the reservation."""
+    w, ix, book, extra, qs = _setup(n0=3000, pool=2000, nq=8)
+    before = ix.stats()
+    ix.reserve(2000, int(extra.nnz))
+    st = ix.stats()
+    assert st["capacity"] >= before["next_id"] + 2000 and st["bytes_store"] > before["bytes_store"]
+    assert st["live"] == before["live"] and st["postings"] == before["postings"]
+    ix.reserve(10, 10)                                 # already there: no change
+    assert ix.stats() == st
+    new = _insert_at(ix, book, extra.slice(0, 2000), 1)
+    after = ix.stats()
+    assert after["capacity"] == st["capacity"] and after["bytes_store"] == st["bytes_store"]
+    assert list(new) == list(range(3000, 5000))
+    ctx = sinnamon.Context(ix, 32 << 20)
+    for s in (0, 1):
+        ctx.set_snapshot(s)
+        _check(*_ctx_search(ctx, _dev_csr(qs, ix.device), 10, 100), book, w, s, qs, 10, 100)
