@@ -536,11 +536,12 @@ def run_ours(args):
     log(f"gpu index built in {time.time() - t0:.1f}s: {st}")
     lens = list_lengths(w, docs)
 
-    # launch tuning chosen by the autotuner on a sample of the step's queries
+    # launch tuning chosen by the autotuner on the step's batch of queries (a
+    # smaller sample misjudges how many queries a launch should take)
     tuning = None
     if not args.no_autotune:
         t0 = time.time()
-        sq = qs.slice(0, min(qs.rows, 2000))
+        sq = qs.slice(0, min(qs.rows, args.autotune_queries or qs.rows))
         tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
                              k, kp, reps=2)
         log(f"autotuned in {time.time() - t0:.1f}s: {tuning}")
@@ -826,7 +827,7 @@ def run_mixed(args, dev):
     ix = build_index(sinnamon, w, docs, dev, 4096, args.scratch_gb)
     torch.cuda.synchronize()
     t_build = time.time() - t0
-    sq = qs.slice(0, min(qs.rows, 2000))
+    sq = qs.slice(0, min(qs.rows, args.autotune_queries or qs.rows))
     tuning = ix.autotune(sq.indptr.astype(np.int64), sq.indices.astype(np.int32), sq.values,
                          k, kp, reps=1)
     g = (torch.from_numpy(qs.indptr.astype(np.int64)).to(dev),
@@ -1062,6 +1063,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--no-graph", action="store_true", help="launch the search directly")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-queries", type=int, default=0,
+                    help="queries the launch autotuner times; 0 = the whole batch")
     ap.add_argument("--tuning", default="",
                     help="launch tuning fields to set, e.g. array_walk=1,tiles_per_block=2")
     ap.add_argument("--skip-variants", action="store_true")
