@@ -1225,15 +1225,41 @@ __global__ void k_pick(Batch bt, uint32_t level) {
   for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) pick_one(bt, bt.flagged[f], level);
 }
 
+// Counts of the next digit (level 1: 12 bits, level 2: 8 bits) of query b's
+// dense keys in [beg, end) that match its current prefix, added into the
+// query's histogram of that level (hist: the block's shared scratch).
+__device__ void hist_keys(Batch bt, uint32_t b, const SelState &st, uint64_t cap, uint64_t beg,
+                          uint64_t end, uint32_t level, uint32_t *hist) {
+  const uint32_t nb = level == 1 ? 4096u : 256u;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const uint32_t shift_p = 32 - st.pbits;  // 20 or 8
+  const uint32_t shift_d = level == 1 ? 8u : 0u;
+  const uint32_t dmask = nb - 1;
+  const uint32_t *keys = bt.keys + (uint64_t)b * cap;
+  for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const uint32_t key = keys[i];
+    if (key != 0u && (key >> shift_p) == st.prefix) atomicAdd(&hist[(key >> shift_d) & dmask], 1u);
+  }
+  __syncthreads();
+  uint32_t *gh = level == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+    if (hist[i]) atomicAdd(&gh[i], hist[i]);
+  __syncthreads();
+}
+
 // Histogram of the next digit over dense keys matching the current prefix.
-// With fuse set, the launch's last block then makes the level's pick.
+// With fuse set, the launch's last block then makes the level's pick; with
+// fuse = 2 (level 1 only) that block also counts and picks level 2 for any
+// query whose boundary bin is still too large (rare: massive ties), so one
+// launch covers both levels.
 __global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t level,
                              uint32_t fuse) {
   __shared__ uint32_t hist[4096];
   __shared__ uint32_t s_any;
+  __shared__ SelState s_st;
   const uint32_t nf = *bt.nflag;
   const uint64_t chunks = (span + kChunk - 1) / kChunk;
-  const uint32_t nb = level == 1 ? 4096u : 256u;
   const SelMode want = level == 1 ? SEL_L1 : SEL_L2;
   // the level is needed only for a boundary bin too large to buffer: look
   // once before walking the keys
@@ -1246,26 +1272,24 @@ __global__ void k_hist_level(Batch bt, uint64_t cap, uint64_t span, uint32_t lev
     const uint32_t b = bt.flagged[w / chunks];
     const SelState st = bt.sel[b];
     if (st.mode != want) continue;
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    const uint32_t shift_p = 32 - st.pbits;  // 20 or 8
-    const uint32_t shift_d = level == 1 ? 8u : 0u;
-    const uint32_t dmask = nb - 1;
-    const uint32_t *keys = bt.keys + (uint64_t)b * cap;
     const uint64_t beg = (w % chunks) * kChunk;
-    const uint64_t end = (beg + kChunk < span) ? beg + kChunk : span;
-    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-      const uint32_t key = keys[i];
-      if (key != 0u && (key >> shift_p) == st.prefix)
-        atomicAdd(&hist[(key >> shift_d) & dmask], 1u);
-    }
-    __syncthreads();
-    uint32_t *gh = level == 1 ? bt.hist1 + (uint64_t)b * 4096 : bt.hist2 + (uint64_t)b * 256;
-    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
-      if (hist[i]) atomicAdd(&gh[i], hist[i]);
-    __syncthreads();
+    hist_keys(bt, b, st, cap, beg, (beg + kChunk < span) ? beg + kChunk : span, level, hist);
   }
-  if (fuse && last_block(bt.tick + level, gridDim.x)) pick_all(bt, level);
+  if (fuse && last_block(bt.tick + level, gridDim.x)) {
+    pick_all(bt, level);
+    if (fuse == 2 && level == 1) {
+      const uint32_t nf2 = __ldcg(bt.nflag);
+      for (uint32_t f = 0; f < nf2; ++f) {
+        const uint32_t b = __ldcg(bt.flagged + f);
+        if (threadIdx.x < sizeof(SelState) / 4)
+          ((uint32_t *)&s_st)[threadIdx.x] = __ldcg((const uint32_t *)&bt.sel[b] + threadIdx.x);
+        __syncthreads();
+        if (s_st.mode == SEL_L2) hist_keys(bt, b, s_st, cap, 0, span, 2, hist);
+        __syncthreads();  // s_st is read again for the next query
+      }
+      pick_all(bt, 2);
+    }
+  }
 }
 
 // Dense-path collection: keys above the boundary bin are candidates; in
@@ -1514,6 +1538,67 @@ __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
 // Alg. 7, result: best k of query b's re-ranked candidates, sorted best
 // first.  One block; the re-ranked keys may come from the same launch (read
 // from L2).
+// The r largest (r <= 32) of kq <= 8 x blockDim distinct non-zero keys into
+// sk[0 .. r), largest first: each warp takes the r largest of its keys (held
+// in registers) by r rounds of a warp-wide maximum whose owner drops it, then
+// warp 0 takes the r largest of the warps' picks the same way from shared
+// memory.  The whole block calls it.
+constexpr uint32_t kSmallPer = 8;  // keys per thread
+__device__ void top_small(const uint64_t *ek, uint32_t kq, uint32_t r, uint64_t *sk) {
+  __shared__ uint64_t wk[32 * 32];  // per warp, its r largest (zeros after)
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t i = threadIdx.x; i < nw * 32; i += blockDim.x) wk[i] = 0ull;
+  uint64_t v[kSmallPer];
+#pragma unroll
+  for (uint32_t u = 0; u < kSmallPer; ++u) {
+    const uint32_t i = threadIdx.x + u * blockDim.x;
+    v[u] = i < kq ? __ldcg(ek + i) : 0ull;
+  }
+  __syncthreads();
+  for (uint32_t j = 0; j < r; ++j) {
+    uint64_t m = v[0];
+    uint32_t um = 0;
+#pragma unroll
+    for (uint32_t u = 1; u < kSmallPer; ++u)
+      if (v[u] > m) {
+        m = v[u];
+        um = u;
+      }
+    uint64_t x = m;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+      x = y > x ? y : x;
+    }
+    if (x != 0ull && m == x) {  // keys are distinct: one owner
+#pragma unroll
+      for (uint32_t u = 0; u < kSmallPer; ++u)
+        if (u == um) v[u] = 0ull;
+    }
+    if (lane == 0) wk[wid * 32 + j] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (uint32_t j = 0; j < r; ++j) {
+      uint64_t m = 0ull;
+      uint32_t im = 0;
+      for (uint32_t i = lane; i < nw * 32; i += 32)
+        if (wk[i] > m) {
+          m = wk[i];
+          im = i;
+        }
+      uint64_t x = m;
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        x = y > x ? y : x;
+      }
+      if (x != 0ull && m == x) wk[im] = 0ull;
+      __syncwarp();
+      if (lane == 0) sk[j] = x;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint32_t q0,
                           uint32_t *out_ids, float *out_scores) {
   __shared__ uint64_t sk[SINN_MAX_K];
@@ -1521,6 +1606,21 @@ __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint
   const uint32_t kq = n_selected(bt.sel[b], kpmax);
   const uint32_t r = min(k, kq);
   const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
+  const uint64_t ob = (uint64_t)(q0 + b) * k;
+  if (r <= 32 && kq <= kSmallPer * blockDim.x) {
+    // few results: a tournament over registers, already in order
+    top_small(ek, kq, r, sk);
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+      if (i < r) {
+        out_ids[ob + i] = ~(uint32_t)sk[i];
+        out_scores[ob + i] = sinn_key2f((uint32_t)(sk[i] >> 32));
+      } else {
+        out_ids[ob + i] = 0xFFFFFFFFu;
+        out_scores[ob + i] = -INFINITY;
+      }
+    }
+    return;
+  }
   uint64_t pre = 0, msk = 0;
   if (kq > 0) block_select_u64(ek, kq, r, &pre, &msk);
   if (threadIdx.x == 0) s_cnt = 0;
@@ -1553,7 +1653,6 @@ __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint
       __syncthreads();
     }
   }
-  const uint64_t ob = (uint64_t)(q0 + b) * k;
   for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
     if (i < r) {
       out_ids[ob + i] = ~(uint32_t)sk[i];
@@ -1922,9 +2021,8 @@ int run_search(sinn_index *ix, const SearchReq &r, cudaStream_t s,
       // (massive ties): a smaller grid keeps the common no-op launch cheap
       const uint32_t gh = std::min<uint32_t>(gc, nb * 64);
       if (fuse) {
-        ix->launches += 3;
-        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1, 1u);
-        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 2, 1u);
+        ix->launches += 2;
+        k_hist_level<<<gh, 256, 0, s>>>(bt, ix->cap, span, 1, 2u);
         k_compact<<<gc, 256, 0, s>>>(bt, ix->cap, span, kpmax, nb);
       } else {
         ix->launches += 7;
