@@ -1538,67 +1538,6 @@ __device__ __forceinline__ uint32_t hslot(uint32_t c, uint32_t mask) {
 // Alg. 7, result: best k of query b's re-ranked candidates, sorted best
 // first.  One block; the re-ranked keys may come from the same launch (read
 // from L2).
-// The r largest (r <= 32) of kq <= 8 x blockDim distinct non-zero keys into
-// sk[0 .. r), largest first: each warp takes the r largest of its keys (held
-// in registers) by r rounds of a warp-wide maximum whose owner drops it, then
-// warp 0 takes the r largest of the warps' picks the same way from shared
-// memory.  The whole block calls it.
-constexpr uint32_t kSmallPer = 8;  // keys per thread
-__device__ void top_small(const uint64_t *ek, uint32_t kq, uint32_t r, uint64_t *sk) {
-  __shared__ uint64_t wk[32 * 32];  // per warp, its r largest (zeros after)
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint32_t i = threadIdx.x; i < nw * 32; i += blockDim.x) wk[i] = 0ull;
-  uint64_t v[kSmallPer];
-#pragma unroll
-  for (uint32_t u = 0; u < kSmallPer; ++u) {
-    const uint32_t i = threadIdx.x + u * blockDim.x;
-    v[u] = i < kq ? __ldcg(ek + i) : 0ull;
-  }
-  __syncthreads();
-  for (uint32_t j = 0; j < r; ++j) {
-    uint64_t m = v[0];
-    uint32_t um = 0;
-#pragma unroll
-    for (uint32_t u = 1; u < kSmallPer; ++u)
-      if (v[u] > m) {
-        m = v[u];
-        um = u;
-      }
-    uint64_t x = m;
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
-      x = y > x ? y : x;
-    }
-    if (x != 0ull && m == x) {  // keys are distinct: one owner
-#pragma unroll
-      for (uint32_t u = 0; u < kSmallPer; ++u)
-        if (u == um) v[u] = 0ull;
-    }
-    if (lane == 0) wk[wid * 32 + j] = x;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    for (uint32_t j = 0; j < r; ++j) {
-      uint64_t m = 0ull;
-      uint32_t im = 0;
-      for (uint32_t i = lane; i < nw * 32; i += 32)
-        if (wk[i] > m) {
-          m = wk[i];
-          im = i;
-        }
-      uint64_t x = m;
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        x = y > x ? y : x;
-      }
-      if (x != 0ull && m == x) wk[im] = 0ull;
-      __syncwarp();
-      if (lane == 0) sk[j] = x;
-    }
-  }
-  __syncthreads();
-}
-
 __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint32_t q0,
                           uint32_t *out_ids, float *out_scores) {
   __shared__ uint64_t sk[SINN_MAX_K];
@@ -1606,21 +1545,6 @@ __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint
   const uint32_t kq = n_selected(bt.sel[b], kpmax);
   const uint32_t r = min(k, kq);
   const uint64_t *ek = bt.ekeys + (uint64_t)b * kpmax;
-  const uint64_t ob = (uint64_t)(q0 + b) * k;
-  if (r <= 32 && kq <= kSmallPer * blockDim.x) {
-    // few results: a tournament over registers, already in order
-    top_small(ek, kq, r, sk);
-    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
-      if (i < r) {
-        out_ids[ob + i] = ~(uint32_t)sk[i];
-        out_scores[ob + i] = sinn_key2f((uint32_t)(sk[i] >> 32));
-      } else {
-        out_ids[ob + i] = 0xFFFFFFFFu;
-        out_scores[ob + i] = -INFINITY;
-      }
-    }
-    return;
-  }
   uint64_t pre = 0, msk = 0;
   if (kq > 0) block_select_u64(ek, kq, r, &pre, &msk);
   if (threadIdx.x == 0) s_cnt = 0;
@@ -1653,6 +1577,7 @@ __device__ void final_one(Batch bt, uint32_t b, uint32_t kpmax, uint32_t k, uint
       __syncthreads();
     }
   }
+  const uint64_t ob = (uint64_t)(q0 + b) * k;
   for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
     if (i < r) {
       out_ids[ob + i] = ~(uint32_t)sk[i];
