@@ -434,15 +434,18 @@ def train_policy(args, w, ix, k, kp):
     pc = kprime.measure_costs(ix, cq, k=k, k_prime=kp)
     mlp.set_policy(shifts, pc, 0.0)
     _, _, ex_c = kprime.labels(ix, cq, k=k, cap=args.kp_cap)
+    curve = []
     margin, cal_rec = kprime.calibrate_margin(ix, mlp, cq, ex_c, k=k, kp_min=k,
-                                              kp_max=args.kp_max, target=args.cal_recall)
+                                              kp_max=args.kp_max, target=args.cal_recall,
+                                              curve=curve)
     info = {"train_queries": tq.rows, "label_cap": args.kp_cap, "search_cap": args.kp_max,
             "certified_labels": float(np.mean(cert)), "levels_shifts": list(shifts),
             "label_median_per_level": [float(np.median(lv[:, i])) for i in range(len(shifts))],
             "label_feasible_per_level": [float(np.mean(lv[:, i] <= args.kp_max))
                                          for i in range(len(shifts))],
             "posting_cost": pc, "margin": margin, "calibration_queries": cq.rows,
-            "calibration_recall": cal_rec, "label_seconds": t_lab, "fit_seconds": t_fit,
+            "calibration_recall": cal_rec, "calibration_curve": curve,
+            "label_seconds": t_lab, "fit_seconds": t_fit,
             "train_seconds": time.time() - t0}
     log(f"budget + k' network trained: {info}")
     return mlp, info

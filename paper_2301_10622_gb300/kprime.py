@@ -198,22 +198,31 @@ def recall(ids, exact_ids, k: int = 10) -> float:
                           for r in range(ids.shape[0])]))
 
 
+CAL_MARGINS = (-2.0, -1.5, -1.25, -1.0, -0.875, -0.75, -0.625, -0.5, -0.375, -0.25, -0.125,
+               0.0, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0)
+
+
 def calibrate_margin(ix, mlp, queries, exact_ids, k: int = 10, kp_min: int = 10,
-                     kp_max: int = 4096, target: float = 0.92,
-                     margins=(0.0, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0)):
+                     kp_max: int = 4096, target: float = 0.92, margins=CAL_MARGINS,
+                     curve=None):
     """The least margin (added to every predicted log2 k') at which the
     learned search keeps mean recall@k >= target on held-out queries whose
     exact top k the method certified; sets it on the network's policy.
-    Returns (margin, recall)."""
+    Margins are tried in increasing order, negative ones first: the pinball
+    fit at tau = 0.9 puts most queries above their label already, so the
+    mean recall at margin 0 can sit well above the target.  `curve`, if a
+    list, receives each (margin, recall) tried.  Returns (margin, recall)."""
     pol = mlp.policy()
     ip, ii = queries.indptr.astype(np.int64), queries.indices.astype(np.int32)
     got = None
-    for mg in margins:
+    for mg in sorted(margins):
         mlp.set_policy(pol["shifts"], pol["posting_cost"], mg)
         ids, _, _ = ix.search_learned(mlp, ip, ii, queries.values, k, kp_min, kp_max)
         ix.sync()
         r = recall(ids, exact_ids, k)
         got = (mg, r)
+        if curve is not None:
+            curve.append((float(mg), float(r)))
         if r >= target:
             break
     return got
