@@ -3,7 +3,9 @@ exact top-k lists, kprime.labels_from gives the approximate rank of the
 keep-th found exact id and certifies the top-k exactly when Thm. 1 allows it
 (every live id a candidate, or the k-th exact score at or above the last
 candidate's approximate score).  Checked against a plain loop on random
-batches with ties, missing ids, padding and garbage beyond each count."""
+batches with ties, missing ids, padding and garbage beyond each count.
+The margin calibration's order (negative margins first, the least margin
+whose held-out recall reaches the target) against a stand-in index."""
 import numpy as np
 import pytest
 
@@ -73,3 +75,68 @@ def test_labels_by_hand():
     cs6 = torch.tensor([[0.9, 0.9, 0.5, 0.2, 9.0, 9.0]])  # garbage beyond the count
     kp, cert = kprime.labels_from(cid6, cs6, cnt, ids, torch.tensor([[0.7, 0.1]]), 6, 2, 2)
     assert kp.tolist() == [3] and cert.tolist() == [True]
+
+
+class _FakeNet:
+    """A network stand-in: keeps the policy kprime.calibrate_margin sets."""
+
+    def __init__(self):
+        self.pol = {"shifts": [0, 1], "posting_cost": 0.001, "margin": 0.0}
+        self.set_calls = []
+
+    def policy(self):
+        return dict(self.pol)
+
+    def set_policy(self, shifts, posting_cost, margin):
+        self.pol = {"shifts": list(shifts), "posting_cost": posting_cost, "margin": margin}
+        self.set_calls.append(margin)
+
+
+class _FakeIndex:
+    """Answers a learned search with the exact top 10 for the first
+    round(recall(margin) * rows) queries and misses them all for the rest."""
+
+    def __init__(self, exact, recall_of):
+        self.exact, self.recall_of, self.net = exact, recall_of, None
+
+    def search_learned(self, net, ip, ii, v, k, kp_min, kp_max):
+        self.net = net
+        rows = self.exact.shape[0]
+        good = int(round(self.recall_of(net.pol["margin"]) * rows))
+        ids = np.where(np.arange(rows)[:, None] < good, self.exact, self.exact + 1000)
+        return torch.from_numpy(ids), None, None
+
+    def sync(self):
+        pass
+
+
+class _Q:
+    def __init__(self, rows):
+        self.indptr = np.arange(rows + 1, dtype=np.int64)
+        self.indices = np.zeros(rows, np.int32)
+        self.values = np.ones(rows, np.float32)
+
+
+def test_calibration_takes_the_least_margin_reaching_the_target():
+    rows = 200
+    exact = np.arange(rows * 10, dtype=np.int64).reshape(rows, 10)
+    # recall rises with the margin: 0.80 at -2, +0.05 per 1/4 of log2 k'
+    rec = lambda mg: min(1.0, 0.80 + 0.2 * (mg + 2.0))  # noqa: E731
+    net, curve = _FakeNet(), []
+    ix = _FakeIndex(exact, rec)
+    mg, r = kprime.calibrate_margin(ix, net, _Q(rows), exact, target=0.92, curve=curve)
+    assert mg == -1.25 and r == pytest.approx(0.95)
+    assert net.pol["margin"] == -1.25                    # left set on the policy
+    assert net.pol["shifts"] == [0, 1] and net.pol["posting_cost"] == 0.001
+    assert [m for m, _ in curve] == [-2.0, -1.5, -1.25]  # increasing, stops at the first
+    assert curve[0][1] == pytest.approx(0.80) and curve[1][1] == pytest.approx(0.90)
+
+
+def test_calibration_ends_at_the_largest_margin_when_the_target_is_out_of_reach():
+    rows = 50
+    exact = np.arange(rows * 10, dtype=np.int64).reshape(rows, 10)
+    net, curve = _FakeNet(), []
+    mg, r = kprime.calibrate_margin(_FakeIndex(exact, lambda mg: 0.5), net, _Q(rows), exact,
+                                    target=0.92, margins=(1.0, -1.0, 0.0), curve=curve)
+    assert mg == 1.0 and r == pytest.approx(0.5)
+    assert [m for m, _ in curve] == [-1.0, 0.0, 1.0]
