@@ -101,8 +101,9 @@ int sinn_search_learned(sinn_index *ix, sinn_mlp *m, const uint64_t *q_indptr,
  *   The network then has n_in = SINN_KP_FEATURES + 1 inputs: the query's
  *   features followed by -shift[l], and its output for that row is log2 of
  *   that level's k'.
- *   k'_l = max(ceil(2^(output + margin)), k_prime_min); the level is
- *   feasible when k'_l <= k_prime_max.  The feasible level of least
+ *   k'_l = max(ceil(2^v), k_prime_min) with v = output + margin clamped
+ *   to [0, 31] (the margin may be negative); the level is feasible when
+ *   k'_l <= k_prime_max.  The feasible level of least
  *   posting_cost * (its postings) + k'_l is chosen (ties: the earlier level,
  *   the larger budget); when no level is feasible, level 0 at k_prime_max.
  *   posting_cost is the time of scoring one posting in units of the time of
@@ -116,7 +117,7 @@ typedef struct sinn_kp_policy {
   uint32_t n_levels;                   /* 1..SINN_KP_MAX_LEVELS */
   uint32_t shift[SINN_KP_MAX_LEVELS];  /* budget P_q / 2^shift[l]; shift[0] = 0 */
   float posting_cost;                  /* >= 0: one posting's cost in candidates */
-  float margin;                        /* added to every predicted log2 k' */
+  float margin;                        /* added to every predicted log2 k' (any finite value) */
 } sinn_kp_policy;
 
 /* Set (p != NULL) or clear (p == NULL) the network's policy.  EINVAL for a
