@@ -117,7 +117,7 @@ typedef struct sinn_kp_policy {
   uint32_t n_levels;                   /* 1..SINN_KP_MAX_LEVELS */
   uint32_t shift[SINN_KP_MAX_LEVELS];  /* budget P_q / 2^shift[l]; shift[0] = 0 */
   float posting_cost;                  /* >= 0: one posting's cost in candidates */
-  float margin;                        /* added to every predicted log2 k' (any finite value) */
+  float margin;                        /* added to each predicted log2 k'; finite */
 } sinn_kp_policy;
 
 /* Set (p != NULL) or clear (p == NULL) the network's policy.  EINVAL for a
