@@ -1033,7 +1033,7 @@ def reconstruct(docs, parts, dels, executed):
     return CSR(ip, idx, val)
 
 
-def main():
+def arg_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -1077,7 +1077,11 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-slot-gb", type=float, default=1.0)
     ap.add_argument("--serve-delay", type=float, default=0.005)
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = arg_parser().parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:

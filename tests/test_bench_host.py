@@ -155,3 +155,42 @@ def test_recall_counts_ties_from_the_exact_list():
     ora2 = FakeOracle(ids, flat, dense)     # every listed score ties the 10th
     assert bench.recall_at_10(ora2, qs, np.array([[0, 1, 2, 3, 4, 5, 6, 7, 8, 500]]), 1) == 1.0
     assert ora2.dense_calls == 1
+
+
+def _profile_commands():
+    """Shell commands of the committed ncu summaries, continuation lines
+    joined: (file, command) pairs."""
+    import glob
+    out = []
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for ln in text.splitlines():
+            if ln.startswith("    "):                      # indented code lines
+                out.append((os.path.basename(path), ln.strip()))
+    return out
+
+
+def test_profile_commands_parse_with_the_bench_flags():
+    """Every bench.py command a profile gives is one bench.py accepts."""
+    import re
+    import shlex
+    seen = 0
+    for name, cmd in _profile_commands():
+        m = re.search(r'bench\.py([^"#>]*)', cmd)
+        if not m:
+            continue
+        seen += 1
+        try:
+            bench.arg_parser().parse_args(shlex.split(m.group(1)))
+        except SystemExit:
+            pytest.fail(f"{name}: bench.py rejects {m.group(1).strip()!r}")
+    assert seen >= 6
+
+
+def test_profile_ncu_commands_leave_the_clocks_alone():
+    """Every ncu command in the summaries passes --clock-control none."""
+    cmds = [(n, c) for n, c in _profile_commands() if c.startswith("ncu ")]
+    assert len(cmds) >= 6
+    for name, cmd in cmds:
+        assert "--clock-control none" in cmd, (name, cmd)
