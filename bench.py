@@ -362,12 +362,14 @@ def profile_figures(name, src_file="search.cu"):
 def dram_figures(fig, launch_ms, peak, units_per_launch, docs):
     """DRAM bytes per launch from a profile's counters, scaled to this run's
     units per launch; the DRAM fraction of peak over the live launch time;
-    and the L1 / L2 throughput fractions the profile read.  None entries
+    the L1 / L2 throughput fractions and the global-load sectors per
+    request (the gathers' coalescing) the profile read.  None entries
     when the profile does not match this kernel or this index size, and no
     traffic when this run's launches hold more than 10% more or fewer units
     than the profiled ones (a launch streams the index about once, so its
     traffic is not proportional to its queries)."""
-    out = {"traffic": None, "dram_frac": None, "l1_frac": None, "l2_frac": None}
+    out = {"traffic": None, "dram_frac": None, "l1_frac": None, "l2_frac": None,
+           "sectors_per_request": None}
     if not fig or fig.get("docs_in_index") != docs:
         return out
     per, q = fig.get("traffic_bytes_per_launch"), fig.get("queries_per_launch")
@@ -377,6 +379,7 @@ def dram_figures(fig, launch_ms, peak, units_per_launch, docs):
         out["dram_frac"] = t / (launch_ms / 1000.0) / 1e9 / peak
     out["l1_frac"] = fig.get("l1_throughput_frac")
     out["l2_frac"] = fig.get("l2_throughput_frac")
+    out["sectors_per_request"] = fig.get("sectors_per_request")
     return out
 
 
@@ -655,7 +658,8 @@ def run_ours(args):
                           "scoring time; queries resident together share each tile's lists and "
                           "sketch rows through L2, so it can exceed 1"),
             "traffic": dr["traffic"], "dram_frac": dr["dram_frac"], "l1_frac": dr["l1_frac"],
-            "l2_frac": dr["l2_frac"], "kernel": "k_score_emit", "launches": launches,
+            "l2_frac": dr["l2_frac"], "sectors_per_request": dr["sectors_per_request"],
+            "kernel": "k_score_emit", "launches": launches,
             "avg_launch_ms": score_ms / launches,
             "peak_source": "measured" if peaks else "fallback",
             "alg_bytes_per_query": float(alg_q.mean()),
@@ -867,6 +871,7 @@ def run_mixed(args, dev):
                         "sector_floor_gbs": fl_gbs, "sector_floor_frac": fl_gbs / peak,
                         "traffic": dr["traffic"], "dram_frac": dr["dram_frac"],
                         "l1_frac": dr["l1_frac"], "l2_frac": dr["l2_frac"],
+                        "sectors_per_request": dr["sectors_per_request"],
                         "kernel": "k_score_emit", "launches": launches,
                         "avg_launch_ms": s_ms / launches,
                         "alg_bytes_per_query": float(alg.mean()),

@@ -90,7 +90,8 @@ def test_profile_figures_scale_and_check_their_source(tmp_path, monkeypatch):
     prof = tmp_path / "profiles" / "k_score_emit_text.md"
     prof.write_text(f"# title: words\nsource_code_sha256_16: {h}\n"
                     "traffic_bytes_per_launch: 1000000\nqueries_per_launch: 100\n"
-                    "docs_in_index: 5000\nl2_throughput_frac: 0.5\n")
+                    "docs_in_index: 5000\nl2_throughput_frac: 0.5\n"
+                    "sectors_per_request: 8.5\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     fig = bench.profile_figures("k_score_emit_text")
     assert fig["traffic_bytes_per_launch"] == 1e6 and fig["docs_in_index"] == 5000
@@ -98,7 +99,7 @@ def test_profile_figures_scale_and_check_their_source(tmp_path, monkeypatch):
     d = bench.dram_figures(fig, 1.0, 1000.0, 95, 5000)
     assert d["traffic"] == pytest.approx(950000.0)
     assert d["dram_frac"] == pytest.approx(950000.0 / 1e-3 / 1e9 / 1000.0)
-    assert d["l2_frac"] == 0.5 and d["l1_frac"] is None
+    assert d["l2_frac"] == 0.5 and d["l1_frac"] is None and d["sectors_per_request"] == 8.5
     # launches half the profiled size: no scaled traffic, the fractions stay
     d = bench.dram_figures(fig, 1.0, 1000.0, 50, 5000)
     assert d["traffic"] is None and d["dram_frac"] is None and d["l2_frac"] == 0.5
